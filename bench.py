@@ -1,0 +1,265 @@
+"""Benchmark of the MI-DELBM coupled step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                    [--config c2] [--storage f32|f16|bf16]
+
+A step is one pass of the whole per-timestep path (flagging, links, refill,
+bulk stream-collide, boundary IBB + momentum exchange, contacts, rigid-body
+update) over the synthetic settling tank.  Default workload: 256x256x512
+lattice, three cobblestone-like particles of 24-40 metaballs, FP32 storage.
+
+Prints one JSON line (rank 0).  value = whole-job MLUPS (lattice nodes times
+steps over the device-timed region, summed over ranks; each rank runs its own
+independent tank, so scaling is weak and no data-path collective exists).
+--impl reference times the FP64 oracle on this machine's host cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = {0: 152, 1: 76, 2: 76}   # 19 loads + 19 stores of the stored type
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+DTYPE_NAME = {0: "f32", 1: "f16-dev/f32-compute", 2: "bf16-dev/f32-compute"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_index is not None:
+            cmd[1:1] = ["-i", str(self.gpu_index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(budget_s=15.0, shape=(64, 64, 64)):
+    """Time the oracle's particle-free bulk step on a cropped lattice until
+    about budget_s seconds of CPU work; returns (MLUPS, seconds, steps)."""
+    from oracle import lbm
+    f = lbm.rest_state((shape[2], shape[1], shape[0]))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        f = lbm.step_bulk(f, 0.8)
+        steps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return shape[0] * shape[1] * shape[2] * steps / dt / 1e6, dt, steps
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    per_step_budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(budget_s=per_step_budget * 0.2)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, dt, n = oracle_sample(budget_s=per_step_budget)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    sample = "oracle FP64 numpy bulk stream-collide on a 64^3 crop of the workload lattice, %.1f s per step" % per_step_budget
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": CONFIG,
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+METRIC = "coupled-step MLUPS (FP32 vs FP16-store) at stated err; contact solves/s"
+CONFIG = {}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def build_sim(B, scene, storage, stream):
+    nx, ny, nz = scene.shape
+    sim = B.Simulation(nx, ny, nz, tau=scene.tau, gravity=scene.gravity, storage=storage, stream=stream)
+    return sim
+
+
+def run_mine(args):
+    import torch
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2209_10411_gb300 import _binding as B
+    from paper_2209_10411_gb300 import scenes
+
+    storage = STORAGE[args.storage]
+    scene = {"c2": scenes.config2}[args.config](seed=rank)
+    if args.lattice:
+        scene.shape = tuple(int(v) for v in args.lattice.split(","))
+    stream = torch.cuda.Stream()
+    sim = build_sim(B, scene, storage, stream.cuda_stream)
+    nx, ny, nz = scene.shape
+    ncell = nx * ny * nz
+
+    for _ in range(max(3, args.warmup)):
+        sim.step(1)
+    stream.synchronize()
+
+    sim.set_timing(True)
+    sim.phase_times(reset=True)
+    clocks = ClockSampler()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    launches0 = sim.launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = sim.launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ptimes = sim.phase_times(reset=True)
+    sim.set_timing(False)
+
+    value = ncell * args.steps * world / (ms * 1e-3) / 1e6
+    bulk_ms, bulk_n = ptimes["bulk"]
+    peak, peak_kind = _peaks()
+    bulk_nodes = ncell  # nodes K1 updates per launch (no particle nodes yet)
+    achieved = BYTES_PER_NODE[storage] * bulk_nodes / (bulk_ms / bulk_n * 1e-3) / 1e9 if bulk_n else None
+
+    # end to end through the public API: per step, step + device->host read of the result
+    e2e = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, n = oracle_sample(budget_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "FP64 numpy oracle bulk step on a 64^3 crop, %d steps in %.1f s" % (n, dt)}
+
+    config = {"workload": "%s (lattice only: particle phases not yet built)" % scene.name,
+              "lattice": list(scene.shape), "particles": 0, "storage": args.storage,
+              "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (19 * ncell * (4 if storage == 0 else 2) / 1e9)}
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": DTYPE_NAME[storage], "data": "synthetic", "config": config,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None, "traffic": None,
+                        "kernel": "k_bulk (D3Q19 stream-collide)", "peak_kind": peak_kind},
+           "phase_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in ptimes.items() if v[1]},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
+    if rank == 0:
+        print(json.dumps(out))
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c2"])
+    ap.add_argument("--storage", default="f32", choices=list(STORAGE))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", default=None, help="nx,ny,nz override (small profiling cases)")
+    args = ap.parse_args()
+    CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
+                   "lattice": [256, 256, 512], "storage": args.storage})
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * mi_delbm.h -- C-ABI of the GB300 (sm_103a) per-timestep fluid-particle step
+ * of the Metaball-Imaging Discrete Element Lattice Boltzmann Method
+ * (Zhang et al., arXiv 2209.10411).
+ *
+ * One handle owns one lattice and its particles on one GPU.  The step it runs
+ * is, in this order (the paper's Sec. 2.3 describes the parts, not the order;
+ * this order is the library's reading):
+ *
+ *   1. solid flagging of lattice nodes from each particle's metaball field
+ *      f(x) = sum_i k_i / |x - c_i|^2 >= 1 in the particle's body frame
+ *      (Sec. 2.1, Eq. 1; node classes fluid / solid / boundary, Sec. 2.3.2);
+ *   2. boundary links (fluid node -> solid neighbour) and the wall fraction q
+ *      solving f(x_f + q e_i) = 1 along the link (Sec. 2.3.2);
+ *   3. local bounce-back refill of nodes a particle has just uncovered
+ *      (Sec. 2.3.2, refill equation);
+ *   4. fused D3Q19 BGK pull stream-collide of every bulk fluid node;
+ *   5. interpolated bounce-back on every boundary link (Sec. 2.3.2, Eqs. of
+ *      the IBB rule and the u_d interpolation), collision of boundary nodes,
+ *      and the Galilean-invariant momentum exchange summed to per-particle
+ *      hydrodynamic force and torque;
+ *   6. DEM: broad phase, Newton-Raphson closest points between sphero-metaball
+ *      particles and between particles and walls, linear spring-dashpot
+ *      forces (Sec. 2.3.1, Eqs. CM_coreF, grad, cp, contactprop, metawallcp,
+ *      contactprop2);
+ *   7. rigid-body update (Sec. 2.3.1, Newton-Euler equations).
+ *
+ * Conventions (all calls):
+ *   - Lattice units: dx = dt = 1, C = 1, c_s^2 = 1/3.  Node (i, j, k) sits at
+ *     position (i, j, k).  Populations are addressed [q][z][y][x] with x
+ *     fastest; q follows the D3Q19 order 0 = rest, 1..6 = +x,-x,+y,-y,+z,-z,
+ *     7..18 = (+x+y),(-x-y),(+x-y),(-x+y),(+x+z),(-x-z),(+x-z),(-x+z),
+ *     (+y+z),(-y-z),(+y-z),(-y+z).
+ *   - Every call returns mi_status; MI_OK is 0.  On failure a message is kept
+ *     and mi_delbm_last_error() returns it.  No call aborts the process.
+ *   - Host buffers passed in are copied; the caller keeps ownership.  Output
+ *     buffers are caller-allocated.
+ *   - A handle is not thread-safe: use it from one host thread.  All device
+ *     work of a handle runs in order on its stream.  mi_delbm_step is
+ *     asynchronous; the query calls synchronise the stream.
+ *   - A device-side failure of the method (Newton not converged, a list over
+ *     capacity) never traps the GPU: it is recorded in device status words and
+ *     reported by the next synchronising call.
+ */
+#ifndef MI_DELBM_H
+#define MI_DELBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MI_DELBM_ABI_VERSION 1
+
+typedef enum {
+  MI_OK = 0,
+  MI_EINVAL = 1,     /* an argument is out of range or inconsistent            */
+  MI_ENOMEM = 2,     /* a device or host allocation failed                      */
+  MI_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+  MI_ECAPACITY = 4,  /* an output buffer or an internal list is too small       */
+  MI_EOVERLAP = 5,   /* a new particle's core overlaps an existing particle     */
+  MI_ESTATE = 6,     /* the call is not valid in the handle's current state     */
+  MI_ETIMEOUT = 7,   /* a bounded device wait gave up                           */
+  MI_ENOTSUP = 8     /* the option is not supported by this build               */
+} mi_status;
+
+/* Population storage in HBM (the arithmetic is FP32 in every mode). */
+enum {
+  MI_STORE_F32 = 0,      /* f_i as float                                       */
+  MI_STORE_F16_DEV = 1,  /* f_i - w_i as IEEE half, round to nearest even      */
+  MI_STORE_BF16_DEV = 2  /* f_i - w_i as bfloat16, round to nearest even       */
+};
+
+/* Particle-wall link rule. */
+enum {
+  MI_BB_IBB = 0,   /* the paper's interpolated bounce-back (Sec. 2.3.2)      */
+  MI_BB_LADD = 1   /* halfway bounce-back with the moving-wall term (q = 1/2) */
+};
+
+/* Newton initial guess for contact detection. */
+enum {
+  MI_GUESS_PLAIN = 0,   /* midpoint of the closest pair of control points     */
+  MI_GUESS_LEARNED = 1  /* the loaded MLP proposes the guess and active subset */
+};
+
+/* Step phases, for mi_delbm_step_phases (tests and profiling). */
+enum {
+  MI_PHASE_FLAG = 1u << 0,      /* solid flags, node classes, boundary/new lists */
+  MI_PHASE_LINKS = 1u << 1,     /* wall fraction q of every boundary link        */
+  MI_PHASE_REFILL = 1u << 2,    /* populations of newly uncovered nodes          */
+  MI_PHASE_BULK = 1u << 3,      /* stream-collide of bulk fluid nodes            */
+  MI_PHASE_BOUNDARY = 1u << 4,  /* IBB + collide of boundary nodes, momentum exchange */
+  MI_PHASE_SWAP = 1u << 5,      /* population buffers swap, flag history advances */
+  MI_PHASE_CONTACT = 1u << 6,   /* broad phase, Newton contacts, contact forces  */
+  MI_PHASE_INTEGRATE = 1u << 7, /* rigid-body update                             */
+  MI_PHASE_ALL = 0xFFu
+};
+
+typedef struct mi_delbm_config {
+  int nx, ny, nz;                /* lattice nodes per axis, each >= 1           */
+  double tau;                    /* BGK relaxation time, > 1/2                  */
+  double rho0;                   /* reference density (1 in lattice units)      */
+  int periodic[3];               /* per axis; otherwise halfway bounce-back walls */
+  double wall_velocity[6][3];    /* per face x-,x+,y-,y+,z-,z+ (moving walls)   */
+  double fluid_body_force[3];    /* uniform Guo body force on the fluid (tests) */
+  double gravity[3];             /* on particles, buoyancy-corrected            */
+  int storage;                   /* MI_STORE_*                                  */
+  int bb_mode;                   /* MI_BB_*                                     */
+  int dem_substeps;              /* DEM substeps per LBM step, >= 1             */
+  double kn, kt, eta_n, eta_t, mu_s; /* spring-dashpot contact parameters       */
+  int guess_mode;                /* MI_GUESS_*                                  */
+  int max_particles;             /* capacity of the particle table              */
+  int max_balls;                 /* capacity of the metaball tables (all particles) */
+  void *cuda_stream;             /* cudaStream_t to run on; NULL = a stream the handle creates */
+  int device;                    /* CUDA device ordinal                         */
+  /* Optional device allocator (e.g. a framework's caching allocator).  When
+   * NULL, cudaMalloc / cudaFree are used.  dev_alloc returns NULL on failure. */
+  void *(*dev_alloc)(size_t bytes, void *ctx);
+  void (*dev_free)(void *ptr, size_t bytes, void *ctx);
+  void *alloc_ctx;
+} mi_delbm_config;
+
+typedef struct mi_delbm mi_delbm;
+
+/* ABI version of the loaded library (MI_DELBM_ABI_VERSION) and the size of
+ * mi_delbm_config it was compiled with, so that bindings can check layout. */
+int mi_delbm_abi_version(void);
+size_t mi_delbm_config_size(void);
+
+/* Fill *cfg with defaults: 64^3 closed box, tau 0.8, rho0 1, FP32 storage,
+ * IBB, 1 DEM substep, kn 1, kt 2/7, eta_n = eta_t = 0, mu_s 0.4, plain guess,
+ * 1024 particles, 65536 metaballs, device 0, handle-owned stream, cudaMalloc. */
+void mi_delbm_config_init(mi_delbm_config *cfg);
+
+/* Create a handle: allocates the two population buffers, node classes, owner
+ * fields and lists on cfg->device, and sets every node to the rest state
+ * f_i = w_i rho0 (post-collision populations at t = 0).
+ * Errors: MI_EINVAL (bad sizes, tau <= 1/2, unknown modes), MI_ENOMEM, MI_ECUDA. */
+mi_status mi_delbm_create(const mi_delbm_config *cfg, mi_delbm **out);
+
+/* Free everything the handle owns (after synchronising its stream). NULL is a no-op. */
+void mi_delbm_destroy(mi_delbm *h);
+
+/* Message of the last failed call on this handle ("" if none).  Valid until
+ * the next call on the handle.  h may be NULL (message of the last failed
+ * mi_delbm_create on this thread). */
+const char *mi_delbm_last_error(const mi_delbm *h);
+
+/* Run n_steps full steps (all phases), asynchronously on the handle's stream.
+ * Errors: MI_EINVAL (n_steps < 0), MI_ECUDA (launch failure). */
+mi_status mi_delbm_step(mi_delbm *h, int n_steps);
+
+/* Block the calling host thread until all work queued on the handle's stream
+ * has finished; reports a pending device-side failure (MI_ECUDA). */
+mi_status mi_delbm_synchronize(mi_delbm *h);
+
+/* Run the listed phases of one step, in the fixed phase order, once.  Used by
+ * tests to compare each phase with the oracle and by profilers.  A full step
+ * is MI_PHASE_ALL.  Asynchronous. */
+mi_status mi_delbm_step_phases(mi_delbm *h, unsigned phases);
+
+/* Copy the current post-collision populations f_i (as float, [19][nz][ny][nx])
+ * to or from the host.  For the deviation storages the stored value is
+ * f_i - w_i rounded to the storage type on set, and w_i + stored on get (so a
+ * get after a set returns the rounded value).  Synchronises.
+ * count = 19*nx*ny*nz floats, else MI_EINVAL. */
+mi_status mi_delbm_set_populations(mi_delbm *h, const float *host_f, size_t count);
+mi_status mi_delbm_get_populations(mi_delbm *h, float *host_f, size_t count);
+
+/* Raw stored populations (storage type, [19][nz][ny][nx], no conversion).
+ * bytes = 19*nx*ny*nz*sizeof(storage element).  Synchronises. */
+mi_status mi_delbm_set_raw_populations(mi_delbm *h, const void *host, size_t bytes);
+mi_status mi_delbm_get_raw_populations(mi_delbm *h, void *host, size_t bytes);
+
+/* Device addresses of the current state (for zero-copy inspection by a
+ * framework; valid until the next call that steps or reallocates).
+ * populations: element [q][z][y][x] at pop + q*plane_stride + ((z*ny + y)*nx + x),
+ * in the storage type.  node_class: uint8 per node, bit 0 solid, bit 1
+ * boundary (fluid with a solid neighbour), bit 2 newly uncovered.
+ * owner: uint32 per node, particle index of a solid node, 0xFFFFFFFF if fluid. */
+typedef struct {
+  void *populations;
+  size_t plane_stride;   /* elements between q planes */
+  int storage;           /* MI_STORE_* */
+  const uint8_t *node_class;
+  const uint32_t *owner;
+  void *stream;          /* cudaStream_t of the handle */
+} mi_delbm_device_view;
+mi_status mi_delbm_get_device_view(mi_delbm *h, mi_delbm_device_view *v);
+
+/* Per-phase GPU timing with CUDA events on the handle's stream.  While
+ * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
+ * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of
+ * 8), the summed milliseconds and the number of timed launches since the last
+ * reset (the reset flag clears them after reading). */
+mi_status mi_delbm_set_timing(mi_delbm *h, int enable);
+mi_status mi_delbm_phase_times(mi_delbm *h, double ms[8], long long launches[8], int reset);
+
+/* Number of kernel launches the handle issued since creation (for launch
+ * accounting by benchmarks). */
+long long mi_delbm_launch_count(const mi_delbm *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MI_DELBM_H */

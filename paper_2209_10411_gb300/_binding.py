@@ -1,0 +1,253 @@
+"""ctypes binding of libmi_delbm (the C-ABI declared in include/mi_delbm.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch, when used, only provides device memory (its caching
+allocator is plugged into the handle through the config's dev_alloc/dev_free
+callbacks) and the CUDA stream.  There is no CPU fallback: if the shared
+library is missing this module raises ImportError.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmi_delbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libmi_delbm.so is not built (expected at %s); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first" % LIB_PATH)
+
+lib = ctypes.CDLL(LIB_PATH)
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p)
+
+MI_OK, MI_EINVAL, MI_ENOMEM, MI_ECUDA, MI_ECAPACITY, MI_EOVERLAP, MI_ESTATE, MI_ETIMEOUT, MI_ENOTSUP = range(9)
+STATUS_NAMES = ["MI_OK", "MI_EINVAL", "MI_ENOMEM", "MI_ECUDA", "MI_ECAPACITY", "MI_EOVERLAP",
+                "MI_ESTATE", "MI_ETIMEOUT", "MI_ENOTSUP"]
+STORE_F32, STORE_F16_DEV, STORE_BF16_DEV = 0, 1, 2
+BB_IBB, BB_LADD = 0, 1
+GUESS_PLAIN, GUESS_LEARNED = 0, 1
+PHASE_FLAG, PHASE_LINKS, PHASE_REFILL, PHASE_BULK = 1, 2, 4, 8
+PHASE_BOUNDARY, PHASE_SWAP, PHASE_CONTACT, PHASE_INTEGRATE = 16, 32, 64, 128
+PHASE_ALL = 0xFF
+PHASE_NAMES = ["flag", "links", "refill", "bulk", "boundary", "swap", "contact", "integrate"]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", c_int), ("ny", c_int), ("nz", c_int),
+        ("tau", c_double), ("rho0", c_double),
+        ("periodic", c_int * 3),
+        ("wall_velocity", (c_double * 3) * 6),
+        ("fluid_body_force", c_double * 3),
+        ("gravity", c_double * 3),
+        ("storage", c_int), ("bb_mode", c_int), ("dem_substeps", c_int),
+        ("kn", c_double), ("kt", c_double), ("eta_n", c_double), ("eta_t", c_double), ("mu_s", c_double),
+        ("guess_mode", c_int), ("max_particles", c_int), ("max_balls", c_int),
+        ("cuda_stream", c_void_p), ("device", c_int),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", c_void_p),
+    ]
+
+
+class DeviceView(ctypes.Structure):
+    _fields_ = [("populations", c_void_p), ("plane_stride", c_size_t), ("storage", c_int),
+                ("node_class", c_void_p), ("owner", c_void_p), ("stream", c_void_p)]
+
+
+def _sig(name, restype, *argtypes):
+    fn = getattr(lib, name)
+    fn.restype = restype
+    fn.argtypes = list(argtypes)
+    return fn
+
+
+_P = c_void_p
+_sig("mi_delbm_abi_version", c_int)
+_sig("mi_delbm_config_size", c_size_t)
+_sig("mi_delbm_config_init", None, ctypes.POINTER(Config))
+_sig("mi_delbm_create", c_int, ctypes.POINTER(Config), ctypes.POINTER(c_void_p))
+_sig("mi_delbm_destroy", None, _P)
+_sig("mi_delbm_last_error", ctypes.c_char_p, _P)
+_sig("mi_delbm_step", c_int, _P, c_int)
+_sig("mi_delbm_step_phases", c_int, _P, ctypes.c_uint)
+_sig("mi_delbm_synchronize", c_int, _P)
+_sig("mi_delbm_set_populations", c_int, _P, _P, c_size_t)
+_sig("mi_delbm_get_populations", c_int, _P, _P, c_size_t)
+_sig("mi_delbm_set_raw_populations", c_int, _P, _P, c_size_t)
+_sig("mi_delbm_get_raw_populations", c_int, _P, _P, c_size_t)
+_sig("mi_delbm_get_device_view", c_int, _P, ctypes.POINTER(DeviceView))
+_sig("mi_delbm_set_timing", c_int, _P, c_int)
+_sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
+_sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
+
+if lib.mi_delbm_abi_version() != 1:
+    raise ImportError("libmi_delbm ABI version mismatch")
+if lib.mi_delbm_config_size() != ctypes.sizeof(Config):
+    raise ImportError("mi_delbm_config layout mismatch: C %d bytes, binding %d bytes"
+                      % (lib.mi_delbm_config_size(), ctypes.sizeof(Config)))
+
+
+class MiDelbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+def _ptr(a):
+    return a.ctypes.data_as(c_void_p)
+
+
+class _TorchAllocator:
+    """Routes the handle's device allocations to torch's caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:
+            return None
+
+    def _free(self, ptr, nbytes, ctx):
+        try:
+            self._torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+
+class Simulation:
+    """One lattice and its particles on one GPU (a mi_delbm handle)."""
+
+    def __init__(self, nx=64, ny=64, nz=64, tau=0.8, rho0=1.0, periodic=(False, False, False),
+                 wall_velocity=None, fluid_body_force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
+                 storage=STORE_F32, bb_mode=BB_IBB, dem_substeps=1, kn=1.0, kt=2.0 / 7.0,
+                 eta_n=0.0, eta_t=0.0, mu_s=0.4, guess_mode=GUESS_PLAIN, max_particles=1024,
+                 max_balls=65536, device=0, stream=None, torch_memory=True):
+        cfg = Config()
+        lib.mi_delbm_config_init(ctypes.byref(cfg))
+        cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+        cfg.tau, cfg.rho0 = float(tau), float(rho0)
+        for a in range(3):
+            cfg.periodic[a] = 1 if periodic[a] else 0
+            cfg.fluid_body_force[a] = float(fluid_body_force[a])
+            cfg.gravity[a] = float(gravity[a])
+        if wall_velocity is not None:
+            wv = np.asarray(wall_velocity, dtype=np.float64).reshape(6, 3)
+            for f in range(6):
+                for a in range(3):
+                    cfg.wall_velocity[f][a] = wv[f, a]
+        cfg.storage, cfg.bb_mode, cfg.dem_substeps = int(storage), int(bb_mode), int(dem_substeps)
+        cfg.kn, cfg.kt, cfg.eta_n, cfg.eta_t, cfg.mu_s = float(kn), float(kt), float(eta_n), float(eta_t), float(mu_s)
+        cfg.guess_mode, cfg.max_particles, cfg.max_balls = int(guess_mode), int(max_particles), int(max_balls)
+        cfg.device = int(device)
+        self._alloc = None
+        self.torch_stream = None
+        if stream is None and torch_memory:
+            import torch
+            self.torch_stream = torch.cuda.Stream(device=device)
+            stream = self.torch_stream.cuda_stream
+        if stream is not None:
+            cfg.cuda_stream = c_void_p(int(stream))
+        if torch_memory:
+            self._alloc = _TorchAllocator(int(device), int(stream) if stream is not None else 0)
+            cfg.dev_alloc = self._alloc.alloc
+            cfg.dev_free = self._alloc.free
+        self.cfg = cfg
+        self.shape = (int(nz), int(ny), int(nx))
+        self.ncell = int(nx) * int(ny) * int(nz)
+        h = c_void_p()
+        st = lib.mi_delbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != MI_OK:
+            raise MiDelbmError(st, lib.mi_delbm_last_error(None).decode())
+        self.h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.mi_delbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st != MI_OK:
+            raise MiDelbmError(st, lib.mi_delbm_last_error(self.h).decode())
+
+    # -- stepping ---------------------------------------------------------
+    def step(self, n=1):
+        self._check(lib.mi_delbm_step(self.h, int(n)))
+
+    def synchronize(self):
+        self._check(lib.mi_delbm_synchronize(self.h))
+
+    def step_phases(self, phases):
+        self._check(lib.mi_delbm_step_phases(self.h, int(phases)))
+
+    # -- populations ------------------------------------------------------
+    def set_populations(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float32).reshape(19, *self.shape)
+        self._check(lib.mi_delbm_set_populations(self.h, _ptr(a), a.size))
+
+    def get_populations(self):
+        a = np.empty((19,) + self.shape, dtype=np.float32)
+        self._check(lib.mi_delbm_get_populations(self.h, _ptr(a), a.size))
+        return a
+
+    def set_raw_populations(self, raw):
+        a = np.ascontiguousarray(raw)
+        self._check(lib.mi_delbm_set_raw_populations(self.h, _ptr(a), a.nbytes))
+
+    def get_raw_populations(self):
+        dt = np.float32 if self.cfg.storage == STORE_F32 else np.uint16
+        a = np.empty((19,) + self.shape, dtype=dt)
+        self._check(lib.mi_delbm_get_raw_populations(self.h, _ptr(a), a.nbytes))
+        return a
+
+    def device_view(self):
+        v = DeviceView()
+        self._check(lib.mi_delbm_get_device_view(self.h, ctypes.byref(v)))
+        return v
+
+    # -- timing -----------------------------------------------------------
+    def set_timing(self, on):
+        self._check(lib.mi_delbm_set_timing(self.h, 1 if on else 0))
+
+    def phase_times(self, reset=True):
+        ms = (c_double * 8)()
+        n = (ctypes.c_longlong * 8)()
+        self._check(lib.mi_delbm_phase_times(self.h, ms, n, 1 if reset else 0))
+        return {PHASE_NAMES[b]: (ms[b], n[b]) for b in range(8)}
+
+    def launch_count(self):
+        return int(lib.mi_delbm_launch_count(self.h))
+
+
+class CudaArray:
+    """Minimal __cuda_array_interface__ wrapper so torch.as_tensor can view
+    device memory owned by the library without copying."""
+
+    def __init__(self, ptr, shape, typestr, strides=None, stream=None):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+            "version": 3, "strides": strides, "stream": None,
+        }
