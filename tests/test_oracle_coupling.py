@@ -1,0 +1,290 @@
+"""Pins of the oracle's metaball, flagging, link, refill, IBB, momentum-exchange
+and rigid-body parts against closed forms, exact integer cases, invariances,
+brute force and conservation laws (no GPU)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import coupling, dem, lbm, metaball
+from oracle.d3q19 import E, OPP, Q, W
+
+
+def _particle(centers, k, pos, quat=(1.0, 0.0, 0.0, 0.0), vel=(0, 0, 0), omega=(0, 0, 0)):
+    return {"centers": np.asarray(centers, dtype=float).reshape(-1, 3), "k": np.asarray(k, dtype=float),
+            "pos": np.asarray(pos, dtype=float), "quat": np.asarray(quat, dtype=float),
+            "vel": np.asarray(vel, dtype=float), "omega": np.asarray(omega, dtype=float)}
+
+
+# ---------------------------------------------------------------- flagging --
+@pytest.mark.parametrize("k", [1, 2, 7, 9, 16, 30])
+def test_single_ball_is_exact_integer_sphere(k):
+    # n = 1 in Eq. 1: f = k / |x - c|^2 >= 1  <=>  |x - c|^2 <= k (exact integers)
+    shape = (20, 21, 22)
+    P = _particle([[0, 0, 0]], [k], [10, 11, 12])
+    owner = metaball.flag_nodes(shape, [P])
+    z, y, x = np.meshgrid(np.arange(22), np.arange(21), np.arange(20), indexing="ij")
+    expect = (x - 10) ** 2 + (y - 11) ** 2 + (z - 12) ** 2 <= k
+    assert np.array_equal(owner >= 0, expect)
+
+
+def test_scale_law():
+    # (c, k, X) -> (2c, 4k, 2X) maps the solid set of node x to node 2x exactly
+    rng = np.random.default_rng(0)
+    c = rng.uniform(-3, 3, (5, 3))
+    k = rng.uniform(2, 6, 5)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    P1 = _particle(c, k, [12.25, 13.5, 11.75], q)
+    P2 = _particle(2 * c, 4 * k, [24.5, 27.0, 23.5], q)
+    o1 = metaball.flag_nodes((26, 26, 26), [P1])
+    o2 = metaball.flag_nodes((52, 52, 52), [P2])
+    assert (o1 >= 0).sum() > 100
+    assert np.array_equal(o1 >= 0, o2[::2, ::2, ::2] >= 0)
+
+
+def test_rotation_maps_body_axes_to_world():
+    # 90 degrees about z: body +x points along world +y
+    s = np.sqrt(0.5)
+    P = _particle([[3, 0, 0]], [0.5], [10, 10, 10], (s, 0, 0, s))
+    R = metaball.quat_to_matrix(P["quat"])
+    assert np.allclose(R @ [1, 0, 0], [0, 1, 0], atol=1e-15)
+    owner = metaball.flag_nodes((20, 20, 20), [P])
+    assert owner[10, 13, 10] == 0 and owner[10, 10, 13] == -1 and owner[10, 7, 10] == -1
+
+
+def test_field_gradient_hessian_against_finite_differences():
+    rng = np.random.default_rng(1)
+    c = rng.uniform(-2, 2, (4, 3))
+    k = rng.uniform(1, 3, 4)
+    x = np.array([3.1, -2.7, 1.3])
+    h = 1e-5
+    g = metaball.gradient(x, c, k)
+    H = metaball.hessian(x, c, k)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        fd = (metaball.field(x + e, c, k) - metaball.field(x - e, c, k)) / (2 * h)
+        assert abs(fd - g[a]) < 1e-8 * max(1, abs(g[a]))
+        gd = (metaball.gradient(x + e, c, k) - metaball.gradient(x - e, c, k)) / (2 * h)
+        assert np.allclose(gd, H[:, a], rtol=1e-6, atol=1e-9)
+
+
+def test_bounding_radius_contains_every_solid_node():
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        c = rng.uniform(-4, 4, (6, 3))
+        k = rng.uniform(1, 8, 6)
+        X = rng.uniform(18, 22, 3)
+        q = rng.normal(size=4)
+        P = _particle(c, k, X, q / np.linalg.norm(q))
+        Rb = metaball.bounding_radius(c, k)
+        owner = metaball.flag_nodes((40, 40, 40), [P])
+        z, y, x = np.nonzero(owner >= 0)
+        d = np.sqrt((x - X[0]) ** 2 + (y - X[1]) ** 2 + (z - X[2]) ** 2)
+        assert len(d) > 0 and d.max() <= Rb
+        # just beyond R_b the field is below one in every direction
+        u = rng.normal(size=(200, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        assert (metaball.field(u * Rb * 1.0001, c, k) < 1).all()
+
+
+def test_overlap_goes_to_lowest_index():
+    P0 = _particle([[0, 0, 0]], [9], [10, 10, 10])
+    P1 = _particle([[0, 0, 0]], [9], [13, 10, 10])
+    owner = metaball.flag_nodes((24, 20, 20), [P1, P0])  # index 0 is the one at x = 13
+    assert owner[10, 10, 12] == 0 and owner[10, 10, 11] == 0 and owner[10, 10, 8] == 1
+
+
+# ------------------------------------------------------------------- links --
+def test_links_match_brute_force_definition():
+    rng = np.random.default_rng(3)
+    shape = (9, 8, 7)
+    owner = np.where(rng.random((7, 8, 9)) < 0.3, rng.integers(0, 3, (7, 8, 9)), -1)
+    for periodic in [(False, False, False), (True, False, True)]:
+        cell, d, p = coupling.find_links(owner, periodic)
+        got = set(zip(map(tuple, cell), d, p))
+        want = set()
+        for z, y, x in itertools.product(range(7), range(8), range(9)):
+            if owner[z, y, x] >= 0:
+                continue
+            for i in range(1, 19):
+                n = [x + E[i, 0], y + E[i, 1], z + E[i, 2]]
+                inside = True
+                for a in range(3):
+                    if periodic[a]:
+                        n[a] %= shape[a]
+                    elif not 0 <= n[a] < shape[a]:
+                        inside = False
+                if inside and owner[n[2], n[1], n[0]] >= 0:
+                    want.add(((x, y, z), i, owner[n[2], n[1], n[0]]))
+        assert got == want
+
+
+def test_wall_fraction_single_sphere_closed_form():
+    X = np.array([10.3, 9.6, 10.1])
+    k = 17.0
+    P = _particle([[0, 0, 0]], [k], X)
+    owner = metaball.flag_nodes((21, 21, 21), [P])
+    cell, d, p = coupling.find_links(owner)
+    q = coupling.wall_fraction(cell, d, P)
+    e = E[d].astype(float)
+    r = cell - X
+    a = (e * e).sum(1)
+    b = (r * e).sum(1)
+    c = (r * r).sum(1) - k
+    root = (-b - np.sqrt(b * b - a * c)) / a  # first crossing along e from the fluid node
+    assert len(q) > 200
+    assert np.abs(q - root).max() < 1e-12
+    assert (q > 0).all() and (q <= 1).all()
+
+
+def test_departure_velocity_is_exact_for_linear_fields():
+    # for u linear along the link, u_d = u(x_f + (2q - 1) e_d) in both branches
+    rng = np.random.default_rng(4)
+    a, b = rng.normal(size=3), rng.normal(size=3)
+    for q in [0.05, 0.3, 0.5, 0.5000001, 0.7, 1.0]:
+        u = lambda s: a + b * s
+        ud = coupling.departure_velocity(np.array([q]), u(0.0)[None], u(-1.0)[None], u(q)[None])[0]
+        assert np.allclose(ud, u(2 * q - 1), atol=1e-14)
+
+
+# ------------------------------------------------------- coupled LBM step --
+def _blob(X, vel=(0, 0, 0), omega=(0, 0, 0), seed=5):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-2.5, 2.5, (4, 3))
+    k = rng.uniform(3, 6, 4)
+    q = rng.normal(size=4)
+    return _particle(c, k, X, q / np.linalg.norm(q), vel, omega)
+
+
+@pytest.mark.parametrize("mode", ["ibb", "ladd"])
+def test_uniform_coflow_is_preserved_with_refill(mode):
+    # fluid and particle move together at u: refill and bounce-back reproduce
+    # f_eq(rho0, u) exactly and the net momentum exchange vanishes
+    shape = (22, 20, 21)
+    u = np.array([0.03, -0.02, 0.01])
+    P = _blob([11.0, 10.0, 10.5], vel=u)
+    Pprev = dict(P, pos=P["pos"] - 0.9 * u / np.linalg.norm(u))
+    owner = metaball.flag_nodes(shape, [P])
+    owner_prev = metaball.flag_nodes(shape, [Pprev])
+    solid, new = coupling.classify(owner, owner_prev)
+    assert new.sum() > 0
+    feq = lbm.equilibrium(np.ones((21, 20, 22)), np.broadcast_to(u.reshape(3, 1, 1, 1), (3, 21, 20, 22)))
+    f0 = feq.copy()
+    f0[:, owner_prev >= 0] = 123.0  # stale values inside the old solid must not leak
+    out, F, T = coupling.coupled_lbm_step(f0, owner, owner_prev, [P], 0.8, bb_mode=mode,
+                                          periodic=(True, True, True))
+    fl = ~solid
+    assert np.abs(out[:, fl] - feq[:, fl]).max() < 1e-15
+    assert np.abs(F).max() < 1e-13
+
+
+def test_rest_state_with_resting_particle():
+    shape = (16, 16, 16)
+    P = _blob([8.0, 8.0, 8.0])
+    owner = metaball.flag_nodes(shape, [P])
+    f0 = lbm.rest_state((16, 16, 16))
+    out, F, T = coupling.coupled_lbm_step(f0, owner, owner, [P], 0.8)
+    assert np.abs(out[:, owner < 0] - f0[:, owner < 0]).max() < 1e-16
+    assert np.abs(F).max() < 1e-13 and np.abs(T).max() < 1e-12
+
+
+@pytest.mark.parametrize("mode", ["ibb", "ladd"])
+def test_momentum_and_mass_balance(mode):
+    # periodic box, no uncovered nodes: the fluid loses exactly what the links
+    # carry into the particles: dM = sum(G - f_d), dP = -sum(e_d f_d - e_j G)
+    shape = (18, 17, 16)
+    rng = np.random.default_rng(6)
+    P = _blob([9.0, 8.5, 8.0], vel=(0.01, 0.02, -0.01), omega=(0.003, -0.002, 0.004))
+    owner = metaball.flag_nodes(shape, [P])
+    f0 = W.reshape(Q, 1, 1, 1) * (1 + 0.05 * rng.standard_normal((Q, 16, 17, 18)))
+    out, F, T, L = coupling.coupled_lbm_step(f0, owner, owner, [P], 0.8, bb_mode=mode,
+                                             periodic=(True, True, True), return_links=True)
+    fl = owner < 0
+    Ef = E.astype(float)
+    M0, M1 = f0[:, fl].sum(), out[:, fl].sum()
+    P0 = np.einsum("ia,in->a", Ef, f0[:, fl])
+    P1 = np.einsum("ia,in->a", Ef, out[:, fl])
+    ed, ej = Ef[L["dir"]], Ef[OPP[L["dir"]]]
+    assert abs((M1 - M0) - (L["G"] - L["f_d"]).sum()) < 1e-12
+    plain = (ed * L["f_d"][:, None] - ej * L["G"][:, None]).sum(0)
+    assert np.abs((P1 - P0) + plain).max() < 1e-12
+    # the Galilean-invariant form differs from the plain one by u_w (f_d - G)
+    gi = plain - (L["u_w"] * (L["f_d"] - L["G"])[:, None]).sum(0)
+    assert np.abs(F[0] - gi).max() < 1e-12
+    # torque about X from the per-link arms
+    assert np.isfinite(T).all()
+
+
+def test_mass_properties_of_a_sphere():
+    k = 16.0
+    mp = metaball.mass_properties(np.zeros((1, 3)), np.array([k]), 2.5, h=0.25)
+    r = np.sqrt(k)
+    V = 4.0 / 3.0 * np.pi * r ** 3
+    assert abs(mp["volume"] - V) / V < 0.01
+    assert np.abs(mp["centroid"]).max() < 1e-9
+    I = 0.4 * mp["mass"] * r * r
+    assert np.allclose(np.diag(mp["inertia"]), I, rtol=0.02)
+    assert np.abs(mp["inertia"] - np.diag(np.diag(mp["inertia"]))).max() < 1e-6 * I
+
+
+# --------------------------------------------------------------- rigid body --
+def _state(**kw):
+    s = {"pos": np.zeros(3), "quat": np.array([1.0, 0, 0, 0]), "vel": np.zeros(3), "omega": np.zeros(3),
+         "mass": 2.0, "volume": 0.8, "inertia": np.diag([1.0, 1.0, 1.0])}
+    s.update(kw)
+    return s
+
+
+def test_constant_force_kinematics():
+    s = _state(vel=np.array([0.1, 0.0, -0.2]))
+    F = np.array([0.02, -0.04, 0.06])
+    n, dt = 50, 0.5
+    for _ in range(n):
+        s = dem.integrate(s, F, np.zeros(3), (0, 0, 0), dt=dt)
+    a = F / 2.0
+    assert np.allclose(s["vel"], [0.1, 0.0, -0.2] + n * dt * a, atol=1e-14)
+    expect = np.array([0.1, 0.0, -0.2]) * n * dt + a * dt * dt * n * (n + 1) / 2
+    assert np.allclose(s["pos"], expect, atol=1e-12)
+
+
+def test_buoyancy_and_gravity():
+    s = _state(mass=2.0, volume=2.0)  # neutrally buoyant in rho0 = 1
+    s2 = dem.integrate(s, np.zeros(3), np.zeros(3), (0, 0, -1e-3))
+    assert np.abs(s2["vel"]).max() == 0.0
+    s = _state(mass=2.5, volume=1.0)
+    s2 = dem.integrate(s, np.zeros(3), np.zeros(3), (0, 0, -1e-3))
+    assert np.allclose(s2["vel"], [0, 0, -1e-3 * 1.5 / 2.5], atol=1e-18)
+
+
+def test_torque_free_isotropic_rotation_is_exact():
+    w = np.array([0.01, -0.02, 0.015])
+    s = _state(omega=w)
+    n = 200
+    for _ in range(n):
+        s = dem.integrate(s, np.zeros(3), np.zeros(3), (0, 0, 0))
+    qe = dem.quat_exp_half(w * n)
+    assert np.allclose(s["quat"], qe, atol=1e-12)
+    assert np.allclose(s["omega"], w, atol=1e-15)
+
+
+def test_euler_equations_symmetric_top_precession():
+    # torque-free symmetric top: Euler's equations give body-frame
+    # w1 = A cos(Om t), w2 = A sin(Om t), w3 constant, Om = (I3 - I1)/I1 w3;
+    # the first-order scheme's phase error after Om t = 2 is ~1e-2 A
+    I1, I3 = 1.0, 2.0
+    w0 = np.array([0.01, 0.0, 0.02])
+    s = _state(inertia=np.diag([I1, I1, I3]), omega=w0)
+    n, dt = 400, 0.25
+    for _ in range(n):
+        s = dem.integrate(s, np.zeros(3), np.zeros(3), (0, 0, 0), dt=dt)
+    R = metaball.quat_to_matrix(s["quat"])
+    wb = R.T @ s["omega"]
+    Om = (I3 - I1) / I1 * w0[2]
+    t = n * dt
+    expect = np.array([0.01 * np.cos(Om * t), 0.01 * np.sin(Om * t), 0.02])
+    assert np.allclose(wb, expect, atol=2e-4)
+    L0 = np.diag([I1, I1, I3]) @ w0
+    L1 = R @ (np.diag([I1, I1, I3]) @ wb)
+    assert abs(np.linalg.norm(L1) - np.linalg.norm(L0)) < 1e-3 * np.linalg.norm(L0)
