@@ -103,31 +103,43 @@ def _dist_env():
 
 
 # ---------------------------------------------------------------------------
-# reference arm: the FP64 oracle on host cores
+# CPU side: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(budget_s=15.0, shape=(64, 64, 64)):
-    """Time the oracle's particle-free bulk step on a cropped lattice until
-    about budget_s seconds of CPU work; returns (MLUPS, seconds, steps)."""
-    from oracle import lbm
-    f = lbm.rest_state((shape[2], shape[1], shape[0]))
+def oracle_sample(budget_s=15.0, crop=96, seed=0):
+    """Time the oracle's coupled LBM step (flags, links, refill, IBB, momentum
+    exchange, stream-collide) plus the rigid-body update on a crop^3 window
+    around the first cobble of the settling tank, until about budget_s seconds
+    of CPU work; returns (MLUPS, seconds, steps)."""
+    from oracle import coupling, dem, lbm, metaball
+    from paper_2209_10411_gb300 import scenes
+    spec = scenes.config2(seed=seed).particles[0]
+    shape = (crop, crop, crop)
+    P = {"centers": spec.centers, "k": spec.k, "pos": np.array([crop / 2.0] * 3), "quat": spec.quat,
+         "vel": np.zeros(3), "omega": np.zeros(3), "mass": 1.0, "volume": 0.4,
+         "inertia": np.eye(3) * 100.0}
+    f = lbm.rest_state((crop, crop, crop))
+    owner_prev = metaball.flag_nodes(shape, [P])
     t0 = time.perf_counter()
     steps = 0
     while True:
-        f = lbm.step_bulk(f, 0.8)
+        owner = metaball.flag_nodes(shape, [P])
+        f, F, T = coupling.coupled_lbm_step(f, owner, owner_prev, [P], 0.8)
+        P = dem.integrate(P, F[0], T[0], (0.0, 0.0, -1e-5))
+        owner_prev = owner
         steps += 1
         dt = time.perf_counter() - t0
         if dt >= budget_s:
             break
-    return shape[0] * shape[1] * shape[2] * steps / dt / 1e6, dt, steps
+    return crop ** 3 * steps / dt / 1e6, dt, steps
 
 
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
         return
-    per_step_budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample(budget_s=per_step_budget * 0.2)
+        oracle_sample(budget_s=0.5)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -135,7 +147,8 @@ def run_reference(args):
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
-    sample = "oracle FP64 numpy bulk stream-collide on a 64^3 crop of the workload lattice, %.1f s per step" % per_step_budget
+    sample = ("FP64 numpy oracle, coupled step + rigid-body update on a 96^3 window around one "
+              "cobble of the tank, %.1f s of CPU work per step" % per_step_budget)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -154,7 +167,11 @@ CONFIG = {}
 # ---------------------------------------------------------------------------
 def build_sim(B, scene, storage, stream):
     nx, ny, nz = scene.shape
-    sim = B.Simulation(nx, ny, nz, tau=scene.tau, gravity=scene.gravity, storage=storage, stream=stream)
+    sim = B.Simulation(nx, ny, nz, tau=scene.tau, gravity=scene.gravity, storage=storage, stream=stream,
+                       max_particles=max(16, len(scene.particles)),
+                       max_balls=max(65536, sum(len(p.k) for p in scene.particles)))
+    for p in scene.particles:
+        sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat, p.vel, p.omega)
     return sim
 
 
@@ -170,16 +187,20 @@ def run_mine(args):
 
     storage = STORAGE[args.storage]
     scene = {"c2": scenes.config2}[args.config](seed=rank)
-    if args.lattice:
+    if args.lattice:  # smaller profiling case: same particles, positions scaled into the box
+        old = np.array(scene.shape, dtype=float)
         scene.shape = tuple(int(v) for v in args.lattice.split(","))
+        for p in scene.particles:
+            p.pos = scenes.f32(p.pos * np.array(scene.shape) / old)
     stream = torch.cuda.Stream()
     sim = build_sim(B, scene, storage, stream.cuda_stream)
     nx, ny, nz = scene.shape
     ncell = nx * ny * nz
+    npart = len(scene.particles)
 
     for _ in range(max(3, args.warmup)):
         sim.step(1)
-    stream.synchronize()
+    sim.synchronize()
 
     sim.set_timing(True)
     sim.phase_times(reset=True)
@@ -206,31 +227,59 @@ def run_mine(args):
         ms = float(t.item())
     ptimes = sim.phase_times(reset=True)
     sim.set_timing(False)
+    stats = sim.stats()
+
+    # nodes the bulk kernel updates: every node that is neither solid nor boundary
+    cls, _ = sim.node_classes()
+    n_solid = int(((cls & 1) != 0).sum())
+    n_boundary = int(((cls & 2) != 0).sum())
+    n_bulk = ncell - n_solid - n_boundary
 
     value = ncell * args.steps * world / (ms * 1e-3) / 1e6
     bulk_ms, bulk_n = ptimes["bulk"]
     peak, peak_kind = _peaks()
-    bulk_nodes = ncell  # nodes K1 updates per launch (no particle nodes yet)
-    achieved = BYTES_PER_NODE[storage] * bulk_nodes / (bulk_ms / bulk_n * 1e-3) / 1e9 if bulk_n else None
+    cls_bytes = ncell if npart else 0
+    alg_bytes = BYTES_PER_NODE[storage] * n_bulk + cls_bytes
+    achieved = alg_bytes / (bulk_ms / bulk_n * 1e-3) / 1e9 if bulk_n else None
 
-    # end to end through the public API: per step, step + device->host read of the result
-    e2e = None
+    # end to end through the public API: per step, upload of the particle
+    # states from page-locked host memory, the step, and a synchronising read
+    # of the hydrodynamic forces and the new states
+    states = torch.empty((npart, 13), dtype=torch.float64, pin_memory=True)
+    Fh = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
+    Th = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
+    sim.get_particle_states_ptr(states.data_ptr(), npart)
+    sim.synchronize()
+    k_e2e = max(10, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sim.set_particle_states_ptr(states.data_ptr(), npart)
+        sim.step(1)
+        sim.get_particle_states_ptr(states.data_ptr(), npart)
+        sim.forces_ptr(Fh.data_ptr(), Th.data_ptr())
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ncell * k_e2e / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": npart * 13 * 8,
+           "d2h_bytes_per_step": npart * (13 + 6) * 8, "steps": k_e2e,
+           "api": "set_particle_states + step + get_particle_states + forces per step (host wall clock)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, n = oracle_sample(budget_s=args.cpu_seconds)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy oracle bulk step on a 64^3 crop, %d steps in %.1f s" % (n, dt)}
+               "sample": "FP64 numpy oracle: coupled step + rigid-body update on a 96^3 window around one "
+                         "cobble, %d steps in %.1f s" % (n, dt)}
 
-    config = {"workload": "%s (lattice only: particle phases not yet built)" % scene.name,
-              "lattice": list(scene.shape), "particles": 0, "storage": args.storage,
+    config = {"workload": scene.name, "lattice": list(scene.shape), "particles": npart,
+              "metaballs": [int(len(p.k)) for p in scene.particles], "storage": args.storage, "tau": scene.tau,
+              "boundary_nodes": stats["boundary_nodes"], "links": stats["links"], "solid_nodes": n_solid,
               "l2": "inputs larger than L2 (populations %.2f GB per buffer)" % (19 * ncell * (4 if storage == 0 else 2) / 1e9)}
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPE_NAME[storage], "data": "synthetic", "config": config,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": None,
-                        "kernel": "k_bulk (D3Q19 stream-collide)", "peak_kind": peak_kind},
+                        "kernel": "k_bulk (D3Q19 stream-collide of bulk fluid nodes)", "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": alg_bytes},
            "phase_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in ptimes.items() if v[1]},
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}

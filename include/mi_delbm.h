@@ -190,6 +190,95 @@ typedef struct {
 } mi_delbm_device_view;
 mi_status mi_delbm_get_device_view(mi_delbm *h, mi_delbm_device_view *v);
 
+/* ------------------------------------------------------------------------
+ * Particles (Sec. 2.1 Eq. 1 shape; Sec. 2.3.1 rigid-body state)
+ * ------------------------------------------------------------------------ */
+
+/* Mass properties of a particle: mass, solid volume (buoyancy uses
+ * rho0*volume) and inertia tensor in body axes about the body origin,
+ * row-major. */
+typedef struct {
+  double mass;
+  double volume;
+  double inertia[9];
+} mi_mass_props;
+
+/* Add a rigid metaball particle: n_balls control points centers[n*3] (body
+ * frame) with coefficients k[n] > 0 (the shape is f(x) = sum k_i/|x-c_i|^2 >= 1,
+ * Eq. 1), density (fluid rho0 = 1 scale), sphero-metaball skin radius skin_Rs
+ * (0 <= skin_Rs < sqrt(sum k)), pose pos[3] and unit quaternion quat[4]
+ * (w, x, y, z; normalised by the library), velocity vel[3] and angular
+ * velocity omega[3] (world frame).
+ * mp == NULL: volume, centroid and inertia are integrated on the GPU by
+ * midpoint quadrature of f >= 1 with spacing 1/4 lattice unit, the control
+ * points are shifted so that the body origin is the centroid, and pos is
+ * moved by R(quat) * centroid so that the particle does not move.
+ * mp != NULL: the given mass properties are used and the body origin is taken
+ * as the centroid (no shift).
+ * On success *id_out is the particle index (0, 1, ... in order of addition).
+ * Allowed between steps.  Errors: MI_EINVAL (bad values), MI_ECAPACITY
+ * (max_particles / max_balls reached), MI_ENOMEM, MI_ECUDA. */
+mi_status mi_delbm_add_particle(mi_delbm *h, int n_balls, const double *centers, const double *k,
+                                double density, double skin_Rs, const double pos[3], const double quat[4],
+                                const double vel[3], const double omega[3], const mi_mass_props *mp,
+                                int *id_out);
+
+/* Number of particles in the handle. */
+int mi_delbm_num_particles(const mi_delbm *h);
+
+/* Kinematic state of particle id (world frame).  get synchronises; set takes
+ * effect at the next step (any pointer may be NULL to leave that part). */
+mi_status mi_delbm_get_particle_state(mi_delbm *h, int id, double pos[3], double quat[4], double vel[3],
+                                      double omega[3]);
+mi_status mi_delbm_set_particle_state(mi_delbm *h, int id, const double pos[3], const double quat[4],
+                                      const double vel[3], const double omega[3]);
+
+/* Kinematic states of all particles as one array of n x 13 doubles per
+ * particle [pos(3), quat(4), vel(3), omega(3)], copied asynchronously on the
+ * handle's stream (use page-locked host memory for a true async copy).  n must
+ * equal mi_delbm_num_particles.  set takes effect at the next step; get
+ * returns the state after the work queued so far (synchronise before
+ * reading the buffer). */
+mi_status mi_delbm_set_particle_states(mi_delbm *h, const double *states, int n);
+mi_status mi_delbm_get_particle_states(mi_delbm *h, double *states, int n);
+
+/* Shape and mass properties of particle id as the library holds them (after
+ * any centroid shift): centers[n*3], k[n] (cap entries available; *n_out is
+ * the ball count), mass properties and bounding radius
+ * R_b = max|c_i| + sqrt(sum k_i) (f < 1 beyond it).  Any output may be NULL. */
+mi_status mi_delbm_get_particle_shape(mi_delbm *h, int id, double *centers, double *k, int cap, int *n_out,
+                                      mi_mass_props *mp, double *Rb);
+
+/* Hydrodynamic force and torque of the last step (momentum exchange, torque
+ * about the particle position) and contact force and torque of the last DEM
+ * substep, each num_particles x 3 doubles, caller-owned; any may be NULL.
+ * Synchronises; reports MI_ECAPACITY if a list overflowed during the step. */
+mi_status mi_delbm_forces(mi_delbm *h, double *F_hydro, double *T_hydro, double *F_contact, double *T_contact);
+
+/* Node classes (bit 0 solid, bit 1 boundary, bit 2 newly uncovered) and
+ * owners (particle index of solid nodes, 0xFFFFFFFF for fluid) of the last
+ * flag phase, count = nx*ny*nz entries each, [z][y][x]; either may be NULL.
+ * Synchronises. */
+mi_status mi_delbm_get_node_classes(mi_delbm *h, uint8_t *node_class, uint32_t *owner, size_t count);
+
+/* Boundary links of the last flag phase: fluid node (linear index
+ * (z*ny + y)*nx + x), direction d (1..18) towards the solid neighbour, its
+ * particle, and the wall fraction q of the last links phase.  Order is
+ * unspecified.  cap entries available per array; *n_out = number of links
+ * (MI_ECAPACITY if larger than cap, nothing written).  Synchronises. */
+mi_status mi_delbm_get_links(mi_delbm *h, size_t cap, int32_t *cell, int8_t *dir, int32_t *particle, float *q,
+                             size_t *n_out);
+
+/* Per-step counters of the last step (synchronises). status: bit 0..2 list
+ * overflow (boundary nodes, links, uncovered nodes), bit 3 contact-pair
+ * overflow, bit 4 contact overflow, bit 5 a particle moved more than two
+ * nodes in one step; the bits are cleared by this call. */
+typedef struct {
+  long long boundary_nodes, links, new_nodes, candidate_pairs, contacts;
+  unsigned status;
+} mi_delbm_stats;
+mi_status mi_delbm_get_stats(mi_delbm *h, mi_delbm_stats *st);
+
 /* Per-phase GPU timing with CUDA events on the handle's stream.  While
  * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
  * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of

@@ -58,6 +58,16 @@ class DeviceView(ctypes.Structure):
                 ("node_class", c_void_p), ("owner", c_void_p), ("stream", c_void_p)]
 
 
+class MassProps(ctypes.Structure):
+    _fields_ = [("mass", c_double), ("volume", c_double), ("inertia", c_double * 9)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("boundary_nodes", ctypes.c_longlong), ("links", ctypes.c_longlong),
+                ("new_nodes", ctypes.c_longlong), ("candidate_pairs", ctypes.c_longlong),
+                ("contacts", ctypes.c_longlong), ("status", ctypes.c_uint)]
+
+
 def _sig(name, restype, *argtypes):
     fn = getattr(lib, name)
     fn.restype = restype
@@ -83,6 +93,19 @@ _sig("mi_delbm_get_device_view", c_int, _P, ctypes.POINTER(DeviceView))
 _sig("mi_delbm_set_timing", c_int, _P, c_int)
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
+_sig("mi_delbm_add_particle", c_int, _P, c_int, _P, _P, c_double, c_double, _P, _P, _P, _P,
+     ctypes.POINTER(MassProps), ctypes.POINTER(c_int))
+_sig("mi_delbm_num_particles", c_int, _P)
+_sig("mi_delbm_get_particle_state", c_int, _P, c_int, _P, _P, _P, _P)
+_sig("mi_delbm_set_particle_state", c_int, _P, c_int, _P, _P, _P, _P)
+_sig("mi_delbm_set_particle_states", c_int, _P, _P, c_int)
+_sig("mi_delbm_get_particle_states", c_int, _P, _P, c_int)
+_sig("mi_delbm_get_particle_shape", c_int, _P, c_int, _P, _P, c_int, ctypes.POINTER(c_int),
+     ctypes.POINTER(MassProps), ctypes.POINTER(c_double))
+_sig("mi_delbm_forces", c_int, _P, _P, _P, _P, _P)
+_sig("mi_delbm_get_node_classes", c_int, _P, _P, _P, c_size_t)
+_sig("mi_delbm_get_links", c_int, _P, c_size_t, _P, _P, _P, _P, ctypes.POINTER(c_size_t))
+_sig("mi_delbm_get_stats", c_int, _P, ctypes.POINTER(Stats))
 
 if lib.mi_delbm_abi_version() != 1:
     raise ImportError("libmi_delbm ABI version mismatch")
@@ -240,6 +263,91 @@ class Simulation:
 
     def launch_count(self):
         return int(lib.mi_delbm_launch_count(self.h))
+
+    # -- particles --------------------------------------------------------
+    def add_particle(self, centers, k, density, skin, pos, quat, vel=(0, 0, 0), omega=(0, 0, 0), mass_props=None):
+        c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
+        kk = np.ascontiguousarray(k, dtype=np.float64).reshape(-1)
+        vecs = [np.ascontiguousarray(v, dtype=np.float64) for v in (pos, quat, vel, omega)]
+        mp = None
+        if mass_props is not None:
+            mp = MassProps()
+            mp.mass = float(mass_props["mass"])
+            mp.volume = float(mass_props["volume"])
+            I = np.asarray(mass_props["inertia"], dtype=np.float64).reshape(9)
+            for j in range(9):
+                mp.inertia[j] = I[j]
+        pid = c_int(-1)
+        self._check(lib.mi_delbm_add_particle(self.h, len(kk), _ptr(c), _ptr(kk), float(density), float(skin),
+                                              *[_ptr(v) for v in vecs],
+                                              ctypes.byref(mp) if mp is not None else None, ctypes.byref(pid)))
+        return pid.value
+
+    def num_particles(self):
+        return int(lib.mi_delbm_num_particles(self.h))
+
+    def get_particle_state(self, pid):
+        out = [np.zeros(3), np.zeros(4), np.zeros(3), np.zeros(3)]
+        self._check(lib.mi_delbm_get_particle_state(self.h, int(pid), *[_ptr(v) for v in out]))
+        return dict(zip(("pos", "quat", "vel", "omega"), out))
+
+    def set_particle_state(self, pid, pos=None, quat=None, vel=None, omega=None):
+        args = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (pos, quat, vel, omega)]
+        self._check(lib.mi_delbm_set_particle_state(self.h, int(pid), *[None if v is None else _ptr(v) for v in args]))
+
+    def set_particle_states_ptr(self, ptr, n):
+        """Queue an async upload of n x 13 doubles from host address ptr."""
+        self._check(lib.mi_delbm_set_particle_states(self.h, c_void_p(int(ptr)), int(n)))
+
+    def get_particle_states_ptr(self, ptr, n):
+        """Queue an async download of n x 13 doubles to host address ptr."""
+        self._check(lib.mi_delbm_get_particle_states(self.h, c_void_p(int(ptr)), int(n)))
+
+    def forces_ptr(self, f_hydro, t_hydro):
+        """Synchronising read of the hydrodynamic force/torque into host addresses."""
+        self._check(lib.mi_delbm_forces(self.h, c_void_p(int(f_hydro)), c_void_p(int(t_hydro)), None, None))
+
+    def get_particle_shape(self, pid):
+        n = c_int(0)
+        self._check(lib.mi_delbm_get_particle_shape(self.h, int(pid), None, None, 0, ctypes.byref(n), None, None))
+        c = np.zeros((n.value, 3))
+        k = np.zeros(n.value)
+        mp = MassProps()
+        rb = c_double(0)
+        self._check(lib.mi_delbm_get_particle_shape(self.h, int(pid), _ptr(c), _ptr(k), n.value, ctypes.byref(n),
+                                                    ctypes.byref(mp), ctypes.byref(rb)))
+        return {"centers": c, "k": k, "mass": mp.mass, "volume": mp.volume,
+                "inertia": np.array(mp.inertia[:]).reshape(3, 3), "Rb": rb.value}
+
+    def forces(self):
+        n = self.num_particles()
+        out = [np.zeros((n, 3)) for _ in range(4)]
+        self._check(lib.mi_delbm_forces(self.h, *[_ptr(v) for v in out]))
+        return dict(zip(("F_hydro", "T_hydro", "F_contact", "T_contact"), out))
+
+    def node_classes(self):
+        cls = np.empty(self.shape, dtype=np.uint8)
+        own = np.empty(self.shape, dtype=np.uint32)
+        self._check(lib.mi_delbm_get_node_classes(self.h, _ptr(cls), _ptr(own), self.ncell))
+        return cls, own
+
+    def links(self):
+        n = c_size_t(0)
+        st = lib.mi_delbm_get_links(self.h, 0, None, None, None, None, ctypes.byref(n))
+        if st not in (MI_OK, MI_ECAPACITY):
+            self._check(st)
+        m = n.value
+        cell = np.empty(m, dtype=np.int32)
+        d = np.empty(m, dtype=np.int8)
+        p = np.empty(m, dtype=np.int32)
+        q = np.empty(m, dtype=np.float32)
+        self._check(lib.mi_delbm_get_links(self.h, m, _ptr(cell), _ptr(d), _ptr(p), _ptr(q), ctypes.byref(n)))
+        return {"cell": cell, "dir": d, "particle": p, "q": q}
+
+    def stats(self):
+        st = Stats()
+        self._check(lib.mi_delbm_get_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
 
 
 class CudaArray:

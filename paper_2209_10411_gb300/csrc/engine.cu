@@ -1,5 +1,7 @@
 // Engine and C-ABI of libmi_delbm: owns the device state of one lattice and
 // its particles, sequences the kernels of one coupled step on one stream.
+#include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -122,6 +124,96 @@ bool mi_delbm::forcing() const {
 // ---------------------------------------------------------------------------
 // Phases
 // ---------------------------------------------------------------------------
+ParticleLaunch mi_delbm::particle_launch() const {
+  ParticleLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.P = dP;
+  L.np = n_particles;
+  L.balls = dballs;
+  L.balls_d = dballs_d;
+  L.max_balls_per_particle = max_balls_pp < 2048 ? max_balls_pp : 2048;
+  L.cur_buf = owner_cur;
+  L.prev_buf = owner_cur ^ 1;
+  L.owner_cur = owner[owner_cur];
+  L.owner_prev = owner[owner_cur ^ 1];
+  L.cls = cls;
+  L.stamp = stamp;
+  L.ctr = dctr;
+  L.facc = facc;
+  L.bc_cell = bc_cell;
+  L.bc_mask = bc_mask;
+  L.bc_loff = bc_loff;
+  L.link_bc = link_bc;
+  L.link_p = link_p;
+  L.link_dir = link_dir;
+  L.link_q = link_q;
+  L.new_cell = new_cell;
+  L.cap_bc = cap_bc;
+  L.cap_links = cap_links;
+  L.cap_new = cap_new;
+  L.blocks_per_particle = blocks_per_particle;
+  L.g = geom();
+  return L;
+}
+
+mi_status mi_delbm::phase_flag() {
+  if (n_particles == 0) return MI_OK;
+  owner_cur ^= 1;  // the buffer holding the flags of two steps ago becomes current
+  ParticleLaunch L = particle_launch();
+  mi_status s;
+  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_prologue(L, stream); })) != MI_OK) return s;
+  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_clear(L, stream); })) != MI_OK) return s;
+  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_flag(L, stream); })) != MI_OK) return s;
+  return launch_phase(this, MI_PHASE_FLAG, [&] { return launch_classify(L, stream); });
+}
+
+mi_status mi_delbm::phase_links() {
+  if (n_particles == 0) return MI_OK;
+  ParticleLaunch L = particle_launch();
+  return launch_phase(this, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 8, stream); });
+}
+
+static BoundaryLaunch boundary_launch(const mi_delbm* h) {
+  BoundaryLaunch L;
+  L.pl = h->particle_launch();
+  L.A = h->pop[h->cur];
+  L.B = h->pop[h->cur ^ 1];
+  L.p = h->collide_params();
+  L.storage = h->cfg.storage;
+  L.forcing = h->forcing();
+  L.bb_mode = h->cfg.bb_mode;
+  L.grid = h->sm_count * 8;
+  return L;
+}
+
+mi_status mi_delbm::phase_refill() {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  return launch_phase(this, MI_PHASE_REFILL, [&] { return launch_refill(L, stream); });
+}
+
+mi_status mi_delbm::phase_boundary() {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  return launch_phase(this, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
+}
+
+mi_status mi_delbm::phase_integrate() {
+  if (n_particles == 0) return MI_OK;
+  IntegrateLaunch L;
+  L.P = dP;
+  L.np = n_particles;
+  L.facc = facc;
+  L.fc = fc;
+  for (int a = 0; a < 3; ++a) L.gravity[a] = cfg.gravity[a];
+  L.rho0 = cfg.rho0;
+  L.dt = 1.0 / cfg.dem_substeps;
+  mi_status s = MI_OK;
+  for (int k = 0; k < cfg.dem_substeps && s == MI_OK; ++k)
+    s = launch_phase(this, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
+  return s;
+}
+
 mi_status mi_delbm::phase_bulk() {
   BulkLaunch L;
   L.A = pop[cur];
@@ -143,8 +235,96 @@ mi_status mi_delbm::phase_swap() {
 
 mi_status mi_delbm::run_phases(unsigned phases) {
   mi_status s = MI_OK;
+  if ((phases & MI_PHASE_FLAG) && (s = phase_flag()) != MI_OK) return s;
+  if ((phases & MI_PHASE_LINKS) && (s = phase_links()) != MI_OK) return s;
+  if ((phases & MI_PHASE_REFILL) && (s = phase_refill()) != MI_OK) return s;
   if ((phases & MI_PHASE_BULK) && (s = phase_bulk()) != MI_OK) return s;
+  if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
+  if ((phases & MI_PHASE_INTEGRATE) && (s = phase_integrate()) != MI_OK) return s;
+  return MI_OK;
+}
+
+mi_status mi_delbm::sync(const char* what) {
+  if (!set_device()) return fail(MI_ECUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return MI_OK;
+}
+
+mi_status mi_delbm::check_status(bool clear) {
+  if (!particles_ready) return MI_OK;
+  DevCounters c;
+  cudaError_t e = cudaMemcpyAsync(&c, dctr, sizeof(c), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading device status");
+  const unsigned bad = c.status & (STATUS_BC_OVERFLOW | STATUS_LINK_OVERFLOW | STATUS_NEW_OVERFLOW |
+                                   STATUS_PAIR_OVERFLOW | STATUS_CONTACT_OVERFLOW);
+  if (clear && c.status) {
+    unsigned zero = 0;
+    cudaMemcpyAsync(&dctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, stream);
+    cudaStreamSynchronize(stream);
+  }
+  if (bad) {
+    return fail(MI_ECAPACITY, "a device list overflowed during the step (status bits " + std::to_string(bad) +
+                                  "; boundary nodes " + std::to_string(c.n_bc) + "/" + std::to_string(cap_bc) +
+                                  ", links " + std::to_string(c.n_links) + "/" + std::to_string(cap_links) +
+                                  ", uncovered " + std::to_string(c.n_new) + "/" + std::to_string(cap_new) + ")");
+  }
+  return MI_OK;
+}
+
+mi_status mi_delbm::ensure_particle_buffers() {
+  if (particles_ready) return MI_OK;
+  const int np = cfg.max_particles > 0 ? cfg.max_particles : 1;
+  const int nb = cfg.max_balls > 0 ? cfg.max_balls : 1;
+  owner[0] = (uint32_t*)dalloc(ncell * 4);
+  owner[1] = (uint32_t*)dalloc(ncell * 4);
+  stamp = (uint32_t*)dalloc(ncell * 4);
+  dctr = (DevCounters*)dalloc(sizeof(DevCounters));
+  facc = (long long*)dalloc(sizeof(long long) * 6 * np);
+  fc = (double*)dalloc(sizeof(double) * 6 * np);
+  dP = (DevParticle*)dalloc(sizeof(DevParticle) * np);
+  dballs = (float4*)dalloc(sizeof(float4) * nb);
+  dballs_d = (double*)dalloc(sizeof(double) * 4 * nb);
+  if (!owner[0] || !owner[1] || !stamp || !dctr || !facc || !fc || !dP || !dballs || !dballs_d)
+    return fail(MI_ENOMEM, "particle buffers: device allocation failed");
+  cudaError_t e = cudaMemsetAsync(owner[0], 0xFF, ncell * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(owner[1], 0xFF, ncell * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(stamp, 0, ncell * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dctr, 0, sizeof(DevCounters), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(facc, 0, sizeof(long long) * 6 * np, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fc, 0, sizeof(double) * 6 * np, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "particle buffers: initialisation");
+  particles_ready = true;
+  return MI_OK;
+}
+
+mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned nnew) {
+  if (bc <= cap_bc && links <= cap_links && nnew <= cap_new) return MI_OK;
+  mi_status s = sync("list reallocation");
+  if (s != MI_OK) return s;
+  bc = bc > cap_bc ? bc : cap_bc;
+  links = links > cap_links ? links : cap_links;
+  nnew = nnew > cap_new ? nnew : cap_new;
+  dfree(bc_cell); dfree(bc_mask); dfree(bc_loff); dfree(link_bc); dfree(link_p); dfree(link_dir);
+  dfree(link_q); dfree(new_cell);
+  bc_cell = (uint32_t*)dalloc(4ull * bc);
+  bc_mask = (uint32_t*)dalloc(4ull * bc);
+  bc_loff = (uint32_t*)dalloc(4ull * bc);
+  link_bc = (uint32_t*)dalloc(4ull * links);
+  link_p = (uint32_t*)dalloc(4ull * links);
+  link_dir = (uint8_t*)dalloc(1ull * links);
+  link_q = (float*)dalloc(4ull * links);
+  new_cell = (uint32_t*)dalloc(4ull * nnew);
+  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell) {
+    cap_bc = cap_links = cap_new = 0;
+    return fail(MI_ENOMEM, "link lists: device allocation failed");
+  }
+  cap_bc = bc;
+  cap_links = links;
+  cap_new = nnew;
   return MI_OK;
 }
 
@@ -209,8 +389,8 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     g_create_error = "mi_delbm_create: unknown bb_mode";
     return MI_EINVAL;
   }
-  if (cfg->dem_substeps < 1 || cfg->max_particles < 0 || cfg->max_balls < 0) {
-    g_create_error = "mi_delbm_create: dem_substeps must be >= 1 and capacities >= 0";
+  if (cfg->dem_substeps < 1 || cfg->max_particles < 0 || cfg->max_balls < 0 || cfg->max_particles > 65535) {
+    g_create_error = "mi_delbm_create: dem_substeps must be >= 1, capacities >= 0, max_particles <= 65535";
     return MI_EINVAL;
   }
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) {
@@ -261,6 +441,11 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     return MI_ECUDA;
   }
   h->tune.bulk_block_x = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && sms > 0)
+      h->sm_count = sms;
+  }
   *out = h;
   return MI_OK;
 }
@@ -407,5 +592,370 @@ mi_status mi_delbm_phase_times(mi_delbm* h, double ms[8], long long launches[8],
 }
 
 long long mi_delbm_launch_count(const mi_delbm* h) { return h ? h->launches : 0; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Particles
+// ---------------------------------------------------------------------------
+namespace {
+bool finite3(const double* v) { return v && std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+void rot_from_quat(const double q[4], double R[9]) {
+  const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+bool invert3(const double A[9], double Ai[9]) {
+  const double c0 = A[4] * A[8] - A[5] * A[7], c1 = A[5] * A[6] - A[3] * A[8], c2 = A[3] * A[7] - A[4] * A[6];
+  const double det = A[0] * c0 + A[1] * c1 + A[2] * c2;
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+  const double id = 1.0 / det;
+  Ai[0] = c0 * id; Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id; Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+  Ai[3] = c1 * id; Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id; Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  Ai[6] = c2 * id; Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id; Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const double* k, double density,
+                                double skin, const double pos[3], const double quat[4], const double vel[3],
+                                const double omega[3], const mi_mass_props* mp, int* id_out) {
+  if (!h) return MI_EINVAL;
+  if (n < 1 || !centers || !k || !pos || !quat) return h->fail(MI_EINVAL, "add_particle: n_balls >= 1 and non-null centers, k, pos, quat required");
+  if (!(density > 0.0) || !(skin >= 0.0) || !finite3(pos)) return h->fail(MI_EINVAL, "add_particle: density > 0, skin >= 0, finite pos required");
+  const double qn2 = quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3];
+  if (!(qn2 > 0.0) || !std::isfinite(qn2)) return h->fail(MI_EINVAL, "add_particle: quaternion must be non-zero and finite");
+  if ((vel && !finite3(vel)) || (omega && !finite3(omega))) return h->fail(MI_EINVAL, "add_particle: non-finite velocity");
+  double sumk = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!(k[i] > 0.0) || !std::isfinite(k[i]) || !finite3(centers + 3 * i))
+      return h->fail(MI_EINVAL, "add_particle: every k_i must be > 0 and every center finite");
+    sumk += k[i];
+  }
+  const double re = std::sqrt(sumk);
+  if (!(skin < re)) return h->fail(MI_EINVAL, "add_particle: skin radius must be below sqrt(sum k)");
+  if (h->n_particles >= h->cfg.max_particles) return h->fail(MI_ECAPACITY, "add_particle: max_particles reached");
+  if (h->n_balls_total + n > h->cfg.max_balls) return h->fail(MI_ECAPACITY, "add_particle: max_balls reached");
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status st = h->ensure_particle_buffers();
+  if (st != MI_OK) return st;
+  st = h->sync("add_particle");
+  if (st != MI_OK) return st;
+
+  std::vector<double> c(centers, centers + 3 * (size_t)n);
+  const int off = h->n_balls_total;
+  auto upload_balls = [&]() -> cudaError_t {
+    std::vector<float4> bf(n);
+    std::vector<double> bd(4 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      bf[i] = make_float4((float)c[3 * i], (float)c[3 * i + 1], (float)c[3 * i + 2], (float)k[i]);
+      bd[4 * i] = c[3 * i];
+      bd[4 * i + 1] = c[3 * i + 1];
+      bd[4 * i + 2] = c[3 * i + 2];
+      bd[4 * i + 3] = k[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(h->dballs + off, bf.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->dballs_d + 4 * (size_t)off, bd.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e;
+  };
+  auto bounding = [&]() {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i)
+      m = std::fmax(m, std::sqrt(c[3 * i] * c[3 * i] + c[3 * i + 1] * c[3 * i + 1] + c[3 * i + 2] * c[3 * i + 2]));
+    return m + re;
+  };
+  cudaError_t e = upload_balls();
+  if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: upload");
+
+  double X[3] = {pos[0], pos[1], pos[2]};
+  double R[9];
+  rot_from_quat(quat, R);
+  double mass, volume, I[9];
+  if (!mp) {
+    // midpoint quadrature of f >= 1, spacing 1/4, over [-Rb, Rb]^3
+    const double hq = 0.25, Rb0 = bounding();
+    const int nside = (int)std::ceil(2.0 * Rb0 / hq);
+    const int blocks = h->sm_count * 4;
+    double* part = (double*)h->dalloc(sizeof(double) * 10 * blocks);
+    if (!part) return h->fail(MI_ENOMEM, "add_particle: quadrature buffer");
+    e = launch_mass_quadrature(h->dballs + off, h->dballs_d + 4 * (size_t)off, n, Rb0, hq, nside, part, blocks, h->stream);
+    std::vector<double> hpart(10 * (size_t)blocks);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hpart.data(), part, sizeof(double) * 10 * blocks, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->dfree(part);
+    if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: quadrature");
+    double S[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < blocks; ++b)
+      for (int j = 0; j < 10; ++j) S[j] += hpart[10 * (size_t)b + j];
+    const double dv = hq * hq * hq;
+    volume = S[0] * dv;
+    if (!(volume > 0.0)) return h->fail(MI_EINVAL, "add_particle: the particle has no solid volume at spacing 1/4");
+    const double cen[3] = {S[1] * dv / volume, S[2] * dv / volume, S[3] * dv / volume};
+    double sec[9] = {S[4] * dv, S[5] * dv, S[6] * dv, S[5] * dv, S[7] * dv, S[8] * dv, S[6] * dv, S[8] * dv, S[9] * dv};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) sec[3 * a + b] -= volume * cen[a] * cen[b];
+    const double tr = sec[0] + sec[4] + sec[8];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) I[3 * a + b] = density * ((a == b ? tr : 0.0) - sec[3 * a + b]);
+    mass = density * volume;
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) c[3 * i + a] -= cen[a];
+    for (int a = 0; a < 3; ++a) X[a] += R[3 * a] * cen[0] + R[3 * a + 1] * cen[1] + R[3 * a + 2] * cen[2];
+    e = upload_balls();
+    if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: upload");
+  } else {
+    mass = mp->mass;
+    volume = mp->volume;
+    for (int j = 0; j < 9; ++j) I[j] = mp->inertia[j];
+    if (!(mass > 0.0) || !(volume > 0.0)) return h->fail(MI_EINVAL, "add_particle: mass and volume must be > 0");
+  }
+  DevParticle P;
+  std::memset(&P, 0, sizeof(P));
+  if (!invert3(I, P.inv_inertia)) return h->fail(MI_EINVAL, "add_particle: singular inertia tensor");
+  const double qn = std::sqrt(qn2);
+  for (int a = 0; a < 3; ++a) {
+    P.pos[a] = X[a];
+    P.vel[a] = vel ? vel[a] : 0.0;
+    P.omega[a] = omega ? omega[a] : 0.0;
+  }
+  (void)qn;  // kept as given: the kernels normalise with the same operations as the definition
+  for (int j = 0; j < 4; ++j) P.quat[j] = quat[j];
+  for (int j = 0; j < 9; ++j) P.inertia[j] = I[j];
+  P.mass = mass;
+  P.volume = volume;
+  P.density = density;
+  P.skin = skin;
+  P.re = re;
+  P.Rb = bounding();
+  P.ball_off = off;
+  P.n_balls = n;
+  for (int a = 0; a < 3; ++a) {
+    P.ext[a] = (int)std::ceil(2.0 * P.Rb) + 4;
+    P.lo[a] = BOX_NONE;
+    P.lo_hist[0][a] = BOX_NONE;
+    P.lo_hist[1][a] = BOX_NONE;
+  }
+  const int id = h->n_particles;
+  e = cudaMemcpyAsync(h->dP + id, &P, sizeof(P), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: particle upload");
+  h->hp.push_back(P);
+  for (int i = 0; i < n; ++i) {
+    h->hballs.push_back(make_float4((float)c[3 * i], (float)c[3 * i + 1], (float)c[3 * i + 2], (float)k[i]));
+    for (int a = 0; a < 3; ++a) h->hballs_d.push_back(c[3 * i + a]);
+    h->hballs_d.push_back(k[i]);
+  }
+  h->n_balls_total += n;
+  if (n > h->max_balls_pp) h->max_balls_pp = n;
+  h->n_particles += 1;
+  // list capacities and box-kernel grid from the particles' box extents
+  unsigned long long sbc = 0;
+  long long maxvol = 1;
+  for (const auto& q : h->hp) {
+    const unsigned long long e2 = (unsigned long long)(q.ext[0] + 4) * (q.ext[0] + 4);
+    sbc += 6ull * e2;
+    const long long v = (long long)(q.ext[0] + 8) * (q.ext[1] + 8) * (q.ext[2] + 8);
+    if (v > maxvol) maxvol = v;
+  }
+  if (sbc > 0x3FFFFFFFull) sbc = 0x3FFFFFFFull;
+  st = h->ensure_list_capacity((unsigned)sbc, (unsigned)std::min<unsigned long long>(6ull * sbc, 0xFFFFFFF0ull), (unsigned)sbc);
+  if (st != MI_OK) return st;
+  long long bpp = (maxvol + 1023) / 1024;
+  h->blocks_per_particle = (int)(bpp < 1 ? 1 : (bpp > 8192 ? 8192 : bpp));
+  if (id_out) *id_out = id;
+  return MI_OK;
+}
+
+int mi_delbm_num_particles(const mi_delbm* h) { return h ? h->n_particles : 0; }
+
+mi_status mi_delbm_get_particle_state(mi_delbm* h, int id, double pos[3], double quat[4], double vel[3],
+                                      double omega[3]) {
+  if (!h) return MI_EINVAL;
+  if (id < 0 || id >= h->n_particles) return h->fail(MI_EINVAL, "get_particle_state: bad id");
+  mi_status st = h->sync("get_particle_state");
+  if (st != MI_OK) return st;
+  DevParticle& P = h->hp[id];
+  cudaError_t e = cudaMemcpy(&P, h->dP + id, sizeof(P), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_particle_state");
+  for (int a = 0; a < 3; ++a) {
+    if (pos) pos[a] = P.pos[a];
+    if (vel) vel[a] = P.vel[a];
+    if (omega) omega[a] = P.omega[a];
+  }
+  if (quat)
+    for (int j = 0; j < 4; ++j) quat[j] = P.quat[j];
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_particle_state(mi_delbm* h, int id, const double pos[3], const double quat[4],
+                                      const double vel[3], const double omega[3]) {
+  if (!h) return MI_EINVAL;
+  if (id < 0 || id >= h->n_particles) return h->fail(MI_EINVAL, "set_particle_state: bad id");
+  if ((pos && !finite3(pos)) || (vel && !finite3(vel)) || (omega && !finite3(omega)))
+    return h->fail(MI_EINVAL, "set_particle_state: non-finite value");
+  mi_status st = h->sync("set_particle_state");
+  if (st != MI_OK) return st;
+  DevParticle& P = h->hp[id];
+  cudaError_t e = cudaMemcpy(&P, h->dP + id, sizeof(P), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_particle_state");
+  if (quat) {
+    const double qn = std::sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
+    if (!(qn > 0.0) || !std::isfinite(qn)) return h->fail(MI_EINVAL, "set_particle_state: bad quaternion");
+    for (int j = 0; j < 4; ++j) P.quat[j] = quat[j];
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (pos) P.pos[a] = pos[a];
+    if (vel) P.vel[a] = vel[a];
+    if (omega) P.omega[a] = omega[a];
+  }
+  e = cudaMemcpy(h->dP + id, &P, sizeof(P), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_particle_state");
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_particle_states(mi_delbm* h, const double* states, int n) {
+  if (!h || !states) return MI_EINVAL;
+  if (n != h->n_particles) return h->fail(MI_EINVAL, "set_particle_states: n must equal the particle count");
+  if (n == 0) return MI_OK;
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  static_assert(offsetof(DevParticle, pos) == 0 && offsetof(DevParticle, omega) == 10 * sizeof(double),
+                "kinematic fields must lead DevParticle");
+  cudaError_t e = cudaMemcpy2DAsync(h->dP, sizeof(DevParticle), states, 13 * sizeof(double), 13 * sizeof(double),
+                                    (size_t)n, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_particle_states");
+  return MI_OK;
+}
+
+mi_status mi_delbm_get_particle_states(mi_delbm* h, double* states, int n) {
+  if (!h || !states) return MI_EINVAL;
+  if (n != h->n_particles) return h->fail(MI_EINVAL, "get_particle_states: n must equal the particle count");
+  if (n == 0) return MI_OK;
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaMemcpy2DAsync(states, 13 * sizeof(double), h->dP, sizeof(DevParticle), 13 * sizeof(double),
+                                    (size_t)n, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_particle_states");
+  return MI_OK;
+}
+
+mi_status mi_delbm_get_particle_shape(mi_delbm* h, int id, double* centers, double* k, int cap, int* n_out,
+                                      mi_mass_props* mp, double* Rb) {
+  if (!h) return MI_EINVAL;
+  if (id < 0 || id >= h->n_particles) return h->fail(MI_EINVAL, "get_particle_shape: bad id");
+  const DevParticle& P = h->hp[id];
+  if (n_out) *n_out = P.n_balls;
+  if ((centers || k) && cap < P.n_balls) return h->fail(MI_ECAPACITY, "get_particle_shape: cap below the ball count");
+  for (int i = 0; i < P.n_balls; ++i) {
+    const double* b = &h->hballs_d[4 * (size_t)(P.ball_off + i)];
+    if (centers)
+      for (int a = 0; a < 3; ++a) centers[3 * i + a] = b[a];
+    if (k) k[i] = b[3];
+  }
+  if (mp) {
+    mp->mass = P.mass;
+    mp->volume = P.volume;
+    for (int j = 0; j < 9; ++j) mp->inertia[j] = P.inertia[j];
+  }
+  if (Rb) *Rb = P.Rb;
+  return MI_OK;
+}
+
+mi_status mi_delbm_forces(mi_delbm* h, double* F_hydro, double* T_hydro, double* F_contact, double* T_contact) {
+  if (!h) return MI_EINVAL;
+  mi_status st = h->sync("mi_delbm_forces");
+  if (st != MI_OK) return st;
+  const int np = h->n_particles;
+  if (np == 0) return MI_OK;
+  std::vector<long long> fa(6 * (size_t)np);
+  std::vector<double> fcv(6 * (size_t)np);
+  cudaError_t e = cudaMemcpy(fa.data(), h->facc, sizeof(long long) * 6 * np, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(fcv.data(), h->fc, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_forces");
+  for (int p = 0; p < np; ++p)
+    for (int a = 0; a < 3; ++a) {
+      if (F_hydro) F_hydro[3 * p + a] = (double)fa[6 * p + a] * FIX_INV;
+      if (T_hydro) T_hydro[3 * p + a] = (double)fa[6 * p + 3 + a] * FIX_INV;
+      if (F_contact) F_contact[3 * p + a] = fcv[6 * p + a];
+      if (T_contact) T_contact[3 * p + a] = fcv[6 * p + 3 + a];
+    }
+  return h->check_status(false);
+}
+
+mi_status mi_delbm_get_node_classes(mi_delbm* h, uint8_t* node_class, uint32_t* owner, size_t count) {
+  if (!h) return MI_EINVAL;
+  if (count != h->ncell) return h->fail(MI_EINVAL, "get_node_classes: count must be nx*ny*nz");
+  mi_status st = h->sync("get_node_classes");
+  if (st != MI_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (node_class) e = cudaMemcpy(node_class, h->cls, h->ncell, cudaMemcpyDeviceToHost);
+  if (owner && e == cudaSuccess) {
+    if (h->particles_ready) e = cudaMemcpy(owner, h->owner[h->owner_cur], 4 * h->ncell, cudaMemcpyDeviceToHost);
+    else std::memset(owner, 0xFF, 4 * h->ncell);
+  }
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_node_classes");
+  return MI_OK;
+}
+
+mi_status mi_delbm_get_links(mi_delbm* h, size_t cap, int32_t* cell, int8_t* dir, int32_t* particle, float* q,
+                             size_t* n_out) {
+  if (!h || !n_out) return MI_EINVAL;
+  mi_status st = h->sync("get_links");
+  if (st != MI_OK) return st;
+  *n_out = 0;
+  if (!h->particles_ready) return MI_OK;
+  DevCounters c;
+  cudaError_t e = cudaMemcpy(&c, h->dctr, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_links");
+  const size_t nl = std::min<size_t>(c.n_links, h->cap_links), nb = std::min<size_t>(c.n_bc, h->cap_bc);
+  *n_out = nl;
+  if (nl > cap) return h->fail(MI_ECAPACITY, "get_links: cap below the link count");
+  std::vector<uint32_t> lbc(nl), lp(nl), bcc(nb);
+  std::vector<uint8_t> ld(nl);
+  std::vector<float> lq(nl);
+  if (nl) {
+    e = cudaMemcpy(lbc.data(), h->link_bc, 4 * nl, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lp.data(), h->link_p, 4 * nl, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(ld.data(), h->link_dir, nl, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lq.data(), h->link_q, 4 * nl, cudaMemcpyDeviceToHost);
+  }
+  if (nb && e == cudaSuccess) e = cudaMemcpy(bcc.data(), h->bc_cell, 4 * nb, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_links");
+  for (size_t l = 0; l < nl; ++l) {
+    if (cell) cell[l] = lbc[l] < nb ? (int32_t)bcc[lbc[l]] : -1;
+    if (dir) dir[l] = (int8_t)ld[l];
+    if (particle) particle[l] = (int32_t)lp[l];
+    if (q) q[l] = lq[l];
+  }
+  return MI_OK;
+}
+
+mi_status mi_delbm_get_stats(mi_delbm* h, mi_delbm_stats* out) {
+  if (!h || !out) return MI_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  mi_status st = h->sync("get_stats");
+  if (st != MI_OK) return st;
+  if (!h->particles_ready) return MI_OK;
+  DevCounters c;
+  cudaError_t e = cudaMemcpy(&c, h->dctr, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_stats");
+  out->boundary_nodes = c.n_bc;
+  out->links = c.n_links;
+  out->new_nodes = c.n_new;
+  out->candidate_pairs = c.n_pairs;
+  out->contacts = c.n_contacts;
+  out->status = c.status;
+  unsigned zero = 0;
+  e = cudaMemcpy(&h->dctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return h->cuda_fail(e, "get_stats");
+  return MI_OK;
+}
 
 }  // extern "C"

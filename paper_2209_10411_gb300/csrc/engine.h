@@ -33,6 +33,30 @@ struct mi_delbm {
 
   int n_particles = 0;
   long long step_index = 0;
+  int sm_count = 148;
+
+  // particles (allocated at the first add_particle)
+  bool particles_ready = false;
+  std::vector<mi::DevParticle> hp;   // host mirror (pose fields refreshed on demand)
+  std::vector<float4> hballs;
+  std::vector<double> hballs_d;
+  mi::DevParticle* dP = nullptr;
+  float4* dballs = nullptr;
+  double* dballs_d = nullptr;
+  int n_balls_total = 0;
+  int max_balls_pp = 0;              // largest ball count of one particle
+  uint32_t* stamp = nullptr;
+  mi::DevCounters* dctr = nullptr;
+  long long* facc = nullptr;         // np x 6 fixed point
+  double* fc = nullptr;              // np x 6 contact force/torque
+  // lists
+  uint32_t *bc_cell = nullptr, *bc_mask = nullptr, *bc_loff = nullptr;
+  uint32_t *link_bc = nullptr, *link_p = nullptr;
+  uint8_t* link_dir = nullptr;
+  float* link_q = nullptr;
+  uint32_t* new_cell = nullptr;
+  unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
+  int blocks_per_particle = 1;
 
   TuneChoice tune;
 
@@ -55,6 +79,17 @@ struct mi_delbm {
   bool forcing() const;
 
   mi_status run_phases(unsigned phases);
+  mi_status phase_flag();
+  mi_status phase_links();
+  mi_status phase_refill();
   mi_status phase_bulk();
+  mi_status phase_boundary();
   mi_status phase_swap();
+  mi_status phase_integrate();
+
+  mi_status ensure_particle_buffers();
+  mi_status ensure_list_capacity(unsigned bc, unsigned links, unsigned nnew);
+  mi::ParticleLaunch particle_launch() const;
+  mi_status check_status(bool clear);
+  mi_status sync(const char* what);
 };

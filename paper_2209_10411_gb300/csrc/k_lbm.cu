@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __res
   const long long nxy = (long long)g.nx * g.ny;
   const long long c = x + (long long)g.nx * y + nxy * z;
   if (HAS_CLS) {
-    if (__ldg(cls + c) != 0) return;  // solid, boundary and new nodes go elsewhere
+    if (__ldg(cls + c) & (CLS_SOLID | CLS_BOUNDARY)) return;  // boundary nodes go to k_boundary
   }
   float h[19];
   const bool interior = (x > 0) & (x < g.nx - 1) & (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
@@ -120,6 +120,291 @@ cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s) {
     case MI_STORE_F32: return launch_bulk_st<MI_STORE_F32>(L, s);
     case MI_STORE_F16_DEV: return launch_bulk_st<MI_STORE_F16_DEV>(L, s);
     case MI_STORE_BF16_DEV: return launch_bulk_st<MI_STORE_BF16_DEV>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Refill of uncovered nodes (the paper's local bounce-back refill, Sec. 2.3.2),
+// applied to the stored post-collision populations f+(t) before streaming:
+//   f+_i(x_new) = f+_opp(i)(x_new + e_i) + 6 w_i rho0 (e_i . u_new)
+// when x_new + e_i is a fluid node that was also fluid at the previous step,
+// else f_eq,i(rho0, u_new); u_new is the rigid velocity at x_new of the
+// particle that covered it.  One thread per uncovered node.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ bool nbr_wrap(int x, int y, int z, int dx, int dy, int dz, const LatticeGeom& g,
+                                         long long& out) {
+  int a = x + dx, b = y + dy, c = z + dz;
+  if (a < 0 || a >= g.nx) {
+    if (!g.periodic[0]) return false;
+    a = (a + g.nx) % g.nx;
+  }
+  if (b < 0 || b >= g.ny) {
+    if (!g.periodic[1]) return false;
+    b = (b + g.ny) % g.ny;
+  }
+  if (c < 0 || c >= g.nz) {
+    if (!g.periodic[2]) return false;
+    c = (c + g.nz) % g.nz;
+  }
+  out = a + (long long)g.nx * (b + (long long)g.ny * c);
+  return true;
+}
+
+__device__ __forceinline__ void rigid_u(const DevParticle& P, double px, double py, double pz, float u[3]) {
+  const float r0 = (float)(px - P.pos[0]), r1 = (float)(py - P.pos[1]), r2 = (float)(pz - P.pos[2]);
+  u[0] = P.velf[0] + (P.omegaf[1] * r2 - P.omegaf[2] * r1);
+  u[1] = P.velf[1] + (P.omegaf[2] * r0 - P.omegaf[0] * r2);
+  u[2] = P.velf[2] + (P.omegaf[0] * r1 - P.omegaf[1] * r0);
+}
+
+__device__ __forceinline__ void coords(long long c, const LatticeGeom& g, int& x, int& y, int& z) {
+  x = (int)(c % g.nx);
+  y = (int)((c / g.nx) % g.ny);
+  z = (int)(c / ((long long)g.nx * g.ny));
+}
+
+template <int ST>
+__device__ __forceinline__ void moments_at(const typename Store<ST>::T* __restrict__ A, long long plane,
+                                           long long c, float& rho, float u[3]) {
+  float h[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) h[i] = Store<ST>::dev(A + i * plane + c, i);
+  float dr = 0.f;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) dr += h[i];
+  rho = 1.0f + dr;
+  const float jx = (h[1] - h[2]) + (h[7] - h[8]) + (h[9] - h[10]) + (h[11] - h[12]) + (h[13] - h[14]);
+  const float jy = (h[3] - h[4]) + (h[7] - h[8]) + (h[10] - h[9]) + (h[15] - h[16]) + (h[17] - h[18]);
+  const float jz = (h[5] - h[6]) + (h[11] - h[12]) + (h[14] - h[13]) + (h[15] - h[16]) + (h[18] - h[17]);
+  u[0] = jx / rho;
+  u[1] = jy / rho;
+  u[2] = jz / rho;
+}
+}  // namespace
+
+template <int ST>
+__global__ void __launch_bounds__(128) k_refill(BoundaryLaunch L) {
+  using T = typename Store<ST>::T;
+  T* A = static_cast<T*>(L.A);
+  const LatticeGeom& g = L.pl.g;
+  const unsigned nn = min(L.pl.ctr->n_new, L.pl.cap_new);
+  const float rho0 = L.p.rho0;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+    const long long c = L.pl.new_cell[k];
+    int x, y, z;
+    coords(c, g, x, y, z);
+    const DevParticle& P = L.pl.P[L.pl.owner_prev[c]];
+    float u[3];
+    rigid_u(P, x, y, z, u);
+    const float usq15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      const float eu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+      long long nb;
+      float h;
+      if (i != 0 && nbr_wrap(x, y, z, cx(i), cy(i), cz(i), g, nb) && L.pl.owner_cur[nb] == OWNER_NONE &&
+          L.pl.owner_prev[nb] == OWNER_NONE) {
+        h = Store<ST>::dev(A + opp(i) * g.plane + nb, opp(i)) + 6.0f * wq(i) * rho0 * eu;
+      } else {
+        h = wq(i) * (rho0 - 1.0f) + wq(i) * rho0 * (3.0f * eu + 4.5f * eu * eu - usq15);
+      }
+      Store<ST>::put(A + i * g.plane + c, i, h);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary nodes: pull streaming where the source is fluid, halfway
+// bounce-back where it is outside the domain, and for every link (x_f, d) to
+// a solid neighbour the paper's interpolated bounce-back (Eqs. eqneq1,
+// eqneq2, neqd) for the missing population j = opp(d):
+//   G_j = f_eq,d(rho_f, u_d) + [f+_d(x_f) - f_eq,d(rho_f, u_f)] + 6 w_d rho0 (e_j . u_w)
+//   u_d = u*/3 + 2 u**/3 (piecewise in q), u_w = v_p + omega_p x (x_w - X_p)
+// (or the halfway rule f+_d + 6 w_d rho0 e_j.u_w in Ladd mode); then BGK
+// collision.  The Galilean-invariant momentum exchange of each link,
+//   dP = (e_d - u_w) f+_d - (e_j - u_w) G_j = e_d (2 w_d + h_d + h_G) - u_w (h_d - h_G),
+// and its torque about X_p are summed per particle in 2^-40 fixed point with
+// 64-bit integer atomics (order-independent, so the sums are deterministic).
+// One thread per boundary node.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ void add_fixed(long long* facc, int p, const double v[6]) {
+  for (int k = 0; k < 6; ++k)
+    atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)__double2ll_rn(v[k] * FIX_SCALE));
+}
+}  // namespace
+
+template <int ST, bool FORCE, bool LADD>
+__global__ void __launch_bounds__(128) k_boundary(BoundaryLaunch L) {
+  using T = typename Store<ST>::T;
+  const T* __restrict__ A = static_cast<const T*>(L.A);
+  T* __restrict__ B = static_cast<T*>(L.B);
+  const LatticeGeom& g = L.pl.g;
+  const ParticleLaunch& pl = L.pl;
+  const unsigned nbc = min(pl.ctr->n_bc, pl.cap_bc);
+  const float rho0 = L.p.rho0;
+  const unsigned lane = threadIdx.x & 31u;
+  for (unsigned base = blockIdx.x * blockDim.x; base < nbc; base += gridDim.x * blockDim.x) {
+    const unsigned bi = base + threadIdx.x;
+    const bool active = bi < nbc;
+    int pacc = -1;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (active) {
+      const long long c = pl.bc_cell[bi];
+      const uint32_t mask = pl.bc_mask[bi];
+      const uint32_t loff = pl.bc_loff[bi];
+      int x, y, z;
+      coords(c, g, x, y, z);
+      float hown[19];
+#pragma unroll
+      for (int i = 0; i < 19; ++i) hown[i] = Store<ST>::dev(A + i * g.plane + c, i);
+      float rho_f, u_f[3];
+      {
+        float dr = 0.f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) dr += hown[i];
+        rho_f = 1.0f + dr;
+        u_f[0] = ((hown[1] - hown[2]) + (hown[7] - hown[8]) + (hown[9] - hown[10]) + (hown[11] - hown[12]) +
+                  (hown[13] - hown[14])) / rho_f;
+        u_f[1] = ((hown[3] - hown[4]) + (hown[7] - hown[8]) + (hown[10] - hown[9]) + (hown[15] - hown[16]) +
+                  (hown[17] - hown[18])) / rho_f;
+        u_f[2] = ((hown[5] - hown[6]) + (hown[11] - hown[12]) + (hown[14] - hown[13]) + (hown[15] - hown[16]) +
+                  (hown[18] - hown[17])) / rho_f;
+      }
+      float h[19];
+#pragma unroll
+      for (int j = 0; j < 19; ++j) {
+        int sx = x - cx(j), sy = y - cy(j), sz = z - cz(j);
+        int face = -1;
+        if (sz < 0) { if (g.periodic[2]) sz += g.nz; else face = 4; }
+        else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else face = 5; }
+        if (sy < 0) { if (g.periodic[1]) sy += g.ny; else face = 2; }
+        else if (sy >= g.ny) { if (g.periodic[1]) sy -= g.ny; else face = 3; }
+        if (sx < 0) { if (g.periodic[0]) sx += g.nx; else face = 0; }
+        else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else face = 1; }
+        if (face >= 0) {
+          h[j] = hown[opp(j)] + L.p.bb_wall[face][j];
+          continue;
+        }
+        const int d = opp(j);
+        if (j == 0 || !((mask >> d) & 1u)) {
+          h[j] = Store<ST>::dev(A + j * g.plane + (sx + (long long)g.nx * (sy + (long long)g.ny * sz)), j);
+          continue;
+        }
+        // link (x_f, d): the population arriving along j comes off the particle wall
+        const unsigned l = loff + __popc(mask & ((1u << d) - 1u));
+        if (l >= pl.cap_links) {
+          h[j] = hown[d];
+          continue;
+        }
+        const int p = (int)pl.link_p[l];
+        const DevParticle& P = pl.P[p];
+        const float q = LADD ? 0.5f : pl.link_q[l];
+        const double wx = x + (double)q * cx(d), wy = y + (double)q * cy(d), wz = z + (double)q * cz(d);
+        float uw[3];
+        rigid_u(P, wx, wy, wz, uw);
+        const float hd = hown[d];
+        const float wall = 6.0f * wq(d) * rho0 * (cx(j) * uw[0] + cy(j) * uw[1] + cz(j) * uw[2]);
+        float G;
+        if (LADD) {
+          G = hd + wall;
+        } else {
+          float u_ff[3] = {u_f[0], u_f[1], u_f[2]};
+          long long ff;
+          if (nbr_wrap(x, y, z, -cx(d), -cy(d), -cz(d), g, ff) && pl.owner_cur[ff] == OWNER_NONE) {
+            float rr;
+            moments_at<ST>(A, g.plane, ff, rr, u_ff);
+          }
+          float ud[3];
+          const float a1 = (1.0f - q) / (1.0f + q), a2 = 2.0f * q / (1.0f + q);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float us = q <= 0.5f ? 2.0f * q * u_f[a] + (1.0f - 2.0f * q) * u_ff[a]
+                                       : ((1.0f - q) / q) * u_f[a] + ((2.0f * q - 1.0f) / q) * uw[a];
+            const float uss = a1 * u_ff[a] + a2 * uw[a];
+            ud[a] = us / 3.0f + 2.0f * uss / 3.0f;
+          }
+          const float eud = cx(d) * ud[0] + cy(d) * ud[1] + cz(d) * ud[2];
+          const float euf = cx(d) * u_f[0] + cy(d) * u_f[1] + cz(d) * u_f[2];
+          const float ud2 = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+          const float uf2 = u_f[0] * u_f[0] + u_f[1] * u_f[1] + u_f[2] * u_f[2];
+          const float dfeq = wq(d) * rho_f * (3.0f * (eud - euf) + 4.5f * (eud * eud - euf * euf) - 1.5f * (ud2 - uf2));
+          G = hd + dfeq + wall;
+        }
+        h[j] = G;
+        // momentum exchange of this link, torque about X_p
+        const float s2 = 2.0f * wq(d) + hd + G, dlt = hd - G;
+        const float dP0 = cx(d) * s2 - uw[0] * dlt, dP1 = cy(d) * s2 - uw[1] * dlt, dP2 = cz(d) * s2 - uw[2] * dlt;
+        const double r0 = wx - P.pos[0], r1 = wy - P.pos[1], r2 = wz - P.pos[2];
+        if (pacc != p) {
+          if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
+          pacc = p;
+          for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+        }
+        acc[0] += dP0;
+        acc[1] += dP1;
+        acc[2] += dP2;
+        acc[3] += r1 * dP2 - r2 * dP1;
+        acc[4] += r2 * dP0 - r0 * dP2;
+        acc[5] += r0 * dP1 - r1 * dP0;
+      }
+      collide_store<ST, FORCE>(h, B, g.plane, c, L.p);
+    }
+    // warp-aggregated flush of the per-node sums (integer adds: order-free)
+    const int p0 = __shfl_sync(0xffffffffu, pacc, 0);
+    const bool uniform = __all_sync(0xffffffffu, pacc == p0 || pacc < 0);
+    if (uniform && p0 >= 0) {
+      long long iv[6];
+      for (int k = 0; k < 6; ++k) iv[k] = pacc >= 0 ? __double2ll_rn(acc[k] * FIX_SCALE) : 0LL;
+      for (int off = 16; off > 0; off >>= 1)
+        for (int k = 0; k < 6; ++k) iv[k] += __shfl_xor_sync(0xffffffffu, iv[k], off);
+      if (lane == 0)
+        for (int k = 0; k < 6; ++k) atomicAdd(reinterpret_cast<unsigned long long*>(pl.facc + 6 * p0 + k), (unsigned long long)iv[k]);
+    } else if (!uniform) {
+      if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
+    } else if (__any_sync(0xffffffffu, pacc >= 0)) {
+      // p0 < 0 but another lane holds sums (lane 0 idle): flush per lane
+      if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
+    }
+  }
+}
+
+template <int ST>
+static cudaError_t launch_refill_st(const BoundaryLaunch& L, cudaStream_t s) {
+  k_refill<ST><<<L.grid, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.pl.np == 0) return cudaSuccess;
+  switch (L.storage) {
+    case MI_STORE_F32: return launch_refill_st<MI_STORE_F32>(L, s);
+    case MI_STORE_F16_DEV: return launch_refill_st<MI_STORE_F16_DEV>(L, s);
+    case MI_STORE_BF16_DEV: return launch_refill_st<MI_STORE_BF16_DEV>(L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int ST, bool FORCE>
+static cudaError_t launch_boundary_f(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.bb_mode == MI_BB_LADD) k_boundary<ST, FORCE, true><<<L.grid, 128, 0, s>>>(L);
+  else k_boundary<ST, FORCE, false><<<L.grid, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_boundary_st(const BoundaryLaunch& L, cudaStream_t s) {
+  return L.forcing ? launch_boundary_f<ST, true>(L, s) : launch_boundary_f<ST, false>(L, s);
+}
+
+cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.pl.np == 0) return cudaSuccess;
+  switch (L.storage) {
+    case MI_STORE_F32: return launch_boundary_st<MI_STORE_F32>(L, s);
+    case MI_STORE_F16_DEV: return launch_boundary_st<MI_STORE_F16_DEV>(L, s);
+    case MI_STORE_BF16_DEV: return launch_boundary_st<MI_STORE_BF16_DEV>(L, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,489 @@
+// Particle-side kernels: per-step prologue, solid flagging from the metaball
+// field (Eq. 1), node classification with boundary/uncovered lists, the wall
+// fraction q of every boundary link, the rigid-body update (Newton-Euler,
+// Sec. 2.3.1) and mass-property quadrature.
+//
+// Flagging decides f >= 1 exactly as an FP64 evaluation would: an FP32 pass
+// with the body-frame point formed in FP64 decides every node whose FP32 value
+// is farther than GUARD from 1 (its error is below 3e-5 for control points at
+// least 0.3 lu from the node), and the rare nodes inside the guard band are
+// re-evaluated in FP64 with unfused operations in the order: x - X, R^T,
+// ball by ball k / |x_b - c|^2 accumulated left to right.
+#include <cfloat>
+
+#include "mi_internal.cuh"
+
+namespace mi {
+
+namespace {
+constexpr float GUARD = 1e-4f;
+
+__device__ __forceinline__ void quat_to_R_exact(const double q[4], double R[9]) {
+  // body -> world rotation of the normalised quaternion, unfused FP64
+  double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])),
+                                            __dmul_rn(q[2], q[2])),
+                                  __dmul_rn(q[3], q[3])));
+  const double w = __ddiv_rn(q[0], n), x = __ddiv_rn(q[1], n), y = __ddiv_rn(q[2], n), z = __ddiv_rn(q[3], n);
+  R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
+  R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+  R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+  R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+  R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
+  R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+  R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+  R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+  R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+}
+
+// f(x) >= 1 in FP64, unfused, same operation order as the definition above.
+__device__ __noinline__ bool inside_exact(const DevParticle& P, const double* balls_d, double xw, double yw,
+                                          double zw) {
+  const double d0 = __dsub_rn(xw, P.pos[0]), d1 = __dsub_rn(yw, P.pos[1]), d2 = __dsub_rn(zw, P.pos[2]);
+  const double* R = P.R;
+  const double b0 = __dadd_rn(__dadd_rn(__dmul_rn(R[0], d0), __dmul_rn(R[3], d1)), __dmul_rn(R[6], d2));
+  const double b1 = __dadd_rn(__dadd_rn(__dmul_rn(R[1], d0), __dmul_rn(R[4], d1)), __dmul_rn(R[7], d2));
+  const double b2 = __dadd_rn(__dadd_rn(__dmul_rn(R[2], d0), __dmul_rn(R[5], d1)), __dmul_rn(R[8], d2));
+  double f = 0.0;
+  for (int i = 0; i < P.n_balls; ++i) {
+    const double* c = balls_d + 4 * (size_t)(P.ball_off + i);
+    const double e0 = __dsub_rn(b0, c[0]), e1 = __dsub_rn(b1, c[1]), e2 = __dsub_rn(b2, c[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+    f = __dadd_rn(f, __ddiv_rn(c[3], r2));
+  }
+  return f >= 1.0;
+}
+
+// Region of a box kernel: box [lo, lo + ext) widened by `pad`, clipped.
+struct Region {
+  int lo[3], n[3];
+  long long total;
+};
+__device__ __forceinline__ Region clip_region(const int lo[3], const int ext[3], int pad, const LatticeGeom& g) {
+  Region r;
+  const int sz[3] = {g.nx, g.ny, g.nz};
+  r.total = 1;
+  for (int a = 0; a < 3; ++a) {
+    int l = lo[a] - pad, h = lo[a] + ext[a] + pad;
+    l = l < 0 ? 0 : l;
+    h = h > sz[a] ? sz[a] : h;
+    r.lo[a] = l;
+    r.n[a] = h > l ? h - l : 0;
+    r.total *= r.n[a];
+  }
+  return r;
+}
+
+__device__ __forceinline__ long long lin(int x, int y, int z, const LatticeGeom& g) {
+  return x + (long long)g.nx * (y + (long long)g.ny * z);
+}
+
+// Neighbour along direction d with periodic wrap; false if outside the domain.
+__device__ __forceinline__ bool neighbour(int x, int y, int z, int dx, int dy, int dz, const LatticeGeom& g,
+                                          long long& out) {
+  int a = x + dx, b = y + dy, c = z + dz;
+  if (a < 0 || a >= g.nx) {
+    if (!g.periodic[0]) return false;
+    a = (a + g.nx) % g.nx;
+  }
+  if (b < 0 || b >= g.ny) {
+    if (!g.periodic[1]) return false;
+    b = (b + g.ny) % g.ny;
+  }
+  if (c < 0 || c >= g.nz) {
+    if (!g.periodic[2]) return false;
+    c = (c + g.nz) % g.nz;
+  }
+  out = lin(a, b, c, g);
+  return true;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Prologue: bump the flag generation, zero counters and hydrodynamic force
+// sums, rotation matrices and node boxes at the current pose.
+// ---------------------------------------------------------------------------
+__global__ void k_prologue(ParticleLaunch L) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) {
+    L.ctr->gen += 1u;
+    L.ctr->n_bc = 0;
+    L.ctr->n_links = 0;
+    L.ctr->n_new = 0;
+  }
+  if (p >= L.np) return;
+  DevParticle& P = L.P[p];
+  quat_to_R_exact(P.quat, P.R);
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = (int)floor(P.pos[a] - P.Rb) - 1;
+    P.posf[a] = (float)P.pos[a];
+    P.velf[a] = (float)P.vel[a];
+    P.omegaf[a] = (float)P.omega[a];
+    const int prev = P.lo_hist[L.prev_buf][a];
+    if (prev != BOX_NONE && abs(P.lo[a] - prev) > 2) atomicOr(&L.ctr->status, STATUS_MOVED_TOO_FAR);
+  }
+  for (int k = 0; k < 6; ++k) L.facc[6 * p + k] = 0;
+}
+
+cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s) {
+  const int blocks = L.np > 0 ? (L.np + 127) / 128 : 1;
+  k_prologue<<<blocks, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Clear the owner buffer about to be rewritten, over the boxes it was last
+// written with.
+// ---------------------------------------------------------------------------
+__global__ void k_clear(ParticleLaunch L) {
+  const DevParticle& P = L.P[blockIdx.y];
+  const int* lo = P.lo_hist[L.cur_buf];
+  if (lo[0] == BOX_NONE) return;
+  const Region r = clip_region(lo, P.ext, 0, L.g);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = r.lo[0] + (int)(i % r.n[0]);
+    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
+    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+    L.owner_cur[lin(x, y, z, L.g)] = OWNER_NONE;
+  }
+}
+
+cudaError_t launch_clear(const ParticleLaunch& L, cudaStream_t s) {
+  if (L.np == 0) return cudaSuccess;
+  dim3 grid(L.blocks_per_particle, L.np);
+  k_clear<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Solid flagging: node x of particle p's box is solid for p when
+// f_p(R_p^T (x - X_p)) >= 1; the owner is the lowest such p (atomicMin).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
+  extern __shared__ float4 sb[];
+  const int p = blockIdx.y;
+  const DevParticle& P = L.P[p];
+  const int nb = P.n_balls;
+  const bool staged = nb <= L.max_balls_per_particle;
+  if (staged)
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = L.balls[P.ball_off + i];
+  __syncthreads();
+  const float4* bl = staged ? sb : L.balls + P.ball_off;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) L.P[p].lo_hist[L.cur_buf][a] = P.lo[a];
+  const Region r = clip_region(P.lo, P.ext, 0, L.g);
+  const double* R = P.R;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = r.lo[0] + (int)(i % r.n[0]);
+    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
+    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+    const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
+    const float b0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);
+    const float b1 = (float)(R[1] * d0 + R[4] * d1 + R[7] * d2);
+    const float b2 = (float)(R[2] * d0 + R[5] * d1 + R[8] * d2);
+    float f = 0.f;
+    bool inside = false, decided = false;
+    for (int b = 0; b < nb; ++b) {
+      const float4 c = bl[b];
+      const float e0 = b0 - c.x, e1 = b1 - c.y, e2 = b2 - c.z;
+      f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
+      if (f > 1.0f + GUARD) {  // partial sums only grow: inside for sure
+        inside = decided = true;
+        break;
+      }
+    }
+    if (!decided) {
+      if (f < 1.0f - GUARD) inside = false;
+      else inside = inside_exact(P, L.balls_d, (double)x, (double)y, (double)z);
+    }
+    if (inside) atomicMin(L.owner_cur + lin(x, y, z, L.g), (uint32_t)p);
+  }
+}
+
+cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s) {
+  if (L.np == 0) return cudaSuccess;
+  dim3 grid(L.blocks_per_particle, L.np);
+  const size_t smem = sizeof(float4) * (size_t)L.max_balls_per_particle;
+  k_flag<<<grid, 256, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Classification over each particle's old and new boxes widened by 2: solid,
+// boundary (fluid with a solid neighbour; 18-bit link mask), uncovered (fluid
+// now, solid at the previous step).  Boxes may overlap: every block writes the
+// same class for a node, and a per-node generation stamp lets exactly one
+// block append it to the boundary / uncovered lists.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
+  const DevParticle& P = L.P[blockIdx.y];
+  int lo[3], ext[3];
+  const int* lp = P.lo_hist[L.prev_buf];
+  for (int a = 0; a < 3; ++a) {
+    if (lp[0] == BOX_NONE) {
+      lo[a] = P.lo[a];
+      ext[a] = P.ext[a];
+    } else {
+      lo[a] = min(P.lo[a], lp[a]);
+      ext[a] = max(P.lo[a], lp[a]) + P.ext[a] - lo[a];
+    }
+  }
+  const Region r = clip_region(lo, ext, 2, L.g);
+  const unsigned gen = L.ctr->gen;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = r.lo[0] + (int)(i % r.n[0]);
+    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
+    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+    const long long c = lin(x, y, z, L.g);
+    const bool solid = L.owner_cur[c] != OWNER_NONE;
+    const bool was = L.owner_prev[c] != OWNER_NONE;
+    uint32_t mask = 0;
+    if (!solid) {
+#pragma unroll
+      for (int d = 1; d < 19; ++d) {
+        long long nbr;
+        if (neighbour(x, y, z, cx(d), cy(d), cz(d), L.g, nbr) && L.owner_cur[nbr] != OWNER_NONE) mask |= 1u << d;
+      }
+    }
+    const bool isnew = !solid && was;
+    L.cls[c] = (uint8_t)((solid ? CLS_SOLID : 0) | (mask ? CLS_BOUNDARY : 0) | (isnew ? CLS_NEW : 0));
+    if (!(mask || isnew)) continue;
+    if (atomicExch(L.stamp + c, gen) == gen) continue;  // another block listed it
+    if (isnew) {
+      const unsigned k = atomicAdd(&L.ctr->n_new, 1u);
+      if (k < L.cap_new) L.new_cell[k] = (uint32_t)c;
+      else atomicOr(&L.ctr->status, STATUS_NEW_OVERFLOW);
+    }
+    if (mask) {
+      const unsigned m = __popc(mask);
+      const unsigned bi = atomicAdd(&L.ctr->n_bc, 1u);
+      const unsigned lo_l = atomicAdd(&L.ctr->n_links, m);
+      if (bi >= L.cap_bc) {
+        atomicOr(&L.ctr->status, STATUS_BC_OVERFLOW);
+        continue;
+      }
+      L.bc_cell[bi] = (uint32_t)c;
+      L.bc_mask[bi] = mask;
+      L.bc_loff[bi] = lo_l;
+      if (lo_l + m > L.cap_links) {
+        atomicOr(&L.ctr->status, STATUS_LINK_OVERFLOW);
+        continue;
+      }
+      unsigned k = 0;
+      for (int d = 1; d < 19; ++d) {
+        if (!((mask >> d) & 1u)) continue;
+        long long nbr;
+        neighbour(x, y, z, cx(d), cy(d), cz(d), L.g, nbr);
+        L.link_bc[lo_l + k] = bi;
+        L.link_dir[lo_l + k] = (uint8_t)d;
+        L.link_p[lo_l + k] = L.owner_cur[nbr];
+        ++k;
+      }
+    }
+  }
+}
+
+cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
+  if (L.np == 0) return cudaSuccess;
+  dim3 grid(L.blocks_per_particle, L.np);
+  k_classify<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Wall fraction of each link: root q in (0, 1] of g(q) = f_p(x_f + q e_d) - 1
+// by Newton steps kept inside a shrinking bracket [lo, hi] (bisection when a
+// Newton step leaves it).  FP32 with the body-frame origin of the link formed
+// in FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
+  const unsigned nl = min(L.ctr->n_links, L.cap_links);
+  const unsigned nbc = min(L.ctr->n_bc, L.cap_bc);
+  for (unsigned l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+    const unsigned bi = L.link_bc[l];
+    if (bi >= nbc) continue;
+    const long long c = L.bc_cell[bi];
+    const int d = L.link_dir[l];
+    const DevParticle& P = L.P[L.link_p[l]];
+    const int x = (int)(c % L.g.nx), y = (int)((c / L.g.nx) % L.g.ny), z = (int)(c / ((long long)L.g.nx * L.g.ny));
+    const double* R = P.R;
+    const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
+    const float p0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);
+    const float p1 = (float)(R[1] * d0 + R[4] * d1 + R[7] * d2);
+    const float p2 = (float)(R[2] * d0 + R[5] * d1 + R[8] * d2);
+    const float e0 = (float)(R[0] * cx(d) + R[3] * cy(d) + R[6] * cz(d));
+    const float e1 = (float)(R[1] * cx(d) + R[4] * cy(d) + R[7] * cz(d));
+    const float e2 = (float)(R[2] * cx(d) + R[5] * cy(d) + R[8] * cz(d));
+    const float4* bl = L.balls + P.ball_off;
+    float lo = 0.f, hi = 1.f, q = 0.5f;
+    for (int it = 0; it < 30; ++it) {
+      float g = -1.f, gp = 0.f;
+      for (int b = 0; b < P.n_balls; ++b) {
+        const float4 cb = __ldg(bl + b);
+        const float a0 = p0 + q * e0 - cb.x, a1 = p1 + q * e1 - cb.y, a2 = p2 + q * e2 - cb.z;
+        const float r2 = a0 * a0 + a1 * a1 + a2 * a2;
+        const float t = __fdividef(cb.w, r2);
+        g += t;
+        gp -= 2.f * __fdividef(t * (a0 * e0 + a1 * e1 + a2 * e2), r2);
+      }
+      if (g >= 0.f) hi = q;
+      else lo = q;
+      float qn = q - g / gp;
+      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
+      const bool done = fabsf(qn - q) < 2e-7f || (hi - lo) < 2e-7f;
+      q = qn;
+      if (done) break;
+    }
+    L.link_q[l] = fminf(fmaxf(q, 1e-6f), 1.0f);
+  }
+}
+
+cudaError_t launch_links_q(const ParticleLaunch& L, int grid, cudaStream_t s) {
+  if (L.np == 0) return cudaSuccess;
+  k_links_q<<<grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rigid-body update, one thread per particle, FP64: semi-implicit Euler for
+// the velocity, Euler's equations in the body frame, exponential map for the
+// orientation; buoyancy-corrected gravity (m - rho0 V) g.
+// ---------------------------------------------------------------------------
+__global__ void k_integrate(IntegrateLaunch L) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.np) return;
+  DevParticle& P = L.P[p];
+  double F[3], T[3];
+  for (int a = 0; a < 3; ++a) {
+    F[a] = (double)L.facc[6 * p + a] * FIX_INV;
+    T[a] = (double)L.facc[6 * p + 3 + a] * FIX_INV;
+    if (L.fc) {
+      F[a] += L.fc[6 * p + a];
+      T[a] += L.fc[6 * p + 3 + a];
+    }
+  }
+  const double m = P.mass, dt = L.dt;
+  const double wg = m - L.rho0 * P.volume;
+  for (int a = 0; a < 3; ++a) P.vel[a] += dt * (F[a] + wg * L.gravity[a]) / m;
+  // rotation at the current pose
+  double q[4];
+  double qn = sqrt(P.quat[0] * P.quat[0] + P.quat[1] * P.quat[1] + P.quat[2] * P.quat[2] + P.quat[3] * P.quat[3]);
+  for (int k = 0; k < 4; ++k) q[k] = P.quat[k] / qn;
+  double R[9];
+  quat_to_R_exact(q, R);
+  double wb[3], Tb[3];
+  for (int a = 0; a < 3; ++a) {
+    wb[a] = R[0 + a] * P.omega[0] + R[3 + a] * P.omega[1] + R[6 + a] * P.omega[2];
+    Tb[a] = R[0 + a] * T[0] + R[3 + a] * T[1] + R[6 + a] * T[2];
+  }
+  const double* I = P.inertia;
+  const double* Ii = P.inv_inertia;
+  double Iw[3], rhs[3];
+  for (int a = 0; a < 3; ++a) Iw[a] = I[3 * a] * wb[0] + I[3 * a + 1] * wb[1] + I[3 * a + 2] * wb[2];
+  rhs[0] = Tb[0] - (wb[1] * Iw[2] - wb[2] * Iw[1]);
+  rhs[1] = Tb[1] - (wb[2] * Iw[0] - wb[0] * Iw[2]);
+  rhs[2] = Tb[2] - (wb[0] * Iw[1] - wb[1] * Iw[0]);
+  for (int a = 0; a < 3; ++a) wb[a] += dt * (Ii[3 * a] * rhs[0] + Ii[3 * a + 1] * rhs[1] + Ii[3 * a + 2] * rhs[2]);
+  // q <- normalize(q (x) exp(wb dt / 2))
+  const double th[3] = {wb[0] * dt, wb[1] * dt, wb[2] * dt};
+  const double tn = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+  double dq[4] = {1.0, 0.0, 0.0, 0.0};
+  if (tn > 0.0) {
+    const double sn = sin(0.5 * tn) / tn;
+    dq[0] = cos(0.5 * tn);
+    dq[1] = sn * th[0];
+    dq[2] = sn * th[1];
+    dq[3] = sn * th[2];
+  }
+  double r[4];
+  r[0] = q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3];
+  r[1] = q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2];
+  r[2] = q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1];
+  r[3] = q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0];
+  const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+  for (int k = 0; k < 4; ++k) P.quat[k] = r[k] / rn;
+  quat_to_R_exact(P.quat, R);
+  for (int a = 0; a < 3; ++a) P.omega[a] = R[3 * a] * wb[0] + R[3 * a + 1] * wb[1] + R[3 * a + 2] * wb[2];
+  for (int a = 0; a < 3; ++a) P.pos[a] += dt * P.vel[a];
+}
+
+cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s) {
+  if (L.np == 0) return cudaSuccess;
+  k_integrate<<<(L.np + 127) / 128, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mass properties: midpoint quadrature of the indicator f >= 1 (FP32 with the
+// FP64 guard band), FP64 moment sums per block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mass(const float4* balls, const double* balls_d, int nb, double Rb,
+                                              double h, int n, double* partials) {
+  __shared__ double red[10][256];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const long long total = (long long)n * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    const double X = __dadd_rn(-Rb, __dmul_rn(ix + 0.5, h));
+    const double Y = __dadd_rn(-Rb, __dmul_rn(iy + 0.5, h));
+    const double Z = __dadd_rn(-Rb, __dmul_rn(iz + 0.5, h));
+    const float xf = (float)X, yf = (float)Y, zf = (float)Z;
+    float f = 0.f;
+    bool inside = false, decided = false;
+    for (int b = 0; b < nb; ++b) {
+      const float4 c = balls[b];
+      const float e0 = xf - c.x, e1 = yf - c.y, e2 = zf - c.z;
+      f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
+      if (f > 1.0f + GUARD) {
+        inside = decided = true;
+        break;
+      }
+    }
+    if (!decided) {
+      if (f < 1.0f - GUARD) {
+        inside = false;
+      } else {
+        double fd = 0.0;
+        for (int b = 0; b < nb; ++b) {
+          const double* c = balls_d + 4 * b;
+          const double e0 = __dsub_rn(X, c[0]), e1 = __dsub_rn(Y, c[1]), e2 = __dsub_rn(Z, c[2]);
+          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+          fd = __dadd_rn(fd, __ddiv_rn(c[3], r2));
+        }
+        inside = fd >= 1.0;
+      }
+    }
+    if (inside) {
+      acc[0] += 1.0;
+      acc[1] += X;
+      acc[2] += Y;
+      acc[3] += Z;
+      acc[4] += X * X;
+      acc[5] += X * Y;
+      acc[6] += X * Z;
+      acc[7] += Y * Y;
+      acc[8] += Y * Z;
+      acc[9] += Z * Z;
+    }
+  }
+  for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+      for (int k = 0; k < 10; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) partials[10 * blockIdx.x + k] = red[k][0];
+}
+
+cudaError_t launch_mass_quadrature(const float4* balls, const double* balls_d, int n_balls, double Rb, double h,
+                                   int n_side, double* partials, int blocks, cudaStream_t s) {
+  k_mass<<<blocks, 256, 0, s>>>(balls, balls_d, n_balls, Rb, h, n_side, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace mi

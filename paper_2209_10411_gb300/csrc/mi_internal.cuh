@@ -110,4 +110,104 @@ cudaError_t launch_fill_rest(void* pop, const LatticeGeom& g, int storage, float
 cudaError_t launch_pack(const float* src, void* pop, const LatticeGeom& g, int storage, cudaStream_t s);
 cudaError_t launch_unpack(const void* pop, float* dst, const LatticeGeom& g, int storage, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Particles
+// ---------------------------------------------------------------------------
+constexpr int BOX_NONE = -(1 << 30);  // "no box written" marker in box histories
+constexpr double FIX_SCALE = 1099511627776.0;  // 2^40: fixed-point scale of force sums
+constexpr double FIX_INV = 1.0 / 1099511627776.0;
+
+// FP64 state of one particle (device table, one entry per particle).
+struct DevParticle {
+  double pos[3], quat[4], vel[3], omega[3];  // world frame; quat = (w, x, y, z)
+  double mass, volume, density, skin, Rb, re;
+  double inertia[9], inv_inertia[9];         // body frame, about the centroid
+  double R[9];                               // body -> world rotation at the current pose
+  float posf[3], velf[3], omegaf[3];         // FP32 copies for the lattice kernels
+  int ball_off, n_balls;
+  int ext[3];                                // node box extent per axis (constant)
+  int lo[3];                                 // node box origin at the current pose
+  int lo_hist[2][3];                         // box origin last flagged into owner buffer b
+};
+
+// Per-step device counters and status (one instance per handle).
+struct DevCounters {
+  unsigned int gen;      // flag generation stamp (bumped once per flag phase)
+  unsigned int n_bc;     // boundary nodes
+  unsigned int n_links;  // boundary links
+  unsigned int n_new;    // uncovered nodes
+  unsigned int status;   // STATUS_* bits, sticky until read
+  unsigned int n_contacts;
+  unsigned int n_pairs;
+  unsigned int pad;
+};
+constexpr unsigned STATUS_BC_OVERFLOW = 1u, STATUS_LINK_OVERFLOW = 2u, STATUS_NEW_OVERFLOW = 4u,
+                   STATUS_PAIR_OVERFLOW = 8u, STATUS_CONTACT_OVERFLOW = 16u, STATUS_MOVED_TOO_FAR = 32u;
+
+struct ParticleLaunch {
+  DevParticle* P;
+  int np;
+  const float4* balls;        // (c_x, c_y, c_z, k) FP32
+  const double* balls_d;      // (c_x, c_y, c_z, k) FP64, 4 per ball
+  int max_balls_per_particle;
+  uint32_t* owner_cur;        // buffer being written this step
+  const uint32_t* owner_prev; // flags of the previous step
+  int cur_buf, prev_buf;      // their indices (for the box histories)
+  uint8_t* cls;
+  uint32_t* stamp;
+  DevCounters* ctr;
+  long long* facc;            // np x 6 fixed-point (F_h, T_h)
+  // lists
+  uint32_t *bc_cell, *bc_mask, *bc_loff;
+  uint32_t *link_bc, *link_p;
+  uint8_t* link_dir;
+  float* link_q;
+  uint32_t* new_cell;
+  unsigned cap_bc, cap_links, cap_new;
+  int blocks_per_particle;
+  LatticeGeom g;
+};
+cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s);
+cudaError_t launch_clear(const ParticleLaunch& L, cudaStream_t s);
+cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s);
+cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s);
+cudaError_t launch_links_q(const ParticleLaunch& L, int grid, cudaStream_t s);
+
+struct BoundaryLaunch {
+  ParticleLaunch pl;
+  void* A;  // f+(t); the refill writes into it at uncovered nodes
+  void* B;  // f+(t+1)
+  CollideParams p;
+  int storage;
+  bool forcing;
+  int bb_mode;
+  int grid;
+};
+cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s);
+cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s);
+
+struct IntegrateLaunch {
+  DevParticle* P;
+  int np;
+  const long long* facc;   // hydrodynamic F, T (fixed point)
+  const double* fc;        // contact F, T (np x 6) or nullptr
+  double gravity[3];
+  double rho0;
+  double dt;
+};
+cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s);
+
+// Mass properties by midpoint quadrature of f >= 1 on a grid of spacing h over
+// [-Rb, Rb]^3 (body frame); out: [count, sx, sy, sz, sxx, sxy, sxz, syy, syz, szz]
+// per block, summed on the host in block order.
+cudaError_t launch_mass_quadrature(const float4* balls, const double* balls_d, int n_balls, double Rb,
+                                   double h, int n_side, double* partials, int blocks, cudaStream_t s);
+
+// D3Q19 direction of the integer offset, or -1.
+__host__ __device__ inline int dir_of(int x, int y, int z) {
+  for (int i = 0; i < 19; ++i)
+    if (cx(i) == x && cy(i) == y && cz(i) == z) return i;
+  return -1;
+}
+
 }  // namespace mi

@@ -1,0 +1,229 @@
+"""GPU parity of the particle phases (flagging, links, refill, IBB, momentum
+exchange, rigid-body update) against the FP64 oracle, through the C-ABI.
+
+Bars: node owners, node classes and the link set bit-exact; wall fraction q
+within 1e-5 (FP32 root of an FP32 field whose body-frame point carries ~1e-6
+absolute rounding); populations at fluid nodes within 1e-5 relative; hydro-
+dynamic force and torque within 1e-4 * max(|F_ref|, 1e-3 * sum_links |dP|)
+per particle (the link-sum scale guards the cancellation of O(0.1) link terms
+into a small net force).
+"""
+import numpy as np
+import pytest
+
+from oracle import coupling, dem, lbm, metaball
+from oracle.d3q19 import E, W
+from paper_2209_10411_gb300 import scenes
+from tests.gpu_helpers import binding
+
+pytestmark = pytest.mark.gpu
+
+TAU = 0.8
+ALL_LBM = 1 | 2 | 4 | 8 | 16 | 32  # flag, links, refill, bulk, boundary, swap
+
+
+def _prepared(spec, pos, quat, vel, omega):
+    """Oracle particle dict with control points shifted to the oracle's
+    quadrature centroid (inputs to both sides)."""
+    mp = metaball.mass_properties(spec.centers, spec.k, spec.density)
+    c = spec.centers - mp["centroid"]
+    mp = metaball.mass_properties(c, spec.k, spec.density)
+    P = {"centers": c, "k": spec.k.copy(), "pos": np.asarray(pos, float), "quat": np.asarray(quat, float),
+         "vel": np.asarray(vel, float), "omega": np.asarray(omega, float), "density": spec.density,
+         "skin": spec.skin, "mass": mp["mass"], "volume": mp["volume"], "inertia": mp["inertia"]}
+    return P
+
+
+def _initial_flow(shape, seed, umax=0.03):
+    nx, ny, nz = shape
+    u = umax * scenes.velocity_field_noise(shape, seed)
+    feq = lbm.equilibrium(np.ones((nz, ny, nx)), u)
+    noise = scenes.lattice_noise(shape, seed).astype(np.float64)
+    return (feq * (1.0 + 0.01 * noise)).astype(np.float32).astype(np.float64)
+
+
+def _run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM):
+    nx, ny, nz = shape
+    sim = B.Simulation(nx, ny, nz, tau=TAU, bb_mode=(B.BB_LADD if mode == "ladd" else B.BB_IBB), storage=storage)
+    for Pp in parts_prev:
+        sim.add_particle(Pp["centers"], Pp["k"], Pp["density"], Pp["skin"], Pp["pos"], Pp["quat"],
+                         Pp["vel"], Pp["omega"],
+                         mass_props={"mass": Pp["mass"], "volume": Pp["volume"], "inertia": Pp["inertia"]})
+    sim.step_phases(1)  # flags at the previous pose
+    for i, P in enumerate(parts):
+        sim.set_particle_state(i, P["pos"], P["quat"], P["vel"], P["omega"])
+    sim.set_populations(f0.astype(np.float32))
+    sim.step_phases(phases)
+    return sim
+
+
+def _compare_step(sim, shape, parts_prev, parts, f0, mode):
+    nx, ny, nz = shape
+    owner = metaball.flag_nodes(shape, parts)
+    owner_prev = metaball.flag_nodes(shape, parts_prev)
+    ref, F, T, L = coupling.coupled_lbm_step(f0, owner, owner_prev, parts, TAU, bb_mode=mode, return_links=True)
+    cls, own = sim.node_classes()
+    own = own.astype(np.int64)
+    own[own == 0xFFFFFFFF] = -1
+    # owners and classes bit-exact
+    assert np.array_equal(own, owner), "owner mismatch at %d nodes" % (own != owner).sum()
+    solid, new = coupling.classify(owner, owner_prev)
+    boundary = np.zeros_like(solid)
+    cl = L["cell"]
+    boundary[cl[:, 2], cl[:, 1], cl[:, 0]] = True
+    assert np.array_equal((cls & 1) != 0, solid)
+    assert np.array_equal((cls & 2) != 0, boundary)
+    assert np.array_equal((cls & 4) != 0, new)
+    # link set bit-exact, q within 1e-5
+    g = sim.links()
+    lin_ref = (cl[:, 2] * ny + cl[:, 1]) * nx + cl[:, 0]
+    key_ref = np.stack([L["particle"], lin_ref, L["dir"]], 1)
+    key_gpu = np.stack([g["particle"].astype(np.int64), g["cell"].astype(np.int64), g["dir"].astype(np.int64)], 1)
+    o_ref = np.lexsort(key_ref.T[::-1])
+    o_gpu = np.lexsort(key_gpu.T[::-1])
+    assert np.array_equal(key_ref[o_ref], key_gpu[o_gpu])
+    dq = np.abs(g["q"][o_gpu].astype(np.float64) - L["q"][o_ref])
+    assert dq.max() < 1e-5, "max |dq| %g" % dq.max()
+    # populations at fluid nodes
+    got = sim.get_populations().astype(np.float64)
+    fl = owner < 0
+    rel = np.abs(got[:, fl] - ref[:, fl]) / np.abs(ref[:, fl])
+    assert rel.max() < 1e-5, "max rel population err %g" % rel.max()
+    # force and torque
+    fr = sim.forces()
+    dP = L["dP"]
+    for p in range(len(parts)):
+        m = L["particle"] == p
+        qw = np.full(m.sum(), 0.5) if mode == "ladd" else L["q"][m]
+        xw = L["cell"][m] + qw[:, None] * E[L["dir"][m]]
+        arm = xw - parts[p]["pos"]
+        scaleF = max(np.linalg.norm(F[p]), 1e-3 * np.abs(dP[m]).sum())
+        scaleT = max(np.linalg.norm(T[p]), 1e-3 * np.abs(np.cross(arm, dP[m])).sum())
+        assert np.linalg.norm(fr["F_hydro"][p] - F[p]) <= 1e-4 * scaleF, (fr["F_hydro"][p], F[p])
+        assert np.linalg.norm(fr["T_hydro"][p] - T[p]) <= 1e-4 * scaleT, (fr["T_hydro"][p], T[p])
+    return F, T
+
+
+@pytest.mark.parametrize("mode", ["ibb", "ladd"])
+def test_one_step_moving_particle(mode):
+    B = binding()
+    shape = (40, 36, 44)
+    rng = np.random.default_rng(7)
+    c, k, _ = scenes.blob_4(rng)
+    spec = scenes.ParticleSpec(c, k, 2.5, 1.0, None, None)
+    q0 = scenes.random_unit_quaternion(rng)
+    X = np.array([20.3, 17.6, 22.1])
+    dX = np.array([0.7, 0.35, -0.2])
+    P = _prepared(spec, X, q0, (0.02, -0.01, 0.015), (0.004, -0.003, 0.002))
+    Pp = dict(P, pos=X - dX, quat=scenes.f32(q0 + np.array([0.0, 0.05, -0.03, 0.02])))
+    f0 = _initial_flow(shape, seed=3)
+    sim = _run_one_step(B, shape, [Pp], [P], f0, mode)
+    owner_prev = metaball.flag_nodes(shape, [Pp])
+    owner = metaball.flag_nodes(shape, [P])
+    assert coupling.classify(owner, owner_prev)[1].sum() > 10  # uncovered nodes are exercised
+    _compare_step(sim, shape, [Pp], [P], f0, mode)
+    sim.close()
+
+
+def test_one_step_two_particles_overlapping_boxes():
+    B = binding()
+    shape = (48, 40, 38)
+    rng = np.random.default_rng(11)
+    parts, prev = [], []
+    for j, X in enumerate([np.array([17.2, 20.4, 19.1]), np.array([30.6, 19.3, 18.7])]):
+        c, k, _ = scenes.blob_4(rng)
+        spec = scenes.ParticleSpec(c, k, 2.5, 1.0, None, None)
+        q = scenes.random_unit_quaternion(rng)
+        v = rng.uniform(-0.02, 0.02, 3)
+        w = rng.uniform(-0.005, 0.005, 3)
+        P = _prepared(spec, X, q, v, w)
+        parts.append(P)
+        prev.append(dict(P, pos=X - np.array([0.4, -0.6, 0.5])))
+    f0 = _initial_flow(shape, seed=4)
+    sim = _run_one_step(B, shape, prev, parts, f0, "ibb")
+    _compare_step(sim, shape, prev, parts, f0, "ibb")
+    sim.close()
+
+
+def test_rigid_body_update_after_step():
+    B = binding()
+    shape = (36, 34, 40)
+    rng = np.random.default_rng(12)
+    c, k, _ = scenes.blob_4(rng)
+    spec = scenes.ParticleSpec(c, k, 2.5, 1.0, None, None)
+    P = _prepared(spec, np.array([17.5, 16.2, 20.3]), scenes.random_unit_quaternion(rng),
+                  (0.01, 0.0, -0.02), (0.002, 0.003, -0.001))
+    f0 = _initial_flow(shape, seed=5)
+    g = (0.0, 0.0, -1e-4)
+    sim = B.Simulation(*shape, tau=TAU, gravity=g)
+    sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"], P["omega"],
+                     mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
+    sim.set_populations(f0.astype(np.float32))
+    sim.step(1)
+    st = sim.get_particle_state(0)
+    owner = metaball.flag_nodes(shape, [P])
+    _, F, T = coupling.coupled_lbm_step(f0, owner, owner, [P], TAU)
+    ref = dem.integrate(P, F[0], T[0], g)
+    dv_ref = ref["vel"] - P["vel"]
+    dv = st["vel"] - P["vel"]
+    assert np.linalg.norm(dv - dv_ref) <= 1e-4 * np.linalg.norm(dv_ref) + 1e-12
+    assert np.linalg.norm(st["pos"] - ref["pos"]) <= 1e-4 * np.linalg.norm(dv_ref) + 1e-12
+    dw_ref = ref["omega"] - P["omega"]
+    assert np.linalg.norm(st["omega"] - ref["omega"]) <= 1e-3 * np.linalg.norm(dw_ref) + 1e-10
+    assert np.abs(np.abs(st["quat"] @ ref["quat"]) - 1.0) < 1e-12
+    sim.close()
+
+
+def test_short_trajectory_config1():
+    """64^3 closed box, one 4-ball particle, density 2.5, gravity 1e-5 (the
+    oracle-size settling case): 12 coupled steps, trajectory and forces vs the
+    oracle."""
+    B = binding()
+    sc = scenes.config1()
+    spec = sc.particles[0]
+    P = _prepared(spec, spec.pos, spec.quat, (0, 0, 0), (0, 0, 0))
+    shape = sc.shape
+    nsteps = 12
+    sim = B.Simulation(*shape, tau=sc.tau, gravity=sc.gravity)
+    sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"], P["omega"],
+                     mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
+    f = lbm.rest_state((shape[2], shape[1], shape[0]))
+    state = dict(P)
+    owner_prev = metaball.flag_nodes(shape, [state])
+    for n in range(nsteps):
+        sim.step(1)
+        fr = sim.forces()
+        owner = metaball.flag_nodes(shape, [state])
+        f, F, T = coupling.coupled_lbm_step(f, owner, owner_prev, [state], sc.tau)
+        owner_prev = owner
+        scale = max(np.linalg.norm(F[0]), 1e-9)
+        assert np.linalg.norm(fr["F_hydro"][0] - F[0]) <= 1e-3 * scale + 1e-9, (n, fr["F_hydro"][0], F[0])
+        state = dem.integrate(state, F[0], T[0], sc.gravity)
+        st = sim.get_particle_state(0)
+        assert np.linalg.norm(st["pos"] - state["pos"]) < 1e-7
+        assert np.linalg.norm(st["vel"] - state["vel"]) < 1e-3 * np.linalg.norm(state["vel"]) + 1e-12
+    got = sim.get_populations().astype(np.float64)
+    fl = metaball.flag_nodes(shape, [state]) < 0
+    fl = fl & np.isfinite(f).all(0)
+    rel = np.abs(got[:, fl] - f[:, fl]) / np.abs(f[:, fl])
+    assert rel.max() < 1e-4
+    sim.close()
+
+
+def test_mass_properties_quadrature_matches_oracle():
+    B = binding()
+    rng = np.random.default_rng(13)
+    c, k, _ = scenes.blob_4(rng)
+    X = np.array([20.0, 21.0, 22.0])
+    q = scenes.random_unit_quaternion(rng)
+    sim = B.Simulation(48, 48, 48, tau=TAU)
+    sim.add_particle(c, k, 2.5, 1.0, X, q)
+    sh = sim.get_particle_shape(0)
+    st = sim.get_particle_state(0)
+    mp = metaball.mass_properties(c, k, 2.5)
+    assert abs(sh["volume"] - mp["volume"]) <= 1e-9 * mp["volume"]
+    assert np.allclose(sh["inertia"], mp["inertia"], rtol=1e-8, atol=1e-8 * np.abs(mp["inertia"]).max())
+    assert np.allclose(sh["centers"], c - mp["centroid"], atol=1e-9)
+    R = metaball.quat_to_matrix(q)
+    assert np.allclose(st["pos"], X + R @ mp["centroid"], atol=1e-9)
+    sim.close()
