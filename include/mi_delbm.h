@@ -279,6 +279,42 @@ typedef struct {
 } mi_delbm_stats;
 mi_status mi_delbm_get_stats(mi_delbm *h, mi_delbm_stats *st);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free mass properties (the paper has no counterpart: this is a
+ * library convenience for particular callers).
+ *
+ * mi_delbm_add_particle computes a particle's mass properties with scratch
+ * memory it obtains from the handle's allocator.  Some callers cannot allow
+ * that: code whose device memory is entirely reserved up front by another
+ * allocator's pool (so a cudaMalloc would fail or fragment that pool), and
+ * latency-critical loops that cannot afford the device-wide synchronisation
+ * a cudaFree implies.  This entry point computes the same quantities -- the
+ * same midpoint quadrature of f >= 1, with the same FP32 test and FP64 guard
+ * band -- and allocates nothing: its scratch (an FP32 copy of at most 4096
+ * balls and 1024 rows of 10 moment sums, about 144 KB) is a fixed static
+ * array in device memory that every GPU which loads the library holds until
+ * the process exits.
+ *
+ * balls_dev: device pointer, n_balls x 4 doubles (c_x, c_y, c_z, k) in the
+ *   body frame, k > 0; 1 <= n_balls <= 4096 (MI_EINVAL otherwise: the static
+ *   scratch holds no more).
+ * density > 0; spacing > 0: the quadrature grid spacing (1/4 is what
+ *   mi_delbm_add_particle uses).
+ * out_dev: device pointer to 14 doubles, written as mass, volume,
+ *   centroid[3], inertia[9] (row-major, about the centroid, body axes).
+ * stream: cudaStream_t to run on (NULL = the default stream).  The call is
+ *   asynchronous; synchronise the stream before reading out_dev.
+ * Runs on the current device.  The first call on a device looks up the
+ *   scratch's device address (cudaGetSymbolAddress) once for that device;
+ *   make that first call before any stream capture.
+ * Every call on a device shares the one scratch array, which keeps the last
+ *   call's contents: calls that overlap on the GPU (on different streams, or
+ *   from different host threads) race and give wrong results.  Serialise them.
+ * Errors (message via mi_delbm_last_error(NULL)): MI_EINVAL, MI_ECUDA.
+ */
+mi_status mi_mass_properties_noalloc(const double *balls_dev, int n_balls, double density, double spacing,
+                                     double *out_dev, void *stream);
+
 /* Per-phase GPU timing with CUDA events on the handle's stream.  While
  * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
  * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of

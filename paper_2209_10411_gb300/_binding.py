@@ -106,6 +106,17 @@ _sig("mi_delbm_forces", c_int, _P, _P, _P, _P, _P)
 _sig("mi_delbm_get_node_classes", c_int, _P, _P, _P, c_size_t)
 _sig("mi_delbm_get_links", c_int, _P, c_size_t, _P, _P, _P, _P, ctypes.POINTER(c_size_t))
 _sig("mi_delbm_get_stats", c_int, _P, ctypes.POINTER(Stats))
+_sig("mi_mass_properties_noalloc", c_int, _P, c_int, c_double, c_double, _P, _P)
+
+
+def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):
+    """Allocation-free mass properties: device input n x 4 doubles, device
+    output 14 doubles (mass, volume, centroid[3], inertia[9]); asynchronous
+    on `stream` (a cudaStream_t handle as int, or None)."""
+    st = lib.mi_mass_properties_noalloc(c_void_p(int(balls_dev_ptr)), int(n_balls), float(density), float(spacing),
+                                        c_void_p(int(out_dev_ptr)), c_void_p(int(stream)) if stream else None)
+    if st != MI_OK:
+        raise MiDelbmError(st, lib.mi_delbm_last_error(None).decode())
 
 if lib.mi_delbm_abi_version() != 1:
     raise ImportError("libmi_delbm ABI version mismatch")

@@ -13,6 +13,15 @@ using namespace mi;
 
 namespace {
 thread_local std::string g_create_error;
+}  // namespace
+
+namespace mi {
+// Message of the last failed handle-less call on this thread (returned by
+// mi_delbm_last_error(NULL)).
+void set_thread_error(const char* msg) { g_create_error = msg; }
+}  // namespace mi
+
+namespace {
 
 // Kernel-launch helper: runs `fn` (which returns a cudaError_t) as one launch
 // of `phase`, bracketed by timing events when timing is enabled.
