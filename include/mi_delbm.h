@@ -255,6 +255,23 @@ mi_status mi_delbm_get_particle_shape(mi_delbm *h, int id, double *centers, doub
  * Synchronises; reports MI_ECAPACITY if a list overflowed during the step. */
 mi_status mi_delbm_forces(mi_delbm *h, double *F_hydro, double *T_hydro, double *F_contact, double *T_contact);
 
+/* Contact candidates of the last DEM substep (Sec. 2.3.1): every broad-phase
+ * pair i < j with |X_i - X_j| <= R_b,i + R_b,j + 1 and every particle-wall
+ * item (j = -1 - face, faces x-,x+,y-,y+,z-,z+ at -1/2 and n - 1/2 of the
+ * non-periodic axes) with its contact point xcp, unit normal n (pointing from
+ * j to i, i.e. into particle i's side; the wall normal for walls), overlap
+ * delta (> 0 means in contact and a force was applied), Newton iterations and
+ * status (0 converged, 1 not converged, 2 singular Hessian, 3 closest point
+ * inside a core, 4 out of range: no force in cases 1-4).  Order is
+ * unspecified.  *n_out = number of candidates; MI_ECAPACITY (nothing written)
+ * if it exceeds cap.  Synchronises. */
+typedef struct {
+  int i, j;
+  double xcp[3], n[3], delta;
+  int iters, status;
+} mi_contact;
+mi_status mi_delbm_contacts(mi_delbm *h, mi_contact *out, int cap, int *n_out);
+
 /* Node classes (bit 0 solid, bit 1 boundary, bit 2 newly uncovered) and
  * owners (particle index of solid nodes, 0xFFFFFFFF for fluid) of the last
  * flag phase, count = nx*ny*nz entries each, [z][y][x]; either may be NULL.

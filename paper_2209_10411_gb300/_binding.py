@@ -68,6 +68,11 @@ class Stats(ctypes.Structure):
                 ("contacts", ctypes.c_longlong), ("status", ctypes.c_uint)]
 
 
+class Contact(ctypes.Structure):
+    _fields_ = [("i", c_int), ("j", c_int), ("xcp", c_double * 3), ("n", c_double * 3), ("delta", c_double),
+                ("iters", c_int), ("status", c_int)]
+
+
 def _sig(name, restype, *argtypes):
     fn = getattr(lib, name)
     fn.restype = restype
@@ -106,6 +111,7 @@ _sig("mi_delbm_forces", c_int, _P, _P, _P, _P, _P)
 _sig("mi_delbm_get_node_classes", c_int, _P, _P, _P, c_size_t)
 _sig("mi_delbm_get_links", c_int, _P, c_size_t, _P, _P, _P, _P, ctypes.POINTER(c_size_t))
 _sig("mi_delbm_get_stats", c_int, _P, ctypes.POINTER(Stats))
+_sig("mi_delbm_contacts", c_int, _P, ctypes.POINTER(Contact), c_int, ctypes.POINTER(c_int))
 _sig("mi_mass_properties_noalloc", c_int, _P, c_int, c_double, c_double, _P, _P)
 
 
@@ -354,6 +360,17 @@ class Simulation:
         q = np.empty(m, dtype=np.float32)
         self._check(lib.mi_delbm_get_links(self.h, m, _ptr(cell), _ptr(d), _ptr(p), _ptr(q), ctypes.byref(n)))
         return {"cell": cell, "dir": d, "particle": p, "q": q}
+
+    def contacts(self):
+        """Candidates of the last DEM substep as a list of dicts."""
+        n = c_int(0)
+        st = lib.mi_delbm_contacts(self.h, None, 0, ctypes.byref(n))
+        if st not in (MI_OK, MI_ECAPACITY):
+            self._check(st)
+        arr = (Contact * max(1, n.value))()
+        self._check(lib.mi_delbm_contacts(self.h, arr, n.value, ctypes.byref(n)))
+        return [{"i": c.i, "j": c.j, "x_cp": np.array(c.xcp[:]), "n": np.array(c.n[:]), "delta": c.delta,
+                 "iters": c.iters, "status": c.status} for c in arr[:n.value]]
 
     def stats(self):
         st = Stats()

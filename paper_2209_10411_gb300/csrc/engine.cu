@@ -207,20 +207,84 @@ mi_status mi_delbm::phase_boundary() {
   return launch_phase(this, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
 }
 
-mi_status mi_delbm::phase_integrate() {
+mi_status mi_delbm::phase_integrate(bool with_contacts) {
   if (n_particles == 0) return MI_OK;
   IntegrateLaunch L;
   L.P = dP;
   L.np = n_particles;
   L.facc = facc;
-  L.fc = fc;
+  L.fc = with_contacts ? fc : nullptr;
   for (int a = 0; a < 3; ++a) L.gravity[a] = cfg.gravity[a];
   L.rho0 = cfg.rho0;
   L.dt = 1.0 / cfg.dem_substeps;
-  mi_status s = MI_OK;
-  for (int k = 0; k < cfg.dem_substeps && s == MI_OK; ++k)
-    s = launch_phase(this, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
-  return s;
+  return launch_phase(this, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
+}
+
+mi_status mi_delbm::ensure_contact_buffers() {
+  if (contacts_ready) return MI_OK;
+  const long long ncap = cfg.max_particles;
+  if (ncap > 16384) return fail(MI_ENOTSUP, "contacts: max_particles above 16384 is not supported (pair history size)");
+  const long long tri = ncap * (ncap - 1) / 2;
+  long long items = std::min<long long>(tri, 64 * ncap) + 6 * ncap;
+  cap_items = (unsigned)std::max<long long>(items, 64);
+  item_i = (int*)dalloc(sizeof(int) * cap_items);
+  item_j = (int*)dalloc(sizeof(int) * cap_items);
+  recs = (ContactRec*)dalloc(sizeof(ContactRec) * cap_items);
+  hist_pair = (HistEntry*)dalloc(sizeof(HistEntry) * (size_t)std::max<long long>(tri, 1));
+  hist_wall = (HistEntry*)dalloc(sizeof(HistEntry) * (size_t)(6 * ncap));
+  work = (unsigned*)dalloc(sizeof(unsigned));
+  substep = (long long*)dalloc(sizeof(long long));
+  if (!item_i || !item_j || !recs || !hist_pair || !hist_wall || !work || !substep)
+    return fail(MI_ENOMEM, "contacts: device allocation failed");
+  cudaError_t e = cudaMemsetAsync(hist_pair, 0, sizeof(HistEntry) * (size_t)std::max<long long>(tri, 1), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(hist_wall, 0, sizeof(HistEntry) * (size_t)(6 * ncap), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(substep, 0, sizeof(long long), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "contacts: initialisation");
+  contacts_ready = true;
+  return MI_OK;
+}
+
+static ContactLaunch contact_launch(const mi_delbm* h) {
+  ContactLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.P = h->dP;
+  L.np = h->n_particles;
+  L.ncap = h->cfg.max_particles;
+  L.balls = h->dballs;
+  L.ctr = h->dctr;
+  L.work = h->work;
+  L.item_i = h->item_i;
+  L.item_j = h->item_j;
+  L.cap_items = h->cap_items;
+  L.recs = h->recs;
+  L.hist_pair = h->hist_pair;
+  L.hist_wall = h->hist_wall;
+  L.fcacc = h->fc;
+  L.substep = h->substep;
+  L.cp.kn = h->cfg.kn;
+  L.cp.kt = h->cfg.kt;
+  L.cp.eta_n = h->cfg.eta_n;
+  L.cp.eta_t = h->cfg.eta_t;
+  L.cp.mu_s = h->cfg.mu_s;
+  L.cp.dt = 1.0 / h->cfg.dem_substeps;
+  L.cp.margin = 1.0;
+  for (int a = 0; a < 3; ++a) L.cp.periodic[a] = h->cfg.periodic[a] ? 1 : 0;
+  L.cp.n[0] = h->cfg.nx;
+  L.cp.n[1] = h->cfg.ny;
+  L.cp.n[2] = h->cfg.nz;
+  L.grid = h->sm_count * 4;
+  return L;
+}
+
+mi_status mi_delbm::phase_contact() {
+  if (n_particles == 0) return MI_OK;
+  mi_status s = ensure_contact_buffers();
+  if (s != MI_OK) return s;
+  ContactLaunch L = contact_launch(this);
+  if ((s = launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_dem_prologue(L, stream); })) != MI_OK) return s;
+  if ((s = launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_broad_phase(L, stream); })) != MI_OK) return s;
+  return launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_contacts(L, stream); });
 }
 
 mi_status mi_delbm::phase_bulk() {
@@ -250,7 +314,12 @@ mi_status mi_delbm::run_phases(unsigned phases) {
   if ((phases & MI_PHASE_BULK) && (s = phase_bulk()) != MI_OK) return s;
   if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
-  if ((phases & MI_PHASE_INTEGRATE) && (s = phase_integrate()) != MI_OK) return s;
+  if (phases & (MI_PHASE_CONTACT | MI_PHASE_INTEGRATE)) {
+    for (int k = 0; k < cfg.dem_substeps; ++k) {
+      if ((phases & MI_PHASE_CONTACT) && (s = phase_contact()) != MI_OK) return s;
+      if ((phases & MI_PHASE_INTEGRATE) && (s = phase_integrate((phases & MI_PHASE_CONTACT) != 0)) != MI_OK) return s;
+    }
+  }
   return MI_OK;
 }
 
@@ -292,7 +361,7 @@ mi_status mi_delbm::ensure_particle_buffers() {
   stamp = (uint32_t*)dalloc(ncell * 4);
   dctr = (DevCounters*)dalloc(sizeof(DevCounters));
   facc = (long long*)dalloc(sizeof(long long) * 6 * np);
-  fc = (double*)dalloc(sizeof(double) * 6 * np);
+  fc = (long long*)dalloc(sizeof(long long) * 6 * np);
   dP = (DevParticle*)dalloc(sizeof(DevParticle) * np);
   dballs = (float4*)dalloc(sizeof(float4) * nb);
   dballs_d = (double*)dalloc(sizeof(double) * 4 * nb);
@@ -303,7 +372,7 @@ mi_status mi_delbm::ensure_particle_buffers() {
   if (e == cudaSuccess) e = cudaMemsetAsync(stamp, 0, ncell * 4, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(dctr, 0, sizeof(DevCounters), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(facc, 0, sizeof(long long) * 6 * np, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(fc, 0, sizeof(double) * 6 * np, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fc, 0, sizeof(long long) * 6 * np, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "particle buffers: initialisation");
   particles_ready = true;
@@ -883,17 +952,16 @@ mi_status mi_delbm_forces(mi_delbm* h, double* F_hydro, double* T_hydro, double*
   if (st != MI_OK) return st;
   const int np = h->n_particles;
   if (np == 0) return MI_OK;
-  std::vector<long long> fa(6 * (size_t)np);
-  std::vector<double> fcv(6 * (size_t)np);
+  std::vector<long long> fa(6 * (size_t)np), fcl(6 * (size_t)np);
   cudaError_t e = cudaMemcpy(fa.data(), h->facc, sizeof(long long) * 6 * np, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(fcv.data(), h->fc, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(fcl.data(), h->fc, sizeof(long long) * 6 * np, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_forces");
   for (int p = 0; p < np; ++p)
     for (int a = 0; a < 3; ++a) {
       if (F_hydro) F_hydro[3 * p + a] = (double)fa[6 * p + a] * FIX_INV;
       if (T_hydro) T_hydro[3 * p + a] = (double)fa[6 * p + 3 + a] * FIX_INV;
-      if (F_contact) F_contact[3 * p + a] = fcv[6 * p + a];
-      if (T_contact) T_contact[3 * p + a] = fcv[6 * p + 3 + a];
+      if (F_contact) F_contact[3 * p + a] = (double)fcl[6 * p + a] * FIX_INV;
+      if (T_contact) T_contact[3 * p + a] = (double)fcl[6 * p + 3 + a] * FIX_INV;
     }
   return h->check_status(false);
 }
@@ -944,6 +1012,27 @@ mi_status mi_delbm_get_links(mi_delbm* h, size_t cap, int32_t* cell, int8_t* dir
     if (q) q[l] = lq[l];
   }
   return MI_OK;
+}
+
+static_assert(sizeof(mi_contact) == sizeof(ContactRec), "mi_contact must mirror the device record");
+
+mi_status mi_delbm_contacts(mi_delbm* h, mi_contact* out, int cap, int* n_out) {
+  if (!h || !n_out) return MI_EINVAL;
+  mi_status st = h->sync("mi_delbm_contacts");
+  if (st != MI_OK) return st;
+  *n_out = 0;
+  if (!h->contacts_ready) return MI_OK;
+  DevCounters c;
+  cudaError_t e = cudaMemcpy(&c, h->dctr, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_contacts");
+  const unsigned n = std::min(c.n_pairs, h->cap_items);
+  *n_out = (int)n;
+  if ((int)n > cap || (n > 0 && !out)) return h->fail(MI_ECAPACITY, "mi_delbm_contacts: cap below the candidate count");
+  if (n) {
+    e = cudaMemcpy(out, h->recs, sizeof(ContactRec) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_contacts");
+  }
+  return h->check_status(false);
 }
 
 mi_status mi_delbm_get_stats(mi_delbm* h, mi_delbm_stats* out) {

@@ -47,8 +47,18 @@ struct mi_delbm {
   int max_balls_pp = 0;              // largest ball count of one particle
   uint32_t* stamp = nullptr;
   mi::DevCounters* dctr = nullptr;
-  long long* facc = nullptr;         // np x 6 fixed point
-  double* fc = nullptr;              // np x 6 contact force/torque
+  long long* facc = nullptr;         // np x 6 fixed point (hydrodynamic)
+  long long* fc = nullptr;           // np x 6 fixed point (contact)
+  // contacts (allocated at the first contact phase)
+  bool contacts_ready = false;
+  int* item_i = nullptr;
+  int* item_j = nullptr;
+  unsigned cap_items = 0;
+  mi::ContactRec* recs = nullptr;
+  mi::HistEntry* hist_pair = nullptr;
+  mi::HistEntry* hist_wall = nullptr;
+  unsigned* work = nullptr;
+  long long* substep = nullptr;
   // lists
   uint32_t *bc_cell = nullptr, *bc_mask = nullptr, *bc_loff = nullptr;
   uint32_t *link_bc = nullptr, *link_p = nullptr;
@@ -85,7 +95,9 @@ struct mi_delbm {
   mi_status phase_bulk();
   mi_status phase_boundary();
   mi_status phase_swap();
-  mi_status phase_integrate();
+  mi_status phase_integrate(bool with_contacts);
+  mi_status phase_contact();
+  mi_status ensure_contact_buffers();
 
   mi_status ensure_particle_buffers();
   mi_status ensure_list_capacity(unsigned bc, unsigned links, unsigned nnew);

@@ -1,0 +1,451 @@
+// DEM contact kernels (Sec. 2.3.1): broad phase, Newton-Raphson closest points
+// between sphero-metaball particles (Eqs. CM_coreF, grad, cp, contactprop) and
+// between a particle and an axis-aligned wall (Eqs. metawallcp, contactprop2),
+// linear spring-dashpot forces with a Coulomb-limited tangential spring.
+//
+// The core of a particle is the iso-surface g = s f = 1, s = ((r_e - R_s)/r_e)^2,
+// r_e = sqrt(sum k).  One warp solves one candidate: the balls of each particle
+// are spread over the lanes, the 10 sums of g, grad g and the Hessian are
+// shuffle-reduced (and broadcast from lane 0, so every lane takes identical
+// branches), and the 3x3 (4x4 for walls) Newton system is solved redundantly
+// in every lane.  Work is taken from an atomic counter (no inter-block waits);
+// a warp leaves when the queue is empty.  Geometry is FP32 in a local frame
+// centred between the particles; forces are FP64, summed per particle in
+// 2^-40 fixed point (order-free).
+#include "mi_internal.cuh"
+
+namespace mi {
+
+namespace {
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_IT = 50;
+constexpr float C_TOL = 1e-6f;
+constexpr float NEWTON_TOL = 1e-5f;  // |dx| <= NEWTON_TOL * R_b,max
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return __shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ void rot(const double q[4], double R[9]) {
+  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// A particle seen from a local origin O: body point x_b = R^T y + o for local y.
+struct Frame {
+  float R[9];  // body -> world
+  float o[3];  // R^T (O - X)
+  float t[3];  // X - O (world offset of the particle origin)
+  float s;     // core scale
+  int off, n;
+};
+
+__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double O[3]) {
+  Frame F;
+  double R[9];
+  rot(P.quat, R);
+  const double d[3] = {O[0] - P.pos[0], O[1] - P.pos[1], O[2] - P.pos[2]};
+  for (int a = 0; a < 3; ++a) {
+    F.o[a] = (float)(R[a] * d[0] + R[3 + a] * d[1] + R[6 + a] * d[2]);
+    F.t[a] = (float)(-d[a]);
+  }
+  for (int k = 0; k < 9; ++k) F.R[k] = (float)R[k];
+  const double r = (P.re - P.skin) / P.re;
+  F.s = (float)(r * r);
+  F.off = P.ball_off;
+  F.n = P.n_balls;
+  return F;
+}
+
+struct GEval {
+  float g, gr[3], H[6];  // core value, world gradient, world Hessian (xx xy xz yy yz zz)
+};
+
+// Warp-cooperative g, grad g, Hessian of g at local point y (every lane passes the same y).
+__device__ __forceinline__ GEval eval(const Frame& F, const float4* __restrict__ balls, const float y[3], int lane) {
+  float xb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xb[a] = F.R[a] * y[0] + F.R[3 + a] * y[1] + F.R[6 + a] * y[2] + F.o[a];
+  float g = 0.f, gb0 = 0.f, gb1 = 0.f, gb2 = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f, h5 = 0.f;
+  for (int b = lane; b < F.n; b += 32) {
+    const float4 c = __ldg(balls + F.off + b);
+    const float d0 = xb[0] - c.x, d1 = xb[1] - c.y, d2 = xb[2] - c.z;
+    const float ir2 = 1.0f / (d0 * d0 + d1 * d1 + d2 * d2);
+    const float t = c.w * ir2;            // k / r^2
+    const float t2 = -2.0f * t * ir2;     // -2 k / r^4
+    const float t3 = 8.0f * t * ir2 * ir2;  // 8 k / r^6
+    g += t;
+    gb0 += t2 * d0;
+    gb1 += t2 * d1;
+    gb2 += t2 * d2;
+    h0 += t3 * d0 * d0 + t2;
+    h1 += t3 * d0 * d1;
+    h2 += t3 * d0 * d2;
+    h3 += t3 * d1 * d1 + t2;
+    h4 += t3 * d1 * d2;
+    h5 += t3 * d2 * d2 + t2;
+  }
+  g = wsum(g);
+  gb0 = wsum(gb0); gb1 = wsum(gb1); gb2 = wsum(gb2);
+  h0 = wsum(h0); h1 = wsum(h1); h2 = wsum(h2); h3 = wsum(h3); h4 = wsum(h4); h5 = wsum(h5);
+  GEval e;
+  const float s = F.s;
+  e.g = s * g;
+  const float* R = F.R;
+  for (int a = 0; a < 3; ++a) e.gr[a] = s * (R[3 * a] * gb0 + R[3 * a + 1] * gb1 + R[3 * a + 2] * gb2);
+  // H_w = R H_b R^T
+  const float Hb[3][3] = {{h0, h1, h2}, {h1, h3, h4}, {h2, h4, h5}};
+  float M[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M[a][b] = R[3 * a] * Hb[0][b] + R[3 * a + 1] * Hb[1][b] + R[3 * a + 2] * Hb[2][b];
+  float Hw[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Hw[a][b] = s * (M[a][0] * R[3 * b] + M[a][1] * R[3 * b + 1] + M[a][2] * R[3 * b + 2]);
+  e.H[0] = Hw[0][0]; e.H[1] = Hw[0][1]; e.H[2] = Hw[0][2];
+  e.H[3] = Hw[1][1]; e.H[4] = Hw[1][2]; e.H[5] = Hw[2][2];
+  return e;
+}
+
+// Gaussian elimination with partial pivoting (n <= 4); false if singular.
+template <int N>
+__device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    int p = i;
+    float best = fabsf(A[i][i]);
+#pragma unroll
+    for (int r = i + 1; r < N; ++r)
+      if (fabsf(A[r][i]) > best) { best = fabsf(A[r][i]); p = r; }
+    if (!(best > 0.f)) return false;
+    if (p != i) {
+#pragma unroll
+      for (int c = 0; c < N; ++c) { const float t = A[i][c]; A[i][c] = A[p][c]; A[p][c] = t; }
+      const float t = b[i]; b[i] = b[p]; b[p] = t;
+    }
+#pragma unroll
+    for (int r = i + 1; r < N; ++r) {
+      const float m = A[r][i] / A[i][i];
+#pragma unroll
+      for (int c = i; c < N; ++c) A[r][c] -= m * A[i][c];
+      b[r] -= m * b[i];
+    }
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    float acc = b[i];
+#pragma unroll
+    for (int c = i + 1; c < N; ++c) acc -= A[i][c] * x[c];
+    x[i] = acc / A[i][i];
+  }
+  return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && (N < 4 || isfinite(x[N - 1]));
+}
+
+__device__ __forceinline__ void add_fixed6(long long* acc, int p, const double v[6]) {
+  for (int k = 0; k < 6; ++k)
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc + 6 * p + k), (unsigned long long)__double2ll_rn(v[k] * FIX_SCALE));
+}
+
+// Spring-dashpot force on particle i (the partner j is a particle, or a wall at rest when Pj == nullptr).
+__device__ void spring_dashpot(const ContactParams& cp, const DevParticle& Pi, const DevParticle* Pj, const double xcp[3],
+                               const double n[3], double delta, HistEntry* h, long long substep, double f[3]) {
+  double v0[3], v1[3] = {0, 0, 0};
+  const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
+  v0[0] = Pi.vel[0] + Pi.omega[1] * ri[2] - Pi.omega[2] * ri[1];
+  v0[1] = Pi.vel[1] + Pi.omega[2] * ri[0] - Pi.omega[0] * ri[2];
+  v0[2] = Pi.vel[2] + Pi.omega[0] * ri[1] - Pi.omega[1] * ri[0];
+  if (Pj) {
+    const double rj[3] = {xcp[0] - Pj->pos[0], xcp[1] - Pj->pos[1], xcp[2] - Pj->pos[2]};
+    v1[0] = Pj->vel[0] + Pj->omega[1] * rj[2] - Pj->omega[2] * rj[1];
+    v1[1] = Pj->vel[1] + Pj->omega[2] * rj[0] - Pj->omega[0] * rj[2];
+    v1[2] = Pj->vel[2] + Pj->omega[0] * rj[1] - Pj->omega[1] * rj[0];
+  }
+  double vr[3], vt[3];
+  for (int a = 0; a < 3; ++a) vr[a] = v1[a] - v0[a];
+  const double vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
+  for (int a = 0; a < 3; ++a) vt[a] = vr[a] - vn * n[a];
+  const double Fn = fmax(0.0, cp.kn * delta + cp.eta_n * vn);
+  double xi[3] = {0, 0, 0};
+  if (h->stamp == substep - 1)
+    for (int a = 0; a < 3; ++a) xi[a] = h->xi[a];
+  const double xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
+  for (int a = 0; a < 3; ++a) xi[a] = xi[a] - xn * n[a] + vt[a] * cp.dt;
+  double Ft[3];
+  for (int a = 0; a < 3; ++a) Ft[a] = cp.kt * xi[a] + cp.eta_t * vt[a];
+  const double nt = sqrt(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+  if (nt > cp.mu_s * Fn) {
+    if (nt > 0.0)
+      for (int a = 0; a < 3; ++a) Ft[a] *= cp.mu_s * Fn / nt;
+    for (int a = 0; a < 3; ++a) xi[a] = cp.kt > 0.0 ? (Ft[a] - cp.eta_t * vt[a]) / cp.kt : 0.0;
+  }
+  for (int a = 0; a < 3; ++a) {
+    f[a] = Fn * n[a] + Ft[a];
+    h->xi[a] = xi[a];
+  }
+  h->stamp = substep;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+__global__ void k_dem_prologue(ContactLaunch L) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *L.substep += 1;
+    L.ctr->n_pairs = 0;
+    L.ctr->n_contacts = 0;
+    *L.work = 0;
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * L.np; k += gridDim.x * blockDim.x) L.fcacc[k] = 0;
+}
+
+cudaError_t launch_dem_prologue(const ContactLaunch& L, cudaStream_t s) {
+  k_dem_prologue<<<1, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// Candidates: pairs i < j with |X_i - X_j| <= R_b,i + R_b,j + margin, and
+// particle-wall items with n_w.(X_i - p_w) <= R_b,i + margin.
+__global__ void k_broad_phase(ContactLaunch L) {
+  const long long np = L.np;
+  const long long total = np * np + 6 * np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    if (t < np * np) {
+      i = (int)(t / np);
+      j = (int)(t % np);
+      if (i >= j) continue;
+      const DevParticle& A = L.P[i];
+      const DevParticle& B = L.P[j];
+      const double d0 = A.pos[0] - B.pos[0], d1 = A.pos[1] - B.pos[1], d2 = A.pos[2] - B.pos[2];
+      if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) <= A.Rb + B.Rb + L.cp.margin)) continue;
+    } else {
+      const long long t2 = t - np * np;
+      i = (int)(t2 / 6);
+      const int face = (int)(t2 % 6), axis = face / 2;
+      if (L.cp.periodic[axis]) continue;
+      const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
+      const double nw = (face & 1) ? -1.0 : 1.0;
+      if (!(nw * (L.P[i].pos[axis] - pw) <= L.P[i].Rb + L.cp.margin)) continue;
+      j = -1 - face;
+    }
+    const unsigned k = atomicAdd(&L.ctr->n_pairs, 1u);
+    if (k < L.cap_items) {
+      L.item_i[k] = i;
+      L.item_j[k] = j;
+    } else {
+      atomicOr(&L.ctr->status, STATUS_PAIR_OVERFLOW);
+    }
+  }
+}
+
+cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
+  const long long total = (long long)L.np * L.np + 6LL * L.np;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  k_broad_phase<<<(unsigned)blocks, 256, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// Persistent warp-per-candidate Newton solver and forces.
+__global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
+  const int lane = threadIdx.x & 31;
+  const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
+  const long long substep = *L.substep;
+  const float4* balls = L.balls;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(L.work, 1u);
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= n_items) break;
+    const int i = L.item_i[it], j = L.item_j[it];
+    const DevParticle& Pi = L.P[i];
+    double O[3];
+    int status = 1, iters = 0;
+    double xcp[3], nrm[3], delta;
+    if (j >= 0) {
+      // ---------------- particle pair ----------------
+      const DevParticle& Pj = L.P[j];
+      for (int a = 0; a < 3; ++a) O[a] = 0.5 * (Pi.pos[a] + Pj.pos[a]);
+      const Frame F0 = make_frame(Pi, O), F1 = make_frame(Pj, O);
+      const float Rb = (float)fmax(Pi.Rb, Pj.Rb);
+      // guess: closest pair of control-point spheres, midpoint of their surface points
+      float best = 3.4e38f;
+      int ba = 0, bb = 0;
+      for (int a = lane; a < F0.n; a += 32) {
+        const float4 ca = __ldg(balls + F0.off + a);
+        float pa[3];
+        for (int c = 0; c < 3; ++c) pa[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c];
+        const float ra = sqrtf(ca.w);
+        for (int b = 0; b < F1.n; ++b) {
+          const float4 cb = __ldg(balls + F1.off + b);
+          float pb[3];
+          for (int c = 0; c < 3; ++c) pb[c] = F1.R[3 * c] * cb.x + F1.R[3 * c + 1] * cb.y + F1.R[3 * c + 2] * cb.z + F1.t[c];
+          const float gap = sqrtf((pa[0] - pb[0]) * (pa[0] - pb[0]) + (pa[1] - pb[1]) * (pa[1] - pb[1]) +
+                                  (pa[2] - pb[2]) * (pa[2] - pb[2])) - ra - sqrtf(cb.w);
+          if (gap < best) { best = gap; ba = a; bb = b; }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float g2 = __shfl_xor_sync(FULL, best, o);
+        const int a2 = __shfl_xor_sync(FULL, ba, o), b2 = __shfl_xor_sync(FULL, bb, o);
+        if (g2 < best || (g2 == best && (a2 < ba || (a2 == ba && b2 < bb)))) { best = g2; ba = a2; bb = b2; }
+      }
+      ba = __shfl_sync(FULL, ba, 0);
+      bb = __shfl_sync(FULL, bb, 0);
+      float y[3];
+      {
+        const float4 ca = __ldg(balls + F0.off + ba), cb = __ldg(balls + F1.off + bb);
+        float pa[3], pb[3], u[3];
+        for (int c = 0; c < 3; ++c) {
+          pa[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c];
+          pb[c] = F1.R[3 * c] * cb.x + F1.R[3 * c + 1] * cb.y + F1.R[3 * c + 2] * cb.z + F1.t[c];
+          u[c] = pb[c] - pa[c];
+        }
+        const float D = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (D > 0.f) for (int c = 0; c < 3; ++c) u[c] /= D;
+        else { u[0] = 1.f; u[1] = u[2] = 0.f; }
+        const float ra = sqrtf(ca.w), rb = sqrtf(cb.w);
+        for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
+      }
+      for (iters = 1; iters <= MAX_IT; ++iters) {
+        const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
+        float A[3][3] = {{e0.H[0] + e1.H[0], e0.H[1] + e1.H[1], e0.H[2] + e1.H[2]},
+                         {e0.H[1] + e1.H[1], e0.H[3] + e1.H[3], e0.H[4] + e1.H[4]},
+                         {e0.H[2] + e1.H[2], e0.H[4] + e1.H[4], e0.H[5] + e1.H[5]}};
+        float b[3] = {e0.gr[0] + e1.gr[0], e0.gr[1] + e1.gr[1], e0.gr[2] + e1.gr[2]};
+        float dx[3];
+        if (!solve<3>(A, b, dx)) { status = 2; break; }
+        for (int c = 0; c < 3; ++c) y[c] -= dx[c];
+        if (sqrtf(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]) <= NEWTON_TOL * Rb) { status = 0; break; }
+      }
+      if (iters > MAX_IT) iters = MAX_IT;
+      const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
+      if (status == 0) {
+        if (e0.g >= 1.f || e1.g >= 1.f) status = 3;
+        else if (e0.g < C_TOL || e1.g < C_TOL) status = 4;
+      }
+      const float q0 = (1.f - e0.g) / (e0.gr[0] * e0.gr[0] + e0.gr[1] * e0.gr[1] + e0.gr[2] * e0.gr[2]);
+      const float q1 = (1.f - e1.g) / (e1.gr[0] * e1.gr[0] + e1.gr[1] * e1.gr[1] + e1.gr[2] * e1.gr[2]);
+      float xc0[3], xc1[3], d[3];
+      for (int c = 0; c < 3; ++c) {
+        xc0[c] = y[c] + q0 * e0.gr[c];
+        xc1[c] = y[c] + q1 * e1.gr[c];
+        d[c] = xc0[c] - xc1[c];
+      }
+      const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      delta = Pi.skin + Pj.skin - (double)dist;
+      for (int c = 0; c < 3; ++c) nrm[c] = dist > 0.f ? (double)(d[c] / dist) : 0.0;
+      for (int c = 0; c < 3; ++c) xcp[c] = O[c] + (double)xc0[c] - (Pi.skin - 0.5 * delta) * nrm[c];
+      if (lane == 0 && status == 0 && delta > 0.0) {
+        const int lo = min(i, j), hi = max(i, j);
+        HistEntry* h = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
+        double f[3];
+        spring_dashpot(L.cp, Pi, &Pj, xcp, nrm, delta, h, substep, f);
+        double vi[6], vj[6];
+        const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
+        const double rj[3] = {xcp[0] - Pj.pos[0], xcp[1] - Pj.pos[1], xcp[2] - Pj.pos[2]};
+        for (int a = 0; a < 3; ++a) {
+          vi[a] = f[a];
+          vj[a] = -f[a];
+        }
+        vi[3] = ri[1] * f[2] - ri[2] * f[1];
+        vi[4] = ri[2] * f[0] - ri[0] * f[2];
+        vi[5] = ri[0] * f[1] - ri[1] * f[0];
+        vj[3] = -(rj[1] * f[2] - rj[2] * f[1]);
+        vj[4] = -(rj[2] * f[0] - rj[0] * f[2]);
+        vj[5] = -(rj[0] * f[1] - rj[1] * f[0]);
+        add_fixed6(L.fcacc, i, vi);
+        add_fixed6(L.fcacc, j, vj);
+        atomicAdd(&L.ctr->n_contacts, 1u);
+      }
+    } else {
+      // ---------------- particle - wall ----------------
+      const int face = -1 - j, axis = face / 2;
+      for (int a = 0; a < 3; ++a) O[a] = Pi.pos[a];
+      const Frame F0 = make_frame(Pi, O);
+      float nw[3] = {0.f, 0.f, 0.f};
+      nw[axis] = (face & 1) ? -1.f : 1.f;
+      const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
+      const float distO = (float)((double)nw[axis] * (O[axis] - pw));
+      const float Rb = (float)Pi.Rb;
+      // guess: the core sphere reaching deepest towards the wall
+      float best = 3.4e38f;
+      int ba = 0;
+      for (int a = lane; a < F0.n; a += 32) {
+        const float4 ca = __ldg(balls + F0.off + a);
+        const float pn = (F0.R[3 * axis] * ca.x + F0.R[3 * axis + 1] * ca.y + F0.R[3 * axis + 2] * ca.z + F0.t[axis]) * nw[axis];
+        const float v = pn - sqrtf(F0.s * ca.w);
+        if (v < best) { best = v; ba = a; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float g2 = __shfl_xor_sync(FULL, best, o);
+        const int a2 = __shfl_xor_sync(FULL, ba, o);
+        if (g2 < best || (g2 == best && a2 < ba)) { best = g2; ba = a2; }
+      }
+      ba = __shfl_sync(FULL, ba, 0);
+      float y[3];
+      {
+        const float4 ca = __ldg(balls + F0.off + ba);
+        const float rs = sqrtf(F0.s * ca.w);
+        for (int c = 0; c < 3; ++c)
+          y[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c] - rs * nw[c];
+      }
+      GEval e = eval(F0, balls, y, lane);
+      float lam = sqrtf(e.gr[0] * e.gr[0] + e.gr[1] * e.gr[1] + e.gr[2] * e.gr[2]);
+      for (iters = 1; iters <= MAX_IT; ++iters) {
+        e = eval(F0, balls, y, lane);
+        float A[4][4] = {{e.H[0], e.H[1], e.H[2], -nw[0]},
+                         {e.H[1], e.H[3], e.H[4], -nw[1]},
+                         {e.H[2], e.H[4], e.H[5], -nw[2]},
+                         {e.gr[0], e.gr[1], e.gr[2], 0.f}};
+        float b[4] = {e.gr[0] - lam * nw[0], e.gr[1] - lam * nw[1], e.gr[2] - lam * nw[2], e.g - 1.f};
+        float dz[4];
+        if (!solve<4>(A, b, dz)) { status = 2; break; }
+        for (int c = 0; c < 3; ++c) y[c] -= dz[c];
+        lam -= dz[3];
+        if (sqrtf(dz[0] * dz[0] + dz[1] * dz[1] + dz[2] * dz[2]) <= NEWTON_TOL * Rb) { status = 0; break; }
+      }
+      if (iters > MAX_IT) iters = MAX_IT;
+      const float dist = nw[0] * y[0] + nw[1] * y[1] + nw[2] * y[2] + distO;
+      delta = Pi.skin - (double)dist;
+      for (int c = 0; c < 3; ++c) {
+        nrm[c] = nw[c];
+        xcp[c] = O[c] + (double)(y[c] - dist * nw[c]) + 0.5 * delta * nrm[c];
+      }
+      if (lane == 0 && status == 0 && delta > 0.0) {
+        HistEntry* h = L.hist_wall + ((long long)i * 6 + face);
+        double f[3];
+        spring_dashpot(L.cp, Pi, nullptr, xcp, nrm, delta, h, substep, f);
+        const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
+        double vi[6] = {f[0], f[1], f[2], ri[1] * f[2] - ri[2] * f[1], ri[2] * f[0] - ri[0] * f[2],
+                        ri[0] * f[1] - ri[1] * f[0]};
+        add_fixed6(L.fcacc, i, vi);
+        atomicAdd(&L.ctr->n_contacts, 1u);
+      }
+    }
+    if (lane == 0) {
+      ContactRec& r = L.recs[it];
+      r.i = i;
+      r.j = j;
+      for (int c = 0; c < 3; ++c) {
+        r.xcp[c] = xcp[c];
+        r.n[c] = nrm[c];
+      }
+      r.delta = delta;
+      r.iters = iters;
+      r.status = status;
+    }
+  }
+}
+
+cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s) {
+  k_contacts<<<L.grid, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace mi

@@ -360,8 +360,8 @@ __global__ void k_integrate(IntegrateLaunch L) {
     F[a] = (double)L.facc[6 * p + a] * FIX_INV;
     T[a] = (double)L.facc[6 * p + 3 + a] * FIX_INV;
     if (L.fc) {
-      F[a] += L.fc[6 * p + a];
-      T[a] += L.fc[6 * p + 3 + a];
+      F[a] += (double)L.fc[6 * p + a] * FIX_INV;
+      T[a] += (double)L.fc[6 * p + 3 + a] * FIX_INV;
     }
   }
   const double m = P.mass, dt = L.dt;

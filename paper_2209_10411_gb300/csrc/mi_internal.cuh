@@ -186,11 +186,49 @@ struct BoundaryLaunch {
 cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s);
 cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// DEM contacts (k_contact.cu)
+// ---------------------------------------------------------------------------
+struct ContactRec {       // one candidate (pair or particle-wall) of the last substep
+  int i, j;               // j >= 0 particle, j = -1 - face for a wall
+  double xcp[3], n[3], delta;
+  int iters, status;      // status: 0 ok, 1 not converged, 2 singular, 3 inside a core, 4 out of range
+};
+struct HistEntry {        // tangential spring of a pair / particle-wall contact
+  double xi[3];
+  long long stamp;        // DEM substep index of the last update (valid if previous substep)
+};
+struct ContactParams {
+  double kn, kt, eta_n, eta_t, mu_s, dt, margin;
+  int periodic[3];
+  int n[3];               // lattice sizes (walls at -1/2 and n - 1/2)
+};
+struct ContactLaunch {
+  DevParticle* P;
+  int np, ncap;           // particles, capacity used to index the pair-history triangle
+  const float4* balls;
+  DevCounters* ctr;
+  unsigned* work;         // persistent-kernel work counter
+  int* item_i;
+  int* item_j;
+  unsigned cap_items;
+  ContactRec* recs;
+  HistEntry* hist_pair;   // ncap (ncap - 1) / 2
+  HistEntry* hist_wall;   // ncap x 6
+  long long* fcacc;       // np x 6 fixed point (contact F, T)
+  long long* substep;     // device substep counter
+  ContactParams cp;
+  int grid;
+};
+cudaError_t launch_dem_prologue(const ContactLaunch& L, cudaStream_t s);
+cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s);
+cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s);
+
 struct IntegrateLaunch {
   DevParticle* P;
   int np;
   const long long* facc;   // hydrodynamic F, T (fixed point)
-  const double* fc;        // contact F, T (np x 6) or nullptr
+  const long long* fc;     // contact F, T (np x 6, fixed point) or nullptr
   double gravity[3];
   double rho0;
   double dt;
