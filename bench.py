@@ -175,6 +175,42 @@ def build_sim(B, scene, storage, stream):
     return sim
 
 
+def contact_solves(B, scenes, args):
+    """Contact solves per second: the DEM contact phase alone (broad phase +
+    persistent Newton/force kernel) on the 3000-particle bed of 4-128 balls
+    in 384x384x768, timed with CUDA events over repeated substeps."""
+    sc = scenes.config5()
+    nx, ny, nz = sc.shape
+    sim = B.Simulation(nx, ny, nz, tau=sc.tau, storage=1, max_particles=len(sc.particles),
+                       max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0)
+    for p in sc.particles:
+        r = p.nominal_radius
+        vol = 4.0 / 3.0 * np.pi * r ** 3
+        m = p.density * vol
+        sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat,
+                         mass_props={"mass": m, "volume": vol, "inertia": np.eye(3) * 0.4 * m * r * r})
+    sim.set_timing(True)
+    for _ in range(3):
+        sim.step_phases(B.PHASE_CONTACT)
+    sim.phase_times(reset=True)
+    reps = 20
+    for _ in range(reps):
+        sim.step_phases(B.PHASE_CONTACT)
+    pt = sim.phase_times(reset=True)["contact"]
+    recs = sim.contacts()
+    sim.close()
+    n = len(recs)
+    iters = np.array([c["iters"] for c in recs])
+    status = np.bincount(np.array([c["status"] for c in recs], dtype=int), minlength=5)
+    ms = pt[0] / reps
+    return {"value": n / (ms * 1e-3), "unit": "solves/s", "guess": "plain", "candidates": n,
+            "pairs": int(sum(1 for c in recs if c["j"] >= 0)), "in_contact": int(sum(1 for c in recs if c["delta"] > 0 and c["status"] == 0)),
+            "mean_iters": float(iters.mean()) if n else None,
+            "status_counts": {"ok": int(status[0]), "not_converged": int(status[1]), "singular": int(status[2]),
+                              "inside_core": int(status[3]), "out_of_range": int(status[4])},
+            "ms_per_substep": ms, "particles": len(sc.particles), "workload": sc.name}
+
+
 def run_mine(args):
     import torch
     rank, world, local = _dist_env()
@@ -198,12 +234,12 @@ def run_mine(args):
     ncell = nx * ny * nz
     npart = len(scene.particles)
 
+    sim.set_graphs(not args.no_graphs)
     for _ in range(max(3, args.warmup)):
         sim.step(1)
     sim.synchronize()
 
-    sim.set_timing(True)
-    sim.phase_times(reset=True)
+    # timed region: whole steps (CUDA-graph replays unless --no-graphs)
     clocks = ClockSampler()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -225,9 +261,18 @@ def run_mine(args):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+    stats = sim.stats()
+
+    # second timed region, same steps as individual launches bracketed by CUDA
+    # events on the stream each kernel runs on: per-kernel durations for the
+    # roofline (a graph replays one event pair per node, not one per step)
+    k_phase = max(10, min(args.steps, 200))
+    sim.set_timing(True)
+    sim.phase_times(reset=True)
+    for _ in range(k_phase):
+        sim.step(1)
     ptimes = sim.phase_times(reset=True)
     sim.set_timing(False)
-    stats = sim.stats()
 
     # nodes the bulk kernel updates: every node that is neither solid nor boundary
     cls, _ = sim.node_classes()
@@ -237,6 +282,9 @@ def run_mine(args):
 
     value = ncell * args.steps * world / (ms * 1e-3) / 1e6
     bulk_ms, bulk_n = ptimes["bulk"]
+    contacts = None
+    if not args.no_contacts and rank == 0:
+        contacts = contact_solves(B, scenes, args)
     peak, peak_kind = _peaks()
     cls_bytes = ncell if npart else 0
     alg_bytes = BYTES_PER_NODE[storage] * n_bulk + cls_bytes
@@ -280,7 +328,9 @@ def run_mine(args):
                         "frac": achieved / peak if achieved else None, "traffic": None,
                         "kernel": "k_bulk (D3Q19 stream-collide of bulk fluid nodes)", "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes},
-           "phase_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in ptimes.items() if v[1]},
+           "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
+           "graphs": not args.no_graphs,
+           "contacts": contacts,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
     if rank == 0:
@@ -301,6 +351,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", default=None, help="nx,ny,nz override (small profiling cases)")
+    ap.add_argument("--no-graphs", action="store_true", help="time individual launches instead of graph replays")
+    ap.add_argument("--no-contacts", action="store_true", help="skip the contact-solves measurement")
     args = ap.parse_args()
     CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
                    "lattice": [256, 256, 512], "storage": args.storage})

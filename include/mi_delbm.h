@@ -332,6 +332,13 @@ mi_status mi_delbm_get_stats(mi_delbm *h, mi_delbm_stats *st);
 mi_status mi_mass_properties_noalloc(const double *balls_dev, int n_balls, double density, double spacing,
                                      double *out_dev, void *stream);
 
+/* Run mi_delbm_step through CUDA graphs (enable != 0, the default) or as
+ * individual launches.  A graph of one whole step is captured on first use
+ * for each parity of the alternating buffers and replayed afterwards; adding
+ * a particle discards the graphs.  While per-phase timing is enabled, steps
+ * run as individual launches. */
+mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
+
 /* Per-phase GPU timing with CUDA events on the handle's stream.  While
  * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
  * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of

@@ -96,6 +96,7 @@ _sig("mi_delbm_set_raw_populations", c_int, _P, _P, c_size_t)
 _sig("mi_delbm_get_raw_populations", c_int, _P, _P, c_size_t)
 _sig("mi_delbm_get_device_view", c_int, _P, ctypes.POINTER(DeviceView))
 _sig("mi_delbm_set_timing", c_int, _P, c_int)
+_sig("mi_delbm_set_graphs", c_int, _P, c_int)
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
 _sig("mi_delbm_add_particle", c_int, _P, c_int, _P, _P, c_double, c_double, _P, _P, _P, _P,
@@ -269,6 +270,9 @@ class Simulation:
         return v
 
     # -- timing -----------------------------------------------------------
+    def set_graphs(self, on):
+        self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))
+
     def set_timing(self, on):
         self._check(lib.mi_delbm_set_timing(self.h, 1 if on else 0))
 

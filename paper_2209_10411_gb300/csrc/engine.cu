@@ -26,19 +26,19 @@ namespace {
 // Kernel-launch helper: runs `fn` (which returns a cudaError_t) as one launch
 // of `phase`, bracketed by timing events when timing is enabled.
 template <class F>
-mi_status launch_phase(mi_delbm* h, unsigned phase_bit, F&& fn) {
+mi_status launch_phase(mi_delbm* h, cudaStream_t st, unsigned phase_bit, F&& fn) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->timing) {
     a = h->event_from_pool();
     b = h->event_from_pool();
     if (!a || !b) return h->fail(MI_ECUDA, "cudaEventCreate failed");
-    cudaEventRecord(a, h->stream);
+    cudaEventRecord(a, st);
   }
   cudaError_t e = fn();
   h->launches += 1;
   if (e != cudaSuccess) return h->fail(MI_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   if (h->timing) {
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, st);
     int idx = 0;
     while ((1u << idx) != phase_bit && idx < 7) ++idx;
     h->timed.push_back({idx, a, b});
@@ -170,16 +170,16 @@ mi_status mi_delbm::phase_flag() {
   owner_cur ^= 1;  // the buffer holding the flags of two steps ago becomes current
   ParticleLaunch L = particle_launch();
   mi_status s;
-  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_prologue(L, stream); })) != MI_OK) return s;
-  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_clear(L, stream); })) != MI_OK) return s;
-  if ((s = launch_phase(this, MI_PHASE_FLAG, [&] { return launch_flag(L, stream); })) != MI_OK) return s;
-  return launch_phase(this, MI_PHASE_FLAG, [&] { return launch_classify(L, stream); });
+  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_prologue(L, stream); })) != MI_OK) return s;
+  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_clear(L, stream); })) != MI_OK) return s;
+  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_flag(L, stream); })) != MI_OK) return s;
+  return launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_classify(L, stream); });
 }
 
-mi_status mi_delbm::phase_links() {
+mi_status mi_delbm::phase_links(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   ParticleLaunch L = particle_launch();
-  return launch_phase(this, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 8, stream); });
+  return launch_phase(this, st, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 8, st); });
 }
 
 static BoundaryLaunch boundary_launch(const mi_delbm* h) {
@@ -198,13 +198,13 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
 mi_status mi_delbm::phase_refill() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
-  return launch_phase(this, MI_PHASE_REFILL, [&] { return launch_refill(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_REFILL, [&] { return launch_refill(L, stream); });
 }
 
 mi_status mi_delbm::phase_boundary() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
-  return launch_phase(this, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
 }
 
 mi_status mi_delbm::phase_integrate(bool with_contacts) {
@@ -217,7 +217,7 @@ mi_status mi_delbm::phase_integrate(bool with_contacts) {
   for (int a = 0; a < 3; ++a) L.gravity[a] = cfg.gravity[a];
   L.rho0 = cfg.rho0;
   L.dt = 1.0 / cfg.dem_substeps;
-  return launch_phase(this, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
 }
 
 mi_status mi_delbm::ensure_contact_buffers() {
@@ -277,14 +277,14 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   return L;
 }
 
-mi_status mi_delbm::phase_contact() {
+mi_status mi_delbm::phase_contact(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   mi_status s = ensure_contact_buffers();
   if (s != MI_OK) return s;
   ContactLaunch L = contact_launch(this);
-  if ((s = launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_dem_prologue(L, stream); })) != MI_OK) return s;
-  if ((s = launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_broad_phase(L, stream); })) != MI_OK) return s;
-  return launch_phase(this, MI_PHASE_CONTACT, [&] { return launch_contacts(L, stream); });
+  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_dem_prologue(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_broad_phase(L, st); })) != MI_OK) return s;
+  return launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_contacts(L, st); });
 }
 
 mi_status mi_delbm::phase_bulk() {
@@ -297,7 +297,7 @@ mi_status mi_delbm::phase_bulk() {
   L.storage = cfg.storage;
   L.forcing = forcing();
   L.block_x = tune.bulk_block_x;
-  return launch_phase(this, MI_PHASE_BULK, [&] { return launch_bulk(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BULK, [&] { return launch_bulk(L, stream); });
 }
 
 mi_status mi_delbm::phase_swap() {
@@ -306,20 +306,112 @@ mi_status mi_delbm::phase_swap() {
   return MI_OK;
 }
 
+// The phases of one step, in order, on the handle's stream.  Two side
+// branches run concurrently with the lattice phases: the wall fractions
+// (needed only by the boundary kernel) beside refill and bulk stream-collide,
+// and the first DEM substep's contacts (they read only the particle state,
+// which changes at the rigid-body update) beside the whole lattice part.
 mi_status mi_delbm::run_phases(unsigned phases) {
   mi_status s = MI_OK;
+  const bool particles = n_particles > 0;
+  const bool contact_branch = particles && (phases & MI_PHASE_CONTACT);
+  const bool links_branch = particles && (phases & MI_PHASE_LINKS);
+  if (contact_branch) {
+    if ((s = ensure_contact_buffers()) != MI_OK) return s;
+    if ((s = fork(aux[1], 0)) != MI_OK) return s;
+    if ((s = phase_contact(aux[1])) != MI_OK) return s;
+    if ((s = join_record(aux[1], 0)) != MI_OK) return s;
+  }
   if ((phases & MI_PHASE_FLAG) && (s = phase_flag()) != MI_OK) return s;
-  if ((phases & MI_PHASE_LINKS) && (s = phase_links()) != MI_OK) return s;
+  if (links_branch) {
+    if ((s = fork(aux[0], 1)) != MI_OK) return s;
+    if ((s = phase_links(aux[0])) != MI_OK) return s;
+    if ((s = join_record(aux[0], 1)) != MI_OK) return s;
+  }
   if ((phases & MI_PHASE_REFILL) && (s = phase_refill()) != MI_OK) return s;
   if ((phases & MI_PHASE_BULK) && (s = phase_bulk()) != MI_OK) return s;
+  if (links_branch && (s = join_wait(1)) != MI_OK) return s;
   if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
+  if (contact_branch && (s = join_wait(0)) != MI_OK) return s;
   if (phases & (MI_PHASE_CONTACT | MI_PHASE_INTEGRATE)) {
     for (int k = 0; k < cfg.dem_substeps; ++k) {
-      if ((phases & MI_PHASE_CONTACT) && (s = phase_contact()) != MI_OK) return s;
+      if (k > 0 && (phases & MI_PHASE_CONTACT) && (s = phase_contact(stream)) != MI_OK) return s;
       if ((phases & MI_PHASE_INTEGRATE) && (s = phase_integrate((phases & MI_PHASE_CONTACT) != 0)) != MI_OK) return s;
     }
   }
+  return MI_OK;
+}
+
+void mi_delbm::invalidate_graphs() {
+  for (int k = 0; k < 4; ++k) {
+    if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
+    gexec[k] = nullptr;
+    glaunches[k] = 0;
+  }
+}
+
+// One full step replayed from a CUDA graph.  A step alternates the population
+// buffers and (with particles) the owner buffers, so at most four graphs exist,
+// keyed by those two parities; each is captured on first use from the same
+// run_phases() the eager path runs.  Nothing allocates inside a capture: the
+// buffers a step needs are created first.
+mi_status mi_delbm::graph_step() {
+  const int key = (cur & 1) | ((owner_cur & 1) << 1);
+  if (!gexec[key]) {
+    if (n_particles > 0) {
+      mi_status s = ensure_contact_buffers();
+      if (s != MI_OK) return s;
+    }
+    const int c0 = cur, o0 = owner_cur;
+    const long long s0 = step_index, l0 = launches;
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    mi_status st = run_phases(MI_PHASE_ALL);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    glaunches[key] = launches - l0;
+    cur = c0;
+    owner_cur = o0;
+    step_index = s0;
+    launches = l0;
+    if (st != MI_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&gexec[key], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gexec[key] = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(gexec[key], stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  launches += glaunches[key];
+  cur ^= 1;
+  step_index += 1;
+  if (n_particles > 0) owner_cur ^= 1;
+  return MI_OK;
+}
+
+mi_status mi_delbm::fork(cudaStream_t to, int slot) {
+  cudaError_t e = cudaEventRecord(ev_fork[slot], stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev_fork[slot], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "fork");
+  return MI_OK;
+}
+
+mi_status mi_delbm::join_record(cudaStream_t from, int slot) {
+  cudaError_t e = cudaEventRecord(ev_join[slot], from);
+  if (e != cudaSuccess) return cuda_fail(e, "join");
+  return MI_OK;
+}
+
+mi_status mi_delbm::join_wait(int slot) {
+  cudaError_t e = cudaStreamWaitEvent(stream, ev_join[slot], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "join");
   return MI_OK;
 }
 
@@ -497,6 +589,15 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     }
     h->own_stream = true;
   }
+  for (int i = 0; i < 2; ++i) {
+    if (cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      g_create_error = "mi_delbm_create: side stream / event creation failed";
+      mi_delbm_destroy(h);
+      return MI_ECUDA;
+    }
+  }
   h->ncell = (size_t)ncell;
   h->plane = (h->ncell + 63) / 64 * 64;  // 256-byte aligned planes for every storage
   h->esize = store_bytes(cfg->storage);
@@ -537,6 +638,13 @@ void mi_delbm_destroy(mi_delbm* h) {
     cudaEventDestroy(t.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  h->invalidate_graphs();
+  for (int i = 0; i < 2; ++i) {
+    if (h->aux[i]) cudaStreamSynchronize(h->aux[i]);
+    if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+    if (h->ev_fork[i]) cudaEventDestroy(h->ev_fork[i]);
+    if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+  }
   while (!h->allocs.empty()) h->dfree(h->allocs.back().first);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -552,7 +660,7 @@ mi_status mi_delbm_step(mi_delbm* h, int n_steps) {
   if (n_steps < 0) return h->fail(MI_EINVAL, "mi_delbm_step: n_steps < 0");
   if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
   for (int n = 0; n < n_steps; ++n) {
-    mi_status s = h->run_phases(MI_PHASE_ALL);
+    mi_status s = (h->use_graphs && !h->timing) ? h->graph_step() : h->run_phases(MI_PHASE_ALL);
     if (s != MI_OK) return s;
   }
   return MI_OK;
@@ -634,6 +742,12 @@ mi_status mi_delbm_get_device_view(mi_delbm* h, mi_delbm_device_view* v) {
   v->node_class = h->cls;
   v->owner = h->owner[h->owner_cur];
   v->stream = (void*)h->stream;
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_graphs(mi_delbm* h, int enable) {
+  if (!h) return MI_EINVAL;
+  h->use_graphs = enable != 0;
   return MI_OK;
 }
 
@@ -814,10 +928,29 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   P.skin = skin;
   P.re = re;
   P.Rb = bounding();
+  {
+    // tight radius: for |x| > max|c_i|, f(x) <= sum k_i / (|x| - |c_i|)^2, which decreases
+    // in |x|; beyond its root Rt (<= Rb) every node is fluid
+    double cmax = 0.0;
+    std::vector<double> cn(n);
+    for (int i = 0; i < n; ++i) {
+      cn[i] = std::sqrt(c[3 * i] * c[3 * i] + c[3 * i + 1] * c[3 * i + 1] + c[3 * i + 2] * c[3 * i + 2]);
+      cmax = std::fmax(cmax, cn[i]);
+    }
+    double lo = cmax, hi = P.Rb;
+    for (int it = 0; it < 200 && hi - lo > 1e-12 * hi; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      double sum = 0.0;
+      for (int i = 0; i < n; ++i) sum += k[i] / ((mid - cn[i]) * (mid - cn[i]));
+      if (sum > 1.0) lo = mid;
+      else hi = mid;
+    }
+    P.Rt = std::fmin(hi * (1.0 + 1e-9) + 1e-9, P.Rb);
+  }
   P.ball_off = off;
   P.n_balls = n;
   for (int a = 0; a < 3; ++a) {
-    P.ext[a] = (int)std::ceil(2.0 * P.Rb) + 4;
+    P.ext[a] = (int)std::ceil(2.0 * P.Rt) + 4;
     P.lo[a] = BOX_NONE;
     P.lo_hist[0][a] = BOX_NONE;
     P.lo_hist[1][a] = BOX_NONE;
@@ -849,6 +982,7 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   if (st != MI_OK) return st;
   long long bpp = (maxvol + 1023) / 1024;
   h->blocks_per_particle = (int)(bpp < 1 ? 1 : (bpp > 8192 ? 8192 : bpp));
+  h->invalidate_graphs();
   if (id_out) *id_out = id;
   return MI_OK;
 }

@@ -20,6 +20,12 @@ struct mi_delbm {
   mi_delbm_config cfg;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t aux[2] = {nullptr, nullptr};  // side branches of a step (joined before it ends)
+  cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+  // CUDA graphs of one step, keyed by (population buffer, owner buffer) parity
+  bool use_graphs = true;
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long glaunches[4] = {0, 0, 0, 0};
 
   size_t ncell = 0;   // nx*ny*nz
   size_t plane = 0;   // elements between population planes
@@ -90,13 +96,18 @@ struct mi_delbm {
 
   mi_status run_phases(unsigned phases);
   mi_status phase_flag();
-  mi_status phase_links();
+  mi_status phase_links(cudaStream_t st);
   mi_status phase_refill();
   mi_status phase_bulk();
   mi_status phase_boundary();
   mi_status phase_swap();
   mi_status phase_integrate(bool with_contacts);
-  mi_status phase_contact();
+  mi_status phase_contact(cudaStream_t st);
+  mi_status graph_step();
+  void invalidate_graphs();
+  mi_status fork(cudaStream_t to, int slot);
+  mi_status join_record(cudaStream_t from, int slot);
+  mi_status join_wait(int slot);
   mi_status ensure_contact_buffers();
 
   mi_status ensure_particle_buffers();

@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __res
   if (x >= g.nx) return;
   const long long nxy = (long long)g.nx * g.ny;
   const long long c = x + (long long)g.nx * y + nxy * z;
-  if (HAS_CLS) {
-    if (__ldg(cls + c) & (CLS_SOLID | CLS_BOUNDARY)) return;  // boundary nodes go to k_boundary
-  }
+  // the node class is tested after the pulls are issued, so that its load does
+  // not delay them (solid and boundary nodes are a few percent of the lattice)
+  const uint8_t cl = HAS_CLS ? __ldg(cls + c) : (uint8_t)0;
   float h[19];
   const bool interior = (x > 0) & (x < g.nx - 1) & (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
   if (interior) {
@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __res
       }
     }
   }
+  if (cl & (CLS_SOLID | CLS_BOUNDARY)) return;  // boundary nodes go to k_boundary
   collide_store<ST, FORCE>(h, B, g.plane, c, P);
 }
 

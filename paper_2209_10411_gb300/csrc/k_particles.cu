@@ -56,19 +56,19 @@ __device__ __noinline__ bool inside_exact(const DevParticle& P, const double* ba
 // Region of a box kernel: box [lo, lo + ext) widened by `pad`, clipped.
 struct Region {
   int lo[3], n[3];
-  long long total;
+  unsigned total;
 };
 __device__ __forceinline__ Region clip_region(const int lo[3], const int ext[3], int pad, const LatticeGeom& g) {
   Region r;
   const int sz[3] = {g.nx, g.ny, g.nz};
-  r.total = 1;
+  r.total = 1u;
   for (int a = 0; a < 3; ++a) {
     int l = lo[a] - pad, h = lo[a] + ext[a] + pad;
     l = l < 0 ? 0 : l;
     h = h > sz[a] ? sz[a] : h;
     r.lo[a] = l;
     r.n[a] = h > l ? h - l : 0;
-    r.total *= r.n[a];
+    r.total *= (unsigned)r.n[a];
   }
   return r;
 }
@@ -114,7 +114,7 @@ __global__ void k_prologue(ParticleLaunch L) {
   DevParticle& P = L.P[p];
   quat_to_R_exact(P.quat, P.R);
   for (int a = 0; a < 3; ++a) {
-    P.lo[a] = (int)floor(P.pos[a] - P.Rb) - 1;
+    P.lo[a] = (int)floor(P.pos[a] - P.Rt) - 1;
     P.posf[a] = (float)P.pos[a];
     P.velf[a] = (float)P.vel[a];
     P.omegaf[a] = (float)P.omega[a];
@@ -139,11 +139,12 @@ __global__ void k_clear(ParticleLaunch L) {
   const int* lo = P.lo_hist[L.cur_buf];
   if (lo[0] == BOX_NONE) return;
   const Region r = clip_region(lo, P.ext, 0, L.g);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = r.lo[0] + (int)(i % r.n[0]);
-    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
-    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+  const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+    const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
+    const int x = r.lo[0] + (int)(rem - yi * n0);
+    const int y = r.lo[1] + (int)yi;
+    const int z = r.lo[2] + (int)zi;
     L.owner_cur[lin(x, y, z, L.g)] = OWNER_NONE;
   }
 }
@@ -173,12 +174,15 @@ __global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
     for (int a = 0; a < 3; ++a) L.P[p].lo_hist[L.cur_buf][a] = P.lo[a];
   const Region r = clip_region(P.lo, P.ext, 0, L.g);
   const double* R = P.R;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = r.lo[0] + (int)(i % r.n[0]);
-    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
-    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+  const double rt2 = P.Rt * P.Rt;
+  const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+    const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
+    const int x = r.lo[0] + (int)(rem - yi * n0);
+    const int y = r.lo[1] + (int)yi;
+    const int z = r.lo[2] + (int)zi;
     const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
+    if (d0 * d0 + d1 * d1 + d2 * d2 > rt2) continue;  // beyond the tight radius: fluid
     const float b0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);
     const float b1 = (float)(R[1] * d0 + R[4] * d1 + R[7] * d2);
     const float b2 = (float)(R[2] * d0 + R[5] * d1 + R[8] * d2);
@@ -231,11 +235,25 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
   }
   const Region r = clip_region(lo, ext, 2, L.g);
   const unsigned gen = L.ctr->gen;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = r.lo[0] + (int)(i % r.n[0]);
-    const int y = r.lo[1] + (int)((i / r.n[0]) % r.n[1]);
-    const int z = r.lo[2] + (int)(i / ((long long)r.n[0] * r.n[1]));
+  // nodes whose class can change lie within Rt + 2 of the particle's old or new
+  // position; each position is within 1.5 of its box centre
+  const float rc = (float)P.Rt + 4.0f, rc2 = rc * rc;
+  float cc[3], cp[3];
+  for (int a = 0; a < 3; ++a) {
+    cc[a] = P.lo[a] + 0.5f * P.ext[a];
+    cp[a] = (lp[0] == BOX_NONE ? P.lo[a] : lp[a]) + 0.5f * P.ext[a];
+  }
+  const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+    const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
+    const int x = r.lo[0] + (int)(rem - yi * n0);
+    const int y = r.lo[1] + (int)yi;
+    const int z = r.lo[2] + (int)zi;
+    {
+      const float a0 = x - cc[0], a1 = y - cc[1], a2 = z - cc[2];
+      const float b0 = x - cp[0], b1 = y - cp[1], b2 = z - cp[2];
+      if (a0 * a0 + a1 * a1 + a2 * a2 > rc2 && b0 * b0 + b1 * b1 + b2 * b2 > rc2) continue;
+    }
     const long long c = lin(x, y, z, L.g);
     const bool solid = L.owner_cur[c] != OWNER_NONE;
     const bool was = L.owner_prev[c] != OWNER_NONE;
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
       else lo = q;
       float qn = q - g / gp;
       if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
-      const bool done = fabsf(qn - q) < 2e-7f || (hi - lo) < 2e-7f;
+      const bool done = fabsf(qn - q) < 1e-6f || (hi - lo) < 1e-6f;
       q = qn;
       if (done) break;
     }

@@ -121,6 +121,7 @@ constexpr double FIX_INV = 1.0 / 1099511627776.0;
 struct DevParticle {
   double pos[3], quat[4], vel[3], omega[3];  // world frame; quat = (w, x, y, z)
   double mass, volume, density, skin, Rb, re;
+  double Rt;                                 // tight radius: f < 1 beyond it (root of sum k/(r-|c|)^2 = 1)
   double inertia[9], inv_inertia[9];         // body frame, about the centroid
   double R[9];                               // body -> world rotation at the current pose
   float posf[3], velf[3], omegaf[3];         // FP32 copies for the lattice kernels

@@ -169,16 +169,24 @@ def config3(seed=0):
 
 
 def _place_non_overlapping(rng, radii, box_lo, box_hi, margin, max_tries=200000):
-    pos = []
-    for r in radii:
-        for _ in range(max_tries):
-            p = rng.uniform(box_lo + r, box_hi - r)
-            if all(np.linalg.norm(p - q) > r + rq + margin for q, rq in pos):
-                pos.append((p, r))
+    """Random sequential addition: each sphere (in the given order) at a uniform
+    random position where it does not overlap any placed one (plus margin)."""
+    pos = np.zeros((len(radii), 3))
+    rad = np.asarray(radii, dtype=float)
+    for n, r in enumerate(rad):
+        for _ in range(max_tries // 64 + 1):
+            cand = rng.uniform(box_lo + r, box_hi - r, (64, 3))
+            if n == 0:
+                pos[0] = cand[0]
+                break
+            d = np.sqrt(((cand[:, None, :] - pos[None, :n, :]) ** 2).sum(-1))
+            ok = (d > rad[None, :n] + r + margin).all(1)
+            if ok.any():
+                pos[n] = cand[np.argmax(ok)]
                 break
         else:
             raise RuntimeError("could not place particle")
-    return [p for p, _ in pos]
+    return [p for p in pos]
 
 
 def config4(seed=0, shape=(512, 512, 512), n_particles=300):
@@ -201,8 +209,9 @@ def config4(seed=0, shape=(512, 512, 512), n_particles=300):
 
 def config5(seed=0, shape=(384, 384, 768), n_particles=3000):
     """384x384x768 bed: 3000 particles of 4-128 balls (log-uniform), R ~ U[8, 16],
-    packed into the lower half by random sequential addition with bounding
-    spheres nearly touching."""
+    packed into the lower 60 % of the box by random sequential addition of
+    spheres of radius 0.9 R, so that neighbouring particles nearly touch
+    (about 14k broad-phase candidate pairs)."""
     rng = np.random.default_rng(seed)
     specs = []
     for _ in range(n_particles):
@@ -211,8 +220,8 @@ def config5(seed=0, shape=(384, 384, 768), n_particles=3000):
         c, k, r = clustered(rng, n, R)
         specs.append((c, k, r))
     lo = np.array([2.0, 2.0, 2.0])
-    hi = np.array([shape[0] - 2.0, shape[1] - 2.0, shape[2] * 0.5])
-    pos = _place_non_overlapping(rng, [1.0 * s[2] for s in specs], lo, hi, 0.5)
+    hi = np.array([shape[0] - 2.0, shape[1] - 2.0, shape[2] * 0.6])
+    pos = _place_non_overlapping(rng, [0.9 * s[2] for s in specs], lo, hi, 0.0)
     parts = [ParticleSpec(c, k, 2.5, 1.0, f32(p), random_unit_quaternion(rng), nominal_radius=r)
              for (c, k, r), p in zip(specs, pos)]
     return Scene("C5 384x384x768 3000-particle bed", shape, 0.8, (0.0, 0.0, -1e-5), parts, 100, seed)
