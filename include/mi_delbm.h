@@ -162,6 +162,7 @@ mi_status mi_delbm_synchronize(mi_delbm *h);
 mi_status mi_delbm_step_phases(mi_delbm *h, unsigned phases);
 
 /* Copy the current post-collision populations f_i (as float, [19][nz][ny][nx])
+ * (the values at solid nodes are unspecified)
  * to or from the host.  For the deviation storages the stored value is
  * f_i - w_i rounded to the storage type on set, and w_i + stored on get (so a
  * get after a set returns the rounded value).  Synchronises.

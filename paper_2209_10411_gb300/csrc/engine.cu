@@ -165,15 +165,15 @@ ParticleLaunch mi_delbm::particle_launch() const {
   return L;
 }
 
-mi_status mi_delbm::phase_flag() {
+mi_status mi_delbm::phase_flag(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   owner_cur ^= 1;  // the buffer holding the flags of two steps ago becomes current
   ParticleLaunch L = particle_launch();
   mi_status s;
-  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_prologue(L, stream); })) != MI_OK) return s;
-  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_clear(L, stream); })) != MI_OK) return s;
-  if ((s = launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_flag(L, stream); })) != MI_OK) return s;
-  return launch_phase(this, stream, MI_PHASE_FLAG, [&] { return launch_classify(L, stream); });
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_prologue(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_clear(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_flag(L, st); })) != MI_OK) return s;
+  return launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_classify(L, st); });
 }
 
 mi_status mi_delbm::phase_links(cudaStream_t st) {
@@ -195,10 +195,17 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
   return L;
 }
 
-mi_status mi_delbm::phase_refill() {
+mi_status mi_delbm::phase_refill(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
-  return launch_phase(this, stream, MI_PHASE_REFILL, [&] { return launch_refill(L, stream); });
+  return launch_phase(this, st, MI_PHASE_REFILL, [&] { return launch_refill(L, st); });
+}
+
+mi_status mi_delbm::phase_near() {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  // timed with the boundary phase: the bulk bucket is the lattice-wide kernel alone
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_near(L, stream); });
 }
 
 mi_status mi_delbm::phase_boundary() {
@@ -291,7 +298,6 @@ mi_status mi_delbm::phase_bulk() {
   BulkLaunch L;
   L.A = pop[cur];
   L.B = pop[cur ^ 1];
-  L.cls = n_particles > 0 ? cls : nullptr;
   L.g = geom();
   L.p = collide_params();
   L.storage = cfg.storage;
@@ -306,30 +312,39 @@ mi_status mi_delbm::phase_swap() {
   return MI_OK;
 }
 
-// The phases of one step, in order, on the handle's stream.  Two side
-// branches run concurrently with the lattice phases: the wall fractions
-// (needed only by the boundary kernel) beside refill and bulk stream-collide,
-// and the first DEM substep's contacts (they read only the particle state,
-// which changes at the rigid-body update) beside the whole lattice part.
+// The phases of one step.  The bulk stream-collide of every node runs on the
+// handle's stream; concurrently, on high-priority side streams, run the
+// particle chain (flag, classify, refill; the wall fractions fork off it) and
+// the first DEM substep's contacts (they read only the particle state, which
+// changes at the rigid-body update).  After the bulk kernel and the particle
+// chain meet, the neighbours of uncovered nodes are recomputed (k_near), then
+// the boundary nodes (after the wall fractions), then the DEM substeps.
 mi_status mi_delbm::run_phases(unsigned phases) {
   mi_status s = MI_OK;
   const bool particles = n_particles > 0;
   const bool contact_branch = particles && (phases & MI_PHASE_CONTACT);
+  const bool chain = particles && (phases & (MI_PHASE_FLAG | MI_PHASE_LINKS | MI_PHASE_REFILL));
   const bool links_branch = particles && (phases & MI_PHASE_LINKS);
   if (contact_branch) {
     if ((s = ensure_contact_buffers()) != MI_OK) return s;
-    if ((s = fork(aux[1], 0)) != MI_OK) return s;
+    if ((s = fork(stream, aux[1], 0)) != MI_OK) return s;
     if ((s = phase_contact(aux[1])) != MI_OK) return s;
     if ((s = join_record(aux[1], 0)) != MI_OK) return s;
   }
-  if ((phases & MI_PHASE_FLAG) && (s = phase_flag()) != MI_OK) return s;
-  if (links_branch) {
-    if ((s = fork(aux[0], 1)) != MI_OK) return s;
-    if ((s = phase_links(aux[0])) != MI_OK) return s;
-    if ((s = join_record(aux[0], 1)) != MI_OK) return s;
+  if (chain) {
+    if ((s = fork(stream, aux[2], 2)) != MI_OK) return s;
+    if ((phases & MI_PHASE_FLAG) && (s = phase_flag(aux[2])) != MI_OK) return s;
+    if (links_branch) {
+      if ((s = fork(aux[2], aux[0], 1)) != MI_OK) return s;
+      if ((s = phase_links(aux[0])) != MI_OK) return s;
+      if ((s = join_record(aux[0], 1)) != MI_OK) return s;
+    }
+    if ((phases & MI_PHASE_REFILL) && (s = phase_refill(aux[2])) != MI_OK) return s;
+    if ((s = join_record(aux[2], 2)) != MI_OK) return s;
   }
-  if ((phases & MI_PHASE_REFILL) && (s = phase_refill()) != MI_OK) return s;
   if ((phases & MI_PHASE_BULK) && (s = phase_bulk()) != MI_OK) return s;
+  if (chain && (s = join_wait(2)) != MI_OK) return s;
+  if ((phases & MI_PHASE_BULK) && (s = phase_near()) != MI_OK) return s;
   if (links_branch && (s = join_wait(1)) != MI_OK) return s;
   if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
@@ -380,7 +395,7 @@ mi_status mi_delbm::graph_step() {
       return st;
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&gexec[key], g, 0);
+    e = cudaGraphInstantiate(&gexec[key], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
       gexec[key] = nullptr;
@@ -396,8 +411,8 @@ mi_status mi_delbm::graph_step() {
   return MI_OK;
 }
 
-mi_status mi_delbm::fork(cudaStream_t to, int slot) {
-  cudaError_t e = cudaEventRecord(ev_fork[slot], stream);
+mi_status mi_delbm::fork(cudaStream_t from, cudaStream_t to, int slot) {
+  cudaError_t e = cudaEventRecord(ev_fork[slot], from);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev_fork[slot], 0);
   if (e != cudaSuccess) return cuda_fail(e, "fork");
   return MI_OK;
@@ -589,8 +604,10 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     }
     h->own_stream = true;
   }
-  for (int i = 0; i < 2; ++i) {
-    if (cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  for (int i = 0; i < 3; ++i) {
+    if (cudaStreamCreateWithPriority(&h->aux[i], cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
       g_create_error = "mi_delbm_create: side stream / event creation failed";
@@ -639,7 +656,7 @@ void mi_delbm_destroy(mi_delbm* h) {
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
   h->invalidate_graphs();
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     if (h->aux[i]) cudaStreamSynchronize(h->aux[i]);
     if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
     if (h->ev_fork[i]) cudaEventDestroy(h->ev_fork[i]);

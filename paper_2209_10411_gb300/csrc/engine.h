@@ -20,8 +20,10 @@ struct mi_delbm {
   mi_delbm_config cfg;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaStream_t aux[2] = {nullptr, nullptr};  // side branches of a step (joined before it ends)
-  cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+  // side branches of a step (high priority; joined before the step ends):
+  // 0 wall fractions, 1 first-substep contacts, 2 particle chain
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork[3] = {nullptr, nullptr, nullptr}, ev_join[3] = {nullptr, nullptr, nullptr};
   // CUDA graphs of one step, keyed by (population buffer, owner buffer) parity
   bool use_graphs = true;
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -95,9 +97,10 @@ struct mi_delbm {
   bool forcing() const;
 
   mi_status run_phases(unsigned phases);
-  mi_status phase_flag();
+  mi_status phase_flag(cudaStream_t st);
   mi_status phase_links(cudaStream_t st);
-  mi_status phase_refill();
+  mi_status phase_refill(cudaStream_t st);
+  mi_status phase_near();
   mi_status phase_bulk();
   mi_status phase_boundary();
   mi_status phase_swap();
@@ -105,7 +108,7 @@ struct mi_delbm {
   mi_status phase_contact(cudaStream_t st);
   mi_status graph_step();
   void invalidate_graphs();
-  mi_status fork(cudaStream_t to, int slot);
+  mi_status fork(cudaStream_t from, cudaStream_t to, int slot);
   mi_status join_record(cudaStream_t from, int slot);
   mi_status join_wait(int slot);
   mi_status ensure_contact_buffers();

@@ -56,19 +56,13 @@ __device__ __forceinline__ void collide_store(const float (&h)[19], typename Sto
   }
 }
 
-template <int ST, bool FORCE, bool HAS_CLS>
-__global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __restrict__ A,
-                                              typename Store<ST>::T* __restrict__ B,
-                                              const uint8_t* __restrict__ cls, LatticeGeom g,
-                                              CollideParams P) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= g.nx) return;
+// Pull streaming (with halfway bounce-back at domain walls) and collision of
+// node (x, y, z), c its linear index.
+template <int ST, bool FORCE>
+__device__ __forceinline__ void update_node(const typename Store<ST>::T* __restrict__ A,
+                                            typename Store<ST>::T* __restrict__ B, const LatticeGeom& g,
+                                            const CollideParams& P, int x, int y, int z, long long c) {
   const long long nxy = (long long)g.nx * g.ny;
-  const long long c = x + (long long)g.nx * y + nxy * z;
-  // the node class is tested after the pulls are issued, so that its load does
-  // not delay them (solid and boundary nodes are a few percent of the lattice)
-  const uint8_t cl = HAS_CLS ? __ldg(cls + c) : (uint8_t)0;
   float h[19];
   const bool interior = (x > 0) & (x < g.nx - 1) & (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
   if (interior) {
@@ -96,23 +90,38 @@ __global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __res
       }
     }
   }
-  if (cl & (CLS_SOLID | CLS_BOUNDARY)) return;  // boundary nodes go to k_boundary
   collide_store<ST, FORCE>(h, B, g.plane, c, P);
 }
 
-template <int ST, bool FORCE, bool HAS_CLS>
+// Every node of the lattice.  With particles this runs concurrently with the
+// particle phases: boundary nodes are rewritten afterwards by k_boundary, solid
+// nodes hold unspecified values, and the nodes next to a node uncovered this
+// step (whose refilled populations this kernel may not have seen) are
+// recomputed by k_near.  Nodes anywhere else have no solid or uncovered
+// neighbour, so their update here is final.
+template <int ST, bool FORCE>
+__global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __restrict__ A,
+                                              typename Store<ST>::T* __restrict__ B, LatticeGeom g,
+                                              CollideParams P) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long c = x + (long long)g.nx * (y + (long long)g.ny * z);
+  update_node<ST, FORCE>(A, B, g, P, x, y, z, c);
+}
+
+template <int ST, bool FORCE>
 static cudaError_t launch_bulk_t(const BulkLaunch& L, cudaStream_t s) {
   using T = typename Store<ST>::T;
   const int bx = L.block_x;
   dim3 grid((L.g.nx + bx - 1) / bx, L.g.ny, L.g.nz);
-  k_bulk<ST, FORCE, HAS_CLS><<<grid, bx, 0, s>>>(static_cast<const T*>(L.A), static_cast<T*>(L.B), L.cls, L.g, L.p);
+  k_bulk<ST, FORCE><<<grid, bx, 0, s>>>(static_cast<const T*>(L.A), static_cast<T*>(L.B), L.g, L.p);
   return cudaGetLastError();
 }
 
 template <int ST>
 static cudaError_t launch_bulk_st(const BulkLaunch& L, cudaStream_t s) {
-  if (L.forcing) return L.cls ? launch_bulk_t<ST, true, true>(L, s) : launch_bulk_t<ST, true, false>(L, s);
-  return L.cls ? launch_bulk_t<ST, false, true>(L, s) : launch_bulk_t<ST, false, false>(L, s);
+  return L.forcing ? launch_bulk_t<ST, true>(L, s) : launch_bulk_t<ST, false>(L, s);
 }
 
 cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s) {
@@ -217,159 +226,231 @@ __global__ void __launch_bounds__(128) k_refill(BoundaryLaunch L) {
 }
 
 // ---------------------------------------------------------------------------
-// Boundary nodes: pull streaming where the source is fluid, halfway
-// bounce-back where it is outside the domain, and for every link (x_f, d) to
-// a solid neighbour the paper's interpolated bounce-back (Eqs. eqneq1,
-// eqneq2, neqd) for the missing population j = opp(d):
+// Nodes next to an uncovered node: recomputed after the refill (the bulk
+// kernel may have read their neighbour's populations before it was refilled).
+// One thread per (uncovered node, direction); a node reached twice is written
+// twice with the same values.
+// ---------------------------------------------------------------------------
+template <int ST, bool FORCE>
+__global__ void __launch_bounds__(128) k_near(BoundaryLaunch L) {
+  using T = typename Store<ST>::T;
+  const T* __restrict__ A = static_cast<const T*>(L.A);
+  T* __restrict__ B = static_cast<T*>(L.B);
+  const LatticeGeom& g = L.pl.g;
+  const unsigned nn = min(L.pl.ctr->n_new, L.pl.cap_new);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nn * 18u; t += gridDim.x * blockDim.x) {
+    const unsigned k = t / 18u;
+    const int d = 1 + (int)(t - 18u * k);
+    int x, y, z;
+    coords(L.pl.new_cell[k], g, x, y, z);
+    long long nb;
+    if (!nbr_wrap(x, y, z, cx(d), cy(d), cz(d), g, nb)) continue;
+    if (L.pl.owner_cur[nb] != OWNER_NONE || (L.pl.cls[nb] & CLS_BOUNDARY)) continue;
+    int a, b, c;
+    coords(nb, g, a, b, c);
+    update_node<ST, FORCE>(A, B, g, L.p, a, b, c, nb);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary nodes, one warp per node, lane j < 19 handling direction j: pull
+// streaming where the source is fluid, halfway bounce-back where it is outside
+// the domain, and for a link (x_f, d = opp j) to a solid neighbour the paper's
+// interpolated bounce-back (Eqs. eqneq1, eqneq2, neqd):
 //   G_j = f_eq,d(rho_f, u_d) + [f+_d(x_f) - f_eq,d(rho_f, u_f)] + 6 w_d rho0 (e_j . u_w)
 //   u_d = u*/3 + 2 u**/3 (piecewise in q), u_w = v_p + omega_p x (x_w - X_p)
 // (or the halfway rule f+_d + 6 w_d rho0 e_j.u_w in Ladd mode); then BGK
-// collision.  The Galilean-invariant momentum exchange of each link,
+// collision with the node's moments from warp sums.  The Galilean-invariant
+// momentum exchange of each link,
 //   dP = (e_d - u_w) f+_d - (e_j - u_w) G_j = e_d (2 w_d + h_d + h_G) - u_w (h_d - h_G),
-// and its torque about X_p are summed per particle in 2^-40 fixed point with
-// 64-bit integer atomics (order-independent, so the sums are deterministic).
-// One thread per boundary node.
+// and its torque about X_p are warp-summed per node, converted to 2^-40 fixed
+// point per node and added with 64-bit integer atomics: the result does not
+// depend on the order in which nodes are visited.
 // ---------------------------------------------------------------------------
 namespace {
-__device__ __forceinline__ void add_fixed(long long* facc, int p, const double v[6]) {
+constexpr unsigned FULLW = 0xffffffffu;
+// direction tables as 2-bit fields (value + 1), so that a lane can look up its
+// own direction without local or constant memory
+__host__ __device__ constexpr unsigned long long pack2(int axis) {
+  unsigned long long v = 0;
+  for (int i = 0; i < 19; ++i)
+    v |= (unsigned long long)((axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
+  return v;
+}
+constexpr unsigned long long EXB = pack2(0), EYB = pack2(1), EZB = pack2(2);
+__device__ __forceinline__ int lex(int j) { return (int)((EXB >> (2 * j)) & 3ull) - 1; }
+__device__ __forceinline__ int ley(int j) { return (int)((EYB >> (2 * j)) & 3ull) - 1; }
+__device__ __forceinline__ int lez(int j) { return (int)((EZB >> (2 * j)) & 3ull) - 1; }
+__device__ __forceinline__ float lw(int j) { return j == 0 ? (1.0f / 3.0f) : (j <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
+__device__ __forceinline__ int lopp(int j) { return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1); }
+
+__device__ __forceinline__ float wsumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLW, v, o);
+  return __shfl_sync(FULLW, v, 0);
+}
+
+__device__ __forceinline__ void add_fixed_ll(long long* facc, int p, const long long v[6]) {
   for (int k = 0; k < 6; ++k)
-    atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)__double2ll_rn(v[k] * FIX_SCALE));
+    atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)v[k]);
 }
 }  // namespace
 
 template <int ST, bool FORCE, bool LADD>
-__global__ void __launch_bounds__(128) k_boundary(BoundaryLaunch L) {
+__global__ void __launch_bounds__(256) k_boundary(BoundaryLaunch L) {
   using T = typename Store<ST>::T;
   const T* __restrict__ A = static_cast<const T*>(L.A);
   T* __restrict__ B = static_cast<T*>(L.B);
   const LatticeGeom& g = L.pl.g;
   const ParticleLaunch& pl = L.pl;
   const unsigned nbc = min(pl.ctr->n_bc, pl.cap_bc);
-  const float rho0 = L.p.rho0;
-  const unsigned lane = threadIdx.x & 31u;
-  for (unsigned base = blockIdx.x * blockDim.x; base < nbc; base += gridDim.x * blockDim.x) {
-    const unsigned bi = base + threadIdx.x;
-    const bool active = bi < nbc;
-    int pacc = -1;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    if (active) {
-      const long long c = pl.bc_cell[bi];
-      const uint32_t mask = pl.bc_mask[bi];
-      const uint32_t loff = pl.bc_loff[bi];
-      int x, y, z;
-      coords(c, g, x, y, z);
-      float hown[19];
-#pragma unroll
-      for (int i = 0; i < 19; ++i) hown[i] = Store<ST>::dev(A + i * g.plane + c, i);
-      float rho_f, u_f[3];
-      {
-        float dr = 0.f;
-#pragma unroll
-        for (int i = 0; i < 19; ++i) dr += hown[i];
-        rho_f = 1.0f + dr;
-        u_f[0] = ((hown[1] - hown[2]) + (hown[7] - hown[8]) + (hown[9] - hown[10]) + (hown[11] - hown[12]) +
-                  (hown[13] - hown[14])) / rho_f;
-        u_f[1] = ((hown[3] - hown[4]) + (hown[7] - hown[8]) + (hown[10] - hown[9]) + (hown[15] - hown[16]) +
-                  (hown[17] - hown[18])) / rho_f;
-        u_f[2] = ((hown[5] - hown[6]) + (hown[11] - hown[12]) + (hown[14] - hown[13]) + (hown[15] - hown[16]) +
-                  (hown[18] - hown[17])) / rho_f;
-      }
-      float h[19];
-#pragma unroll
-      for (int j = 0; j < 19; ++j) {
-        int sx = x - cx(j), sy = y - cy(j), sz = z - cz(j);
-        int face = -1;
-        if (sz < 0) { if (g.periodic[2]) sz += g.nz; else face = 4; }
-        else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else face = 5; }
-        if (sy < 0) { if (g.periodic[1]) sy += g.ny; else face = 2; }
-        else if (sy >= g.ny) { if (g.periodic[1]) sy -= g.ny; else face = 3; }
-        if (sx < 0) { if (g.periodic[0]) sx += g.nx; else face = 0; }
-        else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else face = 1; }
-        if (face >= 0) {
-          h[j] = hown[opp(j)] + L.p.bb_wall[face][j];
-          continue;
-        }
-        const int d = opp(j);
-        if (j == 0 || !((mask >> d) & 1u)) {
-          h[j] = Store<ST>::dev(A + j * g.plane + (sx + (long long)g.nx * (sy + (long long)g.ny * sz)), j);
-          continue;
-        }
-        // link (x_f, d): the population arriving along j comes off the particle wall
+  const float rho0 = L.p.rho0, om = L.p.omega;
+  const int j = threadIdx.x & 31;
+  const bool dirlane = j < 19;
+  const int ej[3] = {lex(j), ley(j), lez(j)};
+  const int d = lopp(j);  // link direction of lane j (towards the solid)
+  const int ed[3] = {-ej[0], -ej[1], -ej[2]};
+  const float wj = dirlane ? lw(j) : 0.f;
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  int pacc = -1;              // lane 0: particle of the running fixed-point sums
+  long long iacc[6] = {0, 0, 0, 0, 0, 0};
+  for (unsigned bi = warp; bi < nbc; bi += nwarps) {
+    const long long c = pl.bc_cell[bi];
+    const uint32_t mask = pl.bc_mask[bi];
+    const uint32_t loff = pl.bc_loff[bi];
+    int x, y, z;
+    coords(c, g, x, y, z);
+    // own post-collision populations and moments (rho_f, u_f)
+    const float hown = dirlane ? Store<ST>::dev(A + j * g.plane + c, j) : 0.f;
+    const float hopp = __shfl_sync(FULLW, hown, d < 19 ? d : 0);  // f+_d(x_f) - w_d
+    const float rho_f = 1.0f + wsumf(hown);
+    const float uf0 = wsumf(ej[0] * hown) / rho_f, uf1 = wsumf(ej[1] * hown) / rho_f,
+                uf2 = wsumf(ej[2] * hown) / rho_f;
+    float hin = 0.f;
+    float dP[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
+    int p = -1;
+    if (dirlane) {
+      int sx = x - ej[0], sy = y - ej[1], sz = z - ej[2];
+      int face = -1;  // a corner crossing is attributed to x, then y, then z
+      if (sz < 0) { if (g.periodic[2]) sz += g.nz; else face = 4; }
+      else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else face = 5; }
+      if (sy < 0) { if (g.periodic[1]) sy += g.ny; else face = 2; }
+      else if (sy >= g.ny) { if (g.periodic[1]) sy -= g.ny; else face = 3; }
+      if (sx < 0) { if (g.periodic[0]) sx += g.nx; else face = 0; }
+      else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else face = 1; }
+      if (face >= 0) {
+        hin = hopp + L.p.bb_wall[face][j];
+      } else if (j == 0 || !((mask >> d) & 1u)) {
+        hin = Store<ST>::dev(A + j * g.plane + (sx + (long long)g.nx * (sy + (long long)g.ny * sz)), j);
+      } else {
         const unsigned l = loff + __popc(mask & ((1u << d) - 1u));
         if (l >= pl.cap_links) {
-          h[j] = hown[d];
-          continue;
-        }
-        const int p = (int)pl.link_p[l];
-        const DevParticle& P = pl.P[p];
-        const float q = LADD ? 0.5f : pl.link_q[l];
-        const double wx = x + (double)q * cx(d), wy = y + (double)q * cy(d), wz = z + (double)q * cz(d);
-        float uw[3];
-        rigid_u(P, wx, wy, wz, uw);
-        const float hd = hown[d];
-        const float wall = 6.0f * wq(d) * rho0 * (cx(j) * uw[0] + cy(j) * uw[1] + cz(j) * uw[2]);
-        float G;
-        if (LADD) {
-          G = hd + wall;
+          hin = hopp;
         } else {
-          float u_ff[3] = {u_f[0], u_f[1], u_f[2]};
-          long long ff;
-          if (nbr_wrap(x, y, z, -cx(d), -cy(d), -cz(d), g, ff) && pl.owner_cur[ff] == OWNER_NONE) {
-            float rr;
-            moments_at<ST>(A, g.plane, ff, rr, u_ff);
-          }
-          float ud[3];
-          const float a1 = (1.0f - q) / (1.0f + q), a2 = 2.0f * q / (1.0f + q);
+          p = (int)pl.link_p[l];
+          const DevParticle& P = pl.P[p];
+          const float q = LADD ? 0.5f : pl.link_q[l];
+          // wall point relative to the particle position: node offset in FP64, once
+          const float r0 = (float)((double)x - P.pos[0]) + q * ed[0];
+          const float r1 = (float)((double)y - P.pos[1]) + q * ed[1];
+          const float r2 = (float)((double)z - P.pos[2]) + q * ed[2];
+          float uw[3];
+          uw[0] = P.velf[0] + (P.omegaf[1] * r2 - P.omegaf[2] * r1);
+          uw[1] = P.velf[1] + (P.omegaf[2] * r0 - P.omegaf[0] * r2);
+          uw[2] = P.velf[2] + (P.omegaf[0] * r1 - P.omegaf[1] * r0);
+          const float wall = 6.0f * wj * rho0 * (ej[0] * uw[0] + ej[1] * uw[1] + ej[2] * uw[2]);
+          float G;
+          if (LADD) {
+            G = hopp + wall;
+          } else {
+            float uff[3] = {uf0, uf1, uf2};
+            long long ff;
+            if (nbr_wrap(x, y, z, ej[0], ej[1], ej[2], g, ff) && pl.owner_cur[ff] == OWNER_NONE) {
+              float rr;
+              moments_at<ST>(A, g.plane, ff, rr, uff);
+            }
+            const float uf[3] = {uf0, uf1, uf2};
+            float ud[3];
+            const float a1 = (1.0f - q) / (1.0f + q), a2 = 2.0f * q / (1.0f + q);
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float us = q <= 0.5f ? 2.0f * q * u_f[a] + (1.0f - 2.0f * q) * u_ff[a]
-                                       : ((1.0f - q) / q) * u_f[a] + ((2.0f * q - 1.0f) / q) * uw[a];
-            const float uss = a1 * u_ff[a] + a2 * uw[a];
-            ud[a] = us / 3.0f + 2.0f * uss / 3.0f;
+            for (int a = 0; a < 3; ++a) {
+              const float us = q <= 0.5f ? 2.0f * q * uf[a] + (1.0f - 2.0f * q) * uff[a]
+                                         : ((1.0f - q) / q) * uf[a] + ((2.0f * q - 1.0f) / q) * uw[a];
+              ud[a] = us / 3.0f + 2.0f * (a1 * uff[a] + a2 * uw[a]) / 3.0f;
+            }
+            const float eud = ed[0] * ud[0] + ed[1] * ud[1] + ed[2] * ud[2];
+            const float euf = ed[0] * uf[0] + ed[1] * uf[1] + ed[2] * uf[2];
+            const float ud2 = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+            const float uf2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+            G = hopp + wj * rho_f * (3.0f * (eud - euf) + 4.5f * (eud * eud - euf * euf) - 1.5f * (ud2 - uf2)) + wall;
           }
-          const float eud = cx(d) * ud[0] + cy(d) * ud[1] + cz(d) * ud[2];
-          const float euf = cx(d) * u_f[0] + cy(d) * u_f[1] + cz(d) * u_f[2];
-          const float ud2 = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
-          const float uf2 = u_f[0] * u_f[0] + u_f[1] * u_f[1] + u_f[2] * u_f[2];
-          const float dfeq = wq(d) * rho_f * (3.0f * (eud - euf) + 4.5f * (eud * eud - euf * euf) - 1.5f * (ud2 - uf2));
-          G = hd + dfeq + wall;
+          hin = G;
+          const float s2 = 2.0f * wj + hopp + G, dl = hopp - G;
+          dP[0] = ed[0] * s2 - uw[0] * dl;
+          dP[1] = ed[1] * s2 - uw[1] * dl;
+          dP[2] = ed[2] * s2 - uw[2] * dl;
+          dT[0] = r1 * dP[2] - r2 * dP[1];
+          dT[1] = r2 * dP[0] - r0 * dP[2];
+          dT[2] = r0 * dP[1] - r1 * dP[0];
         }
-        h[j] = G;
-        // momentum exchange of this link, torque about X_p
-        const float s2 = 2.0f * wq(d) + hd + G, dlt = hd - G;
-        const float dP0 = cx(d) * s2 - uw[0] * dlt, dP1 = cy(d) * s2 - uw[1] * dlt, dP2 = cz(d) * s2 - uw[2] * dlt;
-        const double r0 = wx - P.pos[0], r1 = wy - P.pos[1], r2 = wz - P.pos[2];
-        if (pacc != p) {
-          if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
-          pacc = p;
-          for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-        }
-        acc[0] += dP0;
-        acc[1] += dP1;
-        acc[2] += dP2;
-        acc[3] += r1 * dP2 - r2 * dP1;
-        acc[4] += r2 * dP0 - r0 * dP2;
-        acc[5] += r0 * dP1 - r1 * dP0;
       }
-      collide_store<ST, FORCE>(h, B, g.plane, c, L.p);
     }
-    // warp-aggregated flush of the per-node sums (integer adds: order-free)
-    const int p0 = __shfl_sync(0xffffffffu, pacc, 0);
-    const bool uniform = __all_sync(0xffffffffu, pacc == p0 || pacc < 0);
-    if (uniform && p0 >= 0) {
+    // collision of the node (moments of the incoming populations by warp sums)
+    const float drho = wsumf(hin);
+    const float rho = 1.0f + drho;
+    const float j0 = wsumf(ej[0] * hin), j1 = wsumf(ej[1] * hin), j2 = wsumf(ej[2] * hin);
+    float u0, u1, u2;
+    if (FORCE) {
+      u0 = (j0 + 0.5f * L.p.force[0]) / rho;
+      u1 = (j1 + 0.5f * L.p.force[1]) / rho;
+      u2 = (j2 + 0.5f * L.p.force[2]) / rho;
+    } else {
+      u0 = j0 / rho;
+      u1 = j1 / rho;
+      u2 = j2 / rho;
+    }
+    if (dirlane) {
+      const float eu = ej[0] * u0 + ej[1] * u1 + ej[2] * u2;
+      const float usq15 = 1.5f * (u0 * u0 + u1 * u1 + u2 * u2);
+      const float feq_dev = wj * (drho + rho * (3.0f * eu + 4.5f * eu * eu - usq15));
+      float hp = hin + om * (feq_dev - hin);
+      if (FORCE) {
+        const float eF = ej[0] * L.p.force[0] + ej[1] * L.p.force[1] + ej[2] * L.p.force[2];
+        const float uF = u0 * L.p.force[0] + u1 * L.p.force[1] + u2 * L.p.force[2];
+        hp += (1.0f - 0.5f * om) * wj * (3.0f * (eF - uF) + 9.0f * eu * eF);
+      }
+      Store<ST>::put(B + j * g.plane + c, j, hp);
+    }
+    // momentum exchange: every link's contribution is rounded to 2^-40 fixed
+    // point in its own lane (the rounding is odd-symmetric, so opposite links
+    // of a closed body cancel exactly), summed over the warp in integers, and
+    // kept by lane 0 while the particle does not change
+    if (__any_sync(FULLW, p >= 0)) {
+      const int pmin = __reduce_min_sync(FULLW, p >= 0 ? p : 0x7fffffff);
+      const bool single = __all_sync(FULLW, p < 0 || p == pmin);
+      const float v[6] = {dP[0], dP[1], dP[2], dT[0], dT[1], dT[2]};
       long long iv[6];
-      for (int k = 0; k < 6; ++k) iv[k] = pacc >= 0 ? __double2ll_rn(acc[k] * FIX_SCALE) : 0LL;
-      for (int off = 16; off > 0; off >>= 1)
-        for (int k = 0; k < 6; ++k) iv[k] += __shfl_xor_sync(0xffffffffu, iv[k], off);
-      if (lane == 0)
-        for (int k = 0; k < 6; ++k) atomicAdd(reinterpret_cast<unsigned long long*>(pl.facc + 6 * p0 + k), (unsigned long long)iv[k]);
-    } else if (!uniform) {
-      if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
-    } else if (__any_sync(0xffffffffu, pacc >= 0)) {
-      // p0 < 0 but another lane holds sums (lane 0 idle): flush per lane
-      if (pacc >= 0) add_fixed(pl.facc, pacc, acc);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? fixed40(v[k]) : 0LL;
+      if (single) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          for (int o = 16; o > 0; o >>= 1) iv[k] += __shfl_xor_sync(FULLW, iv[k], o);
+        if (j == 0) {
+          if (pacc != pmin) {
+            if (pacc >= 0) add_fixed_ll(pl.facc, pacc, iacc);
+            pacc = pmin;
+            for (int k = 0; k < 6; ++k) iacc[k] = 0;
+          }
+          for (int k = 0; k < 6; ++k) iacc[k] += iv[k];
+        }
+      } else if (p >= 0) {  // links to several particles: per-link atomics
+        add_fixed_ll(pl.facc, p, iv);
+      }
     }
   }
+  if (j == 0 && pacc >= 0) add_fixed_ll(pl.facc, pacc, iacc);
 }
 
 template <int ST>
@@ -390,9 +471,26 @@ cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s) {
 
 template <int ST, bool FORCE>
 static cudaError_t launch_boundary_f(const BoundaryLaunch& L, cudaStream_t s) {
-  if (L.bb_mode == MI_BB_LADD) k_boundary<ST, FORCE, true><<<L.grid, 128, 0, s>>>(L);
-  else k_boundary<ST, FORCE, false><<<L.grid, 128, 0, s>>>(L);
+  if (L.bb_mode == MI_BB_LADD) k_boundary<ST, FORCE, true><<<L.grid, 256, 0, s>>>(L);
+  else k_boundary<ST, FORCE, false><<<L.grid, 256, 0, s>>>(L);
   return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_near_st(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.forcing) k_near<ST, true><<<L.grid, 128, 0, s>>>(L);
+  else k_near<ST, false><<<L.grid, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.pl.np == 0) return cudaSuccess;
+  switch (L.storage) {
+    case MI_STORE_F32: return launch_near_st<MI_STORE_F32>(L, s);
+    case MI_STORE_F16_DEV: return launch_near_st<MI_STORE_F16_DEV>(L, s);
+    case MI_STORE_BF16_DEV: return launch_near_st<MI_STORE_BF16_DEV>(L, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int ST>

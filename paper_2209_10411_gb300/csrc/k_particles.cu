@@ -174,18 +174,25 @@ __global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
     for (int a = 0; a < 3; ++a) L.P[p].lo_hist[L.cur_buf][a] = P.lo[a];
   const Region r = clip_region(P.lo, P.ext, 0, L.g);
   const double* R = P.R;
-  const double rt2 = P.Rt * P.Rt;
+  // x - X = (x - Xi) - Xf with Xi = floor(X): the integer part is exact in
+  // FP32, the fraction carries one FP32 rounding
+  const double Xi0 = floor(P.pos[0]), Xi1 = floor(P.pos[1]), Xi2 = floor(P.pos[2]);
+  const int xi0 = (int)Xi0, xi1 = (int)Xi1, xi2 = (int)Xi2;
+  const float xf0 = (float)(P.pos[0] - Xi0), xf1 = (float)(P.pos[1] - Xi1), xf2 = (float)(P.pos[2] - Xi2);
+  float Rf[9];
+  for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
+  const float rt = (float)P.Rt * (1.0f + 1e-6f) + 1e-4f, rt2 = rt * rt;
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
     const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
     const int x = r.lo[0] + (int)(rem - yi * n0);
     const int y = r.lo[1] + (int)yi;
     const int z = r.lo[2] + (int)zi;
-    const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
+    const float d0 = (float)(x - xi0) - xf0, d1 = (float)(y - xi1) - xf1, d2 = (float)(z - xi2) - xf2;
     if (d0 * d0 + d1 * d1 + d2 * d2 > rt2) continue;  // beyond the tight radius: fluid
-    const float b0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);
-    const float b1 = (float)(R[1] * d0 + R[4] * d1 + R[7] * d2);
-    const float b2 = (float)(R[2] * d0 + R[5] * d1 + R[8] * d2);
+    const float b0 = Rf[0] * d0 + Rf[3] * d1 + Rf[6] * d2;
+    const float b1 = Rf[1] * d0 + Rf[4] * d1 + Rf[7] * d2;
+    const float b2 = Rf[2] * d0 + Rf[5] * d1 + Rf[8] * d2;
     float f = 0.f;
     bool inside = false, decided = false;
     for (int b = 0; b < nb; ++b) {
@@ -259,10 +266,17 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
     const bool was = L.owner_prev[c] != OWNER_NONE;
     uint32_t mask = 0;
     if (!solid) {
+      const bool interior = (x > 0) & (x < L.g.nx - 1) & (y > 0) & (y < L.g.ny - 1) & (z > 0) & (z < L.g.nz - 1);
+      if (interior) {
+        const long long sy = L.g.nx, sz = (long long)L.g.nx * L.g.ny;
 #pragma unroll
-      for (int d = 1; d < 19; ++d) {
-        long long nbr;
-        if (neighbour(x, y, z, cx(d), cy(d), cz(d), L.g, nbr) && L.owner_cur[nbr] != OWNER_NONE) mask |= 1u << d;
+        for (int d = 1; d < 19; ++d)
+          if (__ldg(L.owner_cur + c + cx(d) + sy * cy(d) + sz * cz(d)) != OWNER_NONE) mask |= 1u << d;
+      } else {
+        for (int d = 1; d < 19; ++d) {
+          long long nbr;
+          if (neighbour(x, y, z, cx(d), cy(d), cz(d), L.g, nbr) && L.owner_cur[nbr] != OWNER_NONE) mask |= 1u << d;
+        }
       }
     }
     const bool isnew = !solid && was;
@@ -349,8 +363,11 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
       if (g >= 0.f) hi = q;
       else lo = q;
       float qn = q - g / gp;
-      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
-      const bool done = fabsf(qn - q) < 1e-6f || (hi - lo) < 1e-6f;
+      const bool newton = qn > lo && qn < hi;
+      if (!newton) qn = 0.5f * (lo + hi);
+      // a Newton step below 1e-5 leaves an error under the FP32 evaluation
+      // noise (~1e-6); a bisection step only bounds it by the bracket
+      const bool done = (newton && fabsf(qn - q) < 1e-5f) || (hi - lo) < 1e-6f;
       q = qn;
       if (done) break;
     }

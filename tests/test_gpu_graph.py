@@ -52,6 +52,7 @@ def test_graph_replay_is_bitwise_identical(dem_substeps):
         for x, y in zip(sa, sb):
             for key in x:
                 assert np.array_equal(x[key], y[key]), key
-    assert np.array_equal(a[1], b[1])
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+    fluid = a[3] == 0xFFFFFFFF  # values at solid nodes are unspecified
+    assert np.array_equal(a[1][:, fluid].view(np.uint32), b[1][:, fluid].view(np.uint32))
     assert np.abs(a[0][-1][0]["F_contact"]).max() > 0  # contacts were exercised
