@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -235,6 +236,8 @@ def run_mine(args):
     npart = len(scene.particles)
 
     sim.set_graphs(not args.no_graphs)
+    sim.step(1)
+    tuning = sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json")) if not args.no_tune else None
     for _ in range(max(3, args.warmup)):
         sim.step(1)
     sim.synchronize()
@@ -330,7 +333,7 @@ def run_mine(args):
                         "kernel": "k_bulk (D3Q19 stream-collide of every node)", "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes},
            "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
-           "graphs": not args.no_graphs,
+           "graphs": not args.no_graphs, "tuning": tuning,
            "contacts": contacts,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
@@ -354,6 +357,7 @@ def main():
     ap.add_argument("--lattice", default=None, help="nx,ny,nz override (small profiling cases)")
     ap.add_argument("--no-graphs", action="store_true", help="time individual launches instead of graph replays")
     ap.add_argument("--no-contacts", action="store_true", help="skip the contact-solves measurement")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
     CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
                    "lattice": [256, 256, 512], "storage": args.storage})

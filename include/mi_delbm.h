@@ -340,6 +340,19 @@ mi_status mi_mass_properties_noalloc(const double *balls_dev, int n_balls, doubl
  * run as individual launches. */
 mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
 
+/* Choose the launch shapes of the bulk kernel (threads per block along x,
+ * from 32/64/128/256) and of the list kernels (blocks per SM for the link,
+ * refill and boundary kernels, from 2/4/8/16/32) by timing each candidate
+ * with CUDA events on the handle's stream, and use the fastest from then on.
+ * With cache_path != NULL, a line {"key": ..., "bulk_block_x": .., "list_blocks_per_sm": ..}
+ * for this device, lattice, storage and particle count is read from that file
+ * if present (no timing), else appended after timing.  The list kernels are
+ * tuned only when the last step produced boundary nodes, so call this after
+ * at least one step.  The trial launches leave the populations untouched and
+ * clear the hydrodynamic force sums.  Synchronises; the chosen values are
+ * returned through the non-NULL pointers. */
+mi_status mi_delbm_autotune(mi_delbm *h, const char *cache_path, int *bulk_block_x, int *list_blocks_per_sm);
+
 /* Per-phase GPU timing with CUDA events on the handle's stream.  While
  * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
  * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of

@@ -97,6 +97,7 @@ _sig("mi_delbm_get_raw_populations", c_int, _P, _P, c_size_t)
 _sig("mi_delbm_get_device_view", c_int, _P, ctypes.POINTER(DeviceView))
 _sig("mi_delbm_set_timing", c_int, _P, c_int)
 _sig("mi_delbm_set_graphs", c_int, _P, c_int)
+_sig("mi_delbm_autotune", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int))
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
 _sig("mi_delbm_add_particle", c_int, _P, c_int, _P, _P, c_double, c_double, _P, _P, _P, _P,
@@ -270,6 +271,12 @@ class Simulation:
         return v
 
     # -- timing -----------------------------------------------------------
+    def autotune(self, cache_path=None):
+        bx, bl = c_int(0), c_int(0)
+        self._check(lib.mi_delbm_autotune(self.h, cache_path.encode() if cache_path else None,
+                                          ctypes.byref(bx), ctypes.byref(bl)))
+        return {"bulk_block_x": bx.value, "list_blocks_per_sm": bl.value}
+
     def set_graphs(self, on):
         self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))
 

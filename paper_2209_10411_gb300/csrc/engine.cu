@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -179,7 +181,8 @@ mi_status mi_delbm::phase_flag(cudaStream_t st) {
 mi_status mi_delbm::phase_links(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   ParticleLaunch L = particle_launch();
-  return launch_phase(this, st, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 8, st); });
+  return launch_phase(this, st, MI_PHASE_LINKS,
+                      [&] { return launch_links_q(L, sm_count * tune.list_blocks_per_sm, st); });
 }
 
 static BoundaryLaunch boundary_launch(const mi_delbm* h) {
@@ -191,7 +194,7 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
   L.storage = h->cfg.storage;
   L.forcing = h->forcing();
   L.bb_mode = h->cfg.bb_mode;
-  L.grid = h->sm_count * 8;
+  L.grid = h->sm_count * h->tune.list_blocks_per_sm;
   return L;
 }
 
@@ -803,6 +806,122 @@ mi_status mi_delbm_phase_times(mi_delbm* h, double ms[8], long long launches[8],
 long long mi_delbm_launch_count(const mi_delbm* h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: launch shapes of the bulk and list kernels, measured with CUDA
+// events and cached as one JSON object per line keyed by device and workload.
+// ---------------------------------------------------------------------------
+std::string mi_delbm::tune_key() const {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, cfg.device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, cfg.device);
+  std::ostringstream k;
+  k << "sm_" << major << minor << "/" << sm_count << "sm/" << cfg.nx << "x" << cfg.ny << "x" << cfg.nz << "/st"
+    << cfg.storage << "/np" << n_particles << "/bb" << cfg.bb_mode << (forcing() ? "/force" : "");
+  return k.str();
+}
+
+float mi_delbm::time_launches(int reps, const std::function<cudaError_t()>& fn) {
+  cudaEvent_t a = event_from_pool(), b = event_from_pool();
+  if (!a || !b) return -1.f;
+  for (int i = 0; i < 2; ++i) fn();  // warm-up
+  cudaEventRecord(a, stream);
+  for (int i = 0; i < reps; ++i) fn();
+  cudaEventRecord(b, stream);
+  float ms = -1.f;
+  if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  event_pool.push_back(a);
+  event_pool.push_back(b);
+  return ms / reps;
+}
+
+static bool read_cached(const char* path, const std::string& key, TuneChoice& t) {
+  if (!path) return false;
+  std::ifstream in(path);
+  std::string line;
+  const std::string tag = "\"key\": \"" + key + "\"";
+  while (std::getline(in, line)) {
+    if (line.find(tag) == std::string::npos) continue;
+    auto grab = [&](const char* name, int& v) {
+      const std::string n = std::string("\"") + name + "\": ";
+      const size_t p = line.find(n);
+      if (p == std::string::npos) return false;
+      v = std::atoi(line.c_str() + p + n.size());
+      return true;
+    };
+    int bx = 0, bl = 0;
+    if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && bx > 0 && bx <= 256 && bx % 32 == 0 &&
+        bl > 0 && bl <= 64) {
+      t.bulk_block_x = bx;
+      t.list_blocks_per_sm = bl;
+      return true;
+    }
+  }
+  return false;
+}
+
+extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int* bulk_block_x,
+                                       int* list_blocks_per_sm) {
+  if (!h) return MI_EINVAL;
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status st = h->sync("mi_delbm_autotune");
+  if (st != MI_OK) return st;
+  const std::string key = h->tune_key();
+  TuneChoice t = h->tune;
+  if (!read_cached(cache_path, key, t)) {
+    // bulk kernel: block width along x
+    BulkLaunch L;
+    L.A = h->pop[h->cur];
+    L.B = h->pop[h->cur ^ 1];
+    L.g = h->geom();
+    L.p = h->collide_params();
+    L.storage = h->cfg.storage;
+    L.forcing = h->forcing();
+    float best = 1e30f;
+    for (int bx : {32, 64, 128, 256}) {
+      if (bx > 32 && bx / 2 >= h->cfg.nx) break;
+      L.block_x = bx;
+      const float ms = h->time_launches(5, [&] { return launch_bulk(L, h->stream); });
+      if (ms > 0.f && ms < best) {
+        best = ms;
+        t.bulk_block_x = bx;
+      }
+    }
+    // list kernels: blocks per SM of the boundary kernel (lists of the last step)
+    if (h->n_particles > 0 && h->particles_ready) {
+      DevCounters c;
+      if (cudaMemcpy(&c, h->dctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess && c.n_bc > 0) {
+        best = 1e30f;
+        const TuneChoice keep = h->tune;
+        for (int bl : {2, 4, 8, 16, 32}) {
+          h->tune.list_blocks_per_sm = bl;
+          BoundaryLaunch B = boundary_launch(h);
+          const float ms = h->time_launches(5, [&] { return launch_boundary(B, h->stream); });
+          if (ms > 0.f && ms < best) {
+            best = ms;
+            t.list_blocks_per_sm = bl;
+          }
+        }
+        h->tune = keep;
+        // the trial launches added into the force sums: clear them
+        cudaMemsetAsync(h->facc, 0, sizeof(long long) * 6 * h->n_particles, h->stream);
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_autotune");
+    if (cache_path) {
+      std::ofstream out(cache_path, std::ios::app);
+      out << "{\"key\": \"" << key << "\", \"bulk_block_x\": " << t.bulk_block_x
+          << ", \"list_blocks_per_sm\": " << t.list_blocks_per_sm << "}\n";
+    }
+  }
+  t.tuned = true;
+  h->tune = t;
+  h->invalidate_graphs();
+  if (bulk_block_x) *bulk_block_x = t.bulk_block_x;
+  if (list_blocks_per_sm) *list_blocks_per_sm = t.list_blocks_per_sm;
+  return MI_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Particles

@@ -1,6 +1,7 @@
 // Handle state of libmi_delbm (internal; the C-ABI is include/mi_delbm.h).
 #pragma once
 
+#include <functional>
 #include <string>
 #include <utility>
 #include <vector>
@@ -13,7 +14,9 @@ struct TimedLaunch {
 };
 
 struct TuneChoice {
-  int bulk_block_x = 128;
+  int bulk_block_x = 128;     // threads per block of the bulk kernel (along x)
+  int list_blocks_per_sm = 8; // grid of the list kernels (links, refill, boundary, near) per SM
+  bool tuned = false;
 };
 
 struct mi_delbm {
@@ -107,6 +110,8 @@ struct mi_delbm {
   mi_status phase_integrate(bool with_contacts);
   mi_status phase_contact(cudaStream_t st);
   mi_status graph_step();
+  std::string tune_key() const;
+  float time_launches(int reps, const std::function<cudaError_t()>& fn);
   void invalidate_graphs();
   mi_status fork(cudaStream_t from, cudaStream_t to, int slot);
   mi_status join_record(cudaStream_t from, int slot);

@@ -297,7 +297,7 @@ __device__ __forceinline__ void add_fixed_ll(long long* facc, int p, const long 
 }  // namespace
 
 template <int ST, bool FORCE, bool LADD>
-__global__ void __launch_bounds__(256) k_boundary(BoundaryLaunch L) {
+__global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
   using T = typename Store<ST>::T;
   const T* __restrict__ A = static_cast<const T*>(L.A);
   T* __restrict__ B = static_cast<T*>(L.B);

@@ -56,3 +56,48 @@ def test_graph_replay_is_bitwise_identical(dem_substeps):
     fluid = a[3] == 0xFFFFFFFF  # values at solid nodes are unspecified
     assert np.array_equal(a[1][:, fluid].view(np.uint32), b[1][:, fluid].view(np.uint32))
     assert np.abs(a[0][-1][0]["F_contact"]).max() > 0  # contacts were exercised
+
+
+def test_autotune_cache_and_bitwise_results(tmp_path):
+    """The autotuner's launch shapes change no result bit (all sums are
+    order-free), and a second handle reads the cached choice."""
+    B = binding()
+    shape = (48, 48, 40)
+    parts = _cluster(7)
+    nx, ny, nz = shape
+    u = 0.02 * scenes.velocity_field_noise(shape, 3)
+    f0 = lbm.equilibrium(np.ones((nz, ny, nx)), u).astype(np.float32)
+    cache = str(tmp_path / "tune.json")
+
+    def make():
+        sim = B.Simulation(*shape, tau=0.8, kn=PARAMS["kn"], kt=PARAMS["kt"], eta_n=PARAMS["eta_n"],
+                           eta_t=PARAMS["eta_t"], mu_s=PARAMS["mu_s"], max_particles=64)
+        for P in parts:
+            sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"],
+                             P["omega"], mass_props={"mass": P["mass"], "volume": P["volume"],
+                                                     "inertia": P["inertia"]})
+        sim.set_populations(f0)
+        return sim
+
+    a, b = make(), make()
+    a.step(1)
+    b.step(1)
+    t1 = a.autotune(cache)
+    assert t1["bulk_block_x"] in (32, 64, 128, 256) and t1["list_blocks_per_sm"] in (2, 4, 8, 16, 32)
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"bulk_block_x": %d' % t1["bulk_block_x"] in lines[0]
+    t2 = b.autotune(cache)  # same key: read back, nothing appended
+    assert t2 == t1 and len(open(cache).read().strip().splitlines()) == 1
+    c = make()  # never tuned
+    c.step(1)
+    for sim in (a, b, c):
+        sim.step(3)
+    ra, rc = a.get_raw_populations(), c.get_raw_populations()
+    _, own = a.node_classes()
+    fluid = own == 0xFFFFFFFF
+    assert np.array_equal(ra[:, fluid].view(np.uint32), rc[:, fluid].view(np.uint32))
+    fa, fc = a.forces(), c.forces()
+    for key in fa:
+        assert np.array_equal(fa[key], fc[key]), key
+    for sim in (a, b, c):
+        sim.close()
