@@ -212,6 +212,37 @@ def contact_solves(B, scenes, args):
             "ms_per_substep": ms, "particles": len(sc.particles), "workload": sc.name}
 
 
+def storage_variant(B, scene, storage, steps, stream_obj):
+    """The same coupled step with 16-bit deviation storage: MLUPS (graph
+    replays) and the bulk kernel's roofline fraction (individual launches)."""
+    import torch
+    sim = build_sim(B, scene, storage, stream_obj.cuda_stream)
+    sim.step(1)
+    sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json"))
+    for _ in range(5):
+        sim.step(1)
+    sim.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream_obj)
+    for _ in range(steps):
+        sim.step(1)
+    ev1.record(stream_obj)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    sim.set_timing(True)
+    sim.phase_times(reset=True)
+    for _ in range(50):
+        sim.step(1)
+    bulk_ms, bulk_n = sim.phase_times(reset=True)["bulk"]
+    sim.close()
+    nx, ny, nz = scene.shape
+    ncell = nx * ny * nz
+    gbs = BYTES_PER_NODE[storage] * ncell / (bulk_ms / bulk_n * 1e-3) / 1e9
+    peak, kind = _peaks()
+    return {"value": ncell / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bytes_per_node": BYTES_PER_NODE[storage]}
+
+
 def run_mine(args):
     import torch
     rank, world, local = _dist_env()
@@ -288,6 +319,10 @@ def run_mine(args):
     contacts = None
     if not args.no_contacts and rank == 0:
         contacts = contact_solves(B, scenes, args)
+    variants = None
+    if storage == 0 and not args.no_variants and rank == 0:
+        variants = {name: storage_variant(B, scene, st, max(50, min(args.steps, 200)), stream)
+                    for name, st in (("f16-dev", 1), ("bf16-dev", 2))}
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node
@@ -334,6 +369,7 @@ def run_mine(args):
                         "algorithmic_bytes_per_launch": alg_bytes},
            "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
            "graphs": not args.no_graphs, "tuning": tuning,
+           "storage_variants": variants,
            "contacts": contacts,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
@@ -358,6 +394,7 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="time individual launches instead of graph replays")
     ap.add_argument("--no-contacts", action="store_true", help="skip the contact-solves measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage measurements")
     args = ap.parse_args()
     CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
                    "lattice": [256, 256, 512], "storage": args.storage})

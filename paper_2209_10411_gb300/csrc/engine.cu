@@ -306,6 +306,7 @@ mi_status mi_delbm::phase_bulk() {
   L.storage = cfg.storage;
   L.forcing = forcing();
   L.block_x = tune.bulk_block_x;
+  L.rows = tune.bulk_rows;
   return launch_phase(this, stream, MI_PHASE_BULK, [&] { return launch_bulk(L, stream); });
 }
 
@@ -640,6 +641,7 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     return MI_ECUDA;
   }
   h->tune.bulk_block_x = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
+  h->tune.bulk_rows = cfg->storage == MI_STORE_F32 ? 1 : 2;
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && sms > 0)
@@ -849,11 +851,12 @@ static bool read_cached(const char* path, const std::string& key, TuneChoice& t)
       v = std::atoi(line.c_str() + p + n.size());
       return true;
     };
-    int bx = 0, bl = 0;
-    if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && bx > 0 && bx <= 256 && bx % 32 == 0 &&
-        bl > 0 && bl <= 64) {
+    int bx = 0, bl = 0, rows = 0;
+    if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && grab("bulk_rows", rows) && bx > 0 &&
+        bx <= 256 && bx % 32 == 0 && bl > 0 && bl <= 64 && (rows == 1 || rows == 2)) {
       t.bulk_block_x = bx;
       t.list_blocks_per_sm = bl;
+      t.bulk_rows = rows;
       return true;
     }
   }
@@ -878,15 +881,18 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
     L.storage = h->cfg.storage;
     L.forcing = h->forcing();
     float best = 1e30f;
-    for (int bx : {32, 64, 128, 256}) {
-      if (bx > 32 && bx / 2 >= h->cfg.nx) break;
-      L.block_x = bx;
-      const float ms = h->time_launches(5, [&] { return launch_bulk(L, h->stream); });
-      if (ms > 0.f && ms < best) {
-        best = ms;
-        t.bulk_block_x = bx;
+    for (int rows : {1, 2})
+      for (int bx : {32, 64, 128, 256}) {
+        if (bx > 32 && bx / 2 >= h->cfg.nx) break;
+        L.block_x = bx;
+        L.rows = rows;
+        const float ms = h->time_launches(5, [&] { return launch_bulk(L, h->stream); });
+        if (ms > 0.f && ms < best) {
+          best = ms;
+          t.bulk_block_x = bx;
+          t.bulk_rows = rows;
+        }
       }
-    }
     // list kernels: blocks per SM of the boundary kernel (lists of the last step)
     if (h->n_particles > 0 && h->particles_ready) {
       DevCounters c;
@@ -912,7 +918,7 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
     if (cache_path) {
       std::ofstream out(cache_path, std::ios::app);
       out << "{\"key\": \"" << key << "\", \"bulk_block_x\": " << t.bulk_block_x
-          << ", \"list_blocks_per_sm\": " << t.list_blocks_per_sm << "}\n";
+          << ", \"bulk_rows\": " << t.bulk_rows << ", \"list_blocks_per_sm\": " << t.list_blocks_per_sm << "}\n";
     }
   }
   t.tuned = true;

@@ -15,6 +15,7 @@ struct TimedLaunch {
 
 struct TuneChoice {
   int bulk_block_x = 128;     // threads per block of the bulk kernel (along x)
+  int bulk_rows = 1;          // rows per thread of the bulk kernel
   int list_blocks_per_sm = 8; // grid of the list kernels (links, refill, boundary, near) per SM
   bool tuned = false;
 };

@@ -56,14 +56,12 @@ __device__ __forceinline__ void collide_store(const float (&h)[19], typename Sto
   }
 }
 
-// Pull streaming (with halfway bounce-back at domain walls) and collision of
-// node (x, y, z), c its linear index.
-template <int ST, bool FORCE>
-__device__ __forceinline__ void update_node(const typename Store<ST>::T* __restrict__ A,
-                                            typename Store<ST>::T* __restrict__ B, const LatticeGeom& g,
-                                            const CollideParams& P, int x, int y, int z, long long c) {
+// Pull streaming (with halfway bounce-back at domain walls) of node (x, y, z),
+// c its linear index: the 19 incoming deviations h_i = f_i - w_i.
+template <int ST>
+__device__ __forceinline__ void pull_node(const typename Store<ST>::T* __restrict__ A, const LatticeGeom& g,
+                                          const CollideParams& P, int x, int y, int z, long long c, float (&h)[19]) {
   const long long nxy = (long long)g.nx * g.ny;
-  float h[19];
   const bool interior = (x > 0) & (x < g.nx - 1) & (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
   if (interior) {
 #pragma unroll
@@ -90,38 +88,55 @@ __device__ __forceinline__ void update_node(const typename Store<ST>::T* __restr
       }
     }
   }
+}
+
+// Pull and collide one node.
+template <int ST, bool FORCE>
+__device__ __forceinline__ void update_node(const typename Store<ST>::T* __restrict__ A,
+                                            typename Store<ST>::T* __restrict__ B, const LatticeGeom& g,
+                                            const CollideParams& P, int x, int y, int z, long long c) {
+  float h[19];
+  pull_node<ST>(A, g, P, x, y, z, c, h);
   collide_store<ST, FORCE>(h, B, g.plane, c, P);
 }
 
-// Every node of the lattice.  With particles this runs concurrently with the
-// particle phases: boundary nodes are rewritten afterwards by k_boundary, solid
-// nodes hold unspecified values, and the nodes next to a node uncovered this
-// step (whose refilled populations this kernel may not have seen) are
+// Every node of the lattice, ROWS consecutive rows (y) per thread: all pulls
+// of a thread are issued before its collisions, so that 16-bit storages keep
+// as many bytes in flight as FP32.  With particles this runs concurrently with
+// the particle phases: boundary nodes are rewritten afterwards by k_boundary,
+// solid nodes hold unspecified values, and the nodes next to a node uncovered
+// this step (whose refilled populations this kernel may not have seen) are
 // recomputed by k_near.  Nodes anywhere else have no solid or uncovered
 // neighbour, so their update here is final.
-template <int ST, bool FORCE>
+template <int ST, bool FORCE, int ROWS>
 __global__ void __launch_bounds__(256) k_bulk(const typename Store<ST>::T* __restrict__ A,
                                               typename Store<ST>::T* __restrict__ B, LatticeGeom g,
                                               CollideParams P) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y0 = blockIdx.y * ROWS, z = blockIdx.z;
   if (x >= g.nx) return;
-  const long long c = x + (long long)g.nx * (y + (long long)g.ny * z);
-  update_node<ST, FORCE>(A, B, g, P, x, y, z, c);
+  float h[ROWS][19];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+    if (y0 + r < g.ny) pull_node<ST>(A, g, P, x, y0 + r, z, x + (long long)g.nx * (y0 + r + (long long)g.ny * z), h[r]);
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+    if (y0 + r < g.ny) collide_store<ST, FORCE>(h[r], B, g.plane, x + (long long)g.nx * (y0 + r + (long long)g.ny * z), P);
 }
 
-template <int ST, bool FORCE>
+template <int ST, bool FORCE, int ROWS>
 static cudaError_t launch_bulk_t(const BulkLaunch& L, cudaStream_t s) {
   using T = typename Store<ST>::T;
   const int bx = L.block_x;
-  dim3 grid((L.g.nx + bx - 1) / bx, L.g.ny, L.g.nz);
-  k_bulk<ST, FORCE><<<grid, bx, 0, s>>>(static_cast<const T*>(L.A), static_cast<T*>(L.B), L.g, L.p);
+  dim3 grid((L.g.nx + bx - 1) / bx, (L.g.ny + ROWS - 1) / ROWS, L.g.nz);
+  k_bulk<ST, FORCE, ROWS><<<grid, bx, 0, s>>>(static_cast<const T*>(L.A), static_cast<T*>(L.B), L.g, L.p);
   return cudaGetLastError();
 }
 
 template <int ST>
 static cudaError_t launch_bulk_st(const BulkLaunch& L, cudaStream_t s) {
-  return L.forcing ? launch_bulk_t<ST, true>(L, s) : launch_bulk_t<ST, false>(L, s);
+  if (L.rows == 2) return L.forcing ? launch_bulk_t<ST, true, 2>(L, s) : launch_bulk_t<ST, false, 2>(L, s);
+  return L.forcing ? launch_bulk_t<ST, true, 1>(L, s) : launch_bulk_t<ST, false, 1>(L, s);
 }
 
 cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s) {

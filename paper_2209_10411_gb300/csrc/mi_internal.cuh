@@ -100,6 +100,7 @@ struct BulkLaunch {
   int storage;
   bool forcing;
   int block_x;         // threads per block along x
+  int rows = 1;        // consecutive rows (y) per thread: 1 or 2
 };
 cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s);
 
