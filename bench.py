@@ -218,7 +218,7 @@ def storage_variant(B, scene, storage, steps, stream_obj):
     import torch
     sim = build_sim(B, scene, storage, stream_obj.cuda_stream)
     sim.step(1)
-    sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json"))
+    tuning = sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json"))
     for _ in range(5):
         sim.step(1)
     sim.synchronize()
@@ -240,7 +240,7 @@ def storage_variant(B, scene, storage, steps, stream_obj):
     gbs = BYTES_PER_NODE[storage] * ncell / (bulk_ms / bulk_n * 1e-3) / 1e9
     peak, kind = _peaks()
     return {"value": ncell / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
-            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bytes_per_node": BYTES_PER_NODE[storage]}
+            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bytes_per_node": BYTES_PER_NODE[storage], "tuning": tuning}
 
 
 def run_mine(args):

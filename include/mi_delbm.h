@@ -353,6 +353,18 @@ mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
  * returned through the non-NULL pointers. */
 mi_status mi_delbm_autotune(mi_delbm *h, const char *cache_path, int *bulk_block_x, int *list_blocks_per_sm);
 
+/* Set the launch shapes directly (what mi_delbm_autotune chooses): bulk
+ * kernel threads per block along x (32..256, a multiple of 32; at most 128
+ * with pairs), rows per thread (1 or 2), paired nodes (0: no; 1 or 2: two
+ * x-adjacent nodes per thread with paired accesses, used only when nx is
+ * even; for 16-bit storages 1 and 2 select a 64- or 80-register budget),
+ * list-kernel blocks per SM (1..64).  Results do not depend on them. */
+mi_status mi_delbm_set_tuning(mi_delbm *h, int bulk_block_x, int bulk_rows, int bulk_pairs, int list_blocks_per_sm);
+
+/* The launch shapes in use (any pointer may be NULL). */
+mi_status mi_delbm_get_tuning(const mi_delbm *h, int *bulk_block_x, int *bulk_rows, int *bulk_pairs,
+                              int *list_blocks_per_sm);
+
 /* Per-phase GPU timing with CUDA events on the handle's stream.  While
  * enabled, each launch of a phase inside mi_delbm_step is bracketed by events.
  * mi_delbm_phase_times synchronises and returns, per phase bit b (index b of

@@ -97,6 +97,9 @@ _sig("mi_delbm_get_raw_populations", c_int, _P, _P, c_size_t)
 _sig("mi_delbm_get_device_view", c_int, _P, ctypes.POINTER(DeviceView))
 _sig("mi_delbm_set_timing", c_int, _P, c_int)
 _sig("mi_delbm_set_graphs", c_int, _P, c_int)
+_sig("mi_delbm_set_tuning", c_int, _P, c_int, c_int, c_int, c_int)
+_sig("mi_delbm_get_tuning", c_int, _P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+     ctypes.POINTER(c_int))
 _sig("mi_delbm_autotune", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int))
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
@@ -271,11 +274,21 @@ class Simulation:
         return v
 
     # -- timing -----------------------------------------------------------
+    def set_tuning(self, bulk_block_x=128, bulk_rows=1, bulk_pairs=False, list_blocks_per_sm=8):
+        self._check(lib.mi_delbm_set_tuning(self.h, int(bulk_block_x), int(bulk_rows), int(bulk_pairs),
+                                            int(list_blocks_per_sm)))
+
     def autotune(self, cache_path=None):
         bx, bl = c_int(0), c_int(0)
         self._check(lib.mi_delbm_autotune(self.h, cache_path.encode() if cache_path else None,
                                           ctypes.byref(bx), ctypes.byref(bl)))
-        return {"bulk_block_x": bx.value, "list_blocks_per_sm": bl.value}
+        return self.get_tuning()
+
+    def get_tuning(self):
+        v = [c_int(0) for _ in range(4)]
+        self._check(lib.mi_delbm_get_tuning(self.h, *[ctypes.byref(x) for x in v]))
+        return {"bulk_block_x": v[0].value, "bulk_rows": v[1].value, "bulk_pairs": v[2].value,
+                "list_blocks_per_sm": v[3].value}
 
     def set_graphs(self, on):
         self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))

@@ -307,6 +307,8 @@ mi_status mi_delbm::phase_bulk() {
   L.forcing = forcing();
   L.block_x = tune.bulk_block_x;
   L.rows = tune.bulk_rows;
+  L.pairs = tune.bulk_pairs != 0;
+  L.pair_mode = tune.bulk_pairs;
   return launch_phase(this, stream, MI_PHASE_BULK, [&] { return launch_bulk(L, stream); });
 }
 
@@ -640,8 +642,9 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     mi_delbm_destroy(h);
     return MI_ECUDA;
   }
-  h->tune.bulk_block_x = cfg->nx >= 128 ? 128 : (cfg->nx >= 64 ? 64 : 32);
-  h->tune.bulk_rows = cfg->storage == MI_STORE_F32 ? 1 : 2;
+  h->tune.bulk_block_x = cfg->nx >= 256 ? 128 : (cfg->nx >= 128 ? 64 : 32);
+  h->tune.bulk_rows = 1;
+  h->tune.bulk_pairs = 0;
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && sms > 0)
@@ -851,16 +854,44 @@ static bool read_cached(const char* path, const std::string& key, TuneChoice& t)
       v = std::atoi(line.c_str() + p + n.size());
       return true;
     };
-    int bx = 0, bl = 0, rows = 0;
-    if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && grab("bulk_rows", rows) && bx > 0 &&
-        bx <= 256 && bx % 32 == 0 && bl > 0 && bl <= 64 && (rows == 1 || rows == 2)) {
+    int bx = 0, bl = 0, rows = 0, pairs = -1;
+    if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && grab("bulk_rows", rows) &&
+        grab("bulk_pairs", pairs) && bx > 0 && bx <= 256 && bx % 32 == 0 && bl > 0 && bl <= 64 &&
+        (rows == 1 || rows == 2) && (pairs >= 0 && pairs <= 2)) {
       t.bulk_block_x = bx;
       t.list_blocks_per_sm = bl;
       t.bulk_rows = rows;
+      t.bulk_pairs = pairs;
       return true;
     }
   }
   return false;
+}
+
+extern "C" mi_status mi_delbm_set_tuning(mi_delbm* h, int bulk_block_x, int bulk_rows, int bulk_pairs,
+                                         int list_blocks_per_sm) {
+  if (!h) return MI_EINVAL;
+  if (bulk_block_x < 32 || bulk_block_x > 256 || bulk_block_x % 32 != 0 || (bulk_rows != 1 && bulk_rows != 2) ||
+      bulk_pairs < 0 || bulk_pairs > 2 || (bulk_pairs && bulk_block_x > 128) || list_blocks_per_sm < 1 ||
+      list_blocks_per_sm > 64)
+    return h->fail(MI_EINVAL, "mi_delbm_set_tuning: block_x 32..256 (multiple of 32, <= 128 with pairs), rows 1|2, "
+                              "pairs 0|1|2, list blocks per SM 1..64");
+  h->tune.bulk_block_x = bulk_block_x;
+  h->tune.bulk_rows = bulk_rows;
+  h->tune.bulk_pairs = bulk_pairs;
+  h->tune.list_blocks_per_sm = list_blocks_per_sm;
+  h->invalidate_graphs();
+  return MI_OK;
+}
+
+extern "C" mi_status mi_delbm_get_tuning(const mi_delbm* h, int* bulk_block_x, int* bulk_rows, int* bulk_pairs,
+                                         int* list_blocks_per_sm) {
+  if (!h) return MI_EINVAL;
+  if (bulk_block_x) *bulk_block_x = h->tune.bulk_block_x;
+  if (bulk_rows) *bulk_rows = h->tune.bulk_rows;
+  if (bulk_pairs) *bulk_pairs = h->tune.bulk_pairs;
+  if (list_blocks_per_sm) *list_blocks_per_sm = h->tune.list_blocks_per_sm;
+  return MI_OK;
 }
 
 extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int* bulk_block_x,
@@ -881,18 +912,28 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
     L.storage = h->cfg.storage;
     L.forcing = h->forcing();
     float best = 1e30f;
-    for (int rows : {1, 2})
+    // variants: 1 row, 2 rows, paired nodes (two register budgets for 16-bit storages)
+    for (int variant = 0; variant < 4; ++variant) {
+      const int pairs = variant >= 2 ? variant - 1 : 0;
+      if (pairs && (h->cfg.nx % 2) != 0) continue;
+      if (pairs == 2 && h->cfg.storage == MI_STORE_F32) continue;
       for (int bx : {32, 64, 128, 256}) {
-        if (bx > 32 && bx / 2 >= h->cfg.nx) break;
+        const int span = pairs ? 2 * bx : bx;
+        if (bx > 32 && span / 2 >= h->cfg.nx) break;
+        if (pairs && bx > 128) break;
         L.block_x = bx;
-        L.rows = rows;
+        L.rows = variant == 1 ? 2 : 1;
+        L.pairs = pairs != 0;
+        L.pair_mode = pairs;
         const float ms = h->time_launches(5, [&] { return launch_bulk(L, h->stream); });
         if (ms > 0.f && ms < best) {
           best = ms;
           t.bulk_block_x = bx;
-          t.bulk_rows = rows;
+          t.bulk_rows = L.rows;
+          t.bulk_pairs = pairs;
         }
       }
+    }
     // list kernels: blocks per SM of the boundary kernel (lists of the last step)
     if (h->n_particles > 0 && h->particles_ready) {
       DevCounters c;
@@ -918,7 +959,8 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
     if (cache_path) {
       std::ofstream out(cache_path, std::ios::app);
       out << "{\"key\": \"" << key << "\", \"bulk_block_x\": " << t.bulk_block_x
-          << ", \"bulk_rows\": " << t.bulk_rows << ", \"list_blocks_per_sm\": " << t.list_blocks_per_sm << "}\n";
+          << ", \"bulk_rows\": " << t.bulk_rows << ", \"bulk_pairs\": " << t.bulk_pairs
+          << ", \"list_blocks_per_sm\": " << t.list_blocks_per_sm << "}\n";
     }
   }
   t.tuned = true;

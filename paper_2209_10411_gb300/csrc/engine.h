@@ -16,6 +16,8 @@ struct TimedLaunch {
 struct TuneChoice {
   int bulk_block_x = 128;     // threads per block of the bulk kernel (along x)
   int bulk_rows = 1;          // rows per thread of the bulk kernel
+  int bulk_pairs = 0;         // 0 one node per thread; 1, 2: two x-adjacent nodes per thread with paired
+                              // accesses (nx even; for 16-bit storages 1 and 2 select the register budget)
   int list_blocks_per_sm = 8; // grid of the list kernels (links, refill, boundary, near) per SM
   bool tuned = false;
 };

@@ -19,9 +19,8 @@ namespace mi {
 //   rho = 1 + sum h_i, j = sum e_i h_i (sum w_i = 1, sum w_i e_i = 0)
 //   f_eq,i - w_i = w_i (rho - 1) + w_i rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)
 //   h+_i = h_i + omega (f_eq,i - w_i - h_i)   [+ Guo source]
-template <int ST, bool FORCE>
-__device__ __forceinline__ void collide_store(const float (&h)[19], typename Store<ST>::T* __restrict__ B,
-                                              long long plane, long long c, const CollideParams& P) {
+template <bool FORCE>
+__device__ __forceinline__ void collide_inplace(float (&h)[19], const CollideParams& P) {
   float drho = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i) drho += h[i];
@@ -52,8 +51,16 @@ __device__ __forceinline__ void collide_store(const float (&h)[19], typename Sto
       const float uF = ux * P.force[0] + uy * P.force[1] + uz * P.force[2];
       hp += (1.0f - 0.5f * om) * wq(i) * (3.0f * (eF - uF) + 9.0f * eu * eF);
     }
-    Store<ST>::put(B + i * plane + c, i, hp);
+    h[i] = hp;
   }
+}
+
+template <int ST, bool FORCE>
+__device__ __forceinline__ void collide_store(float (&h)[19], typename Store<ST>::T* __restrict__ B,
+                                              long long plane, long long c, const CollideParams& P) {
+  collide_inplace<FORCE>(h, P);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Store<ST>::put(B + i * plane + c, i, h[i]);
 }
 
 // Pull streaming (with halfway bounce-back at domain walls) of node (x, y, z),
@@ -133,14 +140,157 @@ static cudaError_t launch_bulk_t(const BulkLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Every node, two x-adjacent nodes (x0, x0 + 1), x0 even, per thread: the
+// pulls of the 9 directions with e_x = 0 are one paired load each; for
+// e_x = +1 (-1) the pair is completed by the high (low) element of the
+// previous (next) lane's paired load, fetched by a shuffle (a scalar load at
+// the warp's edge).  Both collisions store paired.  Nodes on the lattice's
+// boundary rows and edge columns are pulled again by the general path.  The
+// same concurrency contract as k_bulk.  Requires nx even.
+template <int ST, bool FORCE>
+__global__ void __launch_bounds__(128) k_bulk_pairs(const typename Store<ST>::T* __restrict__ A,
+                                                    typename Store<ST>::T* __restrict__ B, LatticeGeom g,
+                                                    CollideParams P) {
+  using T = typename Store<ST>::T;
+  using PR = Pair<ST>;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool active = x0 < g.nx;
+  const int xc = active ? x0 : g.nx - 2;  // idle lanes still take part in the shuffles
+  float h0[19], h1[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const int ys = min(max(y - cy(i), 0), g.ny - 1), zs = min(max(z - cz(i), 0), g.nz - 1);
+    const T* row = A + i * g.plane + ((long long)zs * g.ny + ys) * g.nx;
+    const typename PR::P v = PR::load(row + xc);
+    if (cx(i) == 0) {
+      h0[i] = PR::lo(v, i);
+      h1[i] = PR::hi(v, i);
+    } else if (cx(i) == 1) {  // node x0 pulls from x0 - 1
+      const typename PR::P u = PR::shfl_up(v);
+      float prev = PR::hi(u, i);
+      if (lane == 0) prev = xc > 0 ? Store<ST>::dev(row + xc - 1, i) : 0.f;
+      h0[i] = prev;
+      h1[i] = PR::lo(v, i);
+    } else {  // node x0 + 1 pulls from x0 + 2
+      const typename PR::P u = PR::shfl_down(v);
+      float next = PR::lo(u, i);
+      if (lane == 31) next = xc + 2 < g.nx ? Store<ST>::dev(row + xc + 2, i) : 0.f;
+      h0[i] = PR::hi(v, i);
+      h1[i] = next;
+    }
+  }
+  if (!active) return;
+  const long long c0 = x0 + (long long)g.nx * (y + (long long)g.ny * z);
+  const bool rows_interior = (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
+  if (!rows_interior || x0 == 0) pull_node<ST>(A, g, P, x0, y, z, c0, h0);
+  if (!rows_interior || x0 + 1 == g.nx - 1) pull_node<ST>(A, g, P, x0 + 1, y, z, c0 + 1, h1);
+  collide_inplace<FORCE>(h0, P);
+  collide_inplace<FORCE>(h1, P);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) PR::put(B + i * g.plane + c0, i, h0[i], h1[i]);
+}
+
+// 16-bit storages: the same paired scheme with both nodes' incoming and
+// outgoing values kept packed, one 32-bit register per direction for the two
+// nodes, so that a thread needs about as many registers as the scalar kernel
+// and a warp keeps twice the bytes in flight.
+template <int ST, bool FORCE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_bulk_pairs16(const typename Store<ST>::T* __restrict__ A,
+                                                         typename Store<ST>::T* __restrict__ B, LatticeGeom g,
+                                                         CollideParams P) {
+  using T = typename Store<ST>::T;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool active = x0 < g.nx;
+  const int xc = active ? x0 : g.nx - 2;
+  unsigned in[19];  // low half: node x0, high half: node x0 + 1
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const int ys = min(max(y - cy(i), 0), g.ny - 1), zs = min(max(z - cz(i), 0), g.nz - 1);
+    const unsigned short* row =
+        reinterpret_cast<const unsigned short*>(A + i * g.plane + ((long long)zs * g.ny + ys) * g.nx);
+    const unsigned v = __ldg(reinterpret_cast<const unsigned*>(row + xc));
+    if (cx(i) == 0) {
+      in[i] = v;
+    } else if (cx(i) == 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, v, 1);
+      unsigned prev = u >> 16;
+      if (lane == 0) prev = xc > 0 ? (unsigned)__ldg(row + xc - 1) : 0u;
+      in[i] = prev | (v << 16);
+    } else {
+      const unsigned u = __shfl_down_sync(0xffffffffu, v, 1);
+      unsigned next = u & 0xFFFFu;
+      if (lane == 31) next = xc + 2 < g.nx ? (unsigned)__ldg(row + xc + 2) : 0u;
+      in[i] = (v >> 16) | (next << 16);
+    }
+  }
+  if (!active) return;
+  const long long c0 = x0 + (long long)g.nx * (y + (long long)g.ny * z);
+  const bool rows_interior = (y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1);
+  unsigned out[19];
+  {
+    float h[19];
+    if (!rows_interior || x0 == 0) {
+      pull_node<ST>(A, g, P, x0, y, z, c0, h);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 19; ++i) h[i] = dev16<ST>((unsigned short)(in[i] & 0xFFFFu));
+    }
+    collide_inplace<FORCE>(h, P);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) out[i] = pack16<ST>(h[i]);
+  }
+  {
+    float h[19];
+    if (!rows_interior || x0 + 1 == g.nx - 1) {
+      pull_node<ST>(A, g, P, x0 + 1, y, z, c0 + 1, h);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 19; ++i) h[i] = dev16<ST>((unsigned short)(in[i] >> 16));
+    }
+    collide_inplace<FORCE>(h, P);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) out[i] |= (unsigned)pack16<ST>(h[i]) << 16;
+  }
+#pragma unroll
+  for (int i = 0; i < 19; ++i) __stcs(reinterpret_cast<unsigned*>(B + i * g.plane + c0), out[i]);
+}
+
+template <int ST, bool FORCE>
+static cudaError_t launch_bulk_pairs_t(const BulkLaunch& L, cudaStream_t s) {
+  using T = typename Store<ST>::T;
+  const int bx = L.block_x;
+  const int npair = L.g.nx / 2;
+  dim3 grid((npair + bx - 1) / bx, L.g.ny, L.g.nz);
+  if (ST == MI_STORE_F32)
+    k_bulk_pairs<ST, FORCE><<<grid, bx, 0, s>>>(static_cast<const T*>(L.A), static_cast<T*>(L.B), L.g, L.p);
+  else {
+    constexpr int S16 = ST == MI_STORE_F32 ? MI_STORE_F16_DEV : ST;
+    using T16 = typename Store<S16>::T;
+    if (L.pair_mode == 2)
+      k_bulk_pairs16<S16, FORCE, 6><<<grid, bx, 0, s>>>(reinterpret_cast<const T16*>(L.A), reinterpret_cast<T16*>(L.B),
+                                                        L.g, L.p);
+    else
+      k_bulk_pairs16<S16, FORCE, 8><<<grid, bx, 0, s>>>(reinterpret_cast<const T16*>(L.A), reinterpret_cast<T16*>(L.B),
+                                                        L.g, L.p);
+  }
+  return cudaGetLastError();
+}
+
 template <int ST>
 static cudaError_t launch_bulk_st(const BulkLaunch& L, cudaStream_t s) {
+  if (L.pairs && L.g.nx % 2 == 0 && L.g.nx >= 2)
+    return L.forcing ? launch_bulk_pairs_t<ST, true>(L, s) : launch_bulk_pairs_t<ST, false>(L, s);
   if (L.rows == 2) return L.forcing ? launch_bulk_t<ST, true, 2>(L, s) : launch_bulk_t<ST, false, 2>(L, s);
   return L.forcing ? launch_bulk_t<ST, true, 1>(L, s) : launch_bulk_t<ST, false, 1>(L, s);
 }
 
 cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s) {
   if (L.block_x <= 0 || L.block_x > 256 || (L.block_x % 32) != 0) return cudaErrorInvalidValue;
+  if (L.pairs && L.block_x > 128) return cudaErrorInvalidValue;
   switch (L.storage) {
     case MI_STORE_F32: return launch_bulk_st<MI_STORE_F32>(L, s);
     case MI_STORE_F16_DEV: return launch_bulk_st<MI_STORE_F16_DEV>(L, s);

@@ -75,6 +75,67 @@ template <> struct Store<MI_STORE_BF16_DEV> {
 
 inline size_t store_bytes(int st) { return st == MI_STORE_F32 ? 4 : 2; }
 
+// Two x-adjacent stored elements read or written as one aligned access
+// (the first element at an even index).  P is the register type of a pair.
+template <int ST> struct Pair;
+template <> struct Pair<MI_STORE_F32> {
+  using P = float2;
+  static __device__ __forceinline__ P load(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+  static __device__ __forceinline__ float lo(P v, int i) { return v.x - wq(i); }
+  static __device__ __forceinline__ float hi(P v, int i) { return v.y - wq(i); }
+  static __device__ __forceinline__ void put(float* p, int i, float a, float b) {
+    __stcs(reinterpret_cast<float2*>(p), make_float2(a + wq(i), b + wq(i)));
+  }
+  static __device__ __forceinline__ P shfl_up(P v) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+  }
+  static __device__ __forceinline__ P shfl_down(P v) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+  }
+};
+template <> struct Pair<MI_STORE_F16_DEV> {
+  using P = unsigned int;
+  static __device__ __forceinline__ P load(const __half* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+  static __device__ __forceinline__ float lo(P v, int) { return __half2float(__ushort_as_half((unsigned short)(v & 0xFFFFu))); }
+  static __device__ __forceinline__ float hi(P v, int) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
+  static __device__ __forceinline__ void put(__half* p, int, float a, float b) {
+    const unsigned int v = (unsigned int)__half_as_ushort(__float2half_rn(a)) |
+                           ((unsigned int)__half_as_ushort(__float2half_rn(b)) << 16);
+    __stcs(reinterpret_cast<unsigned int*>(p), v);
+  }
+  static __device__ __forceinline__ P shfl_up(P v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+  static __device__ __forceinline__ P shfl_down(P v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+};
+// 16-bit storage element <-> FP32 deviation
+template <int ST> __device__ __forceinline__ float dev16(unsigned short u);
+template <> __device__ __forceinline__ float dev16<MI_STORE_F16_DEV>(unsigned short u) {
+  return __half2float(__ushort_as_half(u));
+}
+template <> __device__ __forceinline__ float dev16<MI_STORE_BF16_DEV>(unsigned short u) {
+  return __uint_as_float((unsigned)u << 16);
+}
+template <int ST> __device__ __forceinline__ unsigned short pack16(float h);
+template <> __device__ __forceinline__ unsigned short pack16<MI_STORE_F16_DEV>(float h) {
+  return __half_as_ushort(__float2half_rn(h));
+}
+template <> __device__ __forceinline__ unsigned short pack16<MI_STORE_BF16_DEV>(float h) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(h));
+}
+
+template <> struct Pair<MI_STORE_BF16_DEV> {
+  using P = unsigned int;
+  static __device__ __forceinline__ P load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+  static __device__ __forceinline__ float lo(P v, int) { return __uint_as_float(v << 16); }
+  static __device__ __forceinline__ float hi(P v, int) { return __uint_as_float(v & 0xFFFF0000u); }
+  static __device__ __forceinline__ void put(__nv_bfloat16* p, int, float a, float b) {
+    const unsigned int v = (unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+                           ((unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+    __stcs(reinterpret_cast<unsigned int*>(p), v);
+  }
+  static __device__ __forceinline__ P shfl_up(P v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+  static __device__ __forceinline__ P shfl_down(P v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+};
+
 // ---------------------------------------------------------------------------
 // Launch parameters of the lattice kernels.
 // ---------------------------------------------------------------------------
@@ -101,6 +162,8 @@ struct BulkLaunch {
   bool forcing;
   int block_x;         // threads per block along x
   int rows = 1;        // consecutive rows (y) per thread: 1 or 2
+  bool pairs = false;  // two x-adjacent nodes per thread with paired accesses (nx even)
+  int pair_mode = 1;   // 16-bit paired kernel occupancy: 1 = up to 64 registers, 2 = up to 80
 };
 cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s);
 

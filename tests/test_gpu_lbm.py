@@ -34,20 +34,28 @@ CASES = [
     ((33, 7, 6), (True, True, True), None, (1e-5, -2e-5, 3e-5)),
     ((200, 5, 4), (False, True, False), (0, (0.0, 0.01, 0.02)), (0.0, 0.0, 1e-5)),
     ((1, 16, 1), (True, False, True), (3, (0.01, 0.0, 0.0)), None),
+    ((130, 6, 5), (True, True, False), (5, (0.01, -0.02, 0.0)), (2e-5, 0.0, -1e-5)),
 ]
+
+
+# launch variants of the bulk kernel: (threads per block, rows per thread, paired nodes)
+VARIANTS = [(128, 1, 0), (32, 2, 0), (64, 1, 1), (32, 1, 1), (128, 1, 2)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("nsteps", [1, 3])
-def test_bulk_f32_matches_oracle(case, nsteps):
+@pytest.mark.parametrize("variant", range(len(VARIANTS)))
+def test_bulk_f32_matches_oracle(case, nsteps, variant):
     B = binding()
     shape, periodic, wall, force = CASES[case]
     wv = np.zeros((6, 3))
     if wall is not None:
         wv[wall[0]] = wall[1]
     f0 = _initial(shape, seed=case)
+    bx, rows, pairs = VARIANTS[variant]
     with B.Simulation(*shape, tau=TAU, periodic=periodic, wall_velocity=wv,
                       fluid_body_force=force or (0, 0, 0)) as sim:
+        sim.set_tuning(bx, rows, pairs, 8)
         sim.set_populations(f0)
         assert np.array_equal(sim.get_populations(), f0)
         sim.step(nsteps)
@@ -60,13 +68,16 @@ def test_bulk_f32_matches_oracle(case, nsteps):
 
 
 @pytest.mark.parametrize("storage", [1, 2])
-def test_bulk_16bit_deviation_storage(storage):
+@pytest.mark.parametrize("shape,variant", [((45, 10, 9), 0), ((46, 10, 9), 2), ((70, 6, 5), 3), ((64, 7, 6), 1),
+                                           ((262, 5, 4), 4)])
+def test_bulk_16bit_deviation_storage(storage, shape, variant):
     B = binding()
-    shape = (45, 10, 9)
     wv = np.zeros((6, 3))
     wv[5] = (0.02, -0.01, 0.0)
     f0 = _initial(shape, seed=21, amp=0.02)
+    bx, rows, pairs = VARIANTS[variant]
     with B.Simulation(*shape, tau=TAU, wall_velocity=wv, storage=storage) as sim:
+        sim.set_tuning(bx, rows, pairs, 8)
         sim.set_populations(f0)
         raw0 = sim.get_raw_populations()
         h0 = decode(raw0, storage)
@@ -96,15 +107,19 @@ def test_rest_state_and_mass_conservation():
     assert abs(m1 - m0) / m0 < 1e-6
 
 
-def test_bulk_full_size_sampled():
+@pytest.mark.parametrize("variant", [0, 2])
+def test_bulk_full_size_sampled(variant):
     """256x256x512 (the settling-tank lattice), one step in the benchmark's
-    launch configuration, checked on 4096 random nodes plus every corner and
-    edge-adjacent sample against the oracle evaluated node by node."""
+    launch configurations (scalar and paired nodes), checked on 4096 random
+    nodes plus every corner and edge-adjacent sample against the oracle
+    evaluated node by node."""
     import torch
     B = binding()
     shape = (256, 256, 512)
     nx, ny, nz = shape
+    bx, rows, pairs = VARIANTS[variant]
     with B.Simulation(*shape, tau=TAU) as sim:
+        sim.set_tuning(bx, rows, pairs, 8)
         t = pop_tensor(sim)
         g = torch.Generator(device="cuda")
         g.manual_seed(1234)
