@@ -10,14 +10,18 @@ L = max(R_b,i, R_b,j) and positions taken relative to O = (X_i + X_j)/2:
   0:3    (X_j - X_i) / L
   3:7    q_i, sign chosen so that w >= 0
   7:11   q_j, likewise
-  11:14  (x_h - O) / L, x_h the plain guess (the midpoint of the surface
-         points of the closest pair of control-point spheres, as in contact.py)
-  14:16  log g_i(x_h), log g_j(x_h) (core fields)
+  11:14  (x_a - O) / L, x_a the anchor (below)
+  14:16  log g_i(x_a), log g_j(x_a) (core fields)
   16:40  particle i: log(n)/5, log(sum k / L^2), R_b / L, R_s / L, then for
-         the 5 control points nearest to x_h (by distance, ties to the lower
-         index; zeros when fewer): (c - x_h)/L (world frame) and log(s k / L^2)
+         the 5 control points nearest to x_a (by distance, ties to the lower
+         index; zeros when fewer): (c - x_a)/L (world frame) and log(s k / L^2)
   40:64  particle j, likewise
-Outputs (4): (x_m - x_h)/L and log(r_act / L).  Labels: x_m the converged
+Anchor x_a: the control-point sphere (radius sqrt k) of i that reaches
+closest to the origin X_j of j, the one of j closest to X_i, and the midpoint
+of their surface points on the line joining their centres.  It costs
+O(n_i + n_j), against O(n_i n_j) for the plain guess of contact.py (the
+closest pair of spheres); for single-ball particles the two coincide.
+Outputs (4): (x_m - x_a)/L and log(r_act / L).  Labels: x_m the converged
 plain Newton point; r_act the smallest radius around x_m whose control points
 carry 99 % of g_i(x_m) + g_j(x_m).
 
@@ -27,7 +31,7 @@ of the squared error summed over the 4 outputs.
 """
 import numpy as np
 
-from .contact import core_scale, pair_guess, world_centers
+from .contact import core_scale, world_centers
 from .metaball import bounding_radius, field, quat_to_matrix, to_body
 
 SIZES = (64, 256, 256, 4)
@@ -98,12 +102,32 @@ def _core_world(P, x):
     return core_scale(P["k"], P["skin"]) * field(xb[None], P["centers"], P["k"])[0]
 
 
+def _reaching_ball(P, target):
+    """Index of the sphere (centre c, radius sqrt k) of P whose surface comes
+    closest to the point `target`: argmin |c - target| - sqrt k, ties to the
+    lower index."""
+    cw = world_centers(P)
+    gap = np.sqrt(((cw - target) ** 2).sum(1)) - np.sqrt(np.asarray(P["k"], float))
+    return int(np.argmin(gap)), cw
+
+
+def anchor(Pi, Pj):
+    """The anchor x_a of the pair (i, j) (module docstring)."""
+    a, ci = _reaching_ball(Pi, np.asarray(Pj["pos"], float))
+    b, cj = _reaching_ball(Pj, np.asarray(Pi["pos"], float))
+    ra, rb = np.sqrt(float(Pi["k"][a])), np.sqrt(float(Pj["k"][b]))
+    u = cj[b] - ci[a]
+    D = np.linalg.norm(u)
+    u = u / D if D > 0 else np.array([1.0, 0.0, 0.0])
+    return 0.5 * ((ci[a] + ra * u) + (cj[b] - rb * u))
+
+
 def features(Pi, Pj):
-    """The 64 features of the pair (i, j) and the plain guess x_h."""
+    """The 64 features of the pair (i, j) and the anchor x_a."""
     L = max(bounding_radius(Pi["centers"], Pi["k"]), bounding_radius(Pj["centers"], Pj["k"]))
     Xi, Xj = np.asarray(Pi["pos"], float), np.asarray(Pj["pos"], float)
     O = 0.5 * (Xi + Xj)
-    xh = pair_guess(Pi, Pj)
+    xh = anchor(Pi, Pj)
     f = np.zeros(64)
     f[0:3] = (Xj - Xi) / L
     for off, P in ((3, Pi), (7, Pj)):
@@ -129,7 +153,7 @@ def features(Pi, Pj):
 
 
 def labels(Pi, Pj, xm, xh, frac=0.99):
-    """Targets (x_m - x_h)/L and log(r_act/L) for a converged x_m."""
+    """Targets (x_m - x_a)/L and log(r_act/L) for a converged x_m (xh = x_a)."""
     L = max(bounding_radius(Pi["centers"], Pi["k"]), bounding_radius(Pj["centers"], Pj["k"]))
     d, w = [], []
     for P in (Pi, Pj):

@@ -112,3 +112,23 @@ def test_two_sphere_guess_and_labels_closed_form():
     wn = w0 if r0 <= r1 else w1
     expect = near if wn >= 0.99 * (w0 + w1) else far
     assert np.isclose(lab[3], np.log(expect / L))
+
+
+def test_anchor_hand_computed():
+    """Two unit balls at x = -1, +1 (body frame) and a ball of k = 4 six units
+    away: the sphere of i reaching closest to X_j is the one facing it, the
+    surface points are 2 and 4 along the axis, so x_a is 3 along it, whatever
+    the rotation that brings the facing ball round."""
+    bi = {"centers": np.array([[-1.0, 0, 0], [1.0, 0, 0]]), "k": np.array([1.0, 1.0]), "skin": 0.25,
+          "vel": np.zeros(3), "omega": np.zeros(3), "pos": np.zeros(3)}
+    s2 = np.sqrt(0.5)
+    for quat, pj, expect in (((1.0, 0, 0, 0), (6.0, 0, 0), (3.0, 0, 0)),
+                             ((0.0, 0, 0, 1.0), (6.0, 0, 0), (3.0, 0, 0)),      # 180 deg about z
+                             ((s2, 0, 0, s2), (0, 6.0, 0), (0, 3.0, 0)),        # 90 deg about z
+                             ((s2, 0, 0, -s2), (0, -6.0, 0), (0, -3.0, 0))):    # -90 deg about z
+        Pi = dict(bi, quat=np.array(quat))
+        Pj = _sphere(pj, 4.0)
+        assert np.allclose(mlp.anchor(Pi, Pj), expect, atol=1e-12), (quat, pj)
+        # for single-ball pairs the anchor is the plain guess
+    Pa, Pb = _sphere([0.5, -1, 2], 3.0), _sphere([4, 1, 2.5], 5.0)
+    assert np.allclose(mlp.anchor(Pa, Pb), contact.pair_guess(Pa, Pb), atol=1e-12)
