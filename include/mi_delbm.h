@@ -377,6 +377,90 @@ mi_status mi_delbm_phase_times(mi_delbm *h, double ms[8], long long launches[8],
  * accounting by benchmarks). */
 long long mi_delbm_launch_count(const mi_delbm *h);
 
+/* ------------------------------------------------------------------------
+ * Learned Newton guess.  Not in the paper: its closest-point solve (Sec.
+ * 2.3.1, Newton-Raphson on grad(g_i + g_j) = 0 between the two cores) starts
+ * from a heuristic point.  Here a small network, trained on solves the
+ * method itself makes, proposes the starting point and the balls that matter
+ * near the solution; full-set Newton to the unchanged tolerance still decides
+ * the result, and plain Newton from the plain guess takes over whenever the
+ * learned start does not converge.
+ *
+ * Network: 64 -> 256 -> 256 -> 4, ReLU after both hidden layers.  Parameters
+ * are one FP32 array of mi_mlp_param_count() floats: W1 (64 x 256, row-major,
+ * input index first), b1 (256), W2 (256 x 256), b2 (256), W3 (256 x 4), b3 (4).
+ * Every product runs on the tensor cores with BF16 operands and FP32
+ * accumulation; activations, gradients and the AdamW state stay FP32.
+ *
+ * Features of a pair (64, lengths over L = max(R_b,i, R_b,j), positions
+ * relative to O = (X_i + X_j)/2): 0:3 (X_j - X_i)/L; 3:7, 7:11 unit
+ * quaternions with w >= 0; 11:14 (x_a - O)/L with x_a the anchor (midpoint of
+ * the surface points of the ball of i whose sphere, radius sqrt k, reaches
+ * closest to X_j and the ball of j reaching closest to X_i); 14:16 log g_i,
+ * log g_j at x_a; 16:40 and 40:64 per particle log(n)/5, log(sum k / L^2),
+ * R_b/L, R_s/L and, for the 5 balls nearest x_a (ties to the lower index,
+ * zeros when fewer), (c - x_a)/L and log(s k / L^2), s the core scale.
+ * Outputs: (x_m - x_a)/L and log(r_act/L).  The start is x_a + L (out 0:3);
+ * Newton first runs on the balls within L exp(out 3) of it.
+ * ---------------------------------------------------------------------- */
+
+/* Floats in the parameter array (83,460). */
+size_t mi_mlp_param_count(void);
+
+/* Y (n x 4) = MLP(X (n x 64)); acts (n x 512 floats, device) receives the two
+ * hidden layers after ReLU for mi_mlp_backward.  All pointers are device
+ * pointers; asynchronous on stream (a cudaStream_t, NULL: the legacy default
+ * stream).  n == 0 does nothing (the pointers may then be NULL).  Errors:
+ * MI_EINVAL (null pointer, n < 0), MI_ECUDA (launch). */
+mi_status mi_mlp_forward(const float *params, const float *X, int n, float *Y, float *acts, void *stream);
+
+/* Loss = (1/n) sum over rows and outputs of (Y - T)^2 into *loss (device),
+ * and dY = dLoss/dY (n x 4).  scratch: 64 doubles of device memory. */
+mi_status mi_mlp_mse(const float *Y, const float *T, int n, float *dY, float *loss, double *scratch, void *stream);
+
+/* Gradients of the loss with respect to every parameter (same layout as the
+ * parameters) from X, the acts of mi_mlp_forward and dY.  scratch: n x 512
+ * floats of device memory.  Deterministic (no atomics). */
+mi_status mi_mlp_backward(const float *params, const float *X, const float *acts, const float *dY, int n,
+                          float *grads, float *scratch, void *stream);
+
+/* One AdamW step (decoupled weight decay) over all parameters; m and v are
+ * the moment arrays (zero before the first step), step the 1-based count. */
+mi_status mi_mlp_adamw(float *params, const float *grads, float *m, float *v, int step, float lr, float beta1,
+                       float beta2, float eps, float weight_decay, void *stream);
+
+/* Contact guess of the handle's DEM substeps: MI_GUESS_PLAIN, or
+ * MI_GUESS_LEARNED with params (device, mi_mlp_param_count floats, copied into
+ * the handle; the caller keeps ownership of its array).  Wall contacts always
+ * start from the plain guess.  Discards captured graphs.  Errors: MI_EINVAL,
+ * MI_ENOMEM, MI_ECUDA. */
+mi_status mi_delbm_set_guess(mi_delbm *h, int mode, const float *params);
+
+/* Flags of mi_delbm_pair_solve. */
+enum {
+  MI_PAIR_FEATURES = 1,  /* write the 64 features of each pair into X          */
+  MI_PAIR_PLAIN = 2,     /* solve from the plain guess                          */
+  MI_PAIR_LEARNED = 4,   /* solve from the learned start (pred; X holds the
+                            features, computed now when MI_PAIR_FEATURES is set) */
+  MI_PAIR_LABELS = 8     /* write the training targets of converged pairs to T  */
+};
+
+/* Closest points of n explicitly posed pairs of the handle's particle shapes,
+ * one warp per pair, asynchronously on the handle's stream; the lattice and
+ * the particles' own states are not touched.  Device arrays: ij (n x 2
+ * particle indices, which give the shapes), poses (n x 14 doubles: pos_i,
+ * quat_i, pos_j, quat_j), pred (n x 4, LEARNED), X (n x 64, FEATURES or
+ * LEARNED), T (n x 4, LABELS; rows of unconverged pairs untouched), and the
+ * outputs xm (n x 3 doubles, world closest point x_m), iters (Newton
+ * iterations, subset + full set + fallback), evals (ball evaluations of those
+ * iterations), status (0 converged, 1 not converged, 2 singular, 3 inside a
+ * core, 4 out of range, 5 bad index; +16 when the learned start fell back to
+ * plain Newton).  xm, iters, evals and status may be NULL only when neither
+ * PLAIN nor LEARNED is set.  Errors: MI_EINVAL (flags, null pointers),
+ * MI_ECUDA. */
+mi_status mi_delbm_pair_solve(mi_delbm *h, int n, const int *ij, const double *poses, int flags, const float *pred,
+                              float *X, float *T, double *xm, int *iters, int *evals, int *status);
+
 #ifdef __cplusplus
 }
 #endif

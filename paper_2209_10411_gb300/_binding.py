@@ -118,6 +118,16 @@ _sig("mi_delbm_get_links", c_int, _P, c_size_t, _P, _P, _P, _P, ctypes.POINTER(c
 _sig("mi_delbm_get_stats", c_int, _P, ctypes.POINTER(Stats))
 _sig("mi_delbm_contacts", c_int, _P, ctypes.POINTER(Contact), c_int, ctypes.POINTER(c_int))
 _sig("mi_mass_properties_noalloc", c_int, _P, c_int, c_double, c_double, _P, _P)
+_sig("mi_mlp_param_count", c_size_t)
+_sig("mi_mlp_forward", c_int, _P, _P, c_int, _P, _P, _P)
+_sig("mi_mlp_mse", c_int, _P, _P, c_int, _P, _P, _P, _P)
+_sig("mi_mlp_backward", c_int, _P, _P, _P, _P, c_int, _P, _P, _P)
+_sig("mi_mlp_adamw", c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+     ctypes.c_float, _P)
+_sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
+_sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
+
+PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS = 1, 2, 4, 8
 
 
 def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):
@@ -128,6 +138,64 @@ def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_pt
                                         c_void_p(int(out_dev_ptr)), c_void_p(int(stream)) if stream else None)
     if st != MI_OK:
         raise MiDelbmError(st, lib.mi_delbm_last_error(None).decode())
+
+def _tp(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    return c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cur_stream():
+    import torch
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _mlp_check(st):
+    if st != MI_OK:
+        raise MiDelbmError(st, lib.mi_delbm_last_error(None).decode())
+
+
+def mlp_param_count():
+    return int(lib.mi_mlp_param_count())
+
+
+def mlp_forward(params, X):
+    """Y (n x 4) and the saved activations (n x 512) for X (n x 64), all
+    float32 CUDA tensors, on torch's current stream."""
+    import torch
+    n = X.shape[0]
+    Y = torch.empty((n, 4), dtype=torch.float32, device=X.device)
+    acts = torch.empty((n, 512), dtype=torch.float32, device=X.device)
+    _mlp_check(lib.mi_mlp_forward(_tp(params), _tp(X), int(n), _tp(Y), _tp(acts), _cur_stream()))
+    return Y, acts
+
+
+def mlp_mse(Y, T):
+    """(loss as a 1-element device tensor, dY)."""
+    import torch
+    n = Y.shape[0]
+    dY = torch.empty_like(Y)
+    loss = torch.empty(1, dtype=torch.float32, device=Y.device)
+    scratch = torch.empty(64, dtype=torch.float64, device=Y.device)
+    _mlp_check(lib.mi_mlp_mse(_tp(Y), _tp(T), int(n), _tp(dY), _tp(loss), _tp(scratch), _cur_stream()))
+    return loss, dY
+
+
+def mlp_backward(params, X, acts, dY):
+    """Gradients (same layout as params)."""
+    import torch
+    n = X.shape[0]
+    grads = torch.empty_like(params)
+    scratch = torch.empty((n, 512), dtype=torch.float32, device=X.device)
+    _mlp_check(lib.mi_mlp_backward(_tp(params), _tp(X), _tp(acts), _tp(dY), int(n), _tp(grads), _tp(scratch),
+                                   _cur_stream()))
+    return grads
+
+
+def mlp_adamw(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4):
+    """One in-place AdamW step of params (m, v: moment tensors)."""
+    _mlp_check(lib.mi_mlp_adamw(_tp(params), _tp(grads), _tp(m), _tp(v), int(step), float(lr), float(beta1),
+                                float(beta2), float(eps), float(weight_decay), _cur_stream()))
+
 
 if lib.mi_delbm_abi_version() != 1:
     raise ImportError("libmi_delbm ABI version mismatch")
@@ -395,6 +463,52 @@ class Simulation:
         self._check(lib.mi_delbm_contacts(self.h, arr, n.value, ctypes.byref(n)))
         return [{"i": c.i, "j": c.j, "x_cp": np.array(c.xcp[:]), "n": np.array(c.n[:]), "delta": c.delta,
                  "iters": c.iters, "status": c.status} for c in arr[:n.value]]
+
+    # -- learned guess -----------------------------------------------------
+    def set_guess(self, mode, params=None):
+        """GUESS_PLAIN, or GUESS_LEARNED with the MLP parameters (float32 CUDA tensor)."""
+        self._sync_in()
+        self._check(lib.mi_delbm_set_guess(self.h, int(mode), _tp(params)))
+        self._sync_out()
+
+    def _sync_in(self):
+        if self.torch_stream is not None:
+            import torch
+            self.torch_stream.wait_stream(torch.cuda.current_stream())
+
+    def _sync_out(self):
+        if self.torch_stream is not None:
+            import torch
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
+        else:
+            self.synchronize()
+
+    def pair_solve(self, ij, poses, flags, pred=None, X=None):
+        """Closest points of explicitly posed pairs of this handle's particle
+        shapes.  ij: (n, 2) int32 CUDA tensor, poses: (n, 14) float64 CUDA
+        tensor; returns a dict of CUDA tensors (X, T, xm, iters, evals,
+        status; those the flags produce)."""
+        import torch
+        n = int(ij.shape[0])
+        dev = ij.device
+        solve = bool(flags & (PAIR_PLAIN | PAIR_LEARNED))
+        out = {}
+        if flags & PAIR_FEATURES:
+            X = torch.zeros((n, 64), dtype=torch.float32, device=dev)
+        if X is not None:
+            out["X"] = X
+        if flags & PAIR_LABELS:
+            out["T"] = torch.full((n, 4), float("nan"), dtype=torch.float32, device=dev)
+        if solve:
+            out["xm"] = torch.empty((n, 3), dtype=torch.float64, device=dev)
+            for key in ("iters", "evals", "status"):
+                out[key] = torch.empty(n, dtype=torch.int32, device=dev)
+        self._sync_in()
+        self._check(lib.mi_delbm_pair_solve(self.h, n, _tp(ij), _tp(poses), int(flags), _tp(pred), _tp(X),
+                                            _tp(out.get("T")), _tp(out.get("xm")), _tp(out.get("iters")),
+                                            _tp(out.get("evals")), _tp(out.get("status"))))
+        self._sync_out()
+        return out
 
     def stats(self):
         st = Stats()

@@ -1,0 +1,468 @@
+// Device-side pieces of the closest-point solve between sphero-metaball
+// particles (Sec. 2.3.1), shared by the DEM contact kernel and the batch pair
+// solver: the warp-cooperative core field with gradient and Hessian, the small
+// dense solve, the starting guesses and the Newton iteration.  One warp works
+// on one pair: the balls are spread over the lanes, the sums are
+// shuffle-reduced and broadcast from lane 0, so every lane takes the same
+// branches.  Geometry is FP32 in a local frame centred between the particles.
+#pragma once
+
+#include "mi_internal.cuh"
+
+namespace mi {
+namespace cdev {
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_IT = 50;
+constexpr float C_TOL = 1e-6f;
+constexpr float NEWTON_TOL = 1e-5f;  // |dx| <= NEWTON_TOL * R_b,max
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return __shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ void rot(const double q[4], double R[9]) {
+  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// A particle seen from a local origin O: body point x_b = R^T y + o for local y.
+struct Frame {
+  float R[9];  // body -> world
+  float o[3];  // R^T (O - X)
+  float t[3];  // X - O (world offset of the particle origin)
+  float s;     // core scale
+  int off, n;
+};
+
+__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double pos[3], const double quat[4],
+                                            const double O[3]) {
+  Frame F;
+  double R[9];
+  rot(quat, R);
+  const double d[3] = {O[0] - pos[0], O[1] - pos[1], O[2] - pos[2]};
+  for (int a = 0; a < 3; ++a) {
+    F.o[a] = (float)(R[a] * d[0] + R[3 + a] * d[1] + R[6 + a] * d[2]);
+    F.t[a] = (float)(-d[a]);
+  }
+  for (int k = 0; k < 9; ++k) F.R[k] = (float)R[k];
+  const double r = (P.re - P.skin) / P.re;
+  F.s = (float)(r * r);
+  F.off = P.ball_off;
+  F.n = P.n_balls;
+  return F;
+}
+
+__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double O[3]) {
+  return make_frame(P, P.pos, P.quat, O);
+}
+
+struct GEval {
+  float g, gr[3], H[6];  // core value, world gradient, world Hessian (xx xy xz yy yz zz)
+};
+
+// Warp-cooperative g, grad g, Hessian of g at local point y (every lane passes
+// the same y), over every ball of the particle or, with a list, over the m
+// balls it names (an active subset).
+__device__ __forceinline__ GEval eval(const Frame& F, const float4* __restrict__ balls, const float y[3], int lane,
+                                      const unsigned short* list = nullptr, int m = 0) {
+  float xb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xb[a] = F.R[a] * y[0] + F.R[3 + a] * y[1] + F.R[6 + a] * y[2] + F.o[a];
+  float g = 0.f, gb0 = 0.f, gb1 = 0.f, gb2 = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f, h5 = 0.f;
+  const int cnt = list ? m : F.n;
+  for (int u = lane; u < cnt; u += 32) {
+    const int b = list ? (int)list[u] : u;
+    const float4 c = __ldg(balls + F.off + b);
+    const float d0 = xb[0] - c.x, d1 = xb[1] - c.y, d2 = xb[2] - c.z;
+    const float ir2 = 1.0f / (d0 * d0 + d1 * d1 + d2 * d2);
+    const float t = c.w * ir2;            // k / r^2
+    const float t2 = -2.0f * t * ir2;     // -2 k / r^4
+    const float t3 = 8.0f * t * ir2 * ir2;  // 8 k / r^6
+    g += t;
+    gb0 += t2 * d0;
+    gb1 += t2 * d1;
+    gb2 += t2 * d2;
+    h0 += t3 * d0 * d0 + t2;
+    h1 += t3 * d0 * d1;
+    h2 += t3 * d0 * d2;
+    h3 += t3 * d1 * d1 + t2;
+    h4 += t3 * d1 * d2;
+    h5 += t3 * d2 * d2 + t2;
+  }
+  g = wsum(g);
+  gb0 = wsum(gb0); gb1 = wsum(gb1); gb2 = wsum(gb2);
+  h0 = wsum(h0); h1 = wsum(h1); h2 = wsum(h2); h3 = wsum(h3); h4 = wsum(h4); h5 = wsum(h5);
+  GEval e;
+  const float s = F.s;
+  e.g = s * g;
+  const float* R = F.R;
+  for (int a = 0; a < 3; ++a) e.gr[a] = s * (R[3 * a] * gb0 + R[3 * a + 1] * gb1 + R[3 * a + 2] * gb2);
+  // H_w = R H_b R^T
+  const float Hb[3][3] = {{h0, h1, h2}, {h1, h3, h4}, {h2, h4, h5}};
+  float M[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M[a][b] = R[3 * a] * Hb[0][b] + R[3 * a + 1] * Hb[1][b] + R[3 * a + 2] * Hb[2][b];
+  float Hw[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Hw[a][b] = s * (M[a][0] * R[3 * b] + M[a][1] * R[3 * b + 1] + M[a][2] * R[3 * b + 2]);
+  e.H[0] = Hw[0][0]; e.H[1] = Hw[0][1]; e.H[2] = Hw[0][2];
+  e.H[3] = Hw[1][1]; e.H[4] = Hw[1][2]; e.H[5] = Hw[2][2];
+  return e;
+}
+
+// Gaussian elimination with partial pivoting (n <= 4); false if singular.
+template <int N>
+__device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    int p = i;
+    float best = fabsf(A[i][i]);
+#pragma unroll
+    for (int r = i + 1; r < N; ++r)
+      if (fabsf(A[r][i]) > best) { best = fabsf(A[r][i]); p = r; }
+    if (!(best > 0.f)) return false;
+    if (p != i) {
+#pragma unroll
+      for (int c = 0; c < N; ++c) { const float t = A[i][c]; A[i][c] = A[p][c]; A[p][c] = t; }
+      const float t = b[i]; b[i] = b[p]; b[p] = t;
+    }
+#pragma unroll
+    for (int r = i + 1; r < N; ++r) {
+      const float m = A[r][i] / A[i][i];
+#pragma unroll
+      for (int c = i; c < N; ++c) A[r][c] -= m * A[i][c];
+      b[r] -= m * b[i];
+    }
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    float acc = b[i];
+#pragma unroll
+    for (int c = i + 1; c < N; ++c) acc -= A[i][c] * x[c];
+    x[i] = acc / A[i][i];
+  }
+  return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && (N < 4 || isfinite(x[N - 1]));
+}
+
+// Centre of ball c in the local frame.
+__device__ __forceinline__ void ball_local(const Frame& F, const float4 c, float p[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p[k] = F.R[3 * k] * c.x + F.R[3 * k + 1] * c.y + F.R[3 * k + 2] * c.z + F.t[k];
+}
+
+// Midpoint of the surface points of ball a of F0 and ball b of F1 (spheres of
+// radius sqrt k) on the line joining their centres.
+__device__ __forceinline__ void sphere_midpoint(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                                int a, int b, float y[3]) {
+  const float4 ca = __ldg(balls + F0.off + a), cb = __ldg(balls + F1.off + b);
+  float pa[3], pb[3], u[3];
+  ball_local(F0, ca, pa);
+  ball_local(F1, cb, pb);
+  for (int c = 0; c < 3; ++c) u[c] = pb[c] - pa[c];
+  const float D = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (D > 0.f) for (int c = 0; c < 3; ++c) u[c] /= D;
+  else { u[0] = 1.f; u[1] = u[2] = 0.f; }
+  const float ra = sqrtf(ca.w), rb = sqrtf(cb.w);
+  for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
+}
+
+// Plain starting guess: the closest pair of control-point spheres (smallest
+// surface gap, ties to the lower (a, b)), O(n0 n1) per pair.
+__device__ __forceinline__ void plain_guess(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                            int lane, float y[3]) {
+  float best = 3.4e38f;
+  int ba = 0, bb = 0;
+  for (int a = lane; a < F0.n; a += 32) {
+    const float4 ca = __ldg(balls + F0.off + a);
+    float pa[3];
+    ball_local(F0, ca, pa);
+    const float ra = sqrtf(ca.w);
+    for (int b = 0; b < F1.n; ++b) {
+      const float4 cb = __ldg(balls + F1.off + b);
+      float pb[3];
+      ball_local(F1, cb, pb);
+      const float gap = sqrtf((pa[0] - pb[0]) * (pa[0] - pb[0]) + (pa[1] - pb[1]) * (pa[1] - pb[1]) +
+                              (pa[2] - pb[2]) * (pa[2] - pb[2])) - ra - sqrtf(cb.w);
+      if (gap < best) { best = gap; ba = a; bb = b; }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float g2 = __shfl_xor_sync(FULL, best, o);
+    const int a2 = __shfl_xor_sync(FULL, ba, o), b2 = __shfl_xor_sync(FULL, bb, o);
+    if (g2 < best || (g2 == best && (a2 < ba || (a2 == ba && b2 < bb)))) { best = g2; ba = a2; bb = b2; }
+  }
+  ba = __shfl_sync(FULL, ba, 0);
+  bb = __shfl_sync(FULL, bb, 0);
+  sphere_midpoint(F0, F1, balls, ba, bb, y);
+}
+
+// The ball of F whose sphere surface comes closest to the local point tgt:
+// argmin |c - tgt| - sqrt k, ties to the lower index (warp-uniform result).
+__device__ __forceinline__ int reaching_ball(const Frame& F, const float4* __restrict__ balls, const float tgt[3],
+                                             int lane) {
+  float best = 3.4e38f;
+  int bi = 0x7fffffff;
+  for (int b = lane; b < F.n; b += 32) {
+    const float4 c = __ldg(balls + F.off + b);
+    float p[3];
+    ball_local(F, c, p);
+    const float gap = sqrtf((p[0] - tgt[0]) * (p[0] - tgt[0]) + (p[1] - tgt[1]) * (p[1] - tgt[1]) +
+                            (p[2] - tgt[2]) * (p[2] - tgt[2])) - sqrtf(c.w);
+    if (gap < best) { best = gap; bi = b; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float g2 = __shfl_xor_sync(FULL, best, o);
+    const int b2 = __shfl_xor_sync(FULL, bi, o);
+    if (g2 < best || (g2 == best && b2 < bi)) { best = g2; bi = b2; }
+  }
+  return __shfl_sync(FULL, bi, 0);
+}
+
+// Anchor of the learned guess, O(n0 + n1): the ball of particle 0 reaching
+// closest to the origin of particle 1 and vice versa, and the midpoint of
+// their surface points (the particle origins are F.t in the local frame).
+__device__ __forceinline__ void anchor_guess(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                             int lane, float y[3]) {
+  const int a = reaching_ball(F0, balls, F1.t, lane);
+  const int b = reaching_ball(F1, balls, F0.t, lane);
+  sphere_midpoint(F0, F1, balls, a, b, y);
+}
+
+// Newton-Raphson on grad(g0 + g1) = 0 (the closest-point condition of the two
+// cores) from y, over all balls or over the listed subsets.  Stops when
+// |dx| <= tol; returns 0 converged, 1 not converged in max_it, 2 singular;
+// iters counts the iterations taken (a failed solve included).
+__device__ __forceinline__ int newton_pair(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                           int lane, float y[3], float tol, int max_it, int& iters,
+                                           const unsigned short* l0 = nullptr, int m0 = 0,
+                                           const unsigned short* l1 = nullptr, int m1 = 0) {
+  int status = 1;
+  for (iters = 1; iters <= max_it; ++iters) {
+    const GEval e0 = eval(F0, balls, y, lane, l0, m0), e1 = eval(F1, balls, y, lane, l1, m1);
+    float A[3][3] = {{e0.H[0] + e1.H[0], e0.H[1] + e1.H[1], e0.H[2] + e1.H[2]},
+                     {e0.H[1] + e1.H[1], e0.H[3] + e1.H[3], e0.H[4] + e1.H[4]},
+                     {e0.H[2] + e1.H[2], e0.H[4] + e1.H[4], e0.H[5] + e1.H[5]}};
+    float b[3] = {e0.gr[0] + e1.gr[0], e0.gr[1] + e1.gr[1], e0.gr[2] + e1.gr[2]};
+    float dx[3];
+    if (!solve<3>(A, b, dx)) { status = 2; break; }
+    for (int c = 0; c < 3; ++c) y[c] -= dx[c];
+    if (sqrtf(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]) <= tol) { status = 0; break; }
+  }
+  if (iters > max_it) iters = max_it;
+  return status;
+}
+
+constexpr int SUB_CAP = 128;   // largest active subset per particle kept in shared memory
+constexpr int SUB_IT = 3;      // subset Newton iterations at most
+constexpr float SUB_TOL = 1e-3f;  // subset stop: |dx| <= SUB_TOL * R_b,max (a coarse pre-solve)
+
+// Indices of the balls of F whose centre lies within r of y, compacted into
+// list (warp ballot); returns their count (which may exceed SUB_CAP: then the
+// list holds only the first SUB_CAP).
+__device__ __forceinline__ int active_subset(const Frame& F, const float4* __restrict__ balls, const float y[3],
+                                             float r, int lane, unsigned short* list) {
+  int cnt = 0;
+  const float r2 = r * r;
+  for (int base = 0; base < F.n; base += 32) {
+    const int b = base + lane;
+    bool in = false;
+    if (b < F.n) {
+      float p[3];
+      ball_local(F, __ldg(balls + F.off + b), p);
+      const float d2 = (p[0] - y[0]) * (p[0] - y[0]) + (p[1] - y[1]) * (p[1] - y[1]) + (p[2] - y[2]) * (p[2] - y[2]);
+      in = d2 <= r2;
+    }
+    const unsigned m = __ballot_sync(FULL, in);
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    if (in && pos < SUB_CAP) list[pos] = (unsigned short)b;
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  return cnt;
+}
+
+struct SolveCount {
+  int iters;       // Newton iterations: subset + full set (+ plain fallback)
+  int evals;       // ball evaluations of those iterations (one per ball per iteration)
+  int fallback;    // 1 when the learned start failed and plain Newton took over
+};
+
+// Learned start: y0 = L (a + d), with a the anchor / L and d the predicted
+// offset; active subset = balls within r_act = L exp(log_r) of y0.  Newton
+// runs on the subsets first when that at least halves the work of an
+// iteration (both non-empty, within SUB_CAP, together at most half the
+// balls), for at most SUB_IT iterations to the coarse SUB_TOL, and its point
+// is kept only if it converged; then on the full set to the plain tolerance.
+// If the full-set solve fails, plain Newton from the plain guess decides.
+__device__ __forceinline__ int learned_newton(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                              int lane, const float a[3], const float d[4], float L, float Rb,
+                                              unsigned short* l0, unsigned short* l1, float y[3], SolveCount& sc) {
+  sc.iters = sc.evals = sc.fallback = 0;
+  for (int c = 0; c < 3; ++c) y[c] = L * (a[c] + d[c]);
+  bool ok = isfinite(y[0]) && isfinite(y[1]) && isfinite(y[2]);
+  if (ok) {
+    const float r_act = L * expf(fminf(fmaxf(d[3], -8.f), 2.f));
+    const int m0 = active_subset(F0, balls, y, r_act, lane, l0);
+    const int m1 = active_subset(F1, balls, y, r_act, lane, l1);
+    if (m0 > 0 && m1 > 0 && m0 <= SUB_CAP && m1 <= SUB_CAP && 2 * (m0 + m1) <= F0.n + F1.n) {
+      float ys[3] = {y[0], y[1], y[2]};
+      int it = 0;
+      const int st = newton_pair(F0, F1, balls, lane, ys, SUB_TOL * Rb, SUB_IT, it, l0, m0, l1, m1);
+      sc.iters += it;
+      sc.evals += it * (m0 + m1);
+      if (st == 0)
+        for (int c = 0; c < 3; ++c) y[c] = ys[c];
+    }
+    int it = 0;
+    const int st = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
+    sc.iters += it;
+    sc.evals += it * (F0.n + F1.n);
+    ok = st == 0;
+  }
+  if (ok) return 0;
+  sc.fallback = 1;
+  plain_guess(F0, F1, balls, lane, y);
+  int it = 0;
+  const int st = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
+  sc.iters += it;
+  sc.evals += it * (F0.n + F1.n);
+  return st;
+}
+
+constexpr int NEAREST = 5;     // nearest balls per particle in the features
+constexpr float ACT_FRAC = 0.99f;  // share of g0 + g1 the active radius label must carry
+
+// The 64 features of a candidate pair (lengths / L, L = max R_b, positions
+// relative to the pair centre O; the layout of the learned-guess oracle):
+// 0:3 (X_j - X_i)/L, 3:11 unit quaternions with w >= 0, 11:14 anchor, 14:16
+// log g at the anchor, then per particle (16:40, 40:64) log(n)/5,
+// log(sum k / L^2), R_b/L, R_s/L and the 5 balls nearest the anchor (ties to
+// the lower index; zeros when fewer) as (c - x_a)/L and log(s k / L^2).
+// Lane 0 fills the warp's shared row sh, the warp stores it to out; ya
+// returns the anchor in the local frame.
+__device__ __forceinline__ void pair_features(const DevParticle& Pi, const DevParticle& Pj, const double posi[3],
+                                              const double qi[4], const double posj[3], const double qj[4],
+                                              const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                              int lane, float* sh, float* out, float ya[3]) {
+  const double Ld = fmax(Pi.Rb, Pj.Rb);
+  const float L = (float)Ld;
+  anchor_guess(F0, F1, balls, lane, ya);
+  const GEval e0 = eval(F0, balls, ya, lane), e1 = eval(F1, balls, ya, lane);
+  if (lane == 0) {
+    for (int c = 0; c < 3; ++c) sh[c] = (float)((posj[c] - posi[c]) / Ld);
+    for (int side = 0; side < 2; ++side) {
+      const double* q = side ? qj : qi;
+      const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      const double sg = q[0] >= 0.0 ? 1.0 : -1.0;
+      for (int k = 0; k < 4; ++k) sh[3 + 4 * side + k] = (float)(sg * q[k] / n);
+    }
+    for (int c = 0; c < 3; ++c) sh[11 + c] = ya[c] / L;
+    sh[14] = logf(e0.g);
+    sh[15] = logf(e1.g);
+  }
+  for (int side = 0; side < 2; ++side) {
+    const Frame& F = side ? F1 : F0;
+    const DevParticle& P = side ? Pj : Pi;
+    const int off = side ? 40 : 16;
+    if (lane == 0) {
+      sh[off] = logf((float)F.n) / 5.0f;
+      sh[off + 1] = (float)log(P.re * P.re / (Ld * Ld));
+      sh[off + 2] = (float)(P.Rb / Ld);
+      sh[off + 3] = (float)(P.skin / Ld);
+    }
+    float prev_d = -1.f;
+    int prev_i = -1;
+    for (int r = 0; r < NEAREST; ++r) {
+      float best = 3.4e38f;
+      int bi = 0x7fffffff;
+      for (int b = lane; b < F.n; b += 32) {
+        float p[3];
+        ball_local(F, __ldg(balls + F.off + b), p);
+        const float d = sqrtf((p[0] - ya[0]) * (p[0] - ya[0]) + (p[1] - ya[1]) * (p[1] - ya[1]) +
+                              (p[2] - ya[2]) * (p[2] - ya[2]));
+        const bool after = d > prev_d || (d == prev_d && b > prev_i);
+        if (after && (d < best || (d == best && b < bi))) { best = d; bi = b; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float d2 = __shfl_xor_sync(FULL, best, o);
+        const int b2 = __shfl_xor_sync(FULL, bi, o);
+        if (d2 < best || (d2 == best && b2 < bi)) { best = d2; bi = b2; }
+      }
+      best = __shfl_sync(FULL, best, 0);
+      bi = __shfl_sync(FULL, bi, 0);
+      if (lane == 0) {
+        float* row = sh + off + 4 + 4 * r;
+        if (bi < F.n) {
+          const float4 c = __ldg(balls + F.off + bi);
+          float p[3];
+          ball_local(F, c, p);
+          for (int k = 0; k < 3; ++k) row[k] = (p[k] - ya[k]) / L;
+          row[3] = logf(F.s * c.w / (L * L));
+        } else {
+          row[0] = row[1] = row[2] = row[3] = 0.f;
+        }
+      }
+      prev_d = best;
+      prev_i = bi;
+    }
+  }
+  __syncwarp();
+  out[lane] = sh[lane];
+  out[lane + 32] = sh[lane + 32];
+  __syncwarp();
+}
+
+// Distance from y and core weight s k / d^2 of ball t of the pair (balls of
+// particle 0 first, then those of particle 1).
+__device__ __forceinline__ void ball_weight(const Frame& F0, const Frame& F1, const float4* __restrict__ balls, int t,
+                                            const float y[3], float& d, float& w) {
+  const Frame& F = t < F0.n ? F0 : F1;
+  const int b = t < F0.n ? t : t - F0.n;
+  const float4 c = __ldg(balls + F.off + b);
+  float p[3];
+  ball_local(F, c, p);
+  const float d2 = (p[0] - y[0]) * (p[0] - y[0]) + (p[1] - y[1]) * (p[1] - y[1]) + (p[2] - y[2]) * (p[2] - y[2]);
+  d = sqrtf(d2);
+  w = F.s * c.w / d2;
+}
+
+// Training targets of a converged pair: (x_m - x_a)/L and log(r_act/L), with
+// r_act the smallest distance from x_m such that the balls no farther away
+// (ties by index) carry ACT_FRAC of g0(x_m) + g1(x_m).  O((n0 + n1)^2 / 32)
+// per lane: it runs only when training data is generated.
+__device__ __forceinline__ void pair_labels(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                            int lane, const float ym[3], const float ya[3], float L, float* out) {
+  const int N = F0.n + F1.n;
+  float W = 0.f;
+  for (int t = lane; t < N; t += 32) {
+    float d, w;
+    ball_weight(F0, F1, balls, t, ym, d, w);
+    W += w;
+  }
+  W = wsum(W);
+  float best = 3.4e38f;
+  for (int t = lane; t < N; t += 32) {
+    float dt, wt;
+    ball_weight(F0, F1, balls, t, ym, dt, wt);
+    float cum = 0.f;
+    for (int u = 0; u < N; ++u) {
+      float du, wu;
+      ball_weight(F0, F1, balls, u, ym, du, wu);
+      if (du < dt || (du == dt && u <= t)) cum += wu;
+    }
+    if (cum >= ACT_FRAC * W && dt < best) best = dt;
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(FULL, best, o));
+  if (lane == 0) {
+    for (int c = 0; c < 3; ++c) out[c] = (ym[c] - ya[c]) / L;
+    out[3] = logf(best / L);
+  }
+}
+
+}  // namespace cdev
+}  // namespace mi

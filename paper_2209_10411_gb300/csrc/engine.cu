@@ -255,6 +255,17 @@ mi_status mi_delbm::ensure_contact_buffers() {
   return MI_OK;
 }
 
+mi_status mi_delbm::ensure_guess_buffers() {
+  if (guess_feat) return MI_OK;
+  mi_status s = ensure_contact_buffers();
+  if (s != MI_OK) return s;
+  guess_feat = (float*)dalloc(sizeof(float) * 64 * (size_t)cap_items);
+  guess_acts = (float*)dalloc(sizeof(float) * 512 * (size_t)cap_items);
+  guess_pred = (float*)dalloc(sizeof(float) * 4 * (size_t)cap_items);
+  if (!guess_feat || !guess_acts || !guess_pred) return fail(MI_ENOMEM, "learned guess: device allocation failed");
+  return MI_OK;
+}
+
 static ContactLaunch contact_launch(const mi_delbm* h) {
   ContactLaunch L;
   std::memset(&L, 0, sizeof(L));
@@ -279,6 +290,9 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.cp.mu_s = h->cfg.mu_s;
   L.cp.dt = 1.0 / h->cfg.dem_substeps;
   L.cp.margin = 1.0;
+  L.learned = h->learned ? 1 : 0;
+  L.feat = h->guess_feat;
+  L.pred = h->guess_pred;
   for (int a = 0; a < 3; ++a) L.cp.periodic[a] = h->cfg.periodic[a] ? 1 : 0;
   L.cp.n[0] = h->cfg.nx;
   L.cp.n[1] = h->cfg.ny;
@@ -291,9 +305,19 @@ mi_status mi_delbm::phase_contact(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   mi_status s = ensure_contact_buffers();
   if (s != MI_OK) return s;
+  if (learned && (s = ensure_guess_buffers()) != MI_OK) return s;
   ContactLaunch L = contact_launch(this);
   if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_dem_prologue(L, st); })) != MI_OK) return s;
   if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_broad_phase(L, st); })) != MI_OK) return s;
+  if (learned) {
+    // features of the candidates, then the MLP on as many rows as the broad phase found
+    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_item_features(L, st); })) != MI_OK) return s;
+    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] {
+           return mlp_forward_rows(mlp_params, guess_feat, (int)cap_items, &dctr->n_pairs, guess_pred, guess_acts, st);
+         })) != MI_OK)
+      return s;
+    launches += 2;  // the forward pass is three GEMM launches
+  }
   return launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_contacts(L, st); });
 }
 
@@ -584,6 +608,10 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     g_create_error = "mi_delbm_create: dem_substeps must be >= 1, capacities >= 0, max_particles <= 65535";
     return MI_EINVAL;
   }
+  if (cfg->guess_mode != MI_GUESS_PLAIN) {
+    g_create_error = "mi_delbm_create: guess_mode must be MI_GUESS_PLAIN (load a learned guess with mi_delbm_set_guess)";
+    return MI_EINVAL;
+  }
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) {
     g_create_error = "mi_delbm_create: dev_alloc and dev_free must be given together";
     return MI_EINVAL;
@@ -773,6 +801,67 @@ mi_status mi_delbm_get_device_view(mi_delbm* h, mi_delbm_device_view* v) {
 mi_status mi_delbm_set_graphs(mi_delbm* h, int enable) {
   if (!h) return MI_EINVAL;
   h->use_graphs = enable != 0;
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
+  if (!h) return MI_EINVAL;
+  if (mode == MI_GUESS_PLAIN) {
+    if (h->learned) h->invalidate_graphs();
+    h->learned = false;
+    return MI_OK;
+  }
+  if (mode != MI_GUESS_LEARNED) return h->fail(MI_EINVAL, "set_guess: unknown mode");
+  if (!params) return h->fail(MI_EINVAL, "set_guess: learned mode needs the MLP parameters");
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status s = h->ensure_guess_buffers();
+  if (s != MI_OK) return s;
+  const size_t bytes = sizeof(float) * mi_mlp_param_count();
+  if (!h->mlp_params) {
+    h->mlp_params = (float*)h->dalloc(bytes);
+    if (!h->mlp_params) return h->fail(MI_ENOMEM, "set_guess: device allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(h->mlp_params, params, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_guess: parameter copy");
+  h->invalidate_graphs();
+  h->learned = true;
+  return MI_OK;
+}
+
+mi_status mi_delbm_pair_solve(mi_delbm* h, int n, const int* ij, const double* poses, int flags, const float* pred,
+                              float* X, float* T, double* xm, int* iters, int* evals, int* status) {
+  if (!h) return MI_EINVAL;
+  const int known = MI_PAIR_FEATURES | MI_PAIR_PLAIN | MI_PAIR_LEARNED | MI_PAIR_LABELS;
+  const bool plain = flags & MI_PAIR_PLAIN, lrn = flags & MI_PAIR_LEARNED;
+  if (n < 0 || (flags & ~known) || (plain && lrn) || flags == 0)
+    return h->fail(MI_EINVAL, "pair_solve: n < 0, unknown flags, or both PLAIN and LEARNED");
+  if ((flags & MI_PAIR_LABELS) && !plain && !lrn) return h->fail(MI_EINVAL, "pair_solve: LABELS needs a solve");
+  if (n == 0) return MI_OK;
+  if (!ij || !poses || ((flags & (MI_PAIR_FEATURES | MI_PAIR_LEARNED)) && !X) || (lrn && !pred) ||
+      ((flags & MI_PAIR_LABELS) && !T) || ((plain || lrn) && (!xm || !iters || !evals || !status)))
+    return h->fail(MI_EINVAL, "pair_solve: a required array is NULL");
+  if (h->n_particles == 0) return h->fail(MI_EINVAL, "pair_solve: the handle has no particles (shapes)");
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status s = h->ensure_particle_buffers();
+  if (s != MI_OK) return s;
+  PairSolveLaunch S;
+  S.P = h->dP;
+  S.np = h->n_particles;
+  S.balls = h->dballs;
+  S.n = n;
+  S.ij = ij;
+  S.poses = poses;
+  S.flags = flags;
+  S.pred = pred;
+  S.X = X;
+  S.T = T;
+  S.xm = xm;
+  S.iters = iters;
+  S.evals = evals;
+  S.status = status;
+  cudaError_t e = launch_pair_solve(S, h->stream);
+  h->launches += 1;
+  if (e != cudaSuccess) return h->cuda_fail(e, "pair_solve: launch");
   return MI_OK;
 }
 

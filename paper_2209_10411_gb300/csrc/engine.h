@@ -73,6 +73,12 @@ struct mi_delbm {
   mi::HistEntry* hist_wall = nullptr;
   unsigned* work = nullptr;
   long long* substep = nullptr;
+  // learned contact guess (MI_GUESS_LEARNED): parameters and per-item buffers
+  bool learned = false;
+  float* mlp_params = nullptr;
+  float* guess_feat = nullptr;       // cap_items x 64
+  float* guess_acts = nullptr;       // cap_items x 512
+  float* guess_pred = nullptr;       // cap_items x 4
   // lists
   uint32_t *bc_cell = nullptr, *bc_mask = nullptr, *bc_loff = nullptr;
   uint32_t *link_bc = nullptr, *link_p = nullptr;
@@ -120,6 +126,7 @@ struct mi_delbm {
   mi_status join_record(cudaStream_t from, int slot);
   mi_status join_wait(int slot);
   mi_status ensure_contact_buffers();
+  mi_status ensure_guess_buffers();
 
   mi_status ensure_particle_buffers();
   mi_status ensure_list_capacity(unsigned bc, unsigned links, unsigned nnew);

@@ -12,138 +12,12 @@
 // a warp leaves when the queue is empty.  Geometry is FP32 in a local frame
 // centred between the particles; forces are FP64, summed per particle in
 // 2^-40 fixed point (order-free).
-#include "mi_internal.cuh"
+#include "contact_dev.cuh"
 
 namespace mi {
 
 namespace {
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int MAX_IT = 50;
-constexpr float C_TOL = 1e-6f;
-constexpr float NEWTON_TOL = 1e-5f;  // |dx| <= NEWTON_TOL * R_b,max
-
-__device__ __forceinline__ float wsum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return __shfl_sync(FULL, v, 0);
-}
-
-__device__ __forceinline__ void rot(const double q[4], double R[9]) {
-  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
-  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
-  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
-}
-
-// A particle seen from a local origin O: body point x_b = R^T y + o for local y.
-struct Frame {
-  float R[9];  // body -> world
-  float o[3];  // R^T (O - X)
-  float t[3];  // X - O (world offset of the particle origin)
-  float s;     // core scale
-  int off, n;
-};
-
-__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double O[3]) {
-  Frame F;
-  double R[9];
-  rot(P.quat, R);
-  const double d[3] = {O[0] - P.pos[0], O[1] - P.pos[1], O[2] - P.pos[2]};
-  for (int a = 0; a < 3; ++a) {
-    F.o[a] = (float)(R[a] * d[0] + R[3 + a] * d[1] + R[6 + a] * d[2]);
-    F.t[a] = (float)(-d[a]);
-  }
-  for (int k = 0; k < 9; ++k) F.R[k] = (float)R[k];
-  const double r = (P.re - P.skin) / P.re;
-  F.s = (float)(r * r);
-  F.off = P.ball_off;
-  F.n = P.n_balls;
-  return F;
-}
-
-struct GEval {
-  float g, gr[3], H[6];  // core value, world gradient, world Hessian (xx xy xz yy yz zz)
-};
-
-// Warp-cooperative g, grad g, Hessian of g at local point y (every lane passes the same y).
-__device__ __forceinline__ GEval eval(const Frame& F, const float4* __restrict__ balls, const float y[3], int lane) {
-  float xb[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) xb[a] = F.R[a] * y[0] + F.R[3 + a] * y[1] + F.R[6 + a] * y[2] + F.o[a];
-  float g = 0.f, gb0 = 0.f, gb1 = 0.f, gb2 = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f, h5 = 0.f;
-  for (int b = lane; b < F.n; b += 32) {
-    const float4 c = __ldg(balls + F.off + b);
-    const float d0 = xb[0] - c.x, d1 = xb[1] - c.y, d2 = xb[2] - c.z;
-    const float ir2 = 1.0f / (d0 * d0 + d1 * d1 + d2 * d2);
-    const float t = c.w * ir2;            // k / r^2
-    const float t2 = -2.0f * t * ir2;     // -2 k / r^4
-    const float t3 = 8.0f * t * ir2 * ir2;  // 8 k / r^6
-    g += t;
-    gb0 += t2 * d0;
-    gb1 += t2 * d1;
-    gb2 += t2 * d2;
-    h0 += t3 * d0 * d0 + t2;
-    h1 += t3 * d0 * d1;
-    h2 += t3 * d0 * d2;
-    h3 += t3 * d1 * d1 + t2;
-    h4 += t3 * d1 * d2;
-    h5 += t3 * d2 * d2 + t2;
-  }
-  g = wsum(g);
-  gb0 = wsum(gb0); gb1 = wsum(gb1); gb2 = wsum(gb2);
-  h0 = wsum(h0); h1 = wsum(h1); h2 = wsum(h2); h3 = wsum(h3); h4 = wsum(h4); h5 = wsum(h5);
-  GEval e;
-  const float s = F.s;
-  e.g = s * g;
-  const float* R = F.R;
-  for (int a = 0; a < 3; ++a) e.gr[a] = s * (R[3 * a] * gb0 + R[3 * a + 1] * gb1 + R[3 * a + 2] * gb2);
-  // H_w = R H_b R^T
-  const float Hb[3][3] = {{h0, h1, h2}, {h1, h3, h4}, {h2, h4, h5}};
-  float M[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) M[a][b] = R[3 * a] * Hb[0][b] + R[3 * a + 1] * Hb[1][b] + R[3 * a + 2] * Hb[2][b];
-  float Hw[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) Hw[a][b] = s * (M[a][0] * R[3 * b] + M[a][1] * R[3 * b + 1] + M[a][2] * R[3 * b + 2]);
-  e.H[0] = Hw[0][0]; e.H[1] = Hw[0][1]; e.H[2] = Hw[0][2];
-  e.H[3] = Hw[1][1]; e.H[4] = Hw[1][2]; e.H[5] = Hw[2][2];
-  return e;
-}
-
-// Gaussian elimination with partial pivoting (n <= 4); false if singular.
-template <int N>
-__device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    int p = i;
-    float best = fabsf(A[i][i]);
-#pragma unroll
-    for (int r = i + 1; r < N; ++r)
-      if (fabsf(A[r][i]) > best) { best = fabsf(A[r][i]); p = r; }
-    if (!(best > 0.f)) return false;
-    if (p != i) {
-#pragma unroll
-      for (int c = 0; c < N; ++c) { const float t = A[i][c]; A[i][c] = A[p][c]; A[p][c] = t; }
-      const float t = b[i]; b[i] = b[p]; b[p] = t;
-    }
-#pragma unroll
-    for (int r = i + 1; r < N; ++r) {
-      const float m = A[r][i] / A[i][i];
-#pragma unroll
-      for (int c = i; c < N; ++c) A[r][c] -= m * A[i][c];
-      b[r] -= m * b[i];
-    }
-  }
-#pragma unroll
-  for (int i = N - 1; i >= 0; --i) {
-    float acc = b[i];
-#pragma unroll
-    for (int c = i + 1; c < N; ++c) acc -= A[i][c] * x[c];
-    x[i] = acc / A[i][i];
-  }
-  return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && (N < 4 || isfinite(x[N - 1]));
-}
+using namespace cdev;
 
 __device__ __forceinline__ void add_fixed6(long long* acc, int p, const double v[6]) {
   for (int k = 0; k < 6; ++k)
@@ -253,7 +127,8 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
 
 // Persistent warp-per-candidate Newton solver and forces.
 __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
+  const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
   const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
   const long long substep = *L.substep;
   const float4* balls = L.balls;
@@ -273,57 +148,20 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       for (int a = 0; a < 3; ++a) O[a] = 0.5 * (Pi.pos[a] + Pj.pos[a]);
       const Frame F0 = make_frame(Pi, O), F1 = make_frame(Pj, O);
       const float Rb = (float)fmax(Pi.Rb, Pj.Rb);
-      // guess: closest pair of control-point spheres, midpoint of their surface points
-      float best = 3.4e38f;
-      int ba = 0, bb = 0;
-      for (int a = lane; a < F0.n; a += 32) {
-        const float4 ca = __ldg(balls + F0.off + a);
-        float pa[3];
-        for (int c = 0; c < 3; ++c) pa[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c];
-        const float ra = sqrtf(ca.w);
-        for (int b = 0; b < F1.n; ++b) {
-          const float4 cb = __ldg(balls + F1.off + b);
-          float pb[3];
-          for (int c = 0; c < 3; ++c) pb[c] = F1.R[3 * c] * cb.x + F1.R[3 * c + 1] * cb.y + F1.R[3 * c + 2] * cb.z + F1.t[c];
-          const float gap = sqrtf((pa[0] - pb[0]) * (pa[0] - pb[0]) + (pa[1] - pb[1]) * (pa[1] - pb[1]) +
-                                  (pa[2] - pb[2]) * (pa[2] - pb[2])) - ra - sqrtf(cb.w);
-          if (gap < best) { best = gap; ba = a; bb = b; }
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float g2 = __shfl_xor_sync(FULL, best, o);
-        const int a2 = __shfl_xor_sync(FULL, ba, o), b2 = __shfl_xor_sync(FULL, bb, o);
-        if (g2 < best || (g2 == best && (a2 < ba || (a2 == ba && b2 < bb)))) { best = g2; ba = a2; bb = b2; }
-      }
-      ba = __shfl_sync(FULL, ba, 0);
-      bb = __shfl_sync(FULL, bb, 0);
       float y[3];
-      {
-        const float4 ca = __ldg(balls + F0.off + ba), cb = __ldg(balls + F1.off + bb);
-        float pa[3], pb[3], u[3];
-        for (int c = 0; c < 3; ++c) {
-          pa[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c];
-          pb[c] = F1.R[3 * c] * cb.x + F1.R[3 * c + 1] * cb.y + F1.R[3 * c + 2] * cb.z + F1.t[c];
-          u[c] = pb[c] - pa[c];
-        }
-        const float D = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        if (D > 0.f) for (int c = 0; c < 3; ++c) u[c] /= D;
-        else { u[0] = 1.f; u[1] = u[2] = 0.f; }
-        const float ra = sqrtf(ca.w), rb = sqrtf(cb.w);
-        for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
+      if (L.learned) {
+        // learned start: anchor and prediction of this item (features and MLP ran before)
+        const float* x = L.feat + (size_t)it * 64;
+        const float* pr = L.pred + (size_t)it * 4;
+        const float a[3] = {x[11], x[12], x[13]}, d[4] = {pr[0], pr[1], pr[2], pr[3]};
+        SolveCount sc;
+        status = learned_newton(F0, F1, balls, lane, a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc);
+        iters = sc.iters;
+      } else {
+        // plain start: closest pair of control-point spheres, midpoint of their surface points
+        plain_guess(F0, F1, balls, lane, y);
+        status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
       }
-      for (iters = 1; iters <= MAX_IT; ++iters) {
-        const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
-        float A[3][3] = {{e0.H[0] + e1.H[0], e0.H[1] + e1.H[1], e0.H[2] + e1.H[2]},
-                         {e0.H[1] + e1.H[1], e0.H[3] + e1.H[3], e0.H[4] + e1.H[4]},
-                         {e0.H[2] + e1.H[2], e0.H[4] + e1.H[4], e0.H[5] + e1.H[5]}};
-        float b[3] = {e0.gr[0] + e1.gr[0], e0.gr[1] + e1.gr[1], e0.gr[2] + e1.gr[2]};
-        float dx[3];
-        if (!solve<3>(A, b, dx)) { status = 2; break; }
-        for (int c = 0; c < 3; ++c) y[c] -= dx[c];
-        if (sqrtf(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]) <= NEWTON_TOL * Rb) { status = 0; break; }
-      }
-      if (iters > MAX_IT) iters = MAX_IT;
       const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
       if (status == 0) {
         if (e0.g >= 1.f || e1.g >= 1.f) status = 3;

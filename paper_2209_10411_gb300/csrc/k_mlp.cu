@@ -1,0 +1,347 @@
+// MLP of the learned Newton guess (64 -> 256 -> 256 -> 4, ReLU): forward,
+// backward, MSE loss and AdamW on the GPU.  Every matrix product runs on the
+// tensor cores as BF16 x BF16 -> FP32 (mma.sync m16n8k16); parameters,
+// activations and gradients live in FP32 and are rounded to BF16 when a tile
+// is staged in shared memory, so the network computes with BF16 weights and
+// FP32 accumulation while the optimizer keeps FP32 master weights.
+#include <cstring>
+
+#include "mi_internal.cuh"
+
+namespace mi {
+void set_thread_error(const char* msg);  // engine.cu: message for mi_delbm_last_error(NULL)
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+struct GemmArgs {
+  int M, N, K;
+  const unsigned* Mdev;  // when set, the row count is min(M, *Mdev), read on the device
+  const float* A;
+  int lda, transA;   // op(A) is M x K; A is M x K row-major, or K x M when transA
+  const float* B;
+  int ldb, transB;   // op(B) is K x N; B is K x N row-major, or N x K when transB
+  const float* bias; // N, or nullptr
+  const float* mask; // M x N (ldmask): the result is zeroed where mask <= 0, or nullptr
+  int ldmask;
+  int relu;
+  float* C;
+  int ldc;
+};
+
+// Two consecutive BF16 of a shared-memory row (even column: 4-byte aligned,
+// the lower column in the lower half, as the mma fragments want them).
+__device__ __forceinline__ unsigned ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C = op(A) op(B) (+ bias) (ReLU) (masked).  Block tile 64 x 64, K step 32,
+// 4 warps in 2 x 2, each warp 32 x 32 = 2 x 4 mma tiles of 16 x 8.
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+  __shared__ __nv_bfloat16 As[BM][BK + PAD];  // (m, k)
+  __shared__ __nv_bfloat16 Bs[BN][BK + PAD];  // (n, k)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (g.Mdev) {
+    const int Md = (int)min((unsigned)g.M, *g.Mdev);
+    g.M = Md;
+    if (m0 >= Md) return;  // uniform over the block
+  }
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    // stage op(A)[m0:m0+64, k0:k0+32] and op(B)[k0:k0+32, n0:n0+64] as BF16
+    for (int e = tid; e < BM * BK; e += 128) {
+      int m, k;
+      if (g.transA) { m = e % BM; k = e / BM; } else { k = e % BK; m = e / BK; }
+      const int gm = m0 + m, gk = k0 + k;
+      float v = 0.f;
+      if (gm < g.M && gk < g.K) v = g.transA ? g.A[(long long)gk * g.lda + gm] : g.A[(long long)gm * g.lda + gk];
+      As[m][k] = __float2bfloat16_rn(v);
+    }
+    for (int e = tid; e < BN * BK; e += 128) {
+      int n, k;
+      if (g.transB) { k = e % BK; n = e / BK; } else { n = e % BN; k = e / BN; }
+      const int gn = n0 + n, gk = k0 + k;
+      float v = 0.f;
+      if (gn < g.N && gk < g.K) v = g.transB ? g.B[(long long)gn * g.ldb + gk] : g.B[(long long)gk * g.ldb + gn];
+      Bs[n][k] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      unsigned a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + gid;
+        a[i][0] = ld32(&As[r][kk + 2 * tig]);
+        a[i][1] = ld32(&As[r + 8][kk + 2 * tig]);
+        a[i][2] = ld32(&As[r][kk + 2 * tig + 8]);
+        a[i][3] = ld32(&As[r + 8][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + gid;
+        b[j][0] = ld32(&Bs[c][kk + 2 * tig]);
+        b[j][1] = ld32(&Bs[c][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
+    }
+    __syncthreads();
+  }
+  // epilogue
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int row = m0 + wm + 16 * i + gid + (c >= 2 ? 8 : 0);
+        const int col = n0 + wn + 8 * j + 2 * tig + (c & 1);
+        if (row >= g.M || col >= g.N) continue;
+        float v = acc[i][j][c];
+        if (g.bias) v += g.bias[col];
+        if (g.relu) v = fmaxf(v, 0.f);
+        if (g.mask && !(g.mask[(long long)row * g.ldmask + col] > 0.f)) v = 0.f;
+        g.C[(long long)row * g.ldc + col] = v;
+      }
+}
+
+cudaError_t gemm(const GemmArgs& a, cudaStream_t s) {
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
+  if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+  k_gemm<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+GemmArgs gemm_args(int M, int N, int K, const float* A, int lda, int tA, const float* B, int ldb, int tB,
+                   const float* bias, int relu, const float* mask, int ldm, float* C, int ldc) {
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K;
+  g.Mdev = nullptr;
+  g.A = A; g.lda = lda; g.transA = tA;
+  g.B = B; g.ldb = ldb; g.transB = tB;
+  g.bias = bias; g.relu = relu; g.mask = mask; g.ldmask = ldm;
+  g.C = C; g.ldc = ldc;
+  return g;
+}
+
+// dY = 2 (Y - T) / n and per-block partial sums of (Y - T)^2 (summed in block order).
+__global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, int count, float inv_n,
+                      float* __restrict__ dY, double* __restrict__ partial) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const float d = Y[i] - T[i];
+    dY[i] = 2.0f * d * inv_n;
+    acc += (double)d * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_loss_finish(const double* partial, int nb, double inv_n, float* loss) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[b];
+  *loss = (float)(s * inv_n);
+}
+
+// Column sums of an M x N matrix (bias gradients): block (32, 8) covers 32
+// columns, the 8 row phases are added in a fixed order (deterministic).
+__global__ void k_colsum(const float* __restrict__ D, int M, int N, float* __restrict__ out) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float s = 0.f;
+  if (c < N)
+    for (int r = threadIdx.y; r < M; r += 8) s += D[(long long)r * N + c];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < N) {
+    float t = red[0][threadIdx.x];
+    for (int y = 1; y < 8; ++y) t += red[y][threadIdx.x];
+    out[c] = t;
+  }
+}
+
+cudaError_t colsum(const float* D, int M, int N, float* out, cudaStream_t s) {
+  k_colsum<<<(N + 31) / 32, dim3(32, 8), 0, s>>>(D, M, N, out);
+  return cudaGetLastError();
+}
+
+// AdamW (decoupled weight decay) on FP32 master parameters.
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float wd, float c1,
+                        float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float mi = b1 * m[i] + (1.f - b1) * g[i];
+  const float vi = b2 * v[i] + (1.f - b2) * g[i] * g[i];
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / c1, vh = vi / c2;
+  p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+}
+
+}  // namespace
+
+cudaError_t mlp_forward_rows(const float* params, const float* X, int M, const unsigned* Mdev, float* Y, float* acts,
+                             cudaStream_t s) {
+  const float* P[6];
+  P[0] = params;
+  P[1] = P[0] + 64 * 256;
+  P[2] = P[1] + 256;
+  P[3] = P[2] + 256 * 256;
+  P[4] = P[3] + 256;
+  P[5] = P[4] + 256 * 4;
+  float* H1 = acts;
+  float* H2 = acts + (size_t)M * 256;
+  GemmArgs a = gemm_args(M, 256, 64, X, 64, 0, P[0], 256, 0, P[1], 1, nullptr, 0, H1, 256);
+  a.Mdev = Mdev;
+  cudaError_t e = gemm(a, s);
+  if (e != cudaSuccess) return e;
+  a = gemm_args(M, 256, 256, H1, 256, 0, P[2], 256, 0, P[3], 1, nullptr, 0, H2, 256);
+  a.Mdev = Mdev;
+  if ((e = gemm(a, s)) != cudaSuccess) return e;
+  a = gemm_args(M, 4, 256, H2, 256, 0, P[4], 4, 0, P[5], 0, nullptr, 0, Y, 4);
+  a.Mdev = Mdev;
+  return gemm(a, s);
+}
+
+}  // namespace mi
+
+using namespace mi;
+
+extern "C" {
+
+// Parameter block layout (floats): W1 64x256, b1 256, W2 256x256, b2 256, W3 256x4, b3 4.
+size_t mi_mlp_param_count(void) { return 64 * 256 + 256 + 256 * 256 + 256 + 256 * 4 + 4; }
+
+static void split(const float* base, const float* P[6]) {
+  P[0] = base;
+  P[1] = P[0] + 64 * 256;
+  P[2] = P[1] + 256;
+  P[3] = P[2] + 256 * 256;
+  P[4] = P[3] + 256;
+  P[5] = P[4] + 256 * 4;
+}
+
+mi_status mi_mlp_forward(const float* params, const float* X, int n, float* Y, float* acts, void* stream) {
+  if (n < 0 || (n > 0 && (!params || !X || !Y || !acts))) {
+    set_thread_error("mi_mlp_forward: null pointer or negative batch");
+    return MI_EINVAL;
+  }
+  if (n == 0) return MI_OK;
+  const float* P[6];
+  split(params, P);
+  cudaStream_t s = (cudaStream_t)stream;
+  float* H1 = acts;                    // n x 256, relu(X W1 + b1)
+  float* H2 = acts + (size_t)n * 256;  // n x 256, relu(H1 W2 + b2)
+  cudaError_t e = gemm(gemm_args(n, 256, 64, X, 64, 0, P[0], 256, 0, P[1], 1, nullptr, 0, H1, 256), s);
+  if (e == cudaSuccess) e = gemm(gemm_args(n, 256, 256, H1, 256, 0, P[2], 256, 0, P[3], 1, nullptr, 0, H2, 256), s);
+  if (e == cudaSuccess) e = gemm(gemm_args(n, 4, 256, H2, 256, 0, P[4], 4, 0, P[5], 0, nullptr, 0, Y, 4), s);
+  if (e != cudaSuccess) {
+    set_thread_error("mi_mlp_forward: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_mse(const float* Y, const float* T, int n, float* dY, float* loss, double* scratch, void* stream) {
+  if (!Y || !T || !dY || !loss || !scratch || n <= 0) {
+    set_thread_error("mi_mlp_mse: null pointer or empty batch");
+    return MI_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = 64;
+  k_mse<<<blocks, 256, 0, s>>>(Y, T, 4 * n, 1.0f / n, dY, scratch);
+  k_loss_finish<<<1, 32, 0, s>>>(scratch, blocks, 1.0 / n, loss);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_thread_error("mi_mlp_mse: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_backward(const float* params, const float* X, const float* acts, const float* dY, int n,
+                          float* grads, float* scratch, void* stream) {
+  if (!params || !X || !acts || !dY || !grads || !scratch || n <= 0) {
+    set_thread_error("mi_mlp_backward: null pointer or empty batch");
+    return MI_EINVAL;
+  }
+  const float* P[6];
+  split(params, P);
+  float* G[6];
+  {
+    const float* Gc[6];
+    split(grads, Gc);
+    for (int i = 0; i < 6; ++i) G[i] = const_cast<float*>(Gc[i]);
+  }
+  // relu(z) > 0 exactly where z > 0, so the saved activations give the masks.
+  const float* H1 = acts;
+  const float* H2 = acts + (size_t)n * 256;
+  float* dZ2 = scratch;                    // n x 256
+  float* dZ1 = scratch + (size_t)n * 256;  // n x 256
+  cudaStream_t s = (cudaStream_t)stream;
+  // layer 3: dW3 = H2^T dY, db3 = colsum dY
+  cudaError_t e = gemm(gemm_args(256, 4, n, H2, 256, 1, dY, 4, 0, nullptr, 0, nullptr, 0, G[4], 4), s);
+  if (e == cudaSuccess) e = colsum(dY, n, 4, G[5], s);
+  // dZ2 = (dY W3^T) masked by H2 > 0
+  if (e == cudaSuccess) e = gemm(gemm_args(n, 256, 4, dY, 4, 0, P[4], 4, 1, nullptr, 0, H2, 256, dZ2, 256), s);
+  // layer 2: dW2 = H1^T dZ2, db2 = colsum dZ2
+  if (e == cudaSuccess) e = gemm(gemm_args(256, 256, n, H1, 256, 1, dZ2, 256, 0, nullptr, 0, nullptr, 0, G[2], 256), s);
+  if (e == cudaSuccess) e = colsum(dZ2, n, 256, G[3], s);
+  // dZ1 = (dZ2 W2^T) masked by H1 > 0
+  if (e == cudaSuccess) e = gemm(gemm_args(n, 256, 256, dZ2, 256, 0, P[2], 256, 1, nullptr, 0, H1, 256, dZ1, 256), s);
+  // layer 1: dW1 = X^T dZ1, db1 = colsum dZ1
+  if (e == cudaSuccess) e = gemm(gemm_args(64, 256, n, X, 64, 1, dZ1, 256, 0, nullptr, 0, nullptr, 0, G[0], 256), s);
+  if (e == cudaSuccess) e = colsum(dZ1, n, 256, G[1], s);
+  if (e != cudaSuccess) {
+    set_thread_error("mi_mlp_backward: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_adamw(float* params, const float* grads, float* m, float* v, int step, float lr, float beta1,
+                       float beta2, float eps, float weight_decay, void* stream) {
+  if (!params || !grads || !m || !v || step < 1) {
+    set_thread_error("mi_mlp_adamw: null pointer or step < 1");
+    return MI_EINVAL;
+  }
+  const int n = (int)mi_mlp_param_count();
+  const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+  k_adamw<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, n, lr, beta1, beta2, eps,
+                                                             weight_decay, c1, c2);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_thread_error("mi_mlp_adamw: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+}  // extern "C"

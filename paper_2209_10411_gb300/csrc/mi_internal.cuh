@@ -284,10 +284,40 @@ struct ContactLaunch {
   long long* substep;     // device substep counter
   ContactParams cp;
   int grid;
+  int learned;            // 1: pair items start from the learned guess (feat, pred), else the plain guess
+  float* feat;            // cap_items x 64 features of the pair items (learned)
+  const float* pred;      // cap_items x 4 MLP outputs (learned)
 };
 cudaError_t launch_dem_prologue(const ContactLaunch& L, cudaStream_t s);
 cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s);
 cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s);
+cudaError_t launch_item_features(const ContactLaunch& L, cudaStream_t s);
+
+// Batch closest-point solve of explicitly posed particle pairs (shapes of the
+// handle's particles, poses given per pair).
+struct PairSolveLaunch {
+  const DevParticle* P;
+  int np;
+  const float4* balls;
+  int n;                  // pairs
+  const int* ij;          // n x 2 particle indices (shapes)
+  const double* poses;    // n x 14: pos_i, quat_i, pos_j, quat_j
+  int flags;              // MI_PAIR_* bits
+  const float* pred;      // n x 4 (learned start)
+  float* X;               // n x 64 features (in: learned start without FEATURES; out: FEATURES)
+  float* T;               // n x 4 labels (LABELS)
+  double* xm;             // n x 3 closest point (world)
+  int* iters;             // n Newton iterations
+  int* evals;             // n ball evaluations
+  int* status;            // n status (+ 16 when the learned start fell back to plain Newton)
+};
+cudaError_t launch_pair_solve(const PairSolveLaunch& S, cudaStream_t s);
+
+// MLP forward of the learned guess on at most M rows, the row count read on
+// the device from *Mdev (capped at M): used inside a step, whose number of
+// candidates is known only on the device.  acts holds M x 512 floats.
+cudaError_t mlp_forward_rows(const float* params, const float* X, int M, const unsigned* Mdev, float* Y, float* acts,
+                             cudaStream_t s);
 
 struct IntegrateLaunch {
   DevParticle* P;
