@@ -176,40 +176,92 @@ def build_sim(B, scene, storage, stream):
     return sim
 
 
+def train_guess(B):
+    """The learned Newton guess: 2M pair solves of 256 bed shapes (seed 1,
+    shapes and poses independent of the timed bed) made by the plain Newton
+    kernel, and 12k AdamW steps of the BF16 network on them (library
+    kernels; not timed)."""
+    import torch
+    from paper_2209_10411_gb300 import guess
+    t0 = time.perf_counter()
+    shapes = guess.bed_shapes(1, 256)
+    sim = B.Simulation(16, 16, 16, max_particles=len(shapes) + 1, max_balls=sum(len(s["k"]) for s in shapes) + 1)
+    guess.add_shapes(sim, shapes)
+    ij, poses = guess.pair_poses(1, shapes, 2_000_000)
+    X, T, _ = guess.generate(sim, *guess.to_device(ij, poses))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    params, hist = guess.train(X, T, steps=12000, batch=4096, lr=2e-3, seed=0, log_every=4000, standardize=True,
+                               target_weights=(10.0, 10.0, 10.0, 1.0))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    sim.close()
+    info = {"solves": 2_000_000, "samples": int(X.shape[0]), "steps": 12000, "batch": 4096,
+            "generate_s": t1 - t0, "train_s": t2 - t1, "loss": hist}
+    return params, info
+
+
 def contact_solves(B, scenes, args):
     """Contact solves per second: the DEM contact phase alone (broad phase +
-    persistent Newton/force kernel) on the 3000-particle bed of 4-128 balls
-    in 384x384x768, timed with CUDA events over repeated substeps."""
+    persistent Newton/force kernel; with the learned guess also the feature
+    kernel and the MLP) on the 3000-particle bed of 4-128 balls in
+    384x384x768, timed with CUDA events over repeated substeps, with the
+    plain guess and with the learned guess."""
     sc = scenes.config5()
     nx, ny, nz = sc.shape
-    sim = B.Simulation(nx, ny, nz, tau=sc.tau, storage=1, max_particles=len(sc.particles),
-                       max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0)
-    for p in sc.particles:
-        r = p.nominal_radius
-        vol = 4.0 / 3.0 * np.pi * r ** 3
-        m = p.density * vol
-        sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat,
-                         mass_props={"mass": m, "volume": vol, "inertia": np.eye(3) * 0.4 * m * r * r})
-    sim.set_timing(True)
-    for _ in range(3):
-        sim.step_phases(B.PHASE_CONTACT)
-    sim.phase_times(reset=True)
-    reps = 20
-    for _ in range(reps):
-        sim.step_phases(B.PHASE_CONTACT)
-    pt = sim.phase_times(reset=True)["contact"]
-    recs = sim.contacts()
-    sim.close()
-    n = len(recs)
-    iters = np.array([c["iters"] for c in recs])
-    status = np.bincount(np.array([c["status"] for c in recs], dtype=int), minlength=5)
-    ms = pt[0] / reps
-    return {"value": n / (ms * 1e-3), "unit": "solves/s", "guess": "plain", "candidates": n,
-            "pairs": int(sum(1 for c in recs if c["j"] >= 0)), "in_contact": int(sum(1 for c in recs if c["delta"] > 0 and c["status"] == 0)),
-            "mean_iters": float(iters.mean()) if n else None,
-            "status_counts": {"ok": int(status[0]), "not_converged": int(status[1]), "singular": int(status[2]),
-                              "inside_core": int(status[3]), "out_of_range": int(status[4])},
-            "ms_per_substep": ms, "particles": len(sc.particles), "workload": sc.name}
+    params, train_info = train_guess(B)
+    out = {}
+    recs_by_mode = {}
+    for mode in ("plain", "learned"):
+        sim = B.Simulation(nx, ny, nz, tau=sc.tau, storage=1, max_particles=len(sc.particles),
+                           max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0)
+        for p in sc.particles:
+            r = p.nominal_radius
+            vol = 4.0 / 3.0 * np.pi * r ** 3
+            m = p.density * vol
+            sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat,
+                             mass_props={"mass": m, "volume": vol, "inertia": np.eye(3) * 0.4 * m * r * r})
+        if mode == "learned":
+            sim.set_guess(B.GUESS_LEARNED, params)
+        sim.set_timing(True)
+        for _ in range(3):
+            sim.step_phases(B.PHASE_CONTACT)
+        sim.phase_times(reset=True)
+        reps = 20
+        for _ in range(reps):
+            sim.step_phases(B.PHASE_CONTACT)
+        pt = sim.phase_times(reset=True)["contact"]
+        recs = sim.contacts()
+        sim.close()
+        recs_by_mode[mode] = recs
+        n = len(recs)
+        pair_iters = np.array([c["iters"] for c in recs if c["j"] >= 0])
+        status = np.bincount(np.array([c["status"] for c in recs], dtype=int), minlength=5)
+        ms = pt[0] / reps
+        out[mode] = {"value": n / (ms * 1e-3), "unit": "solves/s", "candidates": n,
+                     "pairs": int(len(pair_iters)),
+                     "in_contact": int(sum(1 for c in recs if c["delta"] > 0 and c["status"] == 0)),
+                     "mean_pair_iters": float(pair_iters.mean()) if len(pair_iters) else None,
+                     "status_counts": {"ok": int(status[0]), "not_converged": int(status[1]),
+                                       "singular": int(status[2]), "inside_core": int(status[3]),
+                                       "out_of_range": int(status[4])},
+                     "ms_per_substep": ms, "launches_per_substep": pt[1] / reps}
+    # the two modes must agree: same converged pairs, same contact points (1e-5 of 2 R_b)
+    rb = {i: None for i in range(len(sc.particles))}
+    for i, p in enumerate(sc.particles):
+        rb[i] = float(np.sqrt((p.centers ** 2).sum(1)).max() + np.sqrt(p.k.sum()))
+    a = {(c["i"], c["j"]): c for c in recs_by_mode["plain"] if c["j"] >= 0 and c["status"] == 0}
+    b = {(c["i"], c["j"]): c for c in recs_by_mode["learned"] if c["j"] >= 0 and c["status"] == 0}
+    same = [np.linalg.norm(a[k]["x_cp"] - b[k]["x_cp"]) <= 2e-5 * max(rb[k[0]], rb[k[1]]) for k in a if k in b]
+    res = dict(out["plain"])
+    res.update({"guess": "plain", "workload": sc.name, "particles": len(sc.particles), "learned": out["learned"],
+                "learned_vs_plain": {"solves_per_s": out["learned"]["value"] / out["plain"]["value"],
+                                     "pair_iters": (out["learned"]["mean_pair_iters"] or 0) /
+                                     max(out["plain"]["mean_pair_iters"] or 1, 1e-9),
+                                     "converged_pairs_plain": len(a), "converged_pairs_learned": len(b),
+                                     "same_contact_point": float(np.mean(same)) if same else None},
+                "training": train_info})
+    return res
 
 
 def storage_variant(B, scene, storage, steps, stream_obj):

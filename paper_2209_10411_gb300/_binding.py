@@ -124,6 +124,9 @@ _sig("mi_mlp_mse", c_int, _P, _P, c_int, _P, _P, _P, _P)
 _sig("mi_mlp_backward", c_int, _P, _P, _P, _P, c_int, _P, _P, _P)
 _sig("mi_mlp_adamw", c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
      ctypes.c_float, _P)
+_sig("mi_mlp_image_bytes", c_size_t)
+_sig("mi_mlp_pack", c_int, _P, _P, _P)
+_sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
@@ -167,6 +170,23 @@ def mlp_forward(params, X):
     acts = torch.empty((n, 512), dtype=torch.float32, device=X.device)
     _mlp_check(lib.mi_mlp_forward(_tp(params), _tp(X), int(n), _tp(Y), _tp(acts), _cur_stream()))
     return Y, acts
+
+
+def mlp_pack(params):
+    """The packed BF16 image of the parameters for mlp_infer (uint8 CUDA tensor)."""
+    import torch
+    img = torch.empty(int(lib.mi_mlp_image_bytes()), dtype=torch.uint8, device=params.device)
+    _mlp_check(lib.mi_mlp_pack(_tp(params), _tp(img), _cur_stream()))
+    return img
+
+
+def mlp_infer(image, X):
+    """Y (n x 4) for X (n x 64) through the fused inference kernel."""
+    import torch
+    n = X.shape[0]
+    Y = torch.empty((n, 4), dtype=torch.float32, device=X.device)
+    _mlp_check(lib.mi_mlp_infer(_tp(image), _tp(X), int(n), _tp(Y), _cur_stream()))
+    return Y
 
 
 def mlp_mse(Y, T):

@@ -22,13 +22,6 @@ __device__ __forceinline__ float wsum(float v) {
   return __shfl_sync(FULL, v, 0);
 }
 
-__device__ __forceinline__ void rot(const double q[4], double R[9]) {
-  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
-  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
-  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
-}
 
 // A particle seen from a local origin O: body point x_b = R^T y + o for local y.
 struct Frame {
@@ -39,26 +32,43 @@ struct Frame {
   int off, n;
 };
 
-__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double pos[3], const double quat[4],
-                                            const double O[3]) {
+// Unit quaternion in FP32 (w, x, y, z) of an FP64 one.
+__device__ __forceinline__ float4 unit_quat_f32(const double q[4]) {
+  const float a = (float)q[0], b = (float)q[1], c = (float)q[2], d = (float)q[3];
+  const float inv = 1.0f / sqrtf(a * a + b * b + c * c + d * d);
+  return make_float4(a * inv, b * inv, c * inv, d * inv);
+}
+
+// The frame of particle P for a local origin O, given its unit quaternion q
+// and the offset d = O - X, both FP32.  The geometry the frame serves is
+// FP32; the callers take only the difference of two particle positions in
+// FP64 before rounding, so that positions far from the origin keep their
+// relative accuracy.  (FP64 runs at a small fraction of the FP32 rate on this
+// part, and every candidate pair builds two frames.)
+__device__ __forceinline__ Frame frame_f32(const DevParticle& P, const float4 q, const float d[3]) {
   Frame F;
-  double R[9];
-  rot(quat, R);
-  const double d[3] = {O[0] - pos[0], O[1] - pos[1], O[2] - pos[2]};
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  float* R = F.R;
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
   for (int a = 0; a < 3; ++a) {
-    F.o[a] = (float)(R[a] * d[0] + R[3 + a] * d[1] + R[6 + a] * d[2]);
-    F.t[a] = (float)(-d[a]);
+    F.o[a] = R[a] * d[0] + R[3 + a] * d[1] + R[6 + a] * d[2];
+    F.t[a] = -d[a];
   }
-  for (int k = 0; k < 9; ++k) F.R[k] = (float)R[k];
-  const double r = (P.re - P.skin) / P.re;
-  F.s = (float)(r * r);
+  F.s = P.core_s;
   F.off = P.ball_off;
   F.n = P.n_balls;
   return F;
 }
 
-__device__ __forceinline__ Frame make_frame(const DevParticle& P, const double O[3]) {
-  return make_frame(P, P.pos, P.quat, O);
+// The two frames of a pair about O = (X_i + X_j) / 2 from h = (X_j - X_i) / 2
+// (O - X_i = h, O - X_j = -h).
+__device__ __forceinline__ void pair_frames(const DevParticle& Pi, const DevParticle& Pj, const float4 qi,
+                                            const float4 qj, const float h[3], Frame& F0, Frame& F1) {
+  const float mh[3] = {-h[0], -h[1], -h[2]};
+  F0 = frame_f32(Pi, qi, h);
+  F1 = frame_f32(Pj, qj, mh);
 }
 
 struct GEval {
@@ -337,6 +347,66 @@ __device__ __forceinline__ int learned_newton(const Frame& F0, const Frame& F1, 
 constexpr int NEAREST = 5;     // nearest balls per particle in the features
 constexpr float ACT_FRAC = 0.99f;  // share of g0 + g1 the active radius label must carry
 
+// One pass over the balls of F around the local point y: the core field
+// g(y) = s sum k / |c - y|^2 (warp sum, broadcast) and the NEAREST balls
+// closest to y, ties to the lower index, written by lane 0 into row[4 r ..]
+// as (c - y) / L and log(s k / L^2), zeros when F has fewer balls.  Each lane
+// keeps a sorted list of its own nearest balls in registers; NEAREST rounds
+// of a warp argmin over the lanes' list heads then merge them.
+__device__ __forceinline__ float field_and_nearest(const Frame& F, const float4* __restrict__ balls, const float y[3],
+                                                   float iL, int lane, float* row) {
+  float kd[NEAREST];
+  int kb[NEAREST];
+#pragma unroll
+  for (int r = 0; r < NEAREST; ++r) { kd[r] = 3.4e38f; kb[r] = 0x7fffffff; }
+  float g = 0.f;
+  for (int b = lane; b < F.n; b += 32) {
+    const float4 c = __ldg(balls + F.off + b);
+    float p[3];
+    ball_local(F, c, p);
+    const float d2 = (p[0] - y[0]) * (p[0] - y[0]) + (p[1] - y[1]) * (p[1] - y[1]) + (p[2] - y[2]) * (p[2] - y[2]);
+    g += c.w / d2;
+    float cd = sqrtf(d2);
+    int cb = b;
+#pragma unroll
+    for (int r = 0; r < NEAREST; ++r)  // this lane's balls arrive in index order: strict < keeps ties in order
+      if (cd < kd[r]) {
+        const float td = kd[r]; kd[r] = cd; cd = td;
+        const int tb = kb[r]; kb[r] = cb; cb = tb;
+      }
+  }
+  g = F.s * wsum(g);
+  for (int r = 0; r < NEAREST; ++r) {
+    float best = kd[0];
+    int bi = kb[0];
+    for (int o = 16; o > 0; o >>= 1) {
+      const float d2 = __shfl_xor_sync(FULL, best, o);
+      const int b2 = __shfl_xor_sync(FULL, bi, o);
+      if (d2 < best || (d2 == best && b2 < bi)) { best = d2; bi = b2; }
+    }
+    bi = __shfl_sync(FULL, bi, 0);
+    if (kb[0] == bi && bi != 0x7fffffff) {  // the owning lane pops its head
+#pragma unroll
+      for (int q = 0; q < NEAREST - 1; ++q) { kd[q] = kd[q + 1]; kb[q] = kb[q + 1]; }
+      kd[NEAREST - 1] = 3.4e38f;
+      kb[NEAREST - 1] = 0x7fffffff;
+    }
+    if (lane == 0) {
+      float* out = row + 4 * r;
+      if (bi < F.n) {
+        const float4 c = __ldg(balls + F.off + bi);
+        float p[3];
+        ball_local(F, c, p);
+        for (int k = 0; k < 3; ++k) out[k] = (p[k] - y[k]) * iL;
+        out[3] = logf(F.s * c.w * iL * iL);
+      } else {
+        out[0] = out[1] = out[2] = out[3] = 0.f;
+      }
+    }
+  }
+  return g;
+}
+
 // The 64 features of a candidate pair (lengths / L, L = max R_b, positions
 // relative to the pair centre O; the layout of the learned-guess oracle):
 // 0:3 (X_j - X_i)/L, 3:11 unit quaternions with w >= 0, 11:14 anchor, 14:16
@@ -344,71 +414,38 @@ constexpr float ACT_FRAC = 0.99f;  // share of g0 + g1 the active radius label m
 // log(sum k / L^2), R_b/L, R_s/L and the 5 balls nearest the anchor (ties to
 // the lower index; zeros when fewer) as (c - x_a)/L and log(s k / L^2).
 // Lane 0 fills the warp's shared row sh, the warp stores it to out; ya
-// returns the anchor in the local frame.
-__device__ __forceinline__ void pair_features(const DevParticle& Pi, const DevParticle& Pj, const double posi[3],
-                                              const double qi[4], const double posj[3], const double qj[4],
-                                              const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
-                                              int lane, float* sh, float* out, float ya[3]) {
-  const double Ld = fmax(Pi.Rb, Pj.Rb);
-  const float L = (float)Ld;
+// returns the anchor in the local frame; h = (X_j - X_i) / 2 and the unit
+// quaternions are FP32 (the features are FP32 network inputs).
+__device__ __forceinline__ void pair_features(const DevParticle& Pi, const DevParticle& Pj, const float h[3],
+                                              const float4 qi, const float4 qj, const Frame& F0, const Frame& F1,
+                                              const float4* __restrict__ balls, int lane, float* sh, float* out,
+                                              float ya[3]) {
+  const float L = fmaxf(Pi.Rb_f, Pj.Rb_f);
+  const float iL = 1.0f / L;
   anchor_guess(F0, F1, balls, lane, ya);
-  const GEval e0 = eval(F0, balls, ya, lane), e1 = eval(F1, balls, ya, lane);
+  const float g0 = field_and_nearest(F0, balls, ya, iL, lane, sh + 20);
+  const float g1 = field_and_nearest(F1, balls, ya, iL, lane, sh + 44);
   if (lane == 0) {
-    for (int c = 0; c < 3; ++c) sh[c] = (float)((posj[c] - posi[c]) / Ld);
+    for (int c = 0; c < 3; ++c) sh[c] = 2.0f * h[c] * iL;
     for (int side = 0; side < 2; ++side) {
-      const double* q = side ? qj : qi;
-      const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-      const double sg = q[0] >= 0.0 ? 1.0 : -1.0;
-      for (int k = 0; k < 4; ++k) sh[3 + 4 * side + k] = (float)(sg * q[k] / n);
+      const float4 q = side ? qj : qi;
+      const float sg = q.x >= 0.f ? 1.f : -1.f;
+      sh[3 + 4 * side] = sg * q.x;
+      sh[4 + 4 * side] = sg * q.y;
+      sh[5 + 4 * side] = sg * q.z;
+      sh[6 + 4 * side] = sg * q.w;
     }
-    for (int c = 0; c < 3; ++c) sh[11 + c] = ya[c] / L;
-    sh[14] = logf(e0.g);
-    sh[15] = logf(e1.g);
-  }
-  for (int side = 0; side < 2; ++side) {
-    const Frame& F = side ? F1 : F0;
-    const DevParticle& P = side ? Pj : Pi;
-    const int off = side ? 40 : 16;
-    if (lane == 0) {
+    for (int c = 0; c < 3; ++c) sh[11 + c] = ya[c] * iL;
+    sh[14] = logf(g0);
+    sh[15] = logf(g1);
+    for (int side = 0; side < 2; ++side) {
+      const Frame& F = side ? F1 : F0;
+      const DevParticle& P = side ? Pj : Pi;
+      const int off = side ? 40 : 16;
       sh[off] = logf((float)F.n) / 5.0f;
-      sh[off + 1] = (float)log(P.re * P.re / (Ld * Ld));
-      sh[off + 2] = (float)(P.Rb / Ld);
-      sh[off + 3] = (float)(P.skin / Ld);
-    }
-    float prev_d = -1.f;
-    int prev_i = -1;
-    for (int r = 0; r < NEAREST; ++r) {
-      float best = 3.4e38f;
-      int bi = 0x7fffffff;
-      for (int b = lane; b < F.n; b += 32) {
-        float p[3];
-        ball_local(F, __ldg(balls + F.off + b), p);
-        const float d = sqrtf((p[0] - ya[0]) * (p[0] - ya[0]) + (p[1] - ya[1]) * (p[1] - ya[1]) +
-                              (p[2] - ya[2]) * (p[2] - ya[2]));
-        const bool after = d > prev_d || (d == prev_d && b > prev_i);
-        if (after && (d < best || (d == best && b < bi))) { best = d; bi = b; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float d2 = __shfl_xor_sync(FULL, best, o);
-        const int b2 = __shfl_xor_sync(FULL, bi, o);
-        if (d2 < best || (d2 == best && b2 < bi)) { best = d2; bi = b2; }
-      }
-      best = __shfl_sync(FULL, best, 0);
-      bi = __shfl_sync(FULL, bi, 0);
-      if (lane == 0) {
-        float* row = sh + off + 4 + 4 * r;
-        if (bi < F.n) {
-          const float4 c = __ldg(balls + F.off + bi);
-          float p[3];
-          ball_local(F, c, p);
-          for (int k = 0; k < 3; ++k) row[k] = (p[k] - ya[k]) / L;
-          row[3] = logf(F.s * c.w / (L * L));
-        } else {
-          row[0] = row[1] = row[2] = row[3] = 0.f;
-        }
-      }
-      prev_d = best;
-      prev_i = bi;
+      sh[off + 1] = 2.0f * logf(P.re_f * iL);
+      sh[off + 2] = P.Rb_f * iL;
+      sh[off + 3] = P.skin_f * iL;
     }
   }
   __syncwarp();

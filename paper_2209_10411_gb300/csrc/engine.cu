@@ -244,7 +244,11 @@ mi_status mi_delbm::ensure_contact_buffers() {
   hist_wall = (HistEntry*)dalloc(sizeof(HistEntry) * (size_t)(6 * ncap));
   work = (unsigned*)dalloc(sizeof(unsigned));
   substep = (long long*)dalloc(sizeof(long long));
-  if (!item_i || !item_j || !recs || !hist_pair || !hist_wall || !work || !substep)
+  bp_pos = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
+  bp_quat = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
+  bp_lo = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
+  if (!item_i || !item_j || !recs || !hist_pair || !hist_wall || !work || !substep || !bp_pos || !bp_quat ||
+      !bp_lo)
     return fail(MI_ENOMEM, "contacts: device allocation failed");
   cudaError_t e = cudaMemsetAsync(hist_pair, 0, sizeof(HistEntry) * (size_t)std::max<long long>(tri, 1), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(hist_wall, 0, sizeof(HistEntry) * (size_t)(6 * ncap), stream);
@@ -260,9 +264,9 @@ mi_status mi_delbm::ensure_guess_buffers() {
   mi_status s = ensure_contact_buffers();
   if (s != MI_OK) return s;
   guess_feat = (float*)dalloc(sizeof(float) * 64 * (size_t)cap_items);
-  guess_acts = (float*)dalloc(sizeof(float) * 512 * (size_t)cap_items);
   guess_pred = (float*)dalloc(sizeof(float) * 4 * (size_t)cap_items);
-  if (!guess_feat || !guess_acts || !guess_pred) return fail(MI_ENOMEM, "learned guess: device allocation failed");
+  mlp_image = dalloc(mlp_image_bytes());
+  if (!guess_feat || !guess_pred || !mlp_image) return fail(MI_ENOMEM, "learned guess: device allocation failed");
   return MI_OK;
 }
 
@@ -290,6 +294,9 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.cp.mu_s = h->cfg.mu_s;
   L.cp.dt = 1.0 / h->cfg.dem_substeps;
   L.cp.margin = 1.0;
+  L.pf = h->bp_pos;
+  L.qf = h->bp_quat;
+  L.plo = h->bp_lo;
   L.learned = h->learned ? 1 : 0;
   L.feat = h->guess_feat;
   L.pred = h->guess_pred;
@@ -297,7 +304,7 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.cp.n[0] = h->cfg.nx;
   L.cp.n[1] = h->cfg.ny;
   L.cp.n[2] = h->cfg.nz;
-  L.grid = h->sm_count * 4;
+  L.grid = h->sm_count * 5;  // 128-thread blocks of <= 96 registers: five fit on an SM
   return L;
 }
 
@@ -313,10 +320,9 @@ mi_status mi_delbm::phase_contact(cudaStream_t st) {
     // features of the candidates, then the MLP on as many rows as the broad phase found
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_item_features(L, st); })) != MI_OK) return s;
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] {
-           return mlp_forward_rows(mlp_params, guess_feat, (int)cap_items, &dctr->n_pairs, guess_pred, guess_acts, st);
+           return mlp_infer(mlp_image, guess_feat, (int)cap_items, &dctr->n_pairs, guess_pred, st);
          })) != MI_OK)
       return s;
-    launches += 2;  // the forward pass is three GEMM launches
   }
   return launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_contacts(L, st); });
 }
@@ -816,13 +822,10 @@ mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
   if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
   mi_status s = h->ensure_guess_buffers();
   if (s != MI_OK) return s;
-  const size_t bytes = sizeof(float) * mi_mlp_param_count();
-  if (!h->mlp_params) {
-    h->mlp_params = (float*)h->dalloc(bytes);
-    if (!h->mlp_params) return h->fail(MI_ENOMEM, "set_guess: device allocation failed");
-  }
-  cudaError_t e = cudaMemcpyAsync(h->mlp_params, params, bytes, cudaMemcpyDeviceToDevice, h->stream);
-  if (e != cudaSuccess) return h->cuda_fail(e, "set_guess: parameter copy");
+  cudaError_t e = mlp_infer_prepare();
+  if (e == cudaSuccess) e = mlp_pack(params, h->mlp_image, h->stream);
+  h->launches += 1;
+  if (e != cudaSuccess) return h->cuda_fail(e, "set_guess: packing the parameters");
   h->invalidate_graphs();
   h->learned = true;
   return MI_OK;
@@ -1200,7 +1203,11 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   P.density = density;
   P.skin = skin;
   P.re = re;
+  P.core_s = (float)(((re - skin) / re) * ((re - skin) / re));
+  P.re_f = (float)re;
+  P.skin_f = (float)skin;
   P.Rb = bounding();
+  P.Rb_f = (float)P.Rb;
   {
     // tight radius: for |x| > max|c_i|, f(x) <= sum k_i / (|x| - |c_i|)^2, which decreases
     // in |x|; beyond its root Rt (<= Rb) every node is fluid
@@ -1421,7 +1428,6 @@ mi_status mi_delbm_get_links(mi_delbm* h, size_t cap, int32_t* cell, int8_t* dir
   return MI_OK;
 }
 
-static_assert(sizeof(mi_contact) == sizeof(ContactRec), "mi_contact must mirror the device record");
 
 mi_status mi_delbm_contacts(mi_delbm* h, mi_contact* out, int cap, int* n_out) {
   if (!h || !n_out) return MI_EINVAL;
@@ -1436,8 +1442,24 @@ mi_status mi_delbm_contacts(mi_delbm* h, mi_contact* out, int cap, int* n_out) {
   *n_out = (int)n;
   if ((int)n > cap || (n > 0 && !out)) return h->fail(MI_ECAPACITY, "mi_delbm_contacts: cap below the candidate count");
   if (n) {
-    e = cudaMemcpy(out, h->recs, sizeof(ContactRec) * n, cudaMemcpyDeviceToHost);
+    // the device keeps compact records (FP32 geometry relative to the origin
+    // of particle i); the world contact point is formed here in FP64
+    std::vector<ContactRec> tmp(n);
+    e = cudaMemcpy(tmp.data(), h->recs, sizeof(ContactRec) * n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_contacts");
+    for (unsigned k = 0; k < n; ++k) {
+      const ContactRec& r = tmp[k];
+      mi_contact& c = out[k];
+      c.i = r.i;
+      c.j = r.j;
+      for (int a = 0; a < 3; ++a) {
+        c.xcp[a] = r.X[a] + (double)r.r[a];
+        c.n[a] = (double)r.n[a];
+      }
+      c.delta = (double)r.delta;
+      c.iters = r.iters;
+      c.status = r.status;
+    }
   }
   return h->check_status(false);
 }

@@ -73,11 +73,13 @@ struct mi_delbm {
   mi::HistEntry* hist_wall = nullptr;
   unsigned* work = nullptr;
   long long* substep = nullptr;
+  float4* bp_pos = nullptr;           // FP32 positions and radii of the broad phase
+  float4* bp_quat = nullptr;          // FP32 unit quaternions of the substep
+  float4* bp_lo = nullptr;            // FP32 position remainders of the substep
   // learned contact guess (MI_GUESS_LEARNED): parameters and per-item buffers
   bool learned = false;
-  float* mlp_params = nullptr;
+  void* mlp_image = nullptr;         // packed BF16 parameters of the fused inference kernel
   float* guess_feat = nullptr;       // cap_items x 64
-  float* guess_acts = nullptr;       // cap_items x 512
   float* guess_pred = nullptr;       // cap_items x 4
   // lists
   uint32_t *bc_cell = nullptr, *bc_mask = nullptr, *bc_loff = nullptr;

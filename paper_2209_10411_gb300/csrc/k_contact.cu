@@ -73,55 +73,99 @@ __global__ void k_dem_prologue(ContactLaunch L) {
     *L.work = 0;
   }
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * L.np; k += gridDim.x * blockDim.x) L.fcacc[k] = 0;
+  // per-substep FP32 staging: positions split as hi + lo (hi = the position
+  // rounded to FP32, lo = the remainder rounded), radii, unit quaternions
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.np; k += gridDim.x * blockDim.x) {
+    const DevParticle& P = L.P[k];
+    const float hx = (float)P.pos[0], hy = (float)P.pos[1], hz = (float)P.pos[2];
+    L.pf[k] = make_float4(hx, hy, hz, P.Rb_f);
+    L.plo[k] = make_float4((float)(P.pos[0] - hx), (float)(P.pos[1] - hy), (float)(P.pos[2] - hz), 0.f);
+    L.qf[k] = unit_quat_f32(P.quat);
+  }
 }
 
 cudaError_t launch_dem_prologue(const ContactLaunch& L, cudaStream_t s) {
-  k_dem_prologue<<<1, 256, 0, s>>>(L);
+  k_dem_prologue<<<(L.np + 255) / 256 + 1, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ void append_item(const ContactLaunch& L, int i, int j) {
+  const unsigned k = atomicAdd(&L.ctr->n_pairs, 1u);
+  if (k < L.cap_items) {
+    L.item_i[k] = i;
+    L.item_j[k] = j;
+  } else {
+    atomicOr(&L.ctr->status, STATUS_PAIR_OVERFLOW);
+  }
+}
+
+constexpr int BP_TILE = 64;
+
 // Candidates: pairs i < j with |X_i - X_j| <= R_b,i + R_b,j + margin, and
-// particle-wall items with n_w.(X_i - p_w) <= R_b,i + margin.
-__global__ void k_broad_phase(ContactLaunch L) {
-  const long long np = L.np;
-  const long long total = np * np + 6 * np;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i, j;
-    if (t < np * np) {
-      i = (int)(t / np);
-      j = (int)(t % np);
-      if (i >= j) continue;
-      const DevParticle& A = L.P[i];
-      const DevParticle& B = L.P[j];
-      const double d0 = A.pos[0] - B.pos[0], d1 = A.pos[1] - B.pos[1], d2 = A.pos[2] - B.pos[2];
-      if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) <= A.Rb + B.Rb + L.cp.margin)) continue;
+// particle-wall items with n_w.(X_i - p_w) <= R_b,i + margin, both decided in
+// FP64.  The pairs come in 64 x 64 tiles of the upper triangle, one block per
+// tile, with both particle ranges staged in shared memory; the blocks after
+// the tiles take the particle-wall items.  An FP32 filter settles every pair
+// whose FP32 distance lies farther from the threshold than a bound on its
+// error (each coordinate carries at most 2^-24 of its magnitude from rounding,
+// taken four times over; 1e-5 of the threshold covers the radii and the FP32
+// arithmetic); the rest take the FP64 test, so the list is the FP64 one.
+__global__ void __launch_bounds__(128) k_broad_phase(ContactLaunch L, int n_tiles) {
+  __shared__ float4 A[BP_TILE], Bt[BP_TILE];
+  const int np = L.np;
+  const int b = blockIdx.x;
+  if (b < n_tiles) {
+    // tile (ti, tj), ti <= tj, enumerated as b = tj (tj + 1) / 2 + ti
+    int tj = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while (tj * (tj + 1) / 2 > b) --tj;
+    while ((tj + 1) * (tj + 2) / 2 <= b) ++tj;
+    const int ti = b - tj * (tj + 1) / 2;
+    const int i0 = ti * BP_TILE, j0 = tj * BP_TILE;
+    if (threadIdx.x < BP_TILE) {
+      const int k = i0 + threadIdx.x;
+      A[threadIdx.x] = k < np ? L.pf[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
-      const long long t2 = t - np * np;
-      i = (int)(t2 / 6);
-      const int face = (int)(t2 % 6), axis = face / 2;
-      if (L.cp.periodic[axis]) continue;
-      const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
-      const double nw = (face & 1) ? -1.0 : 1.0;
-      if (!(nw * (L.P[i].pos[axis] - pw) <= L.P[i].Rb + L.cp.margin)) continue;
-      j = -1 - face;
+      const int k = j0 + threadIdx.x - BP_TILE;
+      Bt[threadIdx.x - BP_TILE] = k < np ? L.pf[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const unsigned k = atomicAdd(&L.ctr->n_pairs, 1u);
-    if (k < L.cap_items) {
-      L.item_i[k] = i;
-      L.item_j[k] = j;
-    } else {
-      atomicOr(&L.ctr->status, STATUS_PAIR_OVERFLOW);
+    __syncthreads();
+    for (int e = threadIdx.x; e < BP_TILE * BP_TILE; e += 128) {
+      const int a = e / BP_TILE, c = e % BP_TILE;
+      const int i = i0 + a, j = j0 + c;
+      if (i >= j || j >= np) continue;
+      const float4 pa = A[a], pb = Bt[c];
+      const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+      const float dd = sqrtf(dx * dx + dy * dy + dz * dz);
+      const float thr = pa.w + pb.w + (float)L.cp.margin;
+      const float band = 2.4e-7f * (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z)) +
+                         1e-5f * thr + 1e-6f;
+      if (dd > thr + band) continue;
+      if (dd >= thr - band) {
+        const DevParticle& P = L.P[i];
+        const DevParticle& Q = L.P[j];
+        const double d0 = P.pos[0] - Q.pos[0], d1 = P.pos[1] - Q.pos[1], d2 = P.pos[2] - Q.pos[2];
+        if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) <= P.Rb + Q.Rb + L.cp.margin)) continue;
+      }
+      append_item(L, i, j);
     }
+  } else {
+    const int t = (b - n_tiles) * 128 + threadIdx.x;
+    if (t >= 6 * np) return;
+    const int j = t / 6, face = t % 6, axis = face / 2;
+    if (L.cp.periodic[axis]) return;
+    const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
+    const double nw = (face & 1) ? -1.0 : 1.0;
+    if (!(nw * (L.P[j].pos[axis] - pw) <= L.P[j].Rb + L.cp.margin)) return;
+    append_item(L, j, -1 - face);
   }
 }
 
 cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
-  const long long total = (long long)L.np * L.np + 6LL * L.np;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 65535) blocks = 65535;
-  if (blocks < 1) blocks = 1;
-  k_broad_phase<<<(unsigned)blocks, 256, 0, s>>>(L);
+  if (L.np <= 0) return cudaSuccess;
+  const int nt = (L.np + BP_TILE - 1) / BP_TILE;
+  const int n_tiles = nt * (nt + 1) / 2;
+  const int wall_blocks = (6 * L.np + 127) / 128;
+  k_broad_phase<<<n_tiles + wall_blocks, 128, 0, s>>>(L, n_tiles);
   return cudaGetLastError();
 }
 
@@ -139,15 +183,20 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
     if (it >= n_items) break;
     const int i = L.item_i[it], j = L.item_j[it];
     const DevParticle& Pi = L.P[i];
-    double O[3];
     int status = 1, iters = 0;
-    double xcp[3], nrm[3], delta;
+    float rel[3], nf[3], dl;  // contact point - X_i, normal, overlap (FP32)
     if (j >= 0) {
       // ---------------- particle pair ----------------
       const DevParticle& Pj = L.P[j];
-      for (int a = 0; a < 3; ++a) O[a] = 0.5 * (Pi.pos[a] + Pj.pos[a]);
-      const Frame F0 = make_frame(Pi, O), F1 = make_frame(Pj, O);
-      const float Rb = (float)fmax(Pi.Rb, Pj.Rb);
+      // h = (X_j - X_i) / 2 from the hi/lo split: the hi parts of nearby
+      // particles subtract exactly, so h carries FP32 accuracy relative to
+      // the pair's own size, not to the distance from the origin
+      const float4 hi_i = L.pf[i], hi_j = L.pf[j], lo_i = L.plo[i], lo_j = L.plo[j];
+      const float h[3] = {0.5f * ((hi_j.x - hi_i.x) + (lo_j.x - lo_i.x)), 0.5f * ((hi_j.y - hi_i.y) + (lo_j.y - lo_i.y)),
+                          0.5f * ((hi_j.z - hi_i.z) + (lo_j.z - lo_i.z))};
+      Frame F0, F1;
+      pair_frames(Pi, Pj, L.qf[i], L.qf[j], h, F0, F1);
+      const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
       float y[3];
       if (L.learned) {
         // learned start: anchor and prediction of this item (features and MLP ran before)
@@ -167,6 +216,8 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         if (e0.g >= 1.f || e1.g >= 1.f) status = 3;
         else if (e0.g < C_TOL || e1.g < C_TOL) status = 4;
       }
+      // first-order projections onto the two cores, the normal between them,
+      // the overlap of the skins and the contact point (Eqs. cp, contactprop)
       const float q0 = (1.f - e0.g) / (e0.gr[0] * e0.gr[0] + e0.gr[1] * e0.gr[1] + e0.gr[2] * e0.gr[2]);
       const float q1 = (1.f - e1.g) / (e1.gr[0] * e1.gr[0] + e1.gr[1] * e1.gr[1] + e1.gr[2] * e1.gr[2]);
       float xc0[3], xc1[3], d[3];
@@ -176,16 +227,22 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         d[c] = xc0[c] - xc1[c];
       }
       const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      delta = Pi.skin + Pj.skin - (double)dist;
-      for (int c = 0; c < 3; ++c) nrm[c] = dist > 0.f ? (double)(d[c] / dist) : 0.0;
-      for (int c = 0; c < 3; ++c) xcp[c] = O[c] + (double)xc0[c] - (Pi.skin - 0.5 * delta) * nrm[c];
-      if (lane == 0 && status == 0 && delta > 0.0) {
+      dl = Pi.skin_f + Pj.skin_f - dist;
+      for (int c = 0; c < 3; ++c) {
+        nf[c] = dist > 0.f ? d[c] / dist : 0.f;
+        rel[c] = h[c] + xc0[c] - (Pi.skin_f - 0.5f * dl) * nf[c];
+      }
+      if (lane == 0 && status == 0 && dl > 0.f) {
         const int lo = min(i, j), hi = max(i, j);
-        HistEntry* h = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
-        double f[3];
-        spring_dashpot(L.cp, Pi, &Pj, xcp, nrm, delta, h, substep, f);
+        HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
+        double xcp[3], nrm[3], f[3];
+        for (int c = 0; c < 3; ++c) {
+          xcp[c] = Pi.pos[c] + (double)rel[c];
+          nrm[c] = (double)nf[c];
+        }
+        spring_dashpot(L.cp, Pi, &Pj, xcp, nrm, (double)dl, hp, substep, f);
         double vi[6], vj[6];
-        const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
+        const double ri[3] = {(double)rel[0], (double)rel[1], (double)rel[2]};
         const double rj[3] = {xcp[0] - Pj.pos[0], xcp[1] - Pj.pos[1], xcp[2] - Pj.pos[2]};
         for (int a = 0; a < 3; ++a) {
           vi[a] = f[a];
@@ -204,13 +261,13 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
     } else {
       // ---------------- particle - wall ----------------
       const int face = -1 - j, axis = face / 2;
-      for (int a = 0; a < 3; ++a) O[a] = Pi.pos[a];
-      const Frame F0 = make_frame(Pi, O);
+      const float zero[3] = {0.f, 0.f, 0.f};
+      const Frame F0 = frame_f32(Pi, L.qf[i], zero);  // local origin X_i
       float nw[3] = {0.f, 0.f, 0.f};
       nw[axis] = (face & 1) ? -1.f : 1.f;
       const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
-      const float distO = (float)((double)nw[axis] * (O[axis] - pw));
-      const float Rb = (float)Pi.Rb;
+      const float distO = (float)((double)nw[axis] * (Pi.pos[axis] - pw));
+      const float Rb = Pi.Rb_f;
       // guess: the core sphere reaching deepest towards the wall
       float best = 3.4e38f;
       int ba = 0;
@@ -250,16 +307,20 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       }
       if (iters > MAX_IT) iters = MAX_IT;
       const float dist = nw[0] * y[0] + nw[1] * y[1] + nw[2] * y[2] + distO;
-      delta = Pi.skin - (double)dist;
+      dl = Pi.skin_f - dist;
       for (int c = 0; c < 3; ++c) {
-        nrm[c] = nw[c];
-        xcp[c] = O[c] + (double)(y[c] - dist * nw[c]) + 0.5 * delta * nrm[c];
+        nf[c] = nw[c];
+        rel[c] = (y[c] - dist * nw[c]) + 0.5f * dl * nw[c];
       }
-      if (lane == 0 && status == 0 && delta > 0.0) {
-        HistEntry* h = L.hist_wall + ((long long)i * 6 + face);
-        double f[3];
-        spring_dashpot(L.cp, Pi, nullptr, xcp, nrm, delta, h, substep, f);
-        const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
+      if (lane == 0 && status == 0 && dl > 0.f) {
+        HistEntry* hp = L.hist_wall + ((long long)i * 6 + face);
+        double xcp[3], nrm[3], f[3];
+        for (int c = 0; c < 3; ++c) {
+          xcp[c] = Pi.pos[c] + (double)rel[c];
+          nrm[c] = (double)nw[c];
+        }
+        spring_dashpot(L.cp, Pi, nullptr, xcp, nrm, (double)dl, hp, substep, f);
+        const double ri[3] = {(double)rel[0], (double)rel[1], (double)rel[2]};
         double vi[6] = {f[0], f[1], f[2], ri[1] * f[2] - ri[2] * f[1], ri[2] * f[0] - ri[0] * f[2],
                         ri[0] * f[1] - ri[1] * f[0]};
         add_fixed6(L.fcacc, i, vi);
@@ -271,10 +332,11 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       r.i = i;
       r.j = j;
       for (int c = 0; c < 3; ++c) {
-        r.xcp[c] = xcp[c];
-        r.n[c] = nrm[c];
+        r.X[c] = Pi.pos[c];
+        r.r[c] = rel[c];
+        r.n[c] = nf[c];
       }
-      r.delta = delta;
+      r.delta = dl;
       r.iters = iters;
       r.status = status;
     }

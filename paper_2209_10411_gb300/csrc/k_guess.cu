@@ -22,11 +22,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
     if (j < 0) continue;
     const DevParticle& Pi = L.P[i];
     const DevParticle& Pj = L.P[j];
-    double O[3];
-    for (int a = 0; a < 3; ++a) O[a] = 0.5 * (Pi.pos[a] + Pj.pos[a]);
-    const Frame F0 = make_frame(Pi, O), F1 = make_frame(Pj, O);
+    const float4 hi_i = L.pf[i], hi_j = L.pf[j], lo_i = L.plo[i], lo_j = L.plo[j];
+    const float h[3] = {0.5f * ((hi_j.x - hi_i.x) + (lo_j.x - lo_i.x)), 0.5f * ((hi_j.y - hi_i.y) + (lo_j.y - lo_i.y)),
+                        0.5f * ((hi_j.z - hi_i.z) + (lo_j.z - lo_i.z))};
+    const float4 qi = L.qf[i], qj = L.qf[j];
+    Frame F0, F1;
+    pair_frames(Pi, Pj, qi, qj, h, F0, F1);
     float ya[3];
-    pair_features(Pi, Pj, Pi.pos, Pi.quat, Pj.pos, Pj.quat, F0, F1, L.balls, lane, sh[w], L.feat + (size_t)it * 64, ya);
+    pair_features(Pi, Pj, h, qi, qj, F0, F1, L.balls, lane, sh[w], L.feat + (size_t)it * 64, ya);
   }
 }
 
@@ -45,12 +48,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
     const double* pose = S.poses + (size_t)14 * p;
     const double *posi = pose, *qi = pose + 3, *posj = pose + 7, *qj = pose + 10;
     double O[3];
-    for (int a = 0; a < 3; ++a) O[a] = 0.5 * (posi[a] + posj[a]);
-    const Frame F0 = make_frame(Pi, posi, qi, O), F1 = make_frame(Pj, posj, qj, O);
-    const float Rb = (float)fmax(Pi.Rb, Pj.Rb);
+    float h[3];
+    for (int a = 0; a < 3; ++a) {
+      O[a] = 0.5 * (posi[a] + posj[a]);
+      h[a] = (float)(0.5 * (posj[a] - posi[a]));
+    }
+    const float4 q0 = unit_quat_f32(qi), q1 = unit_quat_f32(qj);
+    Frame F0, F1;
+    pair_frames(Pi, Pj, q0, q1, h, F0, F1);
+    const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
     float ya[3] = {0.f, 0.f, 0.f}, y[3];
     if (S.flags & MI_PAIR_FEATURES) {
-      pair_features(Pi, Pj, posi, qi, posj, qj, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya);
+      pair_features(Pi, Pj, h, q0, q1, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya);
     } else if (S.flags & MI_PAIR_LEARNED) {
       for (int c = 0; c < 3; ++c) ya[c] = Rb * S.X[(size_t)64 * p + 11 + c];
     } else {

@@ -209,28 +209,6 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
 
 }  // namespace
 
-cudaError_t mlp_forward_rows(const float* params, const float* X, int M, const unsigned* Mdev, float* Y, float* acts,
-                             cudaStream_t s) {
-  const float* P[6];
-  P[0] = params;
-  P[1] = P[0] + 64 * 256;
-  P[2] = P[1] + 256;
-  P[3] = P[2] + 256 * 256;
-  P[4] = P[3] + 256;
-  P[5] = P[4] + 256 * 4;
-  float* H1 = acts;
-  float* H2 = acts + (size_t)M * 256;
-  GemmArgs a = gemm_args(M, 256, 64, X, 64, 0, P[0], 256, 0, P[1], 1, nullptr, 0, H1, 256);
-  a.Mdev = Mdev;
-  cudaError_t e = gemm(a, s);
-  if (e != cudaSuccess) return e;
-  a = gemm_args(M, 256, 256, H1, 256, 0, P[2], 256, 0, P[3], 1, nullptr, 0, H2, 256);
-  a.Mdev = Mdev;
-  if ((e = gemm(a, s)) != cudaSuccess) return e;
-  a = gemm_args(M, 4, 256, H2, 256, 0, P[4], 4, 0, P[5], 0, nullptr, 0, Y, 4);
-  a.Mdev = Mdev;
-  return gemm(a, s);
-}
 
 }  // namespace mi
 
@@ -339,6 +317,268 @@ mi_status mi_mlp_adamw(float* params, const float* grads, float* m, float* v, in
                                                              weight_decay, c1, c2);
   if (cudaGetLastError() != cudaSuccess) {
     set_thread_error("mi_mlp_adamw: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fused inference: the whole network for a 64-row tile in one CTA.  The
+// parameters are packed once into a BF16 image laid out as the CTA's shared
+// memory wants it (weights transposed to (n, k) with padded rows, so that
+// every fragment load is one conflict-free 32-bit word); each CTA copies the
+// image with 16-byte loads and then loops over row tiles (persistent).
+// Layers 1 and 2 run on the tensor cores; the 256 -> 4 output layer is done
+// in the epilogue of layer 2 with the same BF16 operands (their products are
+// exact in FP32) and FP32 sums, so H2 never leaves registers.
+// ---------------------------------------------------------------------------
+namespace mi {
+namespace {
+
+constexpr int FT_ROWS = 64;                       // rows per tile
+constexpr int FW1_LD = 72, FW2_LD = 264;          // padded row lengths (bf16) of W1^T, W2^T
+constexpr int FX_LD = 72, FH_LD = 264;            // padded row lengths of the X and H1 tiles
+constexpr size_t IMG_W1 = 0;
+constexpr size_t IMG_W2 = IMG_W1 + 256 * FW1_LD * 2;       // 36864
+constexpr size_t IMG_W3 = IMG_W2 + 256 * FW2_LD * 2;       // 172032: W3^T (4 x 256) as BF16-valued floats
+constexpr size_t IMG_B1 = IMG_W3 + 4 * 256 * 4;
+constexpr size_t IMG_B2 = IMG_B1 + 256 * 4;
+constexpr size_t IMG_B3 = IMG_B2 + 256 * 4;
+constexpr size_t IMG_BYTES = IMG_B3 + 16;                  // 178192 (a multiple of 16)
+constexpr size_t SM_X = IMG_BYTES;
+constexpr size_t SM_H1 = SM_X + FT_ROWS * FX_LD * 2;
+constexpr size_t SM_Y = SM_H1 + FT_ROWS * FH_LD * 2;
+constexpr size_t SM_BYTES = SM_Y + 8 * FT_ROWS * 4 * 4;    // 229392
+static_assert(IMG_BYTES % 16 == 0 && SM_BYTES <= 232448, "fused MLP shared memory layout");
+
+__global__ void k_mlp_pack(const float* __restrict__ p, unsigned char* __restrict__ img) {
+  const float* W1 = p;
+  const float* b1 = W1 + 64 * 256;
+  const float* W2 = b1 + 256;
+  const float* b2 = W2 + 256 * 256;
+  const float* W3 = b2 + 256;
+  const float* b3 = W3 + 256 * 4;
+  __nv_bfloat16* w1t = reinterpret_cast<__nv_bfloat16*>(img + IMG_W1);
+  __nv_bfloat16* w2t = reinterpret_cast<__nv_bfloat16*>(img + IMG_W2);
+  float* w3t = reinterpret_cast<float*>(img + IMG_W3);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int e = tid; e < 256 * FW1_LD; e += nt) {
+    const int n = e / FW1_LD, k = e % FW1_LD;
+    w1t[e] = __float2bfloat16_rn(k < 64 ? W1[k * 256 + n] : 0.f);
+  }
+  for (int e = tid; e < 256 * FW2_LD; e += nt) {
+    const int n = e / FW2_LD, k = e % FW2_LD;
+    w2t[e] = __float2bfloat16_rn(k < 256 ? W2[k * 256 + n] : 0.f);
+  }
+  for (int e = tid; e < 4 * 256; e += nt) {
+    const int o = e / 256, c = e % 256;
+    w3t[e] = __bfloat162float(__float2bfloat16_rn(W3[c * 4 + o]));
+  }
+  for (int e = tid; e < 256; e += nt) {
+    reinterpret_cast<float*>(img + IMG_B1)[e] = b1[e];
+    reinterpret_cast<float*>(img + IMG_B2)[e] = b2[e];
+  }
+  if (tid < 4) reinterpret_cast<float*>(img + IMG_B3)[tid] = b3[tid];
+}
+
+__global__ void __launch_bounds__(256, 1) k_mlp_fused(const uint4* __restrict__ img, const float* __restrict__ X,
+                                                      int M, const unsigned* __restrict__ Mdev,
+                                                      float* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+  if (Mdev) M = min(M, (int)*Mdev);
+  const int tiles = (M + FT_ROWS - 1) / FT_ROWS;
+  if ((int)blockIdx.x >= tiles) return;
+  for (int e = tid; e < (int)(IMG_BYTES / 16); e += 256) reinterpret_cast<uint4*>(sm)[e] = img[e];
+  const __nv_bfloat16(*W1t)[FW1_LD] = reinterpret_cast<const __nv_bfloat16(*)[FW1_LD]>(sm + IMG_W1);
+  const __nv_bfloat16(*W2t)[FW2_LD] = reinterpret_cast<const __nv_bfloat16(*)[FW2_LD]>(sm + IMG_W2);
+  const float* W3t = reinterpret_cast<const float*>(sm + IMG_W3);
+  const float* b1 = reinterpret_cast<const float*>(sm + IMG_B1);
+  const float* b2 = reinterpret_cast<const float*>(sm + IMG_B2);
+  const float* b3 = reinterpret_cast<const float*>(sm + IMG_B3);
+  __nv_bfloat16(*Xs)[FX_LD] = reinterpret_cast<__nv_bfloat16(*)[FX_LD]>(sm + SM_X);
+  __nv_bfloat16(*H1)[FH_LD] = reinterpret_cast<__nv_bfloat16(*)[FH_LD]>(sm + SM_H1);
+  float(*Yp)[FT_ROWS][4] = reinterpret_cast<float(*)[FT_ROWS][4]>(sm + SM_Y);
+  const int wn = warp * 32;  // this warp's 32 output columns of layers 1 and 2
+
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int r0 = t * FT_ROWS;
+    __syncthreads();  // previous tile's readers of Xs, H1 and Yp are done (and the image is in place)
+    for (int e = tid; e < FT_ROWS * 16; e += 256) {
+      const int r = e >> 4, c4 = (e & 15) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + r < M) v = *reinterpret_cast<const float4*>(X + (size_t)(r0 + r) * 64 + c4);
+      Xs[r][c4] = __float2bfloat16_rn(v.x);
+      Xs[r][c4 + 1] = __float2bfloat16_rn(v.y);
+      Xs[r][c4 + 2] = __float2bfloat16_rn(v.z);
+      Xs[r][c4 + 3] = __float2bfloat16_rn(v.w);
+    }
+    __syncthreads();
+    float acc[4][4][4];
+    // ---- layer 1: H1 = relu(X W1 + b1), rows 0..63 x columns wn..wn+31 ----
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 64; kk += 16) {
+      unsigned a[4][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = 16 * i + gid;
+        a[i][0] = ld32(&Xs[r][kk + 2 * tig]);
+        a[i][1] = ld32(&Xs[r + 8][kk + 2 * tig]);
+        a[i][2] = ld32(&Xs[r][kk + 2 * tig + 8]);
+        a[i][3] = ld32(&Xs[r + 8][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + 8 * j + gid;
+        b[j][0] = ld32(&W1t[n][kk + 2 * tig]);
+        b[j][1] = ld32(&W1t[n][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = 16 * i + gid + 8 * h, col = wn + 8 * j + 2 * tig;
+          const float v0 = fmaxf(acc[i][j][2 * h] + b1[col], 0.f);
+          const float v1 = fmaxf(acc[i][j][2 * h + 1] + b1[col + 1], 0.f);
+          __nv_bfloat162 pr;
+          pr.x = __float2bfloat16_rn(v0);
+          pr.y = __float2bfloat16_rn(v1);
+          *reinterpret_cast<__nv_bfloat162*>(&H1[row][col]) = pr;
+        }
+    __syncthreads();
+    // ---- layer 2: H2 = relu(H1 W2 + b2), same warp tiling, K = 256 ----
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+#pragma unroll 4
+    for (int kk = 0; kk < 256; kk += 16) {
+      unsigned a[4][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = 16 * i + gid;
+        a[i][0] = ld32(&H1[r][kk + 2 * tig]);
+        a[i][1] = ld32(&H1[r + 8][kk + 2 * tig]);
+        a[i][2] = ld32(&H1[r][kk + 2 * tig + 8]);
+        a[i][3] = ld32(&H1[r + 8][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + 8 * j + gid;
+        b[j][0] = ld32(&W2t[n][kk + 2 * tig]);
+        b[j][1] = ld32(&W2t[n][kk + 2 * tig + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
+    }
+    // ---- layer 3 in the epilogue: partial Y over this warp's 32 columns ----
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int col = wn + 8 * j + 2 * tig + e;
+            const float hv = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[i][j][2 * h + e] + b2[col], 0.f)));
+#pragma unroll
+            for (int o = 0; o < 4; ++o) y[o] += hv * W3t[o * 256 + col];
+          }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          y[o] += __shfl_xor_sync(0xffffffffu, y[o], 1);
+          y[o] += __shfl_xor_sync(0xffffffffu, y[o], 2);
+        }
+        if (tig == 0) {
+          const int row = 16 * i + gid + 8 * h;
+#pragma unroll
+          for (int o = 0; o < 4; ++o) Yp[warp][row][o] = y[o];
+        }
+      }
+    __syncthreads();
+    {
+      const int row = tid >> 2, o = tid & 3;
+      float v = b3[o];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += Yp[w][row][o];
+      if (r0 + row < M) Y[(size_t)(r0 + row) * 4 + o] = v;
+    }
+  }
+}
+
+}  // namespace
+
+size_t mlp_image_bytes() { return IMG_BYTES; }
+
+cudaError_t mlp_pack(const float* params, void* image, cudaStream_t s) {
+  k_mlp_pack<<<64, 256, 0, s>>>(params, reinterpret_cast<unsigned char*>(image));
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_infer_prepare() {
+  return cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+}
+
+cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int tiles = (M + FT_ROWS - 1) / FT_ROWS;
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = tiles < sms ? tiles : sms;
+  k_mlp_fused<<<grid, 256, SM_BYTES, s>>>(reinterpret_cast<const uint4*>(image), X, M, Mdev, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace mi
+
+extern "C" {
+
+size_t mi_mlp_image_bytes(void) { return mi::IMG_BYTES; }
+
+mi_status mi_mlp_pack(const float* params, void* image, void* stream) {
+  if (!params || !image || (reinterpret_cast<uintptr_t>(image) & 15)) {
+    mi::set_thread_error("mi_mlp_pack: null pointer or image not 16-byte aligned");
+    return MI_EINVAL;
+  }
+  if (mi::mlp_pack(params, image, (cudaStream_t)stream) != cudaSuccess) {
+    mi::set_thread_error("mi_mlp_pack: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_infer(const void* image, const float* X, int n, float* Y, void* stream) {
+  if (n < 0 || (n > 0 && (!image || !X || !Y)) || (reinterpret_cast<uintptr_t>(image) & 15) ||
+      (reinterpret_cast<uintptr_t>(X) & 15)) {
+    mi::set_thread_error("mi_mlp_infer: null pointer, negative batch, or image/X not 16-byte aligned");
+    return MI_EINVAL;
+  }
+  if (n == 0) return MI_OK;
+  if (mi::mlp_infer_prepare() != cudaSuccess || mi::mlp_infer(image, X, n, nullptr, Y, (cudaStream_t)stream) != cudaSuccess) {
+    mi::set_thread_error("mi_mlp_infer: launch failed");
     return MI_ECUDA;
   }
   return MI_OK;

@@ -188,6 +188,8 @@ struct DevParticle {
   double inertia[9], inv_inertia[9];         // body frame, about the centroid
   double R[9];                               // body -> world rotation at the current pose
   float posf[3], velf[3], omegaf[3];         // FP32 copies for the lattice kernels
+  float core_s;                              // core scale s = ((r_e - R_s) / r_e)^2 (constant)
+  float Rb_f, re_f, skin_f;                  // FP32 copies of R_b, r_e, R_s (constant)
   int ball_off, n_balls;
   int ext[3];                                // node box extent per axis (constant)
   int lo[3];                                 // node box origin at the current pose
@@ -256,7 +258,10 @@ cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s);
 // ---------------------------------------------------------------------------
 struct ContactRec {       // one candidate (pair or particle-wall) of the last substep
   int i, j;               // j >= 0 particle, j = -1 - face for a wall
-  double xcp[3], n[3], delta;
+  double X[3];            // origin of particle i at the substep (copied, for the world contact point)
+  float r[3];             // contact point - X_i
+  float n[3];             // unit normal (towards particle i for pairs, into the domain for walls)
+  float delta;            // overlap of the skins
   int iters, status;      // status: 0 ok, 1 not converged, 2 singular, 3 inside a core, 4 out of range
 };
 struct HistEntry {        // tangential spring of a pair / particle-wall contact
@@ -284,6 +289,9 @@ struct ContactLaunch {
   long long* substep;     // device substep counter
   ContactParams cp;
   int grid;
+  float4* pf;             // np FP32 (position rounded to FP32, R_b) of the substep
+  float4* plo;            // np FP32 remainders (position - pf.xyz) of the substep
+  float4* qf;             // np FP32 unit quaternions (w, x, y, z) of the substep
   int learned;            // 1: pair items start from the learned guess (feat, pred), else the plain guess
   float* feat;            // cap_items x 64 features of the pair items (learned)
   const float* pred;      // cap_items x 4 MLP outputs (learned)
@@ -313,11 +321,15 @@ struct PairSolveLaunch {
 };
 cudaError_t launch_pair_solve(const PairSolveLaunch& S, cudaStream_t s);
 
-// MLP forward of the learned guess on at most M rows, the row count read on
-// the device from *Mdev (capped at M): used inside a step, whose number of
-// candidates is known only on the device.  acts holds M x 512 floats.
-cudaError_t mlp_forward_rows(const float* params, const float* X, int M, const unsigned* Mdev, float* Y, float* acts,
-                             cudaStream_t s);
+// Fused MLP inference of the learned guess from a packed BF16 image
+// (mlp_pack): Y (M x 4) for X (M x 64, 16-byte aligned), the row count read
+// on the device from *Mdev when given (capped at M), as a step needs: its
+// number of candidates is known only on the device.  mlp_infer_prepare sets
+// the kernel's shared-memory limit; call it outside any stream capture.
+size_t mlp_image_bytes();
+cudaError_t mlp_pack(const float* params, void* image, cudaStream_t s);
+cudaError_t mlp_infer_prepare();
+cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, cudaStream_t s);
 
 struct IntegrateLaunch {
   DevParticle* P;

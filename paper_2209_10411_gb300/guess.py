@@ -22,7 +22,7 @@ import numpy as np
 
 from . import scenes
 from ._binding import (PAIR_FEATURES, PAIR_LABELS, PAIR_LEARNED, PAIR_PLAIN, mlp_adamw, mlp_backward,
-                       mlp_forward, mlp_mse, mlp_param_count)
+                       mlp_forward, mlp_infer, mlp_mse, mlp_pack, mlp_param_count)
 
 
 def bed_shapes(seed, n_shapes, n_range=(4, 128), R_range=(8.0, 16.0), skin=1.0):
@@ -174,13 +174,9 @@ def _fit(X, T, steps, batch, lr, lr_final, weight_decay, seed, params, log_every
     return p, history
 
 
-def predict(params, X, batch=1 << 17):
-    import torch
-    out = []
-    for a in range(0, X.shape[0], batch):
-        Y, _ = mlp_forward(params, X[a:a + batch].contiguous())
-        out.append(Y)
-    return torch.cat(out) if out else torch.empty((0, 4), device=X.device)
+def predict(params, X):
+    """Network outputs for X through the fused inference kernel."""
+    return mlp_infer(mlp_pack(params), X.contiguous())
 
 
 def compare(sim, params, ij, poses):

@@ -113,6 +113,26 @@ def test_forward_backward_against_oracle(setup, n):
         assert _rel(Gg[k], Gb[k]) <= 2e-3, (k, _rel(Gg[k], Gb[k]))
 
 
+@pytest.mark.parametrize("n", [1, 63, 200, 20000])
+def test_fused_inference_against_oracle(setup, n):
+    """The fused kernel (whole network per 64-row tile, output layer in the
+    epilogue) against the BF16-operand oracle and against the GEMM path;
+    20000 rows exceed one tile per SM, so the persistent loop runs."""
+    B, torch, rng, p = setup
+    X = rng.normal(size=(n, 64)).astype(np.float32).astype(np.float64)
+    dp = torch.as_tensor(_flat(p), device="cuda")
+    dX = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    Yf = B.mlp_infer(B.mlp_pack(dp), dX)
+    Yg, _ = B.mlp_forward(dp, dX)
+    torch.cuda.synchronize()
+    Yf, Yg = Yf.cpu().numpy().astype(np.float64), Yg.cpu().numpy().astype(np.float64)
+    Yb, _, _ = _oracle_bf16(p, X, np.zeros((n, 4)))
+    Yo, _ = mlp.forward(p, X)
+    assert _rel(Yf, Yb) <= 2e-4, _rel(Yf, Yb)
+    assert _rel(Yf, Yg) <= 2e-4, _rel(Yf, Yg)
+    assert _rel(Yf, Yo) <= 1e-2
+
+
 def test_empty_batch_forward(setup):
     B, torch, rng, p = setup
     dp = torch.as_tensor(_flat(p), device="cuda")
