@@ -357,8 +357,10 @@ mi_status mi_delbm_autotune(mi_delbm *h, const char *cache_path, int *bulk_block
  * kernel threads per block along x (32..256, a multiple of 32; at most 128
  * with pairs), rows per thread (1 or 2), paired nodes (0: no; 1 or 2: two
  * x-adjacent nodes per thread with paired accesses, used only when nx is
- * even; for 16-bit storages 1 and 2 select a 64- or 80-register budget),
- * list-kernel blocks per SM (1..64).  Results do not depend on them. */
+ * even; for 16-bit storages 1 and 2 select a 64- or 80-register budget;
+ * 3: four x-adjacent nodes per thread with 64-bit accesses, 16-bit storages
+ * with nx a multiple of 4 only, else the one-node kernel), list-kernel
+ * blocks per SM (1..64).  Results do not depend on them. */
 mi_status mi_delbm_set_tuning(mi_delbm *h, int bulk_block_x, int bulk_rows, int bulk_pairs, int list_blocks_per_sm);
 
 /* The launch shapes in use (any pointer may be NULL). */

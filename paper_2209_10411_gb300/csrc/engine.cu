@@ -679,6 +679,11 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
   h->tune.bulk_block_x = cfg->nx >= 256 ? 128 : (cfg->nx >= 128 ? 64 : 32);
   h->tune.bulk_rows = 1;
   h->tune.bulk_pairs = 0;
+  if (cfg->storage != MI_STORE_F32 && cfg->nx % 4 == 0) {
+    // 16-bit storages: four nodes per thread with 64-bit accesses
+    h->tune.bulk_pairs = 3;
+    h->tune.bulk_block_x = cfg->nx >= 256 ? 64 : 32;
+  }
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && sms > 0)
@@ -964,10 +969,10 @@ extern "C" mi_status mi_delbm_set_tuning(mi_delbm* h, int bulk_block_x, int bulk
                                          int list_blocks_per_sm) {
   if (!h) return MI_EINVAL;
   if (bulk_block_x < 32 || bulk_block_x > 256 || bulk_block_x % 32 != 0 || (bulk_rows != 1 && bulk_rows != 2) ||
-      bulk_pairs < 0 || bulk_pairs > 2 || (bulk_pairs && bulk_block_x > 128) || list_blocks_per_sm < 1 ||
+      bulk_pairs < 0 || bulk_pairs > 3 || (bulk_pairs && bulk_block_x > 128) || list_blocks_per_sm < 1 ||
       list_blocks_per_sm > 64)
     return h->fail(MI_EINVAL, "mi_delbm_set_tuning: block_x 32..256 (multiple of 32, <= 128 with pairs), rows 1|2, "
-                              "pairs 0|1|2, list blocks per SM 1..64");
+                              "pairs 0|1|2|3, list blocks per SM 1..64");
   h->tune.bulk_block_x = bulk_block_x;
   h->tune.bulk_rows = bulk_rows;
   h->tune.bulk_pairs = bulk_pairs;
@@ -1004,13 +1009,15 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
     L.storage = h->cfg.storage;
     L.forcing = h->forcing();
     float best = 1e30f;
-    // variants: 1 row, 2 rows, paired nodes (two register budgets for 16-bit storages)
-    for (int variant = 0; variant < 4; ++variant) {
+    // variants: 1 row, 2 rows, paired nodes (two register budgets for 16-bit
+    // storages), four nodes per thread (16-bit storages)
+    for (int variant = 0; variant < 5; ++variant) {
       const int pairs = variant >= 2 ? variant - 1 : 0;
       if (pairs && (h->cfg.nx % 2) != 0) continue;
-      if (pairs == 2 && h->cfg.storage == MI_STORE_F32) continue;
+      if (pairs >= 2 && h->cfg.storage == MI_STORE_F32) continue;
+      if (pairs == 3 && (h->cfg.nx % 4) != 0) continue;
       for (int bx : {32, 64, 128, 256}) {
-        const int span = pairs ? 2 * bx : bx;
+        const int span = pairs == 3 ? 4 * bx : pairs ? 2 * bx : bx;
         if (bx > 32 && span / 2 >= h->cfg.nx) break;
         if (pairs && bx > 128) break;
         L.block_x = bx;

@@ -259,6 +259,109 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_pairs16(const typename Store
   for (int i = 0; i < 19; ++i) __stcs(reinterpret_cast<unsigned*>(B + i * g.plane + c0), out[i]);
 }
 
+// 16-bit storages: four x-adjacent nodes (x0 .. x0 + 3, x0 a multiple of 4)
+// per thread.  Each pull is one aligned 64-bit load per direction when e_x = 0;
+// for e_x = +1 (-1) the four shifted elements x0 - 1 .. x0 + 2 (x0 + 1 ..
+// x0 + 4) are the quad's own aligned 64-bit word plus the aligned 32-bit
+// word beside it, joined by two byte permutes.  The 16-bit values stay packed
+// in registers until each node's collision, and every direction is stored as
+// one 64-bit streaming store: a 16-bit storage moves half the bytes of FP32
+// per instruction, and the wider accesses keep the instruction count per
+// byte near that of the FP32 kernel.  The quads at the x faces stay on this
+// path (no warp mixes paths): the word beside them comes from the other end
+// of the row when x is periodic, else the face node's pulled value is
+// replaced after unpacking by its halfway bounce-back.  Rows on the y and z
+// faces (whole warps) take the general per-node path.  The same concurrency
+// contract as k_bulk.  Requires nx % 4 == 0.
+template <int ST> __device__ __forceinline__ float2 unpack2(unsigned w);
+template <> __device__ __forceinline__ float2 unpack2<MI_STORE_F16_DEV>(unsigned w) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+template <> __device__ __forceinline__ float2 unpack2<MI_STORE_BF16_DEV>(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+template <int ST> __device__ __forceinline__ unsigned pack2(float a, float b);
+template <> __device__ __forceinline__ unsigned pack2<MI_STORE_F16_DEV>(float a, float b) {
+  const __half2 v = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+template <> __device__ __forceinline__ unsigned pack2<MI_STORE_BF16_DEV>(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <int ST, bool FORCE>
+__global__ void __launch_bounds__(128, FORCE ? 3 : 5) k_bulk_quad16(const typename Store<ST>::T* __restrict__ A,
+                                                     typename Store<ST>::T* __restrict__ B, LatticeGeom g,
+                                                     CollideParams P) {
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x0 >= g.nx) return;
+  const long long c0 = x0 + (long long)g.nx * (y + (long long)g.ny * z);
+  if (!((y > 0) & (y < g.ny - 1) & (z > 0) & (z < g.nz - 1))) {
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) update_node<ST, FORCE>(A, B, g, P, x0 + k, y, z, c0 + k);
+    return;
+  }
+  const bool lo_edge = x0 == 0, hi_edge = x0 == g.nx - 4, xper = g.periodic[0] != 0;
+  const unsigned short* Au = reinterpret_cast<const unsigned short*>(A);
+  const long long nxy = (long long)g.nx * g.ny;
+  uint2 in[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    // aligned position of node x0 in the source row of direction i
+    const unsigned short* row = Au + i * g.plane + (c0 - ((long long)g.nx * cy(i) + nxy * cz(i)));
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(row));
+    if (cx(i) == 0) {
+      in[i] = w;
+    } else if (cx(i) == 1) {  // elements x0 - 1 .. x0 + 2
+      unsigned before;        // its high half: element x0 - 1
+      if (!lo_edge) before = __ldg(reinterpret_cast<const unsigned*>(row - 2));
+      else before = xper ? (unsigned)__ldg(row + g.nx - 1) << 16 : 0u;  // wall: replaced below
+      in[i] = make_uint2(__byte_perm(before, w.x, 0x5432), __byte_perm(w.x, w.y, 0x5432));
+    } else {                  // elements x0 + 1 .. x0 + 4
+      unsigned after;         // its low half: element x0 + 4
+      if (!hi_edge) after = __ldg(reinterpret_cast<const unsigned*>(row + 4));
+      else after = xper ? (unsigned)__ldg(row - x0) : 0u;  // wall: replaced below
+      in[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, after, 0x5432));
+    }
+  }
+  uint2 out[19];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    float h0[19], h1[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      const float2 v = unpack2<ST>(half ? in[i].y : in[i].x);
+      h0[i] = v.x;
+      h1[i] = v.y;
+    }
+    if (!xper) {
+      // halfway bounce-back at the x faces: f_in,i(x) = f+_opp(i)(x) + 6 w_i rho0 e_i.u_wall
+      if (half == 0 && lo_edge) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+          if (cx(i) == 1) h0[i] = dev16<ST>(__ldg(Au + opp(i) * g.plane + c0)) + P.bb_wall[0][i];
+      }
+      if (half == 1 && hi_edge) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+          if (cx(i) == -1) h1[i] = dev16<ST>(__ldg(Au + opp(i) * g.plane + c0 + 3)) + P.bb_wall[1][i];
+      }
+    }
+    collide_inplace<FORCE>(h0, P);
+    collide_inplace<FORCE>(h1, P);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      const unsigned wv = pack2<ST>(h0[i], h1[i]);
+      if (half) out[i].y = wv; else out[i].x = wv;
+    }
+  }
+  unsigned short* Bu = reinterpret_cast<unsigned short*>(B);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) __stcs(reinterpret_cast<uint2*>(Bu + i * g.plane + c0), out[i]);
+}
+
 template <int ST, bool FORCE>
 static cudaError_t launch_bulk_pairs_t(const BulkLaunch& L, cudaStream_t s) {
   using T = typename Store<ST>::T;
@@ -280,9 +383,23 @@ static cudaError_t launch_bulk_pairs_t(const BulkLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int ST, bool FORCE>
+static cudaError_t launch_bulk_quad_t(const BulkLaunch& L, cudaStream_t s) {
+  constexpr int S16 = ST == MI_STORE_F32 ? MI_STORE_F16_DEV : ST;
+  using T16 = typename Store<S16>::T;
+  const int bx = L.block_x;
+  const int nq = L.g.nx / 4;
+  dim3 grid((nq + bx - 1) / bx, L.g.ny, L.g.nz);
+  k_bulk_quad16<S16, FORCE><<<grid, bx, 0, s>>>(reinterpret_cast<const T16*>(L.A), reinterpret_cast<T16*>(L.B), L.g,
+                                                L.p);
+  return cudaGetLastError();
+}
+
 template <int ST>
 static cudaError_t launch_bulk_st(const BulkLaunch& L, cudaStream_t s) {
-  if (L.pairs && L.g.nx % 2 == 0 && L.g.nx >= 2)
+  if (ST != MI_STORE_F32 && L.pair_mode == 3 && L.g.nx % 4 == 0 && L.g.nx >= 4)
+    return L.forcing ? launch_bulk_quad_t<ST, true>(L, s) : launch_bulk_quad_t<ST, false>(L, s);
+  if (L.pairs && L.pair_mode != 3 && L.g.nx % 2 == 0 && L.g.nx >= 2)
     return L.forcing ? launch_bulk_pairs_t<ST, true>(L, s) : launch_bulk_pairs_t<ST, false>(L, s);
   if (L.rows == 2) return L.forcing ? launch_bulk_t<ST, true, 2>(L, s) : launch_bulk_t<ST, false, 2>(L, s);
   return L.forcing ? launch_bulk_t<ST, true, 1>(L, s) : launch_bulk_t<ST, false, 1>(L, s);

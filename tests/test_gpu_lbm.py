@@ -39,7 +39,7 @@ CASES = [
 
 
 # launch variants of the bulk kernel: (threads per block, rows per thread, paired nodes)
-VARIANTS = [(128, 1, 0), (32, 2, 0), (64, 1, 1), (32, 1, 1), (128, 1, 2)]
+VARIANTS = [(128, 1, 0), (32, 2, 0), (64, 1, 1), (32, 1, 1), (128, 1, 2), (32, 1, 3), (128, 1, 3)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -69,7 +69,8 @@ def test_bulk_f32_matches_oracle(case, nsteps, variant):
 
 @pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("shape,variant", [((45, 10, 9), 0), ((46, 10, 9), 2), ((70, 6, 5), 3), ((64, 7, 6), 1),
-                                           ((262, 5, 4), 4)])
+                                           ((262, 5, 4), 4), ((48, 10, 9), 5), ((264, 6, 5), 6), ((50, 8, 7), 5),
+                                           ((12, 5, 4), 6)])
 def test_bulk_16bit_deviation_storage(storage, shape, variant):
     B = binding()
     wv = np.zeros((6, 3))
@@ -139,3 +140,41 @@ def test_bulk_full_size_sampled(variant):
         got = np.stack([after[i, cells[:, 2], cells[:, 1], cells[:, 0]] for i in range(19)])
     rel = np.abs(got - ref) / np.abs(ref)
     assert rel.max() < 1e-5, "max rel err %g" % rel.max()
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_bulk_16bit_full_size_sampled(storage):
+    """256x256x512 in 16-bit deviation storage, one step with the four-node
+    kernel (the benchmark's 16-bit configuration), checked on 4096 random
+    nodes plus corners and edges against the oracle fed the decoded inputs:
+    within one unit in the last place of the stored type (plus 1e-7)."""
+    import torch
+    B = binding()
+    shape = (256, 256, 512)
+    nx, ny, nz = shape
+    bx, rows, pairs = VARIANTS[6]
+    with B.Simulation(*shape, tau=TAU, storage=storage) as sim:
+        sim.set_tuning(bx, rows, pairs, 8)
+        t = pop_tensor(sim)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(4321)
+        w = torch.tensor(W, dtype=torch.float32, device="cuda").reshape(19, 1)
+        ncell = nx * ny * nz
+        dev = w * 0.05 * torch.randn((19, ncell), generator=g, device="cuda")
+        t[:, :ncell] = (dev.half() if storage == 1 else dev.bfloat16()).view(torch.int16)
+        del dev
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(4)
+        cells = np.stack([rng.integers(0, nx, 4096), rng.integers(0, ny, 4096), rng.integers(0, nz, 4096)], 1)
+        corners = np.array([[x, y, z] for x in (0, nx - 1) for y in (0, ny - 1) for z in (0, nz - 1)])
+        edges = np.array([[0, 5, 7], [nx - 1, 100, 200], [3, 9, 9], [4, 9, 9], [nx - 5, 9, 9], [nx - 8, 9, 9],
+                          [17, 0, 300], [18, ny - 1, 1], [200, 3, 0], [9, 9, nz - 1]])
+        cells = np.concatenate([cells, corners, edges])
+        before = DeviceGather(sim)
+        ref = lbm.update_cells(before, cells, TAU)
+        sim.step(1)
+        after = DeviceGather(sim)
+        got = np.stack([after[i, cells[:, 2], cells[:, 1], cells[:, 0]] for i in range(19)])
+    Wc = W.reshape(19, 1)
+    err = np.abs(got - ref)
+    assert np.all(err <= ulp16(ref - Wc, storage) + 1e-7), "max err %g" % err.max()
