@@ -451,10 +451,13 @@ __device__ __forceinline__ void rigid_u(const DevParticle& P, double px, double 
   u[2] = P.velf[2] + (P.omegaf[0] * r1 - P.omegaf[1] * r0);
 }
 
+// Node coordinates of a list entry (particle lists store node indices as
+// uint32, so 32-bit divisions suffice).
 __device__ __forceinline__ void coords(long long c, const LatticeGeom& g, int& x, int& y, int& z) {
-  x = (int)(c % g.nx);
-  y = (int)((c / g.nx) % g.ny);
-  z = (int)(c / ((long long)g.nx * g.ny));
+  const unsigned cu = (unsigned)c, row = cu / (unsigned)g.nx;
+  x = (int)(cu - row * (unsigned)g.nx);
+  z = (int)(row / (unsigned)g.ny);
+  y = (int)(row - (unsigned)z * (unsigned)g.ny);
 }
 
 template <int ST>
@@ -633,10 +636,12 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
           p = (int)pl.link_p[l];
           const DevParticle& P = pl.P[p];
           const float q = LADD ? 0.5f : pl.link_q[l];
-          // wall point relative to the particle position: node offset in FP64, once
-          const float r0 = (float)((double)x - P.pos[0]) + q * ed[0];
-          const float r1 = (float)((double)y - P.pos[1]) + q * ed[1];
-          const float r2 = (float)((double)z - P.pos[2]) + q * ed[2];
+          // wall point relative to the particle position: x - X = (x - floor X) - frac X,
+          // the integer part exact and the fraction rounded once to FP32 (no FP64 here:
+          // it runs at a small fraction of the FP32 rate on this part)
+          const float r0 = ((float)(x - P.pos_i[0]) - P.pos_fr[0]) + q * ed[0];
+          const float r1 = ((float)(y - P.pos_i[1]) - P.pos_fr[1]) + q * ed[1];
+          const float r2 = ((float)(z - P.pos_i[2]) - P.pos_fr[2]) + q * ed[2];
           float uw[3];
           uw[0] = P.velf[0] + (P.omegaf[1] * r2 - P.omegaf[2] * r1);
           uw[1] = P.velf[1] + (P.omegaf[2] * r0 - P.omegaf[0] * r2);

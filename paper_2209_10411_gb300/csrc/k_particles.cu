@@ -113,9 +113,13 @@ __global__ void k_prologue(ParticleLaunch L) {
   if (p >= L.np) return;
   DevParticle& P = L.P[p];
   quat_to_R_exact(P.quat, P.R);
+  for (int k = 0; k < 9; ++k) P.Rf[k] = (float)P.R[k];
   for (int a = 0; a < 3; ++a) {
     P.lo[a] = (int)floor(P.pos[a] - P.Rt) - 1;
     P.posf[a] = (float)P.pos[a];
+    const double fl = floor(P.pos[a]);
+    P.pos_i[a] = (int)fl;
+    P.pos_fr[a] = (float)(P.pos[a] - fl);
     P.velf[a] = (float)P.vel[a];
     P.omegaf[a] = (float)P.omega[a];
     const int prev = P.lo_hist[L.prev_buf][a];
@@ -173,14 +177,14 @@ __global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (int a = 0; a < 3; ++a) L.P[p].lo_hist[L.cur_buf][a] = P.lo[a];
   const Region r = clip_region(P.lo, P.ext, 0, L.g);
-  const double* R = P.R;
   // x - X = (x - Xi) - Xf with Xi = floor(X): the integer part is exact in
-  // FP32, the fraction carries one FP32 rounding
-  const double Xi0 = floor(P.pos[0]), Xi1 = floor(P.pos[1]), Xi2 = floor(P.pos[2]);
-  const int xi0 = (int)Xi0, xi1 = (int)Xi1, xi2 = (int)Xi2;
-  const float xf0 = (float)(P.pos[0] - Xi0), xf1 = (float)(P.pos[1] - Xi1), xf2 = (float)(P.pos[2] - Xi2);
+  // FP32, the fraction carries one FP32 rounding (both set once per particle
+  // by the prologue, with R in FP32: FP64 set-up in every thread would cost
+  // more than the field evaluations on this part)
+  const int xi0 = P.pos_i[0], xi1 = P.pos_i[1], xi2 = P.pos_i[2];
+  const float xf0 = P.pos_fr[0], xf1 = P.pos_fr[1], xf2 = P.pos_fr[2];
   float Rf[9];
-  for (int k = 0; k < 9; ++k) Rf[k] = (float)R[k];
+  for (int k = 0; k < 9; ++k) Rf[k] = P.Rf[k];
   const float rt = (float)P.Rt * (1.0f + 1e-6f) + 1e-4f, rt2 = rt * rt;
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
@@ -339,7 +343,9 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
     const long long c = L.bc_cell[bi];
     const int d = L.link_dir[l];
     const DevParticle& P = L.P[L.link_p[l]];
-    const int x = (int)(c % L.g.nx), y = (int)((c / L.g.nx) % L.g.ny), z = (int)(c / ((long long)L.g.nx * L.g.ny));
+    // node indices of particle lists fit in 32 bits (the lists store them as uint32)
+    const unsigned cu = (unsigned)c, row = cu / (unsigned)L.g.nx;
+    const int x = (int)(cu - row * (unsigned)L.g.nx), z = (int)(row / (unsigned)L.g.ny), y = (int)(row - (unsigned)z * L.g.ny);
     const double* R = P.R;
     const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
     const float p0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);

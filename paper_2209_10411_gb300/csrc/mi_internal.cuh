@@ -188,6 +188,9 @@ struct DevParticle {
   double inertia[9], inv_inertia[9];         // body frame, about the centroid
   double R[9];                               // body -> world rotation at the current pose
   float posf[3], velf[3], omegaf[3];         // FP32 copies for the lattice kernels
+  int pos_i[3];                              // floor(pos), and pos - floor(pos) in FP32: node offsets
+  float pos_fr[3];                           //   x - X = (x - pos_i) - pos_fr without FP64 arithmetic
+  float Rf[9];                               // R rounded to FP32 (set with pos_i, pos_fr each step)
   float core_s;                              // core scale s = ((r_e - R_s) / r_e)^2 (constant)
   float Rb_f, re_f, skin_f;                  // FP32 copies of R_b, r_e, R_s (constant)
   int ball_off, n_balls;
