@@ -209,12 +209,17 @@ def contact_solves(B, scenes, args):
     plain guess and with the learned guess."""
     sc = scenes.config5()
     nx, ny, nz = sc.shape
+    periodic = (False, False, False)
+    if args.small_contact_lattice:  # profiling case: the same particles and pairs, no lattice memory, no walls
+        nx, ny, nz = 16, 16, 16
+        periodic = (True, True, True)
     params, train_info = train_guess(B)
     out = {}
     recs_by_mode = {}
     for mode in ("plain", "learned"):
         sim = B.Simulation(nx, ny, nz, tau=sc.tau, storage=1, max_particles=len(sc.particles),
-                           max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0)
+                           max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0,
+                           periodic=periodic)
         for p in sc.particles:
             r = p.nominal_radius
             vol = 4.0 / 3.0 * np.pi * r ** 3
@@ -254,7 +259,8 @@ def contact_solves(B, scenes, args):
     b = {(c["i"], c["j"]): c for c in recs_by_mode["learned"] if c["j"] >= 0 and c["status"] == 0}
     same = [np.linalg.norm(a[k]["x_cp"] - b[k]["x_cp"]) <= 2e-5 * max(rb[k[0]], rb[k[1]]) for k in a if k in b]
     res = dict(out["plain"])
-    res.update({"guess": "plain", "workload": sc.name, "particles": len(sc.particles), "learned": out["learned"],
+    wl = sc.name + (" (16^3 periodic lattice: profiling case, no walls)" if args.small_contact_lattice else "")
+    res.update({"guess": "plain", "workload": wl, "particles": len(sc.particles), "learned": out["learned"],
                 "learned_vs_plain": {"solves_per_s": out["learned"]["value"] / out["plain"]["value"],
                                      "pair_iters": (out["learned"]["mean_pair_iters"] or 0) /
                                      max(out["plain"]["mean_pair_iters"] or 1, 1e-9),
@@ -447,6 +453,8 @@ def main():
     ap.add_argument("--no-contacts", action="store_true", help="skip the contact-solves measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage measurements")
+    ap.add_argument("--small-contact-lattice", action="store_true",
+                    help="contact bed on a 16^3 periodic lattice (profiling: same pairs, no walls, little memory)")
     args = ap.parse_args()
     CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
                    "lattice": [256, 256, 512], "storage": args.storage})

@@ -11,7 +11,12 @@
 // ball by ball k / |x_b - c|^2 accumulated left to right.
 #include <cfloat>
 
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
+
 #include "mi_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mi {
 
@@ -164,7 +169,7 @@ cudaError_t launch_clear(const ParticleLaunch& L, cudaStream_t s) {
 // Solid flagging: node x of particle p's box is solid for p when
 // f_p(R_p^T (x - X_p)) >= 1; the owner is the lowest such p (atomicMin).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
+__global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
   extern __shared__ float4 sb[];
   const int p = blockIdx.y;
   const DevParticle& P = L.P[p];
@@ -197,19 +202,32 @@ __global__ void __launch_bounds__(256) k_flag(ParticleLaunch L) {
     const float b0 = Rf[0] * d0 + Rf[3] * d1 + Rf[6] * d2;
     const float b1 = Rf[1] * d0 + Rf[4] * d1 + Rf[7] * d2;
     const float b2 = Rf[2] * d0 + Rf[5] * d1 + Rf[8] * d2;
-    float f = 0.f;
+    // four independent partial sums (the terms are positive, so any partial
+    // sum above 1 + GUARD decides "inside"; FP32 reordering moves the sum by
+    // far less than GUARD, and sums within GUARD of 1 are redone in FP64)
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
     bool inside = false, decided = false;
-    for (int b = 0; b < nb; ++b) {
-      const float4 c = bl[b];
-      const float e0 = b0 - c.x, e1 = b1 - c.y, e2 = b2 - c.z;
-      f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
-      if (f > 1.0f + GUARD) {  // partial sums only grow: inside for sure
+    int b = 0;
+    for (; b + 4 <= nb; b += 4) {
+      const float4 c0 = bl[b], c1 = bl[b + 1], c2 = bl[b + 2], c3 = bl[b + 3];
+      f0 += __fdividef(c0.w, (b0 - c0.x) * (b0 - c0.x) + (b1 - c0.y) * (b1 - c0.y) + (b2 - c0.z) * (b2 - c0.z));
+      f1 += __fdividef(c1.w, (b0 - c1.x) * (b0 - c1.x) + (b1 - c1.y) * (b1 - c1.y) + (b2 - c1.z) * (b2 - c1.z));
+      f2 += __fdividef(c2.w, (b0 - c2.x) * (b0 - c2.x) + (b1 - c2.y) * (b1 - c2.y) + (b2 - c2.z) * (b2 - c2.z));
+      f3 += __fdividef(c3.w, (b0 - c3.x) * (b0 - c3.x) + (b1 - c3.y) * (b1 - c3.y) + (b2 - c3.z) * (b2 - c3.z));
+      if ((f0 + f1) + (f2 + f3) > 1.0f + GUARD) {  // partial sums only grow: inside for sure
         inside = decided = true;
         break;
       }
     }
     if (!decided) {
-      if (f < 1.0f - GUARD) inside = false;
+      for (; b < nb; ++b) {
+        const float4 c = bl[b];
+        const float e0 = b0 - c.x, e1 = b1 - c.y, e2 = b2 - c.z;
+        f0 += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
+      }
+      const float f = (f0 + f1) + (f2 + f3);
+      if (f > 1.0f + GUARD) inside = true;
+      else if (f < 1.0f - GUARD) inside = false;
       else inside = inside_exact(P, L.balls_d, (double)x, (double)y, (double)z);
     }
     if (inside) atomicMin(L.owner_cur + lin(x, y, z, L.g), (uint32_t)p);
@@ -287,15 +305,34 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
     L.cls[c] = (uint8_t)((solid ? CLS_SOLID : 0) | (mask ? CLS_BOUNDARY : 0) | (isnew ? CLS_NEW : 0));
     if (!(mask || isnew)) continue;
     if (atomicExch(L.stamp + c, gen) == gen) continue;  // another block listed it
+    // list appends aggregated over the lanes that got here: one atomic per
+    // counter and warp (all boundary nodes share the counters, and
+    // same-address atomics serialise in L2), offsets by ballot ranks and a scan
+    const cg::coalesced_group grp = cg::coalesced_threads();
+    const unsigned below = (1u << grp.thread_rank()) - 1u;
+    const unsigned newm = grp.ballot(isnew), bcm = grp.ballot(mask != 0);
+    const unsigned m = __popc(mask);
+    const unsigned m_excl = cg::exclusive_scan(grp, m);
+    unsigned base_new = 0, base_bc = 0, base_l = 0;
+    if (grp.thread_rank() == 0) {
+      if (newm) base_new = atomicAdd(&L.ctr->n_new, (unsigned)__popc(newm));
+      if (bcm) base_bc = atomicAdd(&L.ctr->n_bc, (unsigned)__popc(bcm));
+    }
+    if (grp.thread_rank() == grp.size() - 1) {
+      const unsigned total = m_excl + m;
+      if (total) base_l = atomicAdd(&L.ctr->n_links, total);
+    }
+    base_new = grp.shfl(base_new, 0);
+    base_bc = grp.shfl(base_bc, 0);
+    base_l = grp.shfl(base_l, grp.size() - 1);
     if (isnew) {
-      const unsigned k = atomicAdd(&L.ctr->n_new, 1u);
+      const unsigned k = base_new + __popc(newm & below);
       if (k < L.cap_new) L.new_cell[k] = (uint32_t)c;
       else atomicOr(&L.ctr->status, STATUS_NEW_OVERFLOW);
     }
     if (mask) {
-      const unsigned m = __popc(mask);
-      const unsigned bi = atomicAdd(&L.ctr->n_bc, 1u);
-      const unsigned lo_l = atomicAdd(&L.ctr->n_links, m);
+      const unsigned bi = base_bc + __popc(bcm & below);
+      const unsigned lo_l = base_l + m_excl;
       if (bi >= L.cap_bc) {
         atomicOr(&L.ctr->status, STATUS_BC_OVERFLOW);
         continue;
