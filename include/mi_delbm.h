@@ -431,17 +431,22 @@ mi_status mi_mlp_backward(const float *params, const float *X, const float *acts
 mi_status mi_mlp_adamw(float *params, const float *grads, float *m, float *v, int step, float lr, float beta1,
                        float beta2, float eps, float weight_decay, void *stream);
 
-/* Fused inference (the path the contact phase takes): the parameters packed
- * once into a BF16 image of mi_mlp_image_bytes() bytes (device, 16-byte
- * aligned, owned by the caller), then Y (n x 4) = MLP(X (n x 64, 16-byte
- * aligned)) by one persistent kernel whose CTAs hold the whole network in
- * shared memory.  Products use the same BF16 operands as mi_mlp_forward; the
- * FP32 sums run in another order, so the two agree to FP32 rounding.
- * n == 0 does nothing.  Errors: MI_EINVAL (null or misaligned pointer,
- * n < 0), MI_ECUDA. */
+/* Fused inference: the parameters packed once into a BF16 image of
+ * mi_mlp_image_bytes() bytes (device, 16-byte aligned, owned by the caller),
+ * then Y (n x 4) = MLP(X (n x 64)) by one persistent kernel.
+ * mi_mlp_infer (the path the contact phase takes) runs on the tcgen05 tensor
+ * cores: 128-row tiles, the FP32 accumulator in tensor memory, the weights
+ * streamed through shared memory by bulk copies; if one of its bounded waits
+ * gives up, the rows it did not finish are written as NaN.  mi_mlp_infer_mma
+ * runs the same network with mma.sync, the whole network resident in shared
+ * memory.  Both use the same BF16 operands as mi_mlp_forward; the FP32 sums
+ * run in other orders, so the three agree to FP32 rounding.  X and Y 16-byte
+ * aligned; n == 0 does nothing.  Errors: MI_EINVAL (null or misaligned
+ * pointer, n < 0), MI_ECUDA. */
 size_t mi_mlp_image_bytes(void);
 mi_status mi_mlp_pack(const float *params, void *image, void *stream);
 mi_status mi_mlp_infer(const void *image, const float *X, int n, float *Y, void *stream);
+mi_status mi_mlp_infer_mma(const void *image, const float *X, int n, float *Y, void *stream);
 
 /* Contact guess of the handle's DEM substeps: MI_GUESS_PLAIN, or
  * MI_GUESS_LEARNED with params (device, mi_mlp_param_count floats, packed

@@ -127,6 +127,7 @@ _sig("mi_mlp_adamw", c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_floa
 _sig("mi_mlp_image_bytes", c_size_t)
 _sig("mi_mlp_pack", c_int, _P, _P, _P)
 _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
+_sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
@@ -180,12 +181,14 @@ def mlp_pack(params):
     return img
 
 
-def mlp_infer(image, X):
-    """Y (n x 4) for X (n x 64) through the fused inference kernel."""
+def mlp_infer(image, X, engine="tcgen05"):
+    """Y (n x 4) for X (n x 64) through the fused inference kernel
+    (engine "tcgen05" or "mma")."""
     import torch
     n = X.shape[0]
     Y = torch.empty((n, 4), dtype=torch.float32, device=X.device)
-    _mlp_check(lib.mi_mlp_infer(_tp(image), _tp(X), int(n), _tp(Y), _cur_stream()))
+    fn = lib.mi_mlp_infer if engine == "tcgen05" else lib.mi_mlp_infer_mma
+    _mlp_check(fn(_tp(image), _tp(X), int(n), _tp(Y), _cur_stream()))
     return Y
 
 

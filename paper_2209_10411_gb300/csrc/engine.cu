@@ -265,7 +265,7 @@ mi_status mi_delbm::ensure_guess_buffers() {
   if (s != MI_OK) return s;
   guess_feat = (float*)dalloc(sizeof(float) * 64 * (size_t)cap_items);
   guess_pred = (float*)dalloc(sizeof(float) * 4 * (size_t)cap_items);
-  mlp_image = dalloc(mlp_image_bytes());
+  mlp_image = dalloc(mlp_image_total());
   if (!guess_feat || !guess_pred || !mlp_image) return fail(MI_ENOMEM, "learned guess: device allocation failed");
   return MI_OK;
 }
@@ -320,7 +320,8 @@ mi_status mi_delbm::phase_contact(cudaStream_t st) {
     // features of the candidates, then the MLP on as many rows as the broad phase found
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_item_features(L, st); })) != MI_OK) return s;
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] {
-           return mlp_infer(mlp_image, guess_feat, (int)cap_items, &dctr->n_pairs, guess_pred, st);
+           return mlp_tc_infer(static_cast<unsigned char*>(mlp_image) + mlp_image_bytes(), guess_feat,
+                               (int)cap_items, &dctr->n_pairs, guess_pred, &dctr->status, STATUS_GUESS_TIMEOUT, st);
          })) != MI_OK)
       return s;
   }
@@ -479,6 +480,15 @@ mi_status mi_delbm::check_status(bool clear) {
   cudaError_t e = cudaMemcpyAsync(&c, dctr, sizeof(c), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "reading device status");
+  if (c.status & STATUS_GUESS_TIMEOUT) {
+    if (clear) {
+      unsigned zero = 0;
+      cudaMemcpyAsync(&dctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, stream);
+      cudaStreamSynchronize(stream);
+    }
+    return fail(MI_ECUDA, "the learned-guess MLP kernel gave up a bounded wait (its rows were marked NaN and the "
+                          "contacts fell back to plain Newton)");
+  }
   const unsigned bad = c.status & (STATUS_BC_OVERFLOW | STATUS_LINK_OVERFLOW | STATUS_NEW_OVERFLOW |
                                    STATUS_PAIR_OVERFLOW | STATUS_CONTACT_OVERFLOW);
   if (clear && c.status) {
@@ -828,8 +838,11 @@ mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
   mi_status s = h->ensure_guess_buffers();
   if (s != MI_OK) return s;
   cudaError_t e = mlp_infer_prepare();
+  if (e == cudaSuccess) e = mlp_tc_prepare();
   if (e == cudaSuccess) e = mlp_pack(params, h->mlp_image, h->stream);
-  h->launches += 1;
+  if (e == cudaSuccess)
+    e = mlp_tc_pack(params, static_cast<unsigned char*>(h->mlp_image) + mlp_image_bytes(), h->stream);
+  h->launches += 2;
   if (e != cudaSuccess) return h->cuda_fail(e, "set_guess: packing the parameters");
   h->invalidate_graphs();
   h->learned = true;

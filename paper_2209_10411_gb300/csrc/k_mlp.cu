@@ -5,6 +5,7 @@
 // is staged in shared memory, so the network computes with BF16 weights and
 // FP32 accumulation while the optimizer keeps FP32 master weights.
 #include <cstring>
+#include <string>
 
 #include "mi_internal.cuh"
 
@@ -554,31 +555,432 @@ cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* 
 
 }  // namespace mi
 
+
+
+// ---------------------------------------------------------------------------
+// Fused inference on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// One CTA of 128 threads (one warpgroup) per 128-row tile, persistent over
+// tiles.  Operands are BF16 in shared memory in the no-swizzle K-major
+// "core matrix" layout (8 rows x 16 bytes contiguous; adjacent core
+// matrices 128 bytes apart along K, a whole K extent apart along M/N).  The
+// weights are packed once into five 32 KB chunks of (N = 256) x (K = 64):
+// W1^T, then W2^T in four K ranges; a single thread streams them through a
+// two-slot shared-memory ring with cp.async.bulk (completion on an
+// mbarrier) and issues the MMAs (M = 128, N = 256, K = 16 each) into one
+// FP32 accumulator of 256 TMEM columns; tcgen05.commit arrives on an
+// mbarrier when they complete (which also frees the ring slot).  Each
+// thread owns one row of the tile: it reads its accumulator row back with
+// tcgen05.ld for the bias + ReLU epilogue of layer 1 (written back as BF16
+// for layer 2's A operand) and for layer 2's epilogue, which also applies
+// the 256 -> 4 output layer with the same BF16-rounded operands as the
+// other paths.  Every wait is bounded: on a timeout the kernel raises its
+// error flag, stops issuing work, waits (bounded) for what it issued and
+// frees its TMEM.
+// ---------------------------------------------------------------------------
+namespace mi {
+namespace {
+
+constexpr int TC_M = 128;
+constexpr unsigned TC_CHUNK = 256 * 64 * 2;                 // one (N=256) x (K=64) BF16 chunk: 32 KB
+constexpr size_t TCI_W = 0;                                  // 5 chunks
+constexpr size_t TCI_W3 = TCI_W + 5 * (size_t)TC_CHUNK;      // W3^T as BF16-valued floats, [4][256]
+constexpr size_t TCI_B1 = TCI_W3 + 4 * 256 * 4;
+constexpr size_t TCI_B2 = TCI_B1 + 256 * 4;
+constexpr size_t TCI_B3 = TCI_B2 + 256 * 4;
+constexpr size_t TC_IMG_BYTES = TCI_B3 + 16;                 // 170000
+// shared memory of the tcgen05 kernel
+constexpr unsigned TS_X = 0;                                 // 128 x 64 BF16 core matrices: 16 KB
+constexpr unsigned TS_H = TS_X + TC_M * 64 * 2;              // 128 x 256 BF16: 64 KB
+constexpr unsigned TS_W = TS_H + TC_M * 256 * 2;             // ring: 2 x 32 KB
+constexpr unsigned TS_P = TS_W + 2 * TC_CHUNK;               // W3^T, b1, b2, b3: 6160 B
+constexpr unsigned TS_BAR = TS_P + 4 * 256 * 4 + 2 * 256 * 4 + 16;  // mbarriers (8 B each)
+constexpr unsigned TS_BYTES = TS_BAR + 64;
+static_assert(TC_IMG_BYTES % 16 == 0 && TS_BYTES <= 232448 && TS_BAR % 8 == 0, "tcgen05 MLP layout");
+
+// byte offset of element (row r, k) in a core-matrix K-major tile with K extent kext
+__host__ __device__ __forceinline__ unsigned cm_off(unsigned r, unsigned k, unsigned kext) {
+  return ((r >> 3) * (kext >> 3) + (k >> 3)) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+__global__ void k_mlp_pack_tc(const float* __restrict__ p, unsigned char* __restrict__ img) {
+  const float* W1 = p;
+  const float* b1 = W1 + 64 * 256;
+  const float* W2 = b1 + 256;
+  const float* b2 = W2 + 256 * 256;
+  const float* W3 = b2 + 256;
+  const float* b3 = W3 + 256 * 4;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  // chunk c, element (n, k): B operand row n (output column), K index k within the chunk
+  for (int e = tid; e < 5 * 256 * 64; e += nt) {
+    const int c = e / (256 * 64), r = e % (256 * 64), n = r / 64, k = r % 64;
+    const float v = c == 0 ? W1[k * 256 + n] : W2[((c - 1) * 64 + k) * 256 + n];
+    *reinterpret_cast<__nv_bfloat16*>(img + TCI_W + (size_t)c * TC_CHUNK + cm_off(n, k, 64)) = __float2bfloat16_rn(v);
+  }
+  for (int e = tid; e < 4 * 256; e += nt) {
+    const int o = e / 256, c = e % 256;
+    reinterpret_cast<float*>(img + TCI_W3)[e] = __bfloat162float(__float2bfloat16_rn(W3[c * 4 + o]));
+  }
+  for (int e = tid; e < 256; e += nt) {
+    reinterpret_cast<float*>(img + TCI_B1)[e] = b1[e];
+    reinterpret_cast<float*>(img + TCI_B2)[e] = b2[e];
+  }
+  if (tid < 4) reinterpret_cast<float*>(img + TCI_B3)[tid] = b3[tid];
+}
+
+}  // namespace
+}  // namespace mi
+
+namespace mi {
+namespace {
+
+constexpr unsigned TC_WAIT_LIMIT = 1u << 24;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+// Bounded wait for the completion of the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
+  for (unsigned it = 0; it < TC_WAIT_LIMIT; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices; lbo =
+// byte step between core matrices along K, sbo = along M/N.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  unsigned long long d = (unsigned long long)((saddr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;  // descriptor version of tcgen05
+  return d;         // base offset 0, layout type 0 (no swizzle)
+}
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 256.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ unsigned pack_bf2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+}  // namespace
+}  // namespace mi
+
+namespace mi {
+namespace {
+
+__global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restrict__ img, const float* __restrict__ X,
+                                                   int M, const unsigned* __restrict__ Mdev, float* __restrict__ Y,
+                                                   unsigned* __restrict__ err, unsigned err_bit) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (Mdev) M = min(M, (int)*Mdev);
+  const int tiles = (M + TC_M - 1) / TC_M;
+  if ((int)blockIdx.x >= tiles) return;  // uniform over the block
+
+  const unsigned sbase = smem_u32(sm);
+  const unsigned full0 = sbase + TS_BAR, empty0 = sbase + TS_BAR + 16, done = sbase + TS_BAR + 32;
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(sm + TS_BAR + 40);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + TS_BAR + 44);
+  float* W3t = reinterpret_cast<float*>(sm + TS_P);
+  float* b1 = W3t + 4 * 256;
+  float* b2 = b1 + 256;
+  float* b3 = b2 + 256;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  {
+    const float* src = reinterpret_cast<const float*>(img + TCI_W3);
+    for (int e = tid; e < 4 * 256 + 2 * 256 + 4; e += 128) W3t[e] = src[e];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *reinterpret_cast<volatile unsigned*>(tmem_slot);
+  const unsigned lane_base = (unsigned)(32 * warp) << 16;  // this warp's TMEM lanes
+
+  // producer / MMA issuer state (thread 0)
+  unsigned g_issued = 0, g_used = 0;   // chunks copied, chunks consumed
+  unsigned n_done = 0;                 // done-barrier completions waited for (every thread)
+  bool ok = true;
+
+  auto issue = [&](int c) {  // thread 0: copy weight chunk c into the next ring slot
+    const unsigned s = g_issued & 1u, use = g_issued >> 1;
+    if (use > 0 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1u)) { ok = false; return; }
+    mbar_expect_tx(full0 + 8 * s, TC_CHUNK);
+    bulk_g2s(sbase + TS_W + s * TC_CHUNK, img + TCI_W + (size_t)c * TC_CHUNK, TC_CHUNK, full0 + 8 * s);
+    ++g_issued;
+  };
+  // thread 0: MMAs of the next copied chunk: A (K extent a_kext, starting K a_k0), accumulate into D
+  auto consume = [&](unsigned a_base, unsigned a_kext, unsigned a_k0, bool first) {
+    const unsigned s = g_used & 1u, use = g_used >> 1;
+    if (!mbar_wait(full0 + 8 * s, use & 1u)) { ok = false; return; }
+    tc_fence_after();
+    const unsigned b_base = sbase + TS_W + s * TC_CHUNK;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned long long a = smem_desc(a_base + cm_off(0, a_k0 + 16 * k, a_kext), 128, (a_kext / 8) * 128);
+      const unsigned long long b = smem_desc(b_base + cm_off(0, 16 * k, 64), 128, (64 / 8) * 128);
+      tc_mma(tmem, a, b, (first && k == 0) ? 0u : 1u);
+    }
+    tc_commit(empty0 + 8 * s);  // the slot is free once these MMAs have read it
+    ++g_used;
+  };
+
+  int t = blockIdx.x;
+  for (; t < tiles; t += gridDim.x) {
+    const int r0 = t * TC_M;
+    // X tile: this thread's row, BF16, core-matrix layout (K extent 64)
+    {
+      const int row = r0 + tid;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (row < M) {
+          a = *reinterpret_cast<const float4*>(X + (size_t)row * 64 + 8 * q);
+          b = *reinterpret_cast<const float4*>(X + (size_t)row * 64 + 8 * q + 4);
+        }
+        *reinterpret_cast<uint4*>(sm + TS_X + cm_off(tid, 8 * q, 64)) =
+            make_uint4(pack_bf2(a.x, a.y), pack_bf2(a.z, a.w), pack_bf2(b.x, b.y), pack_bf2(b.z, b.w));
+      }
+    }
+    fence_proxy_async();  // generic-proxy smem writes -> visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && ok) {
+      issue(0);
+      if (ok) issue(1);
+      if (ok) consume(sbase + TS_X, 64, 0, true);  // layer 1: D = X W1
+      if (ok) tc_commit(done);
+      if (!ok) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    // ---- layer-1 epilogue: H1 = relu(D + b1) as BF16 (A operand of layer 2) ----
+    if (!mbar_wait(done, n_done & 1u)) *abort_flag = 1;
+    ++n_done;
+    tc_fence_after();
+    __syncthreads();
+    if (*abort_flag) break;
+#pragma unroll 1
+    for (int cb = 0; cb < 8; ++cb) {
+      float v[32];
+      tc_ld32(tmem + lane_base + 32 * cb, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 32 * cb + 8 * q;
+        uint4 w;
+        w.x = pack_bf2(fmaxf(v[8 * q] + b1[c], 0.f), fmaxf(v[8 * q + 1] + b1[c + 1], 0.f));
+        w.y = pack_bf2(fmaxf(v[8 * q + 2] + b1[c + 2], 0.f), fmaxf(v[8 * q + 3] + b1[c + 3], 0.f));
+        w.z = pack_bf2(fmaxf(v[8 * q + 4] + b1[c + 4], 0.f), fmaxf(v[8 * q + 5] + b1[c + 5], 0.f));
+        w.w = pack_bf2(fmaxf(v[8 * q + 6] + b1[c + 6], 0.f), fmaxf(v[8 * q + 7] + b1[c + 7], 0.f));
+        *reinterpret_cast<uint4*>(sm + TS_H + cm_off(tid, c, 256)) = w;
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && ok) {
+      for (int c = 1; c <= 4 && ok; ++c) {
+        if (c + 1 <= 4) issue(c + 1);
+        if (ok) consume(sbase + TS_H, 256, 64 * (c - 1), c == 1);  // layer 2: D = H1 W2
+      }
+      if (ok) tc_commit(done);
+      if (!ok) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    // ---- layer-2 epilogue and the output layer ----
+    if (!mbar_wait(done, n_done & 1u)) *abort_flag = 1;
+    ++n_done;
+    tc_fence_after();
+    __syncthreads();
+    if (*abort_flag) break;
+    float y[4] = {b3[0], b3[1], b3[2], b3[3]};
+#pragma unroll 1
+    for (int cb = 0; cb < 8; ++cb) {
+      float v[32];
+      tc_ld32(tmem + lane_base + 32 * cb, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = 32 * cb + j;
+        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + b2[c], 0.f)));
+#pragma unroll
+        for (int o = 0; o < 4; ++o) y[o] += h * W3t[o * 256 + c];
+      }
+    }
+    if (r0 + tid < M) *reinterpret_cast<float4*>(Y + (size_t)(r0 + tid) * 4) = make_float4(y[0], y[1], y[2], y[3]);
+    tc_fence_before();
+    __syncthreads();  // TMEM, X and H1 are reused by the next tile
+    tc_fence_after();
+  }
+  // teardown: after an abort, wait (bounded) for what was issued, then free the TMEM
+  if (*abort_flag) {
+    // rows this block did not finish are marked NaN
+    for (int tt = t; tt < tiles; tt += gridDim.x)
+      if (tt * TC_M + tid < M)
+        *reinterpret_cast<float4*>(Y + (size_t)(tt * TC_M + tid) * 4) = make_float4(NAN, NAN, NAN, NAN);
+    if (tid == 0) {
+      atomicOr(err, err_bit);
+      for (unsigned s = 0; s < 2; ++s) {
+        const unsigned uses = (g_issued + (s == 0 ? 1u : 0u)) >> 1;  // copies into slot s
+        const unsigned consumed = (g_used + (s == 0 ? 1u : 0u)) >> 1;
+        if (uses > consumed) mbar_wait(full0 + 8 * s, consumed & 1u);
+        if (consumed > 0) mbar_wait(empty0 + 8 * s, (consumed - 1) & 1u);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+}
+
+}  // namespace
+
+size_t mlp_tc_image_bytes() { return TC_IMG_BYTES; }
+
+cudaError_t mlp_tc_pack(const float* params, void* image, cudaStream_t s) {
+  k_mlp_pack_tc<<<64, 256, 0, s>>>(params, reinterpret_cast<unsigned char*>(image));
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_tc_prepare() {
+  return cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_BYTES);
+}
+
+cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, unsigned* err,
+                         unsigned err_bit, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int tiles = (M + TC_M - 1) / TC_M;
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = tiles < sms ? tiles : sms;
+  k_mlp_tc<<<grid, 128, TS_BYTES, s>>>(reinterpret_cast<const unsigned char*>(image), X, M, Mdev, Y, err, err_bit);
+  return cudaGetLastError();
+}
+
+}  // namespace mi
+
+namespace mi {
+// Device word the standalone inference reports a tcgen05 wait timeout in.
+__device__ unsigned g_mlp_tc_error;
+
+size_t mlp_image_total() { return IMG_BYTES + TC_IMG_BYTES; }
+}  // namespace mi
+
 extern "C" {
 
-size_t mi_mlp_image_bytes(void) { return mi::IMG_BYTES; }
+// The packed image holds both layouts: the mma.sync kernel's (first
+// IMG_BYTES bytes) and the tcgen05 kernel's (the rest).
+size_t mi_mlp_image_bytes(void) { return mi::mlp_image_total(); }
 
 mi_status mi_mlp_pack(const float* params, void* image, void* stream) {
   if (!params || !image || (reinterpret_cast<uintptr_t>(image) & 15)) {
     mi::set_thread_error("mi_mlp_pack: null pointer or image not 16-byte aligned");
     return MI_EINVAL;
   }
-  if (mi::mlp_pack(params, image, (cudaStream_t)stream) != cudaSuccess) {
+  cudaError_t e = mi::mlp_pack(params, image, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = mi::mlp_tc_pack(params, static_cast<unsigned char*>(image) + mi::IMG_BYTES, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
     mi::set_thread_error("mi_mlp_pack: launch failed");
     return MI_ECUDA;
   }
   return MI_OK;
 }
 
-mi_status mi_mlp_infer(const void* image, const float* X, int n, float* Y, void* stream) {
+static mi_status infer_args(const void* image, const float* X, int n, float* Y, const char* who) {
   if (n < 0 || (n > 0 && (!image || !X || !Y)) || (reinterpret_cast<uintptr_t>(image) & 15) ||
-      (reinterpret_cast<uintptr_t>(X) & 15)) {
-    mi::set_thread_error("mi_mlp_infer: null pointer, negative batch, or image/X not 16-byte aligned");
+      (reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Y) & 15)) {
+    mi::set_thread_error((std::string(who) + ": null pointer, negative batch, or image/X/Y not 16-byte aligned").c_str());
     return MI_EINVAL;
   }
-  if (n == 0) return MI_OK;
-  if (mi::mlp_infer_prepare() != cudaSuccess || mi::mlp_infer(image, X, n, nullptr, Y, (cudaStream_t)stream) != cudaSuccess) {
+  return MI_OK;
+}
+
+mi_status mi_mlp_infer(const void* image, const float* X, int n, float* Y, void* stream) {
+  mi_status st = infer_args(image, X, n, Y, "mi_mlp_infer");
+  if (st != MI_OK || n == 0) return st;
+  unsigned* err = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&err), mi::g_mlp_tc_error) != cudaSuccess ||
+      mi::mlp_tc_prepare() != cudaSuccess ||
+      mi::mlp_tc_infer(static_cast<const unsigned char*>(image) + mi::IMG_BYTES, X, n, nullptr, Y, err, 1u,
+                       (cudaStream_t)stream) != cudaSuccess) {
     mi::set_thread_error("mi_mlp_infer: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_infer_mma(const void* image, const float* X, int n, float* Y, void* stream) {
+  mi_status st = infer_args(image, X, n, Y, "mi_mlp_infer_mma");
+  if (st != MI_OK || n == 0) return st;
+  if (mi::mlp_infer_prepare() != cudaSuccess || mi::mlp_infer(image, X, n, nullptr, Y, (cudaStream_t)stream) != cudaSuccess) {
+    mi::set_thread_error("mi_mlp_infer_mma: launch failed");
     return MI_ECUDA;
   }
   return MI_OK;

@@ -211,7 +211,8 @@ struct DevCounters {
   unsigned int pad;
 };
 constexpr unsigned STATUS_BC_OVERFLOW = 1u, STATUS_LINK_OVERFLOW = 2u, STATUS_NEW_OVERFLOW = 4u,
-                   STATUS_PAIR_OVERFLOW = 8u, STATUS_CONTACT_OVERFLOW = 16u, STATUS_MOVED_TOO_FAR = 32u;
+                   STATUS_PAIR_OVERFLOW = 8u, STATUS_CONTACT_OVERFLOW = 16u, STATUS_MOVED_TOO_FAR = 32u,
+                   STATUS_GUESS_TIMEOUT = 64u;  // a bounded wait of the tcgen05 MLP kernel gave up
 
 struct ParticleLaunch {
   DevParticle* P;
@@ -333,6 +334,14 @@ size_t mlp_image_bytes();
 cudaError_t mlp_pack(const float* params, void* image, cudaStream_t s);
 cudaError_t mlp_infer_prepare();
 cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, cudaStream_t s);
+// The same network on tcgen05/TMEM from its own packed image (mlp_tc_pack);
+// on a wait timeout the kernel ORs err_bit into *err and writes NaN rows.
+size_t mlp_tc_image_bytes();
+size_t mlp_image_total();  // both images back to back (the C-ABI's packed image)
+cudaError_t mlp_tc_pack(const float* params, void* image, cudaStream_t s);
+cudaError_t mlp_tc_prepare();
+cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, unsigned* err,
+                         unsigned err_bit, cudaStream_t s);
 
 struct IntegrateLaunch {
   DevParticle* P;

@@ -115,22 +115,27 @@ def test_forward_backward_against_oracle(setup, n):
 
 @pytest.mark.parametrize("n", [1, 63, 200, 20000])
 def test_fused_inference_against_oracle(setup, n):
-    """The fused kernel (whole network per 64-row tile, output layer in the
-    epilogue) against the BF16-operand oracle and against the GEMM path;
-    20000 rows exceed one tile per SM, so the persistent loop runs."""
+    """Both fused kernels (tcgen05 with 128-row tiles, and mma.sync with
+    64-row tiles; output layer in the epilogue) against the BF16-operand
+    oracle and against the GEMM path; 20000 rows exceed one tile per SM, so
+    the persistent loops run."""
     B, torch, rng, p = setup
     X = rng.normal(size=(n, 64)).astype(np.float32).astype(np.float64)
     dp = torch.as_tensor(_flat(p), device="cuda")
     dX = torch.as_tensor(X, dtype=torch.float32, device="cuda")
-    Yf = B.mlp_infer(B.mlp_pack(dp), dX)
+    img = B.mlp_pack(dp)
+    Yt = B.mlp_infer(img, dX)               # tcgen05 / TMEM
+    Yf = B.mlp_infer(img, dX, engine="mma")  # mma.sync, network resident in shared memory
     Yg, _ = B.mlp_forward(dp, dX)
     torch.cuda.synchronize()
-    Yf, Yg = Yf.cpu().numpy().astype(np.float64), Yg.cpu().numpy().astype(np.float64)
+    Yt, Yf, Yg = (a.cpu().numpy().astype(np.float64) for a in (Yt, Yf, Yg))
     Yb, _, _ = _oracle_bf16(p, X, np.zeros((n, 4)))
     Yo, _ = mlp.forward(p, X)
-    assert _rel(Yf, Yb) <= 2e-4, _rel(Yf, Yb)
-    assert _rel(Yf, Yg) <= 2e-4, _rel(Yf, Yg)
-    assert _rel(Yf, Yo) <= 1e-2
+    for Y in (Yt, Yf):
+        assert np.isfinite(Y).all()
+        assert _rel(Y, Yb) <= 2e-4, _rel(Y, Yb)
+        assert _rel(Y, Yg) <= 2e-4, _rel(Y, Yg)
+        assert _rel(Y, Yo) <= 1e-2
 
 
 def test_empty_batch_forward(setup):
