@@ -30,6 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE = {0: 152, 1: 76, 2: 76}   # 19 loads + 19 stores of the stored type
+# DRAM bytes (read + write) of one bulk launch on the 256x256x512 tank, from
+# ncu captures of the same kernels on 256x256x128 scaled by the nodes
+# processed (profiles/k_bulk_stream_collide_f32.md, k_bulk_quad16_f16.md);
+# keyed by (storage, four-node kernel).  Reported only for the kernel that
+# was captured.
+BULK_TRAFFIC = {(0, False): 4 * 1222.0e6, (1, True): 4 * 591.1e6}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 DTYPE_NAME = {0: "f32", 1: "f16-dev/f32-compute", 2: "bf16-dev/f32-compute"}
 
@@ -386,6 +392,11 @@ def run_mine(args):
     # boundary kernel): 19 loads + 19 stores of the stored type per node
     alg_bytes = BYTES_PER_NODE[storage] * ncell
     achieved = alg_bytes / (bulk_ms / bulk_n * 1e-3) / 1e9 if bulk_n else None
+    used = tuning if tuning else sim.get_tuning()
+    quad = storage != 0 and used.get("bulk_pairs") == 3 and nx % 4 == 0
+    traffic = BULK_TRAFFIC.get((storage, quad)) if (nx, ny, nz) == (256, 256, 512) else None
+    bulk_name = ("k_bulk_quad16 (D3Q19 stream-collide, four nodes per thread)" if quad
+                 else "k_bulk (D3Q19 stream-collide of every node)")
 
     # end to end through the public API: per step, upload of the particle
     # states from page-locked host memory, the step, and a synchronising read
@@ -422,8 +433,8 @@ def run_mine(args):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPE_NAME[storage], "data": "synthetic", "config": config,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak if achieved else None, "traffic": None,
-                        "kernel": "k_bulk (D3Q19 stream-collide of every node)", "peak_kind": peak_kind,
+                        "frac": achieved / peak if achieved else None, "traffic": traffic,
+                        "kernel": bulk_name, "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes},
            "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
            "graphs": not args.no_graphs, "tuning": tuning,
