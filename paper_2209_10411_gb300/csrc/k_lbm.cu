@@ -575,6 +575,19 @@ __device__ __forceinline__ float wsumf(float v) {
   return __shfl_sync(FULLW, v, 0);
 }
 
+// Exact warp sum of 64-bit fixed-point values (|v| < 2^62): three 22-bit
+// pieces, each summed by one integer warp reduction (at most 32 x 2^22 < 2^27,
+// no overflow), recombined; the result is in every lane.
+__device__ __forceinline__ long long warp_sum_fixed(long long v) {
+  const unsigned c0 = (unsigned)(v & 0x3FFFFFLL);
+  const unsigned c1 = (unsigned)((v >> 22) & 0x3FFFFFLL);
+  const int c2 = (int)(v >> 44);
+  const unsigned s0 = __reduce_add_sync(FULLW, c0);
+  const unsigned s1 = __reduce_add_sync(FULLW, c1);
+  const int s2 = __reduce_add_sync(FULLW, c2);
+  return (long long)s0 + ((long long)s1 << 22) + ((long long)s2 << 44);
+}
+
 __device__ __forceinline__ void add_fixed_ll(long long* facc, int p, const long long v[6]) {
   for (int k = 0; k < 6; ++k)
     atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)v[k]);
@@ -610,8 +623,9 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
     const float hown = dirlane ? Store<ST>::dev(A + j * g.plane + c, j) : 0.f;
     const float hopp = __shfl_sync(FULLW, hown, d < 19 ? d : 0);  // f+_d(x_f) - w_d
     const float rho_f = 1.0f + wsumf(hown);
-    const float uf0 = wsumf(ej[0] * hown) / rho_f, uf1 = wsumf(ej[1] * hown) / rho_f,
-                uf2 = wsumf(ej[2] * hown) / rho_f;
+    const float irho_f = 1.0f / rho_f;
+    const float uf0 = wsumf(ej[0] * hown) * irho_f, uf1 = wsumf(ej[1] * hown) * irho_f,
+                uf2 = wsumf(ej[2] * hown) * irho_f;
     float hin = 0.f;
     float dP[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
     int p = -1;
@@ -659,11 +673,12 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
             }
             const float uf[3] = {uf0, uf1, uf2};
             float ud[3];
-            const float a1 = (1.0f - q) / (1.0f + q), a2 = 2.0f * q / (1.0f + q);
+            const float i1q = 1.0f / (1.0f + q), iq = 1.0f / q;
+            const float a1 = (1.0f - q) * i1q, a2 = 2.0f * q * i1q;
+            const float b1 = (1.0f - q) * iq, b2 = (2.0f * q - 1.0f) * iq;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const float us = q <= 0.5f ? 2.0f * q * uf[a] + (1.0f - 2.0f * q) * uff[a]
-                                         : ((1.0f - q) / q) * uf[a] + ((2.0f * q - 1.0f) / q) * uw[a];
+              const float us = q <= 0.5f ? 2.0f * q * uf[a] + (1.0f - 2.0f * q) * uff[a] : b1 * uf[a] + b2 * uw[a];
               ud[a] = us / 3.0f + 2.0f * (a1 * uff[a] + a2 * uw[a]) / 3.0f;
             }
             const float eud = ed[0] * ud[0] + ed[1] * ud[1] + ed[2] * ud[2];
@@ -688,14 +703,15 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
     const float rho = 1.0f + drho;
     const float j0 = wsumf(ej[0] * hin), j1 = wsumf(ej[1] * hin), j2 = wsumf(ej[2] * hin);
     float u0, u1, u2;
+    const float irho = 1.0f / rho;
     if (FORCE) {
-      u0 = (j0 + 0.5f * L.p.force[0]) / rho;
-      u1 = (j1 + 0.5f * L.p.force[1]) / rho;
-      u2 = (j2 + 0.5f * L.p.force[2]) / rho;
+      u0 = (j0 + 0.5f * L.p.force[0]) * irho;
+      u1 = (j1 + 0.5f * L.p.force[1]) * irho;
+      u2 = (j2 + 0.5f * L.p.force[2]) * irho;
     } else {
-      u0 = j0 / rho;
-      u1 = j1 / rho;
-      u2 = j2 / rho;
+      u0 = j0 * irho;
+      u1 = j1 * irho;
+      u2 = j2 * irho;
     }
     if (dirlane) {
       const float eu = ej[0] * u0 + ej[1] * u1 + ej[2] * u2;
@@ -718,12 +734,13 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
       const bool single = __all_sync(FULLW, p < 0 || p == pmin);
       const float v[6] = {dP[0], dP[1], dP[2], dT[0], dT[1], dT[2]};
       long long iv[6];
+      // v * 2^40 is exact in FP32 and the conversion rounds to nearest even:
+      // odd-symmetric, so opposite links of a closed body cancel exactly
 #pragma unroll
-      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? fixed40(v[k]) : 0LL;
+      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? __float2ll_rn(v[k] * 1099511627776.0f) : 0LL;
       if (single) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-          for (int o = 16; o > 0; o >>= 1) iv[k] += __shfl_xor_sync(FULLW, iv[k], o);
+        for (int k = 0; k < 6; ++k) iv[k] = warp_sum_fixed(iv[k]);
         if (j == 0) {
           if (pacc != pmin) {
             if (pacc >= 0) add_fixed_ll(pl.facc, pacc, iacc);

@@ -360,29 +360,6 @@ cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s);
 cudaError_t launch_mass_quadrature(const float4* balls, const double* balls_d, int n_balls, double Rb,
                                    double h, int n_side, double* partials, int blocks, cudaStream_t s);
 
-// Exact 2^40 fixed-point value of an FP32 number, rounded to nearest even
-// (the same integer as rint((double)v * 2^40)), with integer operations only.
-// |v| must be below 2^23.
-__device__ __forceinline__ long long fixed40(float v) {
-  const unsigned u = __float_as_uint(v);
-  const int e = (int)((u >> 23) & 0xFFu);
-  if (e == 0) return 0;  // zero or subnormal (< 2^-126): rounds to 0
-  const long long M = (long long)((u & 0x7FFFFFu) | 0x800000u);
-  const int sh = e - 110;  // v * 2^40 = M * 2^(e - 150 + 40)
-  long long r;
-  if (sh >= 0) {
-    r = M << sh;
-  } else {
-    const int s = -sh;
-    if (s >= 25) {
-      r = 0;
-    } else {
-      const long long q = M >> s, rem = M & ((1LL << s) - 1), half = 1LL << (s - 1);
-      r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-    }
-  }
-  return (u >> 31) ? -r : r;
-}
 
 // D3Q19 direction of the integer offset, or -1.
 __host__ __device__ inline int dir_of(int x, int y, int z) {
