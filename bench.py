@@ -257,6 +257,34 @@ def contact_solves(B, scenes, args):
                                        "singular": int(status[2]), "inside_core": int(status[3]),
                                        "out_of_range": int(status[4])},
                      "ms_per_substep": ms, "launches_per_substep": pt[1] / reps}
+    # DEM substeps of a moving bed (contact + rigid-body update, 10 substeps per
+    # call: the particles move between substeps), plain vs warm start
+    moving = {}
+    for name, mode in (("plain", B.GUESS_PLAIN), ("warm", B.GUESS_WARM)):
+        sim = B.Simulation(nx, ny, nz, tau=sc.tau, storage=1, max_particles=len(sc.particles),
+                           max_balls=sum(len(p.k) for p in sc.particles) + 16, kn=1.0, kt=2.0 / 7.0,
+                           periodic=periodic, dem_substeps=10, guess_mode=mode, gravity=sc.gravity)
+        for p in sc.particles:
+            r = p.nominal_radius
+            vol = 4.0 / 3.0 * np.pi * r ** 3
+            m = p.density * vol
+            sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat,
+                             mass_props={"mass": m, "volume": vol, "inertia": np.eye(3) * 0.4 * m * r * r})
+        sim.set_timing(True)
+        for _ in range(2):
+            sim.step_phases(B.PHASE_CONTACT | B.PHASE_INTEGRATE)
+        sim.phase_times(reset=True)
+        calls = 3
+        for _ in range(calls):
+            sim.step_phases(B.PHASE_CONTACT | B.PHASE_INTEGRATE)
+        pt = sim.phase_times(reset=True)
+        recs = sim.contacts()
+        sim.close()
+        it = np.array([c["iters"] for c in recs if c["j"] >= 0 and c["status"] == 0])
+        ms = pt["contact"][0] / (10 * calls)
+        moving[name] = {"value": len(recs) / (ms * 1e-3), "unit": "solves/s", "ms_per_substep": ms,
+                        "mean_pair_iters_last_substep": float(it.mean()) if len(it) else None,
+                        "candidates": len(recs)}
     # the two modes must agree: same converged pairs, same contact points (1e-5 of 2 R_b)
     rb = {i: None for i in range(len(sc.particles))}
     for i, p in enumerate(sc.particles):
@@ -272,7 +300,8 @@ def contact_solves(B, scenes, args):
                                      max(out["plain"]["mean_pair_iters"] or 1, 1e-9),
                                      "converged_pairs_plain": len(a), "converged_pairs_learned": len(b),
                                      "same_contact_point": float(np.mean(same)) if same else None},
-                "training": train_info})
+                "training": train_info,
+                "moving_bed_10_substeps": moving})
     return res
 
 

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define MI_DELBM_ABI_VERSION 1
+#define MI_DELBM_ABI_VERSION 2
 
 typedef enum {
   MI_OK = 0,
@@ -82,7 +82,9 @@ enum {
 /* Newton initial guess for contact detection. */
 enum {
   MI_GUESS_PLAIN = 0,   /* midpoint of the closest pair of control points     */
-  MI_GUESS_LEARNED = 1  /* the loaded MLP proposes the guess and active subset */
+  MI_GUESS_LEARNED = 1, /* the loaded MLP proposes the guess and active subset */
+  MI_GUESS_WARM = 2     /* the pair's closest point of the previous DEM substep
+                           (when the pair was solved there), else the plain guess */
 };
 
 /* Step phases, for mi_delbm_step_phases (tests and profiling). */
@@ -120,6 +122,14 @@ typedef struct mi_delbm_config {
   void *(*dev_alloc)(size_t bytes, void *ctx);
   void (*dev_free)(void *ptr, size_t bytes, void *ctx);
   void *alloc_ctx;
+  /* Nonzero: mi_delbm_add_particle rejects (MI_EOVERLAP) a particle whose
+   * core overlaps an existing particle's, judged by the method's own closest-
+   * point solve (Sec. 2.3.1): for every existing particle whose bounding
+   * sphere meets the new one, plain Newton on grad(g_i + g_j) = 0 from the
+   * plain guess, overlap when the converged point lies inside a core.
+   * Default 0 (packed synthetic scenes and shape libraries add overlapping
+   * particles on purpose). */
+  int check_overlap;
 } mi_delbm_config;
 
 typedef struct mi_delbm mi_delbm;
@@ -448,9 +458,10 @@ mi_status mi_mlp_pack(const float *params, void *image, void *stream);
 mi_status mi_mlp_infer(const void *image, const float *X, int n, float *Y, void *stream);
 mi_status mi_mlp_infer_mma(const void *image, const float *X, int n, float *Y, void *stream);
 
-/* Contact guess of the handle's DEM substeps: MI_GUESS_PLAIN, or
- * MI_GUESS_LEARNED with params (device, mi_mlp_param_count floats, packed
- * into the handle; the caller keeps ownership of its array).  Wall contacts always
+/* Contact guess of the handle's DEM substeps: MI_GUESS_PLAIN, MI_GUESS_WARM
+ * (params ignored), or MI_GUESS_LEARNED with params (device,
+ * mi_mlp_param_count floats, packed into the handle; the caller keeps
+ * ownership of its array).  Wall contacts always
  * start from the plain guess.  Discards captured graphs.  Errors: MI_EINVAL,
  * MI_ENOMEM, MI_ECUDA. */
 mi_status mi_delbm_set_guess(mi_delbm *h, int mode, const float *params);

@@ -30,7 +30,7 @@ STATUS_NAMES = ["MI_OK", "MI_EINVAL", "MI_ENOMEM", "MI_ECUDA", "MI_ECAPACITY", "
                 "MI_ESTATE", "MI_ETIMEOUT", "MI_ENOTSUP"]
 STORE_F32, STORE_F16_DEV, STORE_BF16_DEV = 0, 1, 2
 BB_IBB, BB_LADD = 0, 1
-GUESS_PLAIN, GUESS_LEARNED = 0, 1
+GUESS_PLAIN, GUESS_LEARNED, GUESS_WARM = 0, 1, 2
 PHASE_FLAG, PHASE_LINKS, PHASE_REFILL, PHASE_BULK = 1, 2, 4, 8
 PHASE_BOUNDARY, PHASE_SWAP, PHASE_CONTACT, PHASE_INTEGRATE = 16, 32, 64, 128
 PHASE_ALL = 0xFF
@@ -50,6 +50,7 @@ class Config(ctypes.Structure):
         ("guess_mode", c_int), ("max_particles", c_int), ("max_balls", c_int),
         ("cuda_stream", c_void_p), ("device", c_int),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", c_void_p),
+        ("check_overlap", c_int),
     ]
 
 
@@ -220,7 +221,7 @@ def mlp_adamw(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e
                                 float(beta2), float(eps), float(weight_decay), _cur_stream()))
 
 
-if lib.mi_delbm_abi_version() != 1:
+if lib.mi_delbm_abi_version() != 2:
     raise ImportError("libmi_delbm ABI version mismatch")
 if lib.mi_delbm_config_size() != ctypes.sizeof(Config):
     raise ImportError("mi_delbm_config layout mismatch: C %d bytes, binding %d bytes"
@@ -268,7 +269,7 @@ class Simulation:
                  wall_velocity=None, fluid_body_force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0),
                  storage=STORE_F32, bb_mode=BB_IBB, dem_substeps=1, kn=1.0, kt=2.0 / 7.0,
                  eta_n=0.0, eta_t=0.0, mu_s=0.4, guess_mode=GUESS_PLAIN, max_particles=1024,
-                 max_balls=65536, device=0, stream=None, torch_memory=True):
+                 max_balls=65536, device=0, stream=None, torch_memory=True, check_overlap=False):
         cfg = Config()
         lib.mi_delbm_config_init(ctypes.byref(cfg))
         cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
@@ -286,6 +287,7 @@ class Simulation:
         cfg.kn, cfg.kt, cfg.eta_n, cfg.eta_t, cfg.mu_s = float(kn), float(kt), float(eta_n), float(eta_t), float(mu_s)
         cfg.guess_mode, cfg.max_particles, cfg.max_balls = int(guess_mode), int(max_particles), int(max_balls)
         cfg.device = int(device)
+        cfg.check_overlap = 1 if check_overlap else 0
         self._alloc = None
         self.torch_stream = None
         if stream is None and torch_memory:
@@ -489,7 +491,7 @@ class Simulation:
 
     # -- learned guess -----------------------------------------------------
     def set_guess(self, mode, params=None):
-        """GUESS_PLAIN, or GUESS_LEARNED with the MLP parameters (float32 CUDA tensor)."""
+        """GUESS_PLAIN, GUESS_WARM, or GUESS_LEARNED with the MLP parameters (float32 CUDA tensor)."""
         self._sync_in()
         self._check(lib.mi_delbm_set_guess(self.h, int(mode), _tp(params)))
         self._sync_out()

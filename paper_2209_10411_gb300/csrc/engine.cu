@@ -298,6 +298,7 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.qf = h->bp_quat;
   L.plo = h->bp_lo;
   L.learned = h->learned ? 1 : 0;
+  L.warm = h->warm ? 1 : 0;
   L.feat = h->guess_feat;
   L.pred = h->guess_pred;
   for (int a = 0; a < 3; ++a) L.cp.periodic[a] = h->cfg.periodic[a] ? 1 : 0;
@@ -486,8 +487,8 @@ mi_status mi_delbm::check_status(bool clear) {
       cudaMemcpyAsync(&dctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, stream);
       cudaStreamSynchronize(stream);
     }
-    return fail(MI_ECUDA, "the learned-guess MLP kernel gave up a bounded wait (its rows were marked NaN and the "
-                          "contacts fell back to plain Newton)");
+    return fail(MI_ETIMEOUT, "the learned-guess MLP kernel gave up a bounded wait (its rows were marked NaN and the "
+                             "contacts fell back to plain Newton)");
   }
   const unsigned bad = c.status & (STATUS_BC_OVERFLOW | STATUS_LINK_OVERFLOW | STATUS_NEW_OVERFLOW |
                                    STATUS_PAIR_OVERFLOW | STATUS_CONTACT_OVERFLOW);
@@ -582,6 +583,7 @@ void mi_delbm_config_init(mi_delbm_config* c) {
   c->eta_t = 0.0;
   c->mu_s = 0.4;
   c->guess_mode = MI_GUESS_PLAIN;
+  c->check_overlap = 0;
   c->max_particles = 1024;
   c->max_balls = 65536;
   c->cuda_stream = nullptr;
@@ -624,8 +626,9 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     g_create_error = "mi_delbm_create: dem_substeps must be >= 1, capacities >= 0, max_particles <= 65535";
     return MI_EINVAL;
   }
-  if (cfg->guess_mode != MI_GUESS_PLAIN) {
-    g_create_error = "mi_delbm_create: guess_mode must be MI_GUESS_PLAIN (load a learned guess with mi_delbm_set_guess)";
+  if (cfg->guess_mode != MI_GUESS_PLAIN && cfg->guess_mode != MI_GUESS_WARM) {
+    g_create_error = "mi_delbm_create: guess_mode must be MI_GUESS_PLAIN or MI_GUESS_WARM (load a learned guess "
+                     "with mi_delbm_set_guess)";
     return MI_EINVAL;
   }
   if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) {
@@ -638,6 +641,7 @@ mi_status mi_delbm_create(const mi_delbm_config* cfg, mi_delbm** out) {
     return MI_ENOMEM;
   }
   h->cfg = *cfg;
+  h->warm = cfg->guess_mode == MI_GUESS_WARM;
   if (!h->set_device()) {
     g_create_error = "mi_delbm_create: cudaSetDevice failed";
     delete h;
@@ -827,9 +831,10 @@ mi_status mi_delbm_set_graphs(mi_delbm* h, int enable) {
 
 mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
   if (!h) return MI_EINVAL;
-  if (mode == MI_GUESS_PLAIN) {
-    if (h->learned) h->invalidate_graphs();
+  if (mode == MI_GUESS_PLAIN || mode == MI_GUESS_WARM) {
+    if (h->learned || h->warm != (mode == MI_GUESS_WARM)) h->invalidate_graphs();
     h->learned = false;
+    h->warm = mode == MI_GUESS_WARM;
     return MI_OK;
   }
   if (mode != MI_GUESS_LEARNED) return h->fail(MI_EINVAL, "set_guess: unknown mode");
@@ -846,6 +851,7 @@ mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
   if (e != cudaSuccess) return h->cuda_fail(e, "set_guess: packing the parameters");
   h->invalidate_graphs();
   h->learned = true;
+  h->warm = false;
   return MI_OK;
 }
 
@@ -1111,6 +1117,70 @@ bool invert3(const double A[9], double Ai[9]) {
 
 extern "C" {
 
+// Core-overlap test of a new particle (uploaded at slot id) against the
+// existing ones: the plain closest-point solve between it and every particle
+// whose bounding sphere it meets; overlap when the converged point lies
+// inside a core (status 3).  Synchronises.
+static mi_status overlap_check(mi_delbm* h, int id, const DevParticle& P) {
+  std::vector<DevParticle> cur(id);
+  cudaError_t e = cudaMemcpyAsync(cur.data(), h->dP, sizeof(DevParticle) * id, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: reading particle states");
+  std::vector<int> ij;
+  std::vector<double> poses;
+  for (int i = 0; i < id; ++i) {
+    const double d0 = P.pos[0] - cur[i].pos[0], d1 = P.pos[1] - cur[i].pos[1], d2 = P.pos[2] - cur[i].pos[2];
+    if (std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) > P.Rb + cur[i].Rb) continue;
+    ij.push_back(i);
+    ij.push_back(id);
+    for (int a = 0; a < 3; ++a) poses.push_back(cur[i].pos[a]);
+    for (int a = 0; a < 4; ++a) poses.push_back(cur[i].quat[a]);
+    for (int a = 0; a < 3; ++a) poses.push_back(P.pos[a]);
+    for (int a = 0; a < 4; ++a) poses.push_back(P.quat[a]);
+  }
+  const int n = (int)(ij.size() / 2);
+  if (n == 0) return MI_OK;
+  int* d_ij = (int*)h->dalloc(sizeof(int) * 2 * n);
+  double* d_pose = (double*)h->dalloc(sizeof(double) * 14 * n);
+  double* d_xm = (double*)h->dalloc(sizeof(double) * 3 * n);
+  int* d_out = (int*)h->dalloc(sizeof(int) * 3 * n);  // iterations, evaluations, status
+  mi_status st = MI_OK;
+  std::vector<int> status(n, 0);
+  if (!d_ij || !d_pose || !d_xm || !d_out) {
+    st = h->fail(MI_ENOMEM, "add_particle: overlap check buffers");
+  } else {
+    PairSolveLaunch S;
+    std::memset(&S, 0, sizeof(S));
+    S.P = h->dP;
+    S.np = id + 1;
+    S.balls = h->dballs;
+    S.n = n;
+    S.ij = d_ij;
+    S.poses = d_pose;
+    S.flags = MI_PAIR_PLAIN;
+    S.xm = d_xm;
+    S.iters = d_out;
+    S.evals = d_out + n;
+    S.status = d_out + 2 * n;
+    e = cudaMemcpyAsync(d_ij, ij.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pose, poses.data(), sizeof(double) * 14 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_pair_solve(S, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), d_out + 2 * n, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->launches += 1;
+    if (e != cudaSuccess) st = h->cuda_fail(e, "add_particle: overlap check");
+  }
+  h->dfree(d_ij);
+  h->dfree(d_pose);
+  h->dfree(d_xm);
+  h->dfree(d_out);
+  if (st != MI_OK) return st;
+  for (int k = 0; k < n; ++k)
+    if ((status[k] & 15) == 3)
+      return h->fail(MI_EOVERLAP, "add_particle: the new particle's core overlaps particle " + std::to_string(ij[2 * k]));
+  return MI_OK;
+}
+
 mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const double* k, double density,
                                 double skin, const double pos[3], const double quat[4], const double vel[3],
                                 const double omega[3], const mi_mass_props* mp, int* id_out) {
@@ -1259,6 +1329,10 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   e = cudaMemcpyAsync(h->dP + id, &P, sizeof(P), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "add_particle: particle upload");
+  if (h->cfg.check_overlap && id > 0) {
+    // nothing is committed yet: on rejection the slot and the ball range are reused by the next add
+    if ((st = overlap_check(h, id, P)) != MI_OK) return st;
+  }
   h->hp.push_back(P);
   for (int i = 0; i < n; ++i) {
     h->hballs.push_back(make_float4((float)c[3 * i], (float)c[3 * i + 1], (float)c[3 * i + 2], (float)k[i]));

@@ -78,6 +78,7 @@ struct mi_delbm {
   float4* bp_lo = nullptr;            // FP32 position remainders of the substep
   // learned contact guess (MI_GUESS_LEARNED): parameters and per-item buffers
   bool learned = false;
+  bool warm = false;                 // MI_GUESS_WARM
   void* mlp_image = nullptr;         // packed BF16 parameters of the fused inference kernel
   float* guess_feat = nullptr;       // cap_items x 64
   float* guess_pred = nullptr;       // cap_items x 4

@@ -198,7 +198,21 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       pair_frames(Pi, Pj, L.qf[i], L.qf[j], h, F0, F1);
       const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
       float y[3];
-      if (L.learned) {
+      const int lo = min(i, j), hi = max(i, j);
+      HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
+      // substeps count from 1 and the history starts zeroed: a stamp is valid from 1 on
+      const bool have_warm = L.warm && substep >= 2 && hp->xm_stamp == substep - 1;
+      if (have_warm) {
+        // warm start: the pair's closest point of the previous substep (x - O = (x - X_i) - h)
+        for (int c = 0; c < 3; ++c) y[c] = hp->xm_rel[c] - h[c];
+        status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
+        if (status != 0) {  // the plain start decides
+          int more = 0;
+          plain_guess(F0, F1, balls, lane, y);
+          status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, more);
+          iters += more;
+        }
+      } else if (L.learned) {
         // learned start: anchor and prediction of this item (features and MLP ran before)
         const float* x = L.feat + (size_t)it * 64;
         const float* pr = L.pred + (size_t)it * 4;
@@ -232,9 +246,11 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         nf[c] = dist > 0.f ? d[c] / dist : 0.f;
         rel[c] = h[c] + xc0[c] - (Pi.skin_f - 0.5f * dl) * nf[c];
       }
+      if (lane == 0 && L.warm && status == 0) {
+        for (int c = 0; c < 3; ++c) hp->xm_rel[c] = y[c] + h[c];
+        hp->xm_stamp = substep;
+      }
       if (lane == 0 && status == 0 && dl > 0.f) {
-        const int lo = min(i, j), hi = max(i, j);
-        HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
         double xcp[3], nrm[3], f[3];
         for (int c = 0; c < 3; ++c) {
           xcp[c] = Pi.pos[c] + (double)rel[c];

@@ -271,6 +271,9 @@ struct ContactRec {       // one candidate (pair or particle-wall) of the last s
 struct HistEntry {        // tangential spring of a pair / particle-wall contact
   double xi[3];
   long long stamp;        // DEM substep index of the last update (valid if previous substep)
+  float xm_rel[3];        // last converged closest point of the pair, relative to particle i (warm start)
+  int pad;
+  long long xm_stamp;     // DEM substep of xm_rel
 };
 struct ContactParams {
   double kn, kt, eta_n, eta_t, mu_s, dt, margin;
@@ -297,6 +300,7 @@ struct ContactLaunch {
   float4* plo;            // np FP32 remainders (position - pf.xyz) of the substep
   float4* qf;             // np FP32 unit quaternions (w, x, y, z) of the substep
   int learned;            // 1: pair items start from the learned guess (feat, pred), else the plain guess
+  int warm;               // 1: pair items start from the previous substep's closest point when it exists
   float* feat;            // cap_items x 64 features of the pair items (learned)
   const float* pred;      // cap_items x 4 MLP outputs (learned)
 };

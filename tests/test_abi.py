@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_config_layout_matches_binding(lib):
     from paper_2209_10411_gb300 import _binding as B
-    assert B.lib.mi_delbm_abi_version() == 1
+    assert B.lib.mi_delbm_abi_version() == 2
     assert B.lib.mi_delbm_config_size() == ctypes.sizeof(B.Config)
     cfg = B.Config()
     B.lib.mi_delbm_config_init(ctypes.byref(cfg))

@@ -158,3 +158,66 @@ def test_full_coupled_step_with_contacts():
             st = sim.get_particle_state(i)
             assert np.linalg.norm(st["pos"] - S.particles[i]["pos"]) < 1e-6
     sim.close()
+
+
+def test_add_particle_overlap_check():
+    """With check_overlap, a particle whose core overlaps an existing one is
+    rejected with MI_EOVERLAP (judged by the closest-point solve: the
+    converged point lies inside a core) and nothing is added; a particle in
+    skin contact only is accepted; without the check both are accepted."""
+    B = binding()
+    a = _particle([[-1, 0, 0], [1, 0, 0]], [3, 3], (13.0, 14.0, 14.0), (0.9, 0.1, 0.2, 0.1))
+    overlapping = _particle([[0, 0, 0], [0.8, 0.3, 0]], [4, 2], (17.0, 14.3, 14.2), (0.8, 0.3, 0.1, 0.4))
+    touching = _particle([[0, 0, 0], [0.8, 0.3, 0]], [4, 2], (17.8, 14.3, 14.2), (0.8, 0.3, 0.1, 0.4))
+    assert contact.newton_pair(a, overlapping)["status"] == contact.INSIDE
+    r = contact.newton_pair(a, touching)
+    assert r["status"] == contact.OK and r["delta"] > 0
+
+    def add(sim, P):
+        sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"],
+                         mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
+
+    with B.Simulation(32, 28, 30, check_overlap=True, max_particles=8) as sim:
+        add(sim, a)
+        with pytest.raises(B.MiDelbmError) as ei:
+            add(sim, overlapping)
+        assert ei.value.status == B.MI_EOVERLAP
+        assert sim.num_particles() == 1
+        add(sim, touching)
+        assert sim.num_particles() == 2
+        sim.step(1)  # the rejected particle left nothing behind
+        assert np.isfinite(sim.forces()["F_contact"]).all()
+    with B.Simulation(32, 28, 30, max_particles=8) as sim:
+        add(sim, a)
+        add(sim, overlapping)
+        assert sim.num_particles() == 2
+
+
+def test_warm_guess_same_contacts_fewer_iterations():
+    """MI_GUESS_WARM starts each pair's Newton solve at the pair's closest point
+    of the previous DEM substep: over 8 substeps per step the cluster gets the
+    same contacts, points and forces as with the plain guess (to the
+    convergence tolerance) in fewer iterations."""
+    B = binding()
+    parts = _cluster(5)
+    for P in parts:
+        P["vel"] = P["vel"] * 10.0
+    res = {}
+    for mode in (B.GUESS_PLAIN, B.GUESS_WARM):
+        sim = _sim(B, (48, 48, 40), parts, dem_substeps=8, guess_mode=mode)
+        sim.step(2)
+        recs = sorted(sim.contacts(), key=_key)
+        res[mode] = (recs, sim.forces(), [sim.get_particle_state(i) for i in range(len(parts))])
+        sim.close()
+    (rp, fp, sp), (rw, fw, sw) = res[B.GUESS_PLAIN], res[B.GUESS_WARM]
+    assert [_key(c) for c in rp] == [_key(c) for c in rw]
+    pairs_p = [c for c in rp if c["j"] >= 0 and c["status"] == 0]
+    pairs_w = [c for c in rw if c["j"] >= 0 and c["status"] == 0]
+    assert len(pairs_p) == len(pairs_w) > 0
+    for a, b in zip(pairs_p, pairs_w):
+        assert np.linalg.norm(a["x_cp"] - b["x_cp"]) <= 1e-4, (a, b)
+    scale = np.abs(fp["F_contact"]).max()
+    assert np.abs(fp["F_contact"] - fw["F_contact"]).max() <= 1e-3 * scale + 1e-9
+    it_p = np.mean([c["iters"] for c in pairs_p])
+    it_w = np.mean([c["iters"] for c in pairs_w])
+    assert it_w < it_p, (it_w, it_p)
