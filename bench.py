@@ -104,11 +104,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
-
-
 # ---------------------------------------------------------------------------
 # CPU side: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
@@ -141,7 +136,8 @@ def oracle_sample(budget_s=15.0, crop=96, seed=0):
 
 
 def run_reference(args):
-    rank, world, _ = _dist_env()
+    from paper_2209_10411_gb300 import replicas
+    rank, world, _ = replicas.rank_env()
     if rank != 0:
         return
     per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
@@ -338,7 +334,8 @@ def storage_variant(B, scene, storage, steps, stream_obj):
 
 def run_mine(args):
     import torch
-    rank, world, local = _dist_env()
+    from paper_2209_10411_gb300 import replicas
+    rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -370,8 +367,7 @@ def run_mine(args):
     clocks = ClockSampler()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.25)
@@ -384,10 +380,7 @@ def run_mine(args):
     launches = sim.launch_count() - launches0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, world, device="cuda")
     stats = sim.stats()
 
     # second timed region, same steps as individual launches bracketed by CUDA
@@ -407,7 +400,7 @@ def run_mine(args):
     n_boundary = int(((cls & 2) != 0).sum())
     n_bulk = ncell - n_solid - n_boundary
 
-    value = ncell * args.steps * world / (ms * 1e-3) / 1e6
+    value = replicas.aggregate_throughput(ncell * args.steps, world, ms) / 1e6
     bulk_ms, bulk_n = ptimes["bulk"]
     contacts = None
     if not args.no_contacts and rank == 0:
