@@ -363,6 +363,14 @@ mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
  * returned through the non-NULL pointers. */
 mi_status mi_delbm_autotune(mi_delbm *h, const char *cache_path, int *bulk_block_x, int *list_blocks_per_sm);
 
+/* Step schedule.  overlap_boundary != 0: the boundary nodes (interpolated
+ * bounce-back, momentum exchange, collision) are computed on the particle
+ * side stream while the bulk kernel runs, into a side buffer, and copied into
+ * the new populations after the bulk and near kernels (the results are the
+ * same bits as the default order, in which they are computed after those
+ * kernels).  Applies to steps that run all phases.  Discards captured graphs. */
+mi_status mi_delbm_set_schedule(mi_delbm *h, int overlap_boundary);
+
 /* Set the launch shapes directly (what mi_delbm_autotune chooses): bulk
  * kernel threads per block along x (32..256, a multiple of 32; at most 128
  * with pairs), rows per thread (1 or 2), paired nodes (0: no; 1 or 2: two

@@ -130,6 +130,7 @@ _sig("mi_mlp_pack", c_int, _P, _P, _P)
 _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
+_sig("mi_delbm_set_schedule", c_int, _P, c_int)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS = 1, 2, 4, 8
@@ -382,6 +383,10 @@ class Simulation:
         self._check(lib.mi_delbm_get_tuning(self.h, *[ctypes.byref(x) for x in v]))
         return {"bulk_block_x": v[0].value, "bulk_rows": v[1].value, "bulk_pairs": v[2].value,
                 "list_blocks_per_sm": v[3].value}
+
+    def set_schedule(self, overlap_boundary):
+        """Compute the boundary nodes beside the bulk kernel (True) or after it."""
+        self._check(lib.mi_delbm_set_schedule(self.h, 1 if overlap_boundary else 0))
 
     def set_graphs(self, on):
         self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))

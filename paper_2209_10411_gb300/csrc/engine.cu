@@ -195,6 +195,7 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
   L.forcing = h->forcing();
   L.bb_mode = h->cfg.bb_mode;
   L.grid = h->sm_count * h->tune.list_blocks_per_sm;
+  L.tmp = nullptr;
   return L;
 }
 
@@ -215,6 +216,23 @@ mi_status mi_delbm::phase_boundary() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
   return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
+}
+
+// Overlapped schedule: the boundary nodes' new values go to bc_tmp on a side
+// stream while the bulk kernel writes B (k_boundary reads only A, which the
+// refill completes before it), and are scattered into B after k_near.
+mi_status mi_delbm::phase_boundary_beside(cudaStream_t st) {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  L.tmp = bc_tmp;
+  return launch_phase(this, st, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, st); });
+}
+
+mi_status mi_delbm::phase_scatter_boundary() {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  L.tmp = bc_tmp;
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_scatter_boundary(L, stream); });
 }
 
 mi_status mi_delbm::phase_integrate(bool with_contacts) {
@@ -363,6 +381,9 @@ mi_status mi_delbm::run_phases(unsigned phases) {
   const bool contact_branch = particles && (phases & MI_PHASE_CONTACT);
   const bool chain = particles && (phases & (MI_PHASE_FLAG | MI_PHASE_LINKS | MI_PHASE_REFILL));
   const bool links_branch = particles && (phases & MI_PHASE_LINKS);
+  // overlapped boundary schedule: needs the whole chain, the wall fractions and the bulk kernel in this call
+  const bool beside = overlap_boundary && links_branch && (phases & MI_PHASE_BOUNDARY) && (phases & MI_PHASE_BULK) &&
+                      (phases & MI_PHASE_FLAG) && (phases & MI_PHASE_REFILL);
   if (contact_branch) {
     if ((s = ensure_contact_buffers()) != MI_OK) return s;
     if ((s = fork(stream, aux[1], 0)) != MI_OK) return s;
@@ -378,13 +399,24 @@ mi_status mi_delbm::run_phases(unsigned phases) {
       if ((s = join_record(aux[0], 1)) != MI_OK) return s;
     }
     if ((phases & MI_PHASE_REFILL) && (s = phase_refill(aux[2])) != MI_OK) return s;
+    if (beside) {
+      // the boundary nodes beside the bulk kernel: after the refill and the wall fractions
+      cudaError_t e = cudaEventRecord(ev_join[1], aux[0]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux[2], ev_join[1], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "join");
+      if ((s = phase_boundary_beside(aux[2])) != MI_OK) return s;
+    }
     if ((s = join_record(aux[2], 2)) != MI_OK) return s;
   }
   if ((phases & MI_PHASE_BULK) && (s = phase_bulk()) != MI_OK) return s;
   if (chain && (s = join_wait(2)) != MI_OK) return s;
   if ((phases & MI_PHASE_BULK) && (s = phase_near()) != MI_OK) return s;
-  if (links_branch && (s = join_wait(1)) != MI_OK) return s;
-  if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
+  if (beside) {
+    if ((s = phase_scatter_boundary()) != MI_OK) return s;
+  } else {
+    if (links_branch && (s = join_wait(1)) != MI_OK) return s;
+    if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
+  }
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
   if (contact_branch && (s = join_wait(0)) != MI_OK) return s;
   if (phases & (MI_PHASE_CONTACT | MI_PHASE_INTEGRATE)) {
@@ -541,7 +573,7 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   links = links > cap_links ? links : cap_links;
   nnew = nnew > cap_new ? nnew : cap_new;
   dfree(bc_cell); dfree(bc_mask); dfree(bc_loff); dfree(link_bc); dfree(link_p); dfree(link_dir);
-  dfree(link_q); dfree(new_cell);
+  dfree(link_q); dfree(new_cell); dfree(bc_tmp);
   bc_cell = (uint32_t*)dalloc(4ull * bc);
   bc_mask = (uint32_t*)dalloc(4ull * bc);
   bc_loff = (uint32_t*)dalloc(4ull * bc);
@@ -550,7 +582,8 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   link_dir = (uint8_t*)dalloc(1ull * links);
   link_q = (float*)dalloc(4ull * links);
   new_cell = (uint32_t*)dalloc(4ull * nnew);
-  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell) {
+  bc_tmp = dalloc(19ull * store_bytes(cfg.storage) * bc);
+  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell || !bc_tmp) {
     cap_bc = cap_links = cap_new = 0;
     return fail(MI_ENOMEM, "link lists: device allocation failed");
   }
@@ -889,6 +922,13 @@ mi_status mi_delbm_pair_solve(mi_delbm* h, int n, const int* ij, const double* p
   cudaError_t e = launch_pair_solve(S, h->stream);
   h->launches += 1;
   if (e != cudaSuccess) return h->cuda_fail(e, "pair_solve: launch");
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_schedule(mi_delbm* h, int overlap_boundary) {
+  if (!h) return MI_EINVAL;
+  if (h->overlap_boundary != (overlap_boundary != 0)) h->invalidate_graphs();
+  h->overlap_boundary = overlap_boundary != 0;
   return MI_OK;
 }
 

@@ -89,6 +89,8 @@ struct mi_delbm {
   float* link_q = nullptr;
   uint32_t* new_cell = nullptr;
   unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
+  void* bc_tmp = nullptr;            // 19 stored values per boundary node (overlapped schedule)
+  bool overlap_boundary = false;     // boundary nodes computed beside the bulk kernel, scattered after it
   int blocks_per_particle = 1;
 
   TuneChoice tune;
@@ -118,6 +120,8 @@ struct mi_delbm {
   mi_status phase_near();
   mi_status phase_bulk();
   mi_status phase_boundary();
+  mi_status phase_boundary_beside(cudaStream_t st);
+  mi_status phase_scatter_boundary();
   mi_status phase_swap();
   mi_status phase_integrate(bool with_contacts);
   mi_status phase_contact(cudaStream_t st);

@@ -723,7 +723,8 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
         const float uF = u0 * L.p.force[0] + u1 * L.p.force[1] + u2 * L.p.force[2];
         hp += (1.0f - 0.5f * om) * wj * (3.0f * (eF - uF) + 9.0f * eu * eF);
       }
-      Store<ST>::put(B + j * g.plane + c, j, hp);
+      if (L.tmp) Store<ST>::put(static_cast<T*>(L.tmp) + 19 * (size_t)bi + j, j, hp);
+      else Store<ST>::put(B + j * g.plane + c, j, hp);
     }
     // momentum exchange: every link's contribution is rounded to 2^-40 fixed
     // point in its own lane (the rounding is odd-symmetric, so opposite links
@@ -800,6 +801,24 @@ cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s) {
 template <int ST>
 static cudaError_t launch_boundary_st(const BoundaryLaunch& L, cudaStream_t s) {
   return L.forcing ? launch_boundary_f<ST, true>(L, s) : launch_boundary_f<ST, false>(L, s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_boundary(BoundaryLaunch L) {
+  const unsigned nbc = min(L.pl.ctr->n_bc, L.pl.cap_bc);
+  const T* __restrict__ tmp = static_cast<const T*>(L.tmp);
+  T* __restrict__ B = static_cast<T*>(L.B);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < 19u * nbc; e += gridDim.x * blockDim.x) {
+    const unsigned k = e / 19u, j = e - 19u * k;
+    B[j * L.pl.g.plane + L.pl.bc_cell[k]] = tmp[e];
+  }
+}
+
+cudaError_t launch_scatter_boundary(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.pl.np == 0 || !L.tmp) return cudaSuccess;
+  if (L.storage == MI_STORE_F32) k_scatter_boundary<float><<<L.grid, 256, 0, s>>>(L);
+  else k_scatter_boundary<unsigned short><<<L.grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s) {

@@ -252,10 +252,13 @@ struct BoundaryLaunch {
   bool forcing;
   int bb_mode;
   int grid;
+  void* tmp;  // when set, k_boundary writes node k's 19 values to tmp[19 k ..] instead of B
 };
 cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s);
 cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s);
 cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s);
+// Copy the boundary nodes' values from L.tmp into B (stored format, no arithmetic).
+cudaError_t launch_scatter_boundary(const BoundaryLaunch& L, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // DEM contacts (k_contact.cu)
