@@ -181,24 +181,53 @@ __device__ __forceinline__ void sphere_midpoint(const Frame& F0, const Frame& F1
   for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
 }
 
+constexpr int PG_CAP = 128;  // balls of particle 1 the plain guess stages in shared memory
+
 // Plain starting guess: the closest pair of control-point spheres (smallest
-// surface gap, ties to the lower (a, b)), O(n0 n1) per pair.
+// surface gap, ties to the lower (a, b)), O(n0 n1) per pair.  With a warp's
+// shared buffer of PG_CAP float4 (and n1 <= PG_CAP), particle 1's spheres
+// (local centre, radius) are formed once and read back by broadcast instead
+// of being transformed again for every ball of particle 0; the arithmetic
+// and the order are the same either way.
 __device__ __forceinline__ void plain_guess(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
-                                            int lane, float y[3]) {
+                                            int lane, float y[3], float4* stage = nullptr) {
   float best = 3.4e38f;
   int ba = 0, bb = 0;
-  for (int a = lane; a < F0.n; a += 32) {
-    const float4 ca = __ldg(balls + F0.off + a);
-    float pa[3];
-    ball_local(F0, ca, pa);
-    const float ra = sqrtf(ca.w);
-    for (int b = 0; b < F1.n; ++b) {
+  if (stage && F1.n <= PG_CAP) {
+    for (int b = lane; b < F1.n; b += 32) {
       const float4 cb = __ldg(balls + F1.off + b);
       float pb[3];
       ball_local(F1, cb, pb);
-      const float gap = sqrtf((pa[0] - pb[0]) * (pa[0] - pb[0]) + (pa[1] - pb[1]) * (pa[1] - pb[1]) +
-                              (pa[2] - pb[2]) * (pa[2] - pb[2])) - ra - sqrtf(cb.w);
-      if (gap < best) { best = gap; ba = a; bb = b; }
+      stage[b] = make_float4(pb[0], pb[1], pb[2], sqrtf(cb.w));
+    }
+    __syncwarp();
+    for (int a = lane; a < F0.n; a += 32) {
+      const float4 ca = __ldg(balls + F0.off + a);
+      float pa[3];
+      ball_local(F0, ca, pa);
+      const float ra = sqrtf(ca.w);
+      for (int b = 0; b < F1.n; ++b) {
+        const float4 q = stage[b];
+        const float gap = sqrtf((pa[0] - q.x) * (pa[0] - q.x) + (pa[1] - q.y) * (pa[1] - q.y) +
+                                (pa[2] - q.z) * (pa[2] - q.z)) - ra - q.w;
+        if (gap < best) { best = gap; ba = a; bb = b; }
+      }
+    }
+    __syncwarp();  // the buffer is free again
+  } else {
+    for (int a = lane; a < F0.n; a += 32) {
+      const float4 ca = __ldg(balls + F0.off + a);
+      float pa[3];
+      ball_local(F0, ca, pa);
+      const float ra = sqrtf(ca.w);
+      for (int b = 0; b < F1.n; ++b) {
+        const float4 cb = __ldg(balls + F1.off + b);
+        float pb[3];
+        ball_local(F1, cb, pb);
+        const float gap = sqrtf((pa[0] - pb[0]) * (pa[0] - pb[0]) + (pa[1] - pb[1]) * (pa[1] - pb[1]) +
+                                (pa[2] - pb[2]) * (pa[2] - pb[2])) - ra - sqrtf(cb.w);
+        if (gap < best) { best = gap; ba = a; bb = b; }
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -311,7 +340,8 @@ struct SolveCount {
 // If the full-set solve fails, plain Newton from the plain guess decides.
 __device__ __forceinline__ int learned_newton(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
                                               int lane, const float a[3], const float d[4], float L, float Rb,
-                                              unsigned short* l0, unsigned short* l1, float y[3], SolveCount& sc) {
+                                              unsigned short* l0, unsigned short* l1, float y[3], SolveCount& sc,
+                                              float4* stage = nullptr) {
   sc.iters = sc.evals = sc.fallback = 0;
   for (int c = 0; c < 3; ++c) y[c] = L * (a[c] + d[c]);
   bool ok = isfinite(y[0]) && isfinite(y[1]) && isfinite(y[2]);
@@ -336,7 +366,7 @@ __device__ __forceinline__ int learned_newton(const Frame& F0, const Frame& F1, 
   }
   if (ok) return 0;
   sc.fallback = 1;
-  plain_guess(F0, F1, balls, lane, y);
+  plain_guess(F0, F1, balls, lane, y, stage);
   int it = 0;
   const int st = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
   sc.iters += it;

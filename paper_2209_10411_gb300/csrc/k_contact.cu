@@ -172,6 +172,7 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
 // Persistent warp-per-candidate Newton solver and forces.
 __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
   __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
+  __shared__ float4 stage[4][PG_CAP];             // the plain guess's staged spheres, per warp
   const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
   const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
   const long long substep = *L.substep;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
         if (status != 0) {  // the plain start decides
           int more = 0;
-          plain_guess(F0, F1, balls, lane, y);
+          plain_guess(F0, F1, balls, lane, y, stage[warp_in_block]);
           status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, more);
           iters += more;
         }
@@ -218,11 +219,12 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         const float* pr = L.pred + (size_t)it * 4;
         const float a[3] = {x[11], x[12], x[13]}, d[4] = {pr[0], pr[1], pr[2], pr[3]};
         SolveCount sc;
-        status = learned_newton(F0, F1, balls, lane, a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc);
+        status = learned_newton(F0, F1, balls, lane, a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc,
+                                stage[warp_in_block]);
         iters = sc.iters;
       } else {
         // plain start: closest pair of control-point spheres, midpoint of their surface points
-        plain_guess(F0, F1, balls, lane, y);
+        plain_guess(F0, F1, balls, lane, y, stage[warp_in_block]);
         status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
       }
       const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);

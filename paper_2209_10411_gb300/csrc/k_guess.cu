@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
 __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
   __shared__ float sh[WARPS][64];
   __shared__ unsigned short sub[WARPS][2][SUB_CAP];
+  __shared__ float4 stage[WARPS][PG_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int p = blockIdx.x * WARPS + w; p < S.n; p += gridDim.x * WARPS) {
     const int i = S.ij[2 * p], j = S.ij[2 * p + 1];
@@ -71,9 +72,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
       const float a[3] = {ya[0] / Rb, ya[1] / Rb, ya[2] / Rb};
       const float* pr = S.pred + (size_t)4 * p;
       const float d[4] = {pr[0], pr[1], pr[2], pr[3]};
-      status = learned_newton(F0, F1, S.balls, lane, a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc);
+      status = learned_newton(F0, F1, S.balls, lane, a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc, stage[w]);
     } else if (S.flags & MI_PAIR_PLAIN) {
-      plain_guess(F0, F1, S.balls, lane, y);
+      plain_guess(F0, F1, S.balls, lane, y, stage[w]);
       status = newton_pair(F0, F1, S.balls, lane, y, NEWTON_TOL * Rb, MAX_IT, sc.iters);
       sc.evals = sc.iters * (F0.n + F1.n);
     }
