@@ -533,3 +533,214 @@ __device__ __forceinline__ void pair_labels(const Frame& F0, const Frame& F1, co
 
 }  // namespace cdev
 }  // namespace mi
+
+namespace mi {
+namespace cdev {
+
+__device__ __forceinline__ void reaching_staged2(const float4* s0, int n0, const float t0[3], const float4* s1, int n1,
+                                                 const float t1[3], int lane, int& a, int& b);
+__device__ __forceinline__ void field_nearest_staged2(const float4* s0, int n0, float sc0, const float4* s1, int n1,
+                                                      float sc1, const float y[3], float iL, int lane, float* row0,
+                                                      float* row1, float& g0, float& g1);
+
+// Staged form of the feature computation: the local centres and k of both
+// particles' balls (at most PG_CAP each) are formed once into the warp's
+// shared buffers s0, s1 and every scan reads them back; the five nearest-ball
+// rows of a particle are written by lanes 0..4 at once.  The values are those
+// of pair_features (same operations on the same operands).
+// pair_features with both particles staged in s0, s1 (PG_CAP float4 each);
+// falls back to pair_features when a particle has more balls.
+__device__ __forceinline__ void pair_features_staged(const DevParticle& Pi, const DevParticle& Pj, const float h[3],
+                                                     const float4 qi, const float4 qj, const Frame& F0,
+                                                     const Frame& F1, const float4* __restrict__ balls, int lane,
+                                                     float* sh, float* out, float ya[3], float4* s0, float4* s1) {
+  if (F0.n > PG_CAP || F1.n > PG_CAP) {
+    pair_features(Pi, Pj, h, qi, qj, F0, F1, balls, lane, sh, out, ya);
+    return;
+  }
+  for (int b = lane; b < F0.n; b += 32) {
+    const float4 c = __ldg(balls + F0.off + b);
+    float p[3];
+    ball_local(F0, c, p);
+    s0[b] = make_float4(p[0], p[1], p[2], c.w);
+  }
+  for (int b = lane; b < F1.n; b += 32) {
+    const float4 c = __ldg(balls + F1.off + b);
+    float p[3];
+    ball_local(F1, c, p);
+    s1[b] = make_float4(p[0], p[1], p[2], c.w);
+  }
+  __syncwarp();
+  const float L = fmaxf(Pi.Rb_f, Pj.Rb_f);
+  const float iL = 1.0f / L;
+  {
+    // anchor: the sphere of each particle reaching closest to the other's origin
+    int a, b;
+    reaching_staged2(s0, F0.n, F1.t, s1, F1.n, F0.t, lane, a, b);
+    const float4 pa = s0[a], pb = s1[b];
+    float u[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
+    const float D = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (D > 0.f) for (int c = 0; c < 3; ++c) u[c] /= D;
+    else { u[0] = 1.f; u[1] = u[2] = 0.f; }
+    const float ra = sqrtf(pa.w), rb = sqrtf(pb.w);
+    ya[0] = 0.5f * ((pa.x + ra * u[0]) + (pb.x - rb * u[0]));
+    ya[1] = 0.5f * ((pa.y + ra * u[1]) + (pb.y - rb * u[1]));
+    ya[2] = 0.5f * ((pa.z + ra * u[2]) + (pb.z - rb * u[2]));
+  }
+  float g0, g1;
+  field_nearest_staged2(s0, F0.n, F0.s, s1, F1.n, F1.s, ya, iL, lane, sh + 20, sh + 44, g0, g1);
+  if (lane == 0) {
+    for (int c = 0; c < 3; ++c) sh[c] = 2.0f * h[c] * iL;
+    for (int side = 0; side < 2; ++side) {
+      const float4 q = side ? qj : qi;
+      const float sg = q.x >= 0.f ? 1.f : -1.f;
+      sh[3 + 4 * side] = sg * q.x;
+      sh[4 + 4 * side] = sg * q.y;
+      sh[5 + 4 * side] = sg * q.z;
+      sh[6 + 4 * side] = sg * q.w;
+    }
+    for (int c = 0; c < 3; ++c) sh[11 + c] = ya[c] * iL;
+    sh[14] = logf(g0);
+    sh[15] = logf(g1);
+    for (int side = 0; side < 2; ++side) {
+      const Frame& F = side ? F1 : F0;
+      const DevParticle& P = side ? Pj : Pi;
+      const int off = side ? 40 : 16;
+      sh[off] = logf((float)F.n) / 5.0f;
+      sh[off + 1] = 2.0f * logf(P.re_f * iL);
+      sh[off + 2] = P.Rb_f * iL;
+      sh[off + 3] = P.skin_f * iL;
+    }
+  }
+  __syncwarp();
+  out[lane] = sh[lane];
+  out[lane + 32] = sh[lane + 32];
+  __syncwarp();
+}
+
+}  // namespace cdev
+}  // namespace mi
+
+namespace mi {
+namespace cdev {
+
+// Both particles at once (the same values as two reaching_staged /
+// field_nearest_staged calls): the two independent reductions of every step
+// are interleaved, which halves the dependent shuffle latency per pair.
+__device__ __forceinline__ void argmin2(float& b0, int& i0, float& b1, int& i1) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float g0 = __shfl_xor_sync(FULL, b0, o), g1 = __shfl_xor_sync(FULL, b1, o);
+    const int j0 = __shfl_xor_sync(FULL, i0, o), j1 = __shfl_xor_sync(FULL, i1, o);
+    if (g0 < b0 || (g0 == b0 && j0 < i0)) { b0 = g0; i0 = j0; }
+    if (g1 < b1 || (g1 == b1 && j1 < i1)) { b1 = g1; i1 = j1; }
+  }
+  i0 = __shfl_sync(FULL, i0, 0);
+  i1 = __shfl_sync(FULL, i1, 0);
+}
+
+__device__ __forceinline__ void reaching_staged2(const float4* s0, int n0, const float t0[3], const float4* s1, int n1,
+                                                 const float t1[3], int lane, int& a, int& b) {
+  float b0 = 3.4e38f, b1 = 3.4e38f;
+  int i0 = 0x7fffffff, i1 = 0x7fffffff;
+  const int n = max(n0, n1);
+  for (int k = lane; k < n; k += 32) {
+    if (k < n0) {
+      const float4 q = s0[k];
+      const float gap = sqrtf((q.x - t0[0]) * (q.x - t0[0]) + (q.y - t0[1]) * (q.y - t0[1]) +
+                              (q.z - t0[2]) * (q.z - t0[2])) - sqrtf(q.w);
+      if (gap < b0) { b0 = gap; i0 = k; }
+    }
+    if (k < n1) {
+      const float4 q = s1[k];
+      const float gap = sqrtf((q.x - t1[0]) * (q.x - t1[0]) + (q.y - t1[1]) * (q.y - t1[1]) +
+                              (q.z - t1[2]) * (q.z - t1[2])) - sqrtf(q.w);
+      if (gap < b1) { b1 = gap; i1 = k; }
+    }
+  }
+  argmin2(b0, i0, b1, i1);
+  a = i0;
+  b = i1;
+}
+
+__device__ __forceinline__ void topk_insert(float (&kd)[NEAREST], int (&kb)[NEAREST], float cd, int cb) {
+#pragma unroll
+  for (int r = 0; r < NEAREST; ++r)  // a lane's balls arrive in index order: strict < keeps ties in order
+    if (cd < kd[r]) {
+      const float td = kd[r]; kd[r] = cd; cd = td;
+      const int tb = kb[r]; kb[r] = cb; cb = tb;
+    }
+}
+
+__device__ __forceinline__ void topk_pop(float (&kd)[NEAREST], int (&kb)[NEAREST], int bi) {
+  if (kb[0] == bi && bi != 0x7fffffff) {
+#pragma unroll
+    for (int q = 0; q < NEAREST - 1; ++q) { kd[q] = kd[q + 1]; kb[q] = kb[q + 1]; }
+    kd[NEAREST - 1] = 3.4e38f;
+    kb[NEAREST - 1] = 0x7fffffff;
+  }
+}
+
+__device__ __forceinline__ void nearest_row(const float4* st, int n, float s, const float y[3], float iL, int mine,
+                                            float* out) {
+  if (mine < n) {
+    const float4 q = st[mine];
+    out[0] = (q.x - y[0]) * iL;
+    out[1] = (q.y - y[1]) * iL;
+    out[2] = (q.z - y[2]) * iL;
+    out[3] = logf(s * q.w * iL * iL);
+  } else {
+    out[0] = out[1] = out[2] = out[3] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void field_nearest_staged2(const float4* s0, int n0, float sc0, const float4* s1, int n1,
+                                                      float sc1, const float y[3], float iL, int lane, float* row0,
+                                                      float* row1, float& g0, float& g1) {
+  float kd0[NEAREST], kd1[NEAREST];
+  int kb0[NEAREST], kb1[NEAREST];
+#pragma unroll
+  for (int r = 0; r < NEAREST; ++r) {
+    kd0[r] = kd1[r] = 3.4e38f;
+    kb0[r] = kb1[r] = 0x7fffffff;
+  }
+  float a0 = 0.f, a1 = 0.f;
+  const int n = max(n0, n1);
+  for (int k = lane; k < n; k += 32) {
+    if (k < n0) {
+      const float4 q = s0[k];
+      const float d2 = (q.x - y[0]) * (q.x - y[0]) + (q.y - y[1]) * (q.y - y[1]) + (q.z - y[2]) * (q.z - y[2]);
+      a0 += q.w / d2;
+      topk_insert(kd0, kb0, sqrtf(d2), k);
+    }
+    if (k < n1) {
+      const float4 q = s1[k];
+      const float d2 = (q.x - y[0]) * (q.x - y[0]) + (q.y - y[1]) * (q.y - y[1]) + (q.z - y[2]) * (q.z - y[2]);
+      a1 += q.w / d2;
+      topk_insert(kd1, kb1, sqrtf(d2), k);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(FULL, a0, o);
+    a1 += __shfl_xor_sync(FULL, a1, o);
+  }
+  g0 = sc0 * __shfl_sync(FULL, a0, 0);
+  g1 = sc1 * __shfl_sync(FULL, a1, 0);
+  int mine0 = 0x7fffffff, mine1 = 0x7fffffff;
+  for (int r = 0; r < NEAREST; ++r) {
+    float b0 = kd0[0], b1 = kd1[0];
+    int i0 = kb0[0], i1 = kb1[0];
+    argmin2(b0, i0, b1, i1);
+    topk_pop(kd0, kb0, i0);
+    topk_pop(kd1, kb1, i1);
+    if (lane == r) { mine0 = i0; mine1 = i1; }
+  }
+  if (lane < NEAREST) {
+    nearest_row(s0, n0, sc0, y, iL, mine0, row0 + 4 * lane);
+    nearest_row(s1, n1, sc1, y, iL, mine1, row1 + 4 * lane);
+  }
+}
+
+}  // namespace cdev
+}  // namespace mi

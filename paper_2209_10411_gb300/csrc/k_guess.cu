@@ -15,6 +15,7 @@ constexpr int WARPS = 4;
 // candidates are left alone: walls always start from the plain guess).
 __global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
   __shared__ float sh[WARPS][64];
+  __shared__ float4 stage[WARPS][2][PG_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
   for (unsigned it = blockIdx.x * WARPS + w; it < n_items; it += gridDim.x * WARPS) {
@@ -29,14 +30,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
     Frame F0, F1;
     pair_frames(Pi, Pj, qi, qj, h, F0, F1);
     float ya[3];
-    pair_features(Pi, Pj, h, qi, qj, F0, F1, L.balls, lane, sh[w], L.feat + (size_t)it * 64, ya);
+    pair_features_staged(Pi, Pj, h, qi, qj, F0, F1, L.balls, lane, sh[w], L.feat + (size_t)it * 64, ya, stage[w][0],
+                         stage[w][1]);
   }
 }
 
 __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
   __shared__ float sh[WARPS][64];
   __shared__ unsigned short sub[WARPS][2][SUB_CAP];
-  __shared__ float4 stage[WARPS][PG_CAP];
+  __shared__ float4 stage[WARPS][2][PG_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int p = blockIdx.x * WARPS + w; p < S.n; p += gridDim.x * WARPS) {
     const int i = S.ij[2 * p], j = S.ij[2 * p + 1];
@@ -60,7 +62,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
     const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
     float ya[3] = {0.f, 0.f, 0.f}, y[3];
     if (S.flags & MI_PAIR_FEATURES) {
-      pair_features(Pi, Pj, h, q0, q1, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya);
+      pair_features_staged(Pi, Pj, h, q0, q1, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya, stage[w][0],
+                           stage[w][1]);
     } else if (S.flags & MI_PAIR_LEARNED) {
       for (int c = 0; c < 3; ++c) ya[c] = Rb * S.X[(size_t)64 * p + 11 + c];
     } else {
@@ -72,9 +75,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
       const float a[3] = {ya[0] / Rb, ya[1] / Rb, ya[2] / Rb};
       const float* pr = S.pred + (size_t)4 * p;
       const float d[4] = {pr[0], pr[1], pr[2], pr[3]};
-      status = learned_newton(F0, F1, S.balls, lane, a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc, stage[w]);
+      status = learned_newton(F0, F1, S.balls, lane, a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc, stage[w][0]);
     } else if (S.flags & MI_PAIR_PLAIN) {
-      plain_guess(F0, F1, S.balls, lane, y, stage[w]);
+      plain_guess(F0, F1, S.balls, lane, y, stage[w][0]);
       status = newton_pair(F0, F1, S.balls, lane, y, NEWTON_TOL * Rb, MAX_IT, sc.iters);
       sc.evals = sc.iters * (F0.n + F1.n);
     }

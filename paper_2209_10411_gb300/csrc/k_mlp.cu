@@ -560,8 +560,7 @@ cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* 
 // ---------------------------------------------------------------------------
 // Fused inference on the 5th-generation tensor cores (tcgen05, TMEM).
 //
-// One CTA of 128 threads (one warpgroup) per 128-row tile, persistent over
-// tiles.  Operands are BF16 in shared memory in the no-swizzle K-major
+// One CTA of 256 threads per 128-row tile, persistent over tiles.  Operands are BF16 in shared memory in the no-swizzle K-major
 // "core matrix" layout (8 rows x 16 bytes contiguous; adjacent core
 // matrices 128 bytes apart along K, a whole K extent apart along M/N).  The
 // weights are packed once into five 32 KB chunks of (N = 256) x (K = 64):
@@ -569,12 +568,13 @@ cudaError_t mlp_infer(const void* image, const float* X, int M, const unsigned* 
 // two-slot shared-memory ring with cp.async.bulk (completion on an
 // mbarrier) and issues the MMAs (M = 128, N = 256, K = 16 each) into one
 // FP32 accumulator of 256 TMEM columns; tcgen05.commit arrives on an
-// mbarrier when they complete (which also frees the ring slot).  Each
-// thread owns one row of the tile: it reads its accumulator row back with
+// mbarrier when they complete (which also frees the ring slot).  Two
+// threads own each row of the tile (warp w reads TMEM lanes 32 (w % 4) ..,
+// column half w / 4): they read their half of the accumulator row back with
 // tcgen05.ld for the bias + ReLU epilogue of layer 1 (written back as BF16
 // for layer 2's A operand) and for layer 2's epilogue, which also applies
 // the 256 -> 4 output layer with the same BF16-rounded operands as the
-// other paths.  Every wait is bounded: on a timeout the kernel raises its
+// other paths (the two half-row partial sums meet in shared memory).  Every wait is bounded: on a timeout the kernel raises its
 // error flag, stops issuing work, waits (bounded) for what it issued and
 // frees its TMEM.
 // ---------------------------------------------------------------------------
@@ -594,8 +594,10 @@ constexpr unsigned TS_X = 0;                                 // 128 x 64 BF16 co
 constexpr unsigned TS_H = TS_X + TC_M * 64 * 2;              // 128 x 256 BF16: 64 KB
 constexpr unsigned TS_W = TS_H + TC_M * 256 * 2;             // ring: 2 x 32 KB
 constexpr unsigned TS_P = TS_W + 2 * TC_CHUNK;               // W3^T, b1, b2, b3: 6160 B
-constexpr unsigned TS_BAR = TS_P + 4 * 256 * 4 + 2 * 256 * 4 + 16;  // mbarriers (8 B each)
+constexpr unsigned TS_YP = TS_P + 4 * 256 * 4 + 2 * 256 * 4 + 16;  // output-layer partials [2][128][4]
+constexpr unsigned TS_BAR = TS_YP + 2 * TC_M * 4 * 4;               // mbarriers (8 B each)
 constexpr unsigned TS_BYTES = TS_BAR + 64;
+constexpr int TC_THREADS = 256;  // two threads per tile row: one per half of the 256 columns
 static_assert(TC_IMG_BYTES % 16 == 0 && TS_BYTES <= 232448 && TS_BAR % 8 == 0, "tcgen05 MLP layout");
 
 // byte offset of element (row r, k) in a core-matrix K-major tile with K extent kext
@@ -715,11 +717,13 @@ __device__ __forceinline__ unsigned pack_bf2(float a, float b) {
 namespace mi {
 namespace {
 
-__global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restrict__ img, const float* __restrict__ X,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* __restrict__ img, const float* __restrict__ X,
                                                    int M, const unsigned* __restrict__ Mdev, float* __restrict__ Y,
                                                    unsigned* __restrict__ err, unsigned err_bit) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // warp w reads TMEM lanes 32 (w % 4) ..: this thread's tile row, and column half w / 4
+  const int row_t = 32 * (warp & 3) + lane, half = warp >> 2;
   if (Mdev) M = min(M, (int)*Mdev);
   const int tiles = (M + TC_M - 1) / TC_M;
   if ((int)blockIdx.x >= tiles) return;  // uniform over the block
@@ -750,13 +754,14 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
   }
   {
     const float* src = reinterpret_cast<const float*>(img + TCI_W3);
-    for (int e = tid; e < 4 * 256 + 2 * 256 + 4; e += 128) W3t[e] = src[e];
+    for (int e = tid; e < 4 * 256 + 2 * 256 + 4; e += TC_THREADS) W3t[e] = src[e];
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *reinterpret_cast<volatile unsigned*>(tmem_slot);
-  const unsigned lane_base = (unsigned)(32 * warp) << 16;  // this warp's TMEM lanes
+  const unsigned lane_base = (unsigned)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+  float(*Yp)[TC_M][4] = reinterpret_cast<float(*)[TC_M][4]>(sm + TS_YP);
 
   // producer / MMA issuer state (thread 0)
   unsigned g_issued = 0, g_used = 0;   // chunks copied, chunks consumed
@@ -789,17 +794,17 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
   int t = blockIdx.x;
   for (; t < tiles; t += gridDim.x) {
     const int r0 = t * TC_M;
-    // X tile: this thread's row, BF16, core-matrix layout (K extent 64)
+    // X tile: this thread's half of its row, BF16, core-matrix layout (K extent 64)
     {
-      const int row = r0 + tid;
+      const int row = r0 + row_t;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 4 * half; q < 4 * half + 4; ++q) {
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         if (row < M) {
           a = *reinterpret_cast<const float4*>(X + (size_t)row * 64 + 8 * q);
           b = *reinterpret_cast<const float4*>(X + (size_t)row * 64 + 8 * q + 4);
         }
-        *reinterpret_cast<uint4*>(sm + TS_X + cm_off(tid, 8 * q, 64)) =
+        *reinterpret_cast<uint4*>(sm + TS_X + cm_off(row_t, 8 * q, 64)) =
             make_uint4(pack_bf2(a.x, a.y), pack_bf2(a.z, a.w), pack_bf2(b.x, b.y), pack_bf2(b.z, b.w));
       }
     }
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
     __syncthreads();
     if (*abort_flag) break;
 #pragma unroll 1
-    for (int cb = 0; cb < 8; ++cb) {
+    for (int cb = 4 * half; cb < 4 * half + 4; ++cb) {
       float v[32];
       tc_ld32(tmem + lane_base + 32 * cb, v);
 #pragma unroll
@@ -834,7 +839,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
         w.y = pack_bf2(fmaxf(v[8 * q + 2] + b1[c + 2], 0.f), fmaxf(v[8 * q + 3] + b1[c + 3], 0.f));
         w.z = pack_bf2(fmaxf(v[8 * q + 4] + b1[c + 4], 0.f), fmaxf(v[8 * q + 5] + b1[c + 5], 0.f));
         w.w = pack_bf2(fmaxf(v[8 * q + 6] + b1[c + 6], 0.f), fmaxf(v[8 * q + 7] + b1[c + 7], 0.f));
-        *reinterpret_cast<uint4*>(sm + TS_H + cm_off(tid, c, 256)) = w;
+        *reinterpret_cast<uint4*>(sm + TS_H + cm_off(row_t, c, 256)) = w;
       }
     }
     fence_proxy_async();
@@ -857,9 +862,9 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
     tc_fence_after();
     __syncthreads();
     if (*abort_flag) break;
-    float y[4] = {b3[0], b3[1], b3[2], b3[3]};
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
-    for (int cb = 0; cb < 8; ++cb) {
+    for (int cb = 4 * half; cb < 4 * half + 4; ++cb) {
       float v[32];
       tc_ld32(tmem + lane_base + 32 * cb, v);
 #pragma unroll
@@ -870,7 +875,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
         for (int o = 0; o < 4; ++o) y[o] += h * W3t[o * 256 + c];
       }
     }
-    if (r0 + tid < M) *reinterpret_cast<float4*>(Y + (size_t)(r0 + tid) * 4) = make_float4(y[0], y[1], y[2], y[3]);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) Yp[half][row_t][o] = y[o];
+    __syncthreads();
+    if (half == 0 && r0 + row_t < M) {
+      float r[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) r[o] = b3[o] + (Yp[0][row_t][o] + Yp[1][row_t][o]);
+      *reinterpret_cast<float4*>(Y + (size_t)(r0 + row_t) * 4) = make_float4(r[0], r[1], r[2], r[3]);
+    }
     tc_fence_before();
     __syncthreads();  // TMEM, X and H1 are reused by the next tile
     tc_fence_after();
@@ -879,8 +892,8 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const unsigned char* __restri
   if (*abort_flag) {
     // rows this block did not finish are marked NaN
     for (int tt = t; tt < tiles; tt += gridDim.x)
-      if (tt * TC_M + tid < M)
-        *reinterpret_cast<float4*>(Y + (size_t)(tt * TC_M + tid) * 4) = make_float4(NAN, NAN, NAN, NAN);
+      if (half == 0 && tt * TC_M + row_t < M)
+        *reinterpret_cast<float4*>(Y + (size_t)(tt * TC_M + row_t) * 4) = make_float4(NAN, NAN, NAN, NAN);
     if (tid == 0) {
       atomicOr(err, err_bit);
       for (unsigned s = 0; s < 2; ++s) {
@@ -920,7 +933,7 @@ cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigne
   const int tiles = (M + TC_M - 1) / TC_M;
   if (tiles <= 0) return cudaSuccess;
   const int grid = tiles < sms ? tiles : sms;
-  k_mlp_tc<<<grid, 128, TS_BYTES, s>>>(reinterpret_cast<const unsigned char*>(image), X, M, Mdev, Y, err, err_bit);
+  k_mlp_tc<<<grid, TC_THREADS, TS_BYTES, s>>>(reinterpret_cast<const unsigned char*>(image), X, M, Mdev, Y, err, err_bit);
   return cudaGetLastError();
 }
 
