@@ -744,3 +744,284 @@ __device__ __forceinline__ void field_nearest_staged2(const float4* s0, int n0, 
 
 }  // namespace cdev
 }  // namespace mi
+
+
+namespace mi {
+namespace cdev {
+
+// ---------------------------------------------------------------------------
+// Staged pair solve.  When both particles together have at most NT_CAP balls,
+// their centres in the pair's local frame are formed once per pair into a
+// warp's shared buffer: st[k] = (p_k, s k_k) and rad[k] = sqrt k_k, particle 0
+// first (k < n0).  The core field of the pair at a local point y is then
+// sum_k w_k / |y - p_k|^2 with its gradient and Hessian in the local frame
+// directly, so a Newton iteration accumulates both particles' terms in the
+// same lanes and reduces nine sums once, with no rotation per evaluation.
+// The guesses read the same staged centres; their arithmetic is that of the
+// unstaged versions (ball_local of the same frame), term for term.
+// ---------------------------------------------------------------------------
+constexpr int NT_CAP = 2 * PG_CAP;
+
+__device__ __forceinline__ bool stage_pair(const Frame& F0, const Frame& F1, const float4* __restrict__ balls, int lane,
+                                           float4* st, float* rad) {
+  if (F0.n + F1.n > NT_CAP) return false;
+  for (int b = lane; b < F0.n; b += 32) {
+    const float4 c = __ldg(balls + F0.off + b);
+    float p[3];
+    ball_local(F0, c, p);
+    st[b] = make_float4(p[0], p[1], p[2], F0.s * c.w);
+    rad[b] = sqrtf(c.w);
+  }
+  for (int b = lane; b < F1.n; b += 32) {
+    const float4 c = __ldg(balls + F1.off + b);
+    float p[3];
+    ball_local(F1, c, p);
+    st[F0.n + b] = make_float4(p[0], p[1], p[2], F1.s * c.w);
+    rad[F0.n + b] = sqrtf(c.w);
+  }
+  __syncwarp();
+  return true;
+}
+
+// Warp sum of eight values per lane, each total broadcast to every lane:
+// three halving exchanges leave lane l with the partial sum of value
+// 4 b4 + 2 b3 + b2 (b = bits of l) over the eight lanes that share l's low
+// two bits; two butterflies finish it and the totals are read from lanes
+// 0, 4, ..., 28.  Seventeen shuffles instead of forty-eight.
+__device__ __forceinline__ void wsum8(float v[8], int lane) {
+  const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4;
+  float w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float keep = u4 ? v[j + 4] : v[j], send = u4 ? v[j] : v[j + 4];
+    w[j] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+  float x[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float keep = u3 ? w[j + 2] : w[j], send = u3 ? w[j] : w[j + 2];
+    x[j] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  float z;
+  {
+    const float keep = u2 ? x[1] : x[0], send = u2 ? x[0] : x[1];
+    z = keep + __shfl_xor_sync(FULL, send, 4);
+  }
+  z += __shfl_xor_sync(FULL, z, 2);
+  z += __shfl_xor_sync(FULL, z, 1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(FULL, z, 4 * j);
+}
+
+// Newton-Raphson on grad(g0 + g1) = 0 from the staged balls, over all n of
+// them or over the listed subsets (l0: indices of particle 0's balls, l1 of
+// particle 1's, offset by n0 in st).  Step, stopping rule, status and
+// iteration count as in newton_pair.
+__device__ __forceinline__ int newton_staged(const float4* st, int n, int lane, float y[3], float tol, int max_it,
+                                             int& iters, const unsigned short* l0 = nullptr, int m0 = 0,
+                                             const unsigned short* l1 = nullptr, int m1 = 0, int n0 = 0) {
+  int status = 1;
+  const int cnt = l0 ? m0 + m1 : n;
+  for (iters = 1; iters <= max_it; ++iters) {
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // grad (3), Hessian xx xy xz yy yz
+    float h5 = 0.f;                                          // Hessian zz
+    for (int u = lane; u < cnt; u += 32) {
+      const int k = l0 ? (u < m0 ? (int)l0[u] : n0 + (int)l1[u - m0]) : u;
+      const float4 q = st[k];
+      const float d0 = y[0] - q.x, d1 = y[1] - q.y, d2 = y[2] - q.z;
+      const float ir2 = 1.0f / (d0 * d0 + d1 * d1 + d2 * d2);
+      const float t = q.w * ir2;              // w / r^2
+      const float t2 = -2.0f * t * ir2;       // -2 w / r^4
+      const float t3 = 8.0f * t * ir2 * ir2;  // 8 w / r^6
+      v[0] += t2 * d0;
+      v[1] += t2 * d1;
+      v[2] += t2 * d2;
+      v[3] += t3 * d0 * d0 + t2;
+      v[4] += t3 * d0 * d1;
+      v[5] += t3 * d0 * d2;
+      v[6] += t3 * d1 * d1 + t2;
+      v[7] += t3 * d1 * d2;
+      h5 += t3 * d2 * d2 + t2;
+    }
+    wsum8(v, lane);
+    h5 = wsum(h5);
+    float A[3][3] = {{v[3], v[4], v[5]}, {v[4], v[6], v[7]}, {v[5], v[7], h5}};
+    float b[3] = {v[0], v[1], v[2]};
+    float dx[3];
+    if (!solve<3>(A, b, dx)) { status = 2; break; }
+    for (int c = 0; c < 3; ++c) y[c] -= dx[c];
+    if (sqrtf(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]) <= tol) { status = 0; break; }
+  }
+  if (iters > max_it) iters = max_it;
+  return status;
+}
+
+// Core values and gradients of each particle at y from the staged balls (the
+// final evaluation of a pair solve: status, projections, normal).
+__device__ __forceinline__ void final_staged(const float4* st, int n0, int n, int lane, const float y[3], float& g0,
+                                             float gr0[3], float& g1, float gr1[3]) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = lane; k < n; k += 32) {
+    const float4 q = st[k];
+    const float d0 = y[0] - q.x, d1 = y[1] - q.y, d2 = y[2] - q.z;
+    const float ir2 = 1.0f / (d0 * d0 + d1 * d1 + d2 * d2);
+    const float t = q.w * ir2, t2 = -2.0f * t * ir2;
+    if (k < n0) {
+      a[0] += t; a[1] += t2 * d0; a[2] += t2 * d1; a[3] += t2 * d2;
+    } else {
+      a[4] += t; a[5] += t2 * d0; a[6] += t2 * d1; a[7] += t2 * d2;
+    }
+  }
+  wsum8(a, lane);
+  g0 = a[0];
+  g1 = a[4];
+  for (int c = 0; c < 3; ++c) {
+    gr0[c] = a[1 + c];
+    gr1[c] = a[5 + c];
+  }
+}
+
+// sphere_midpoint of staged balls a (particle 0) and b (particle 1).
+__device__ __forceinline__ void sphere_midpoint_staged(const float4* st, const float* rad, int n0, int a, int b,
+                                                       float y[3]) {
+  const float4 qa = st[a], qb = st[n0 + b];
+  const float pa[3] = {qa.x, qa.y, qa.z}, pb[3] = {qb.x, qb.y, qb.z};
+  float u[3];
+  for (int c = 0; c < 3; ++c) u[c] = pb[c] - pa[c];
+  const float D = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (D > 0.f) for (int c = 0; c < 3; ++c) u[c] /= D;
+  else { u[0] = 1.f; u[1] = u[2] = 0.f; }
+  const float ra = rad[a], rb = rad[n0 + b];
+  for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
+}
+
+// plain_guess from the staged balls.
+__device__ __forceinline__ void plain_staged(const float4* st, const float* rad, int n0, int n1, int lane, float y[3]) {
+  float best = 3.4e38f;
+  int ba = 0, bb = 0;
+  for (int a = lane; a < n0; a += 32) {
+    const float4 pa = st[a];
+    const float ra = rad[a];
+    for (int b = 0; b < n1; ++b) {
+      const float4 q = st[n0 + b];
+      const float gap = sqrtf((pa.x - q.x) * (pa.x - q.x) + (pa.y - q.y) * (pa.y - q.y) + (pa.z - q.z) * (pa.z - q.z)) -
+                        ra - rad[n0 + b];
+      if (gap < best) { best = gap; ba = a; bb = b; }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float g2 = __shfl_xor_sync(FULL, best, o);
+    const int a2 = __shfl_xor_sync(FULL, ba, o), b2 = __shfl_xor_sync(FULL, bb, o);
+    if (g2 < best || (g2 == best && (a2 < ba || (a2 == ba && b2 < bb)))) { best = g2; ba = a2; bb = b2; }
+  }
+  ba = __shfl_sync(FULL, ba, 0);
+  bb = __shfl_sync(FULL, bb, 0);
+  sphere_midpoint_staged(st, rad, n0, ba, bb, y);
+}
+
+// active_subset over the staged balls st[base, base + n).
+__device__ __forceinline__ int active_staged(const float4* st, int base, int n, const float y[3], float r, int lane,
+                                             unsigned short* list) {
+  int cnt = 0;
+  const float r2 = r * r;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int b = b0 + lane;
+    bool in = false;
+    if (b < n) {
+      const float4 p = st[base + b];
+      const float d2 = (p.x - y[0]) * (p.x - y[0]) + (p.y - y[1]) * (p.y - y[1]) + (p.z - y[2]) * (p.z - y[2]);
+      in = d2 <= r2;
+    }
+    const unsigned m = __ballot_sync(FULL, in);
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    if (in && pos < SUB_CAP) list[pos] = (unsigned short)b;
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  return cnt;
+}
+
+// A pair's solver state: the frames, and (when the pair fits) its staged
+// balls; every piece of the solve goes through the staged path when it can
+// and through the unstaged warp evaluation otherwise.
+struct PairSolver {
+  const Frame& F0;
+  const Frame& F1;
+  const float4* __restrict__ balls;
+  float4* st;
+  float* rad;
+  int lane;
+  bool staged;
+
+  __device__ __forceinline__ PairSolver(const Frame& f0, const Frame& f1, const float4* __restrict__ b, float4* s,
+                                        float* r, int ln)
+      : F0(f0), F1(f1), balls(b), st(s), rad(r), lane(ln) {
+    staged = stage_pair(F0, F1, balls, lane, st, rad);
+  }
+  __device__ __forceinline__ int nballs() const { return F0.n + F1.n; }
+  __device__ __forceinline__ void plain(float y[3]) const {
+    if (staged) plain_staged(st, rad, F0.n, F1.n, lane, y);
+    else plain_guess(F0, F1, balls, lane, y, st);
+  }
+  __device__ __forceinline__ int newton(float y[3], float tol, int max_it, int& iters) const {
+    return staged ? newton_staged(st, F0.n + F1.n, lane, y, tol, max_it, iters)
+                  : newton_pair(F0, F1, balls, lane, y, tol, max_it, iters);
+  }
+  // plain start, then Newton to the contact tolerance
+  __device__ __forceinline__ int plain_newton(float y[3], float tol, int& iters) const {
+    plain(y);
+    return newton(y, tol, MAX_IT, iters);
+  }
+  __device__ __forceinline__ void final_eval(const float y[3], float& g0, float gr0[3], float& g1, float gr1[3]) const {
+    if (staged) {
+      final_staged(st, F0.n, F0.n + F1.n, lane, y, g0, gr0, g1, gr1);
+    } else {
+      const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
+      g0 = e0.g;
+      g1 = e1.g;
+      for (int c = 0; c < 3; ++c) {
+        gr0[c] = e0.gr[c];
+        gr1[c] = e1.gr[c];
+      }
+    }
+  }
+  // learned_newton through the staged path (same stages, gates and fallback)
+  __device__ __forceinline__ int learned(const float a[3], const float d[4], float L, float Rb, unsigned short* l0,
+                                         unsigned short* l1, float y[3], SolveCount& sc) const {
+    if (!staged) return learned_newton(F0, F1, balls, lane, a, d, L, Rb, l0, l1, y, sc, st);
+    const int n0 = F0.n, n1 = F1.n;
+    sc.iters = sc.evals = sc.fallback = 0;
+    for (int c = 0; c < 3; ++c) y[c] = L * (a[c] + d[c]);
+    bool ok = isfinite(y[0]) && isfinite(y[1]) && isfinite(y[2]);
+    if (ok) {
+      const float r_act = L * expf(fminf(fmaxf(d[3], -8.f), 2.f));
+      const int m0 = active_staged(st, 0, n0, y, r_act, lane, l0);
+      const int m1 = active_staged(st, n0, n1, y, r_act, lane, l1);
+      if (m0 > 0 && m1 > 0 && m0 <= SUB_CAP && m1 <= SUB_CAP && 2 * (m0 + m1) <= n0 + n1) {
+        float ys[3] = {y[0], y[1], y[2]};
+        int it = 0;
+        const int s = newton_staged(st, n0 + n1, lane, ys, SUB_TOL * Rb, SUB_IT, it, l0, m0, l1, m1, n0);
+        sc.iters += it;
+        sc.evals += it * (m0 + m1);
+        if (s == 0)
+          for (int c = 0; c < 3; ++c) y[c] = ys[c];
+      }
+      int it = 0;
+      const int s = newton_staged(st, n0 + n1, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
+      sc.iters += it;
+      sc.evals += it * (n0 + n1);
+      ok = s == 0;
+    }
+    if (ok) return 0;
+    sc.fallback = 1;
+    plain_staged(st, rad, n0, n1, lane, y);
+    int it = 0;
+    const int s = newton_staged(st, n0 + n1, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
+    sc.iters += it;
+    sc.evals += it * (n0 + n1);
+    return s;
+  }
+};
+
+}  // namespace cdev
+}  // namespace mi

@@ -172,7 +172,8 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
 // Persistent warp-per-candidate Newton solver and forces.
 __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
   __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
-  __shared__ float4 stage[4][PG_CAP];             // the plain guess's staged spheres, per warp
+  __shared__ float4 stage[4][NT_CAP];              // the pair's staged balls, per warp
+  __shared__ float rad[4][NT_CAP];
   const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
   const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
   const long long substep = *L.substep;
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       Frame F0, F1;
       pair_frames(Pi, Pj, L.qf[i], L.qf[j], h, F0, F1);
       const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
+      const PairSolver S(F0, F1, balls, stage[warp_in_block], rad[warp_in_block], lane);
       float y[3];
       const int lo = min(i, j), hi = max(i, j);
       HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
@@ -206,11 +208,10 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       if (have_warm) {
         // warm start: the pair's closest point of the previous substep (x - O = (x - X_i) - h)
         for (int c = 0; c < 3; ++c) y[c] = hp->xm_rel[c] - h[c];
-        status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
+        status = S.newton(y, NEWTON_TOL * Rb, MAX_IT, iters);
         if (status != 0) {  // the plain start decides
           int more = 0;
-          plain_guess(F0, F1, balls, lane, y, stage[warp_in_block]);
-          status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, more);
+          status = S.plain_newton(y, NEWTON_TOL * Rb, more);
           iters += more;
         }
       } else if (L.learned) {
@@ -219,15 +220,14 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         const float* pr = L.pred + (size_t)it * 4;
         const float a[3] = {x[11], x[12], x[13]}, d[4] = {pr[0], pr[1], pr[2], pr[3]};
         SolveCount sc;
-        status = learned_newton(F0, F1, balls, lane, a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc,
-                                stage[warp_in_block]);
+        status = S.learned(a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc);
         iters = sc.iters;
       } else {
         // plain start: closest pair of control-point spheres, midpoint of their surface points
-        plain_guess(F0, F1, balls, lane, y, stage[warp_in_block]);
-        status = newton_pair(F0, F1, balls, lane, y, NEWTON_TOL * Rb, MAX_IT, iters);
+        status = S.plain_newton(y, NEWTON_TOL * Rb, iters);
       }
-      const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
+      GEval e0, e1;
+      S.final_eval(y, e0.g, e0.gr, e1.g, e1.gr);
       if (status == 0) {
         if (e0.g >= 1.f || e1.g >= 1.f) status = 3;
         else if (e0.g < C_TOL || e1.g < C_TOL) status = 4;

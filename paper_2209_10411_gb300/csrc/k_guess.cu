@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
 __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
   __shared__ float sh[WARPS][64];
   __shared__ unsigned short sub[WARPS][2][SUB_CAP];
-  __shared__ float4 stage[WARPS][2][PG_CAP];
+  __shared__ float4 stage[WARPS][NT_CAP];
+  __shared__ float rad[WARPS][NT_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int p = blockIdx.x * WARPS + w; p < S.n; p += gridDim.x * WARPS) {
     const int i = S.ij[2 * p], j = S.ij[2 * p + 1];
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
     const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
     float ya[3] = {0.f, 0.f, 0.f}, y[3];
     if (S.flags & MI_PAIR_FEATURES) {
-      pair_features_staged(Pi, Pj, h, q0, q1, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya, stage[w][0],
-                           stage[w][1]);
+      pair_features_staged(Pi, Pj, h, q0, q1, F0, F1, S.balls, lane, sh[w], S.X + (size_t)64 * p, ya, stage[w],
+                           stage[w] + PG_CAP);
     } else if (S.flags & MI_PAIR_LEARNED) {
       for (int c = 0; c < 3; ++c) ya[c] = Rb * S.X[(size_t)64 * p + 11 + c];
     } else {
@@ -71,18 +72,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
     }
     int status = -1;
     SolveCount sc = {0, 0, 0};
+    if (!(S.flags & (MI_PAIR_LEARNED | MI_PAIR_PLAIN))) continue;  // features only
+    __syncwarp();  // the features' use of the buffer is over
+    const PairSolver PS(F0, F1, S.balls, stage[w], rad[w], lane);
     if (S.flags & MI_PAIR_LEARNED) {
       const float a[3] = {ya[0] / Rb, ya[1] / Rb, ya[2] / Rb};
       const float* pr = S.pred + (size_t)4 * p;
       const float d[4] = {pr[0], pr[1], pr[2], pr[3]};
-      status = learned_newton(F0, F1, S.balls, lane, a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc, stage[w][0]);
-    } else if (S.flags & MI_PAIR_PLAIN) {
-      plain_guess(F0, F1, S.balls, lane, y, stage[w][0]);
-      status = newton_pair(F0, F1, S.balls, lane, y, NEWTON_TOL * Rb, MAX_IT, sc.iters);
+      status = PS.learned(a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc);
+    } else {
+      status = PS.plain_newton(y, NEWTON_TOL * Rb, sc.iters);
       sc.evals = sc.iters * (F0.n + F1.n);
     }
-    if (status < 0) continue;  // features only
-    const GEval e0 = eval(F0, S.balls, y, lane), e1 = eval(F1, S.balls, y, lane);
+    GEval e0, e1;
+    PS.final_eval(y, e0.g, e0.gr, e1.g, e1.gr);
     if (status == 0) {
       if (e0.g >= 1.f || e1.g >= 1.f) status = 3;
       else if (e0.g < C_TOL || e1.g < C_TOL) status = 4;
