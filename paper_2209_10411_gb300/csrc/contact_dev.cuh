@@ -126,21 +126,23 @@ __device__ __forceinline__ GEval eval(const Frame& F, const float4* __restrict__
 }
 
 // Gaussian elimination with partial pivoting (n <= 4); false if singular.
+// The pivot search swaps row i with each later row whose entry in column i
+// is larger in magnitude than the current pivot: the pivot chosen is the
+// first largest, and every index is a compile-time constant, so the system
+// stays in registers.
 template <int N>
 __device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    int p = i;
-    float best = fabsf(A[i][i]);
 #pragma unroll
-    for (int r = i + 1; r < N; ++r)
-      if (fabsf(A[r][i]) > best) { best = fabsf(A[r][i]); p = r; }
-    if (!(best > 0.f)) return false;
-    if (p != i) {
+    for (int r = i + 1; r < N; ++r) {
+      if (fabsf(A[r][i]) > fabsf(A[i][i])) {
 #pragma unroll
-      for (int c = 0; c < N; ++c) { const float t = A[i][c]; A[i][c] = A[p][c]; A[p][c] = t; }
-      const float t = b[i]; b[i] = b[p]; b[p] = t;
+        for (int c = i; c < N; ++c) { const float t = A[i][c]; A[i][c] = A[r][c]; A[r][c] = t; }
+        const float t = b[i]; b[i] = b[r]; b[r] = t;
+      }
     }
+    if (!(fabsf(A[i][i]) > 0.f)) return false;
 #pragma unroll
     for (int r = i + 1; r < N; ++r) {
       const float m = A[r][i] / A[i][i];

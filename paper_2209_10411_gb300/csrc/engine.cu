@@ -265,8 +265,9 @@ mi_status mi_delbm::ensure_contact_buffers() {
   bp_pos = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
   bp_quat = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
   bp_lo = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(ncap, 1));
+  bp_vel = (float4*)dalloc(sizeof(float4) * (size_t)std::max<long long>(2 * ncap, 1));
   if (!item_i || !item_j || !recs || !hist_pair || !hist_wall || !work || !substep || !bp_pos || !bp_quat ||
-      !bp_lo)
+      !bp_lo || !bp_vel)
     return fail(MI_ENOMEM, "contacts: device allocation failed");
   cudaError_t e = cudaMemsetAsync(hist_pair, 0, sizeof(HistEntry) * (size_t)std::max<long long>(tri, 1), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(hist_wall, 0, sizeof(HistEntry) * (size_t)(6 * ncap), stream);
@@ -315,6 +316,8 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.pf = h->bp_pos;
   L.qf = h->bp_quat;
   L.plo = h->bp_lo;
+  L.vw = h->bp_vel;
+  L.cf = {(float)L.cp.kn, (float)L.cp.kt, (float)L.cp.eta_n, (float)L.cp.eta_t, (float)L.cp.mu_s, (float)L.cp.dt};
   L.learned = h->learned ? 1 : 0;
   L.warm = h->warm ? 1 : 0;
   L.feat = h->guess_feat;

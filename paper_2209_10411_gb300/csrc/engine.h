@@ -76,6 +76,7 @@ struct mi_delbm {
   float4* bp_pos = nullptr;           // FP32 positions and radii of the broad phase
   float4* bp_quat = nullptr;          // FP32 unit quaternions of the substep
   float4* bp_lo = nullptr;            // FP32 position remainders of the substep
+  float4* bp_vel = nullptr;           // FP32 velocities and angular velocities of the substep (2 per particle)
   // learned contact guess (MI_GUESS_LEARNED): parameters and per-item buffers
   bool learned = false;
   bool warm = false;                 // MI_GUESS_WARM

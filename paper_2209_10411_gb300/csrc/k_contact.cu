@@ -10,8 +10,9 @@
 // branches), and the 3x3 (4x4 for walls) Newton system is solved redundantly
 // in every lane.  Work is taken from an atomic counter (no inter-block waits);
 // a warp leaves when the queue is empty.  Geometry is FP32 in a local frame
-// centred between the particles; forces are FP64, summed per particle in
-// 2^-40 fixed point (order-free).
+// centred between the particles; the spring-dashpot forces are FP32 from
+// velocities staged per substep, summed per particle in 2^-40 fixed point
+// (order-free); the tangential spring is stored in FP64.
 #include "contact_dev.cuh"
 
 namespace mi {
@@ -19,46 +20,52 @@ namespace mi {
 namespace {
 using namespace cdev;
 
-__device__ __forceinline__ void add_fixed6(long long* acc, int p, const double v[6]) {
+__device__ __forceinline__ void add_fixed6(long long* acc, int p, const float v[6]) {
   for (int k = 0; k < 6; ++k)
-    atomicAdd(reinterpret_cast<unsigned long long*>(acc + 6 * p + k), (unsigned long long)__double2ll_rn(v[k] * FIX_SCALE));
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc + 6 * p + k),
+              (unsigned long long)__float2ll_rn(v[k] * (float)FIX_SCALE));
 }
 
-// Spring-dashpot force on particle i (the partner j is a particle, or a wall at rest when Pj == nullptr).
-__device__ void spring_dashpot(const ContactParams& cp, const DevParticle& Pi, const DevParticle* Pj, const double xcp[3],
-                               const double n[3], double delta, HistEntry* h, long long substep, double f[3]) {
-  double v0[3], v1[3] = {0, 0, 0};
-  const double ri[3] = {xcp[0] - Pi.pos[0], xcp[1] - Pi.pos[1], xcp[2] - Pi.pos[2]};
-  v0[0] = Pi.vel[0] + Pi.omega[1] * ri[2] - Pi.omega[2] * ri[1];
-  v0[1] = Pi.vel[1] + Pi.omega[2] * ri[0] - Pi.omega[0] * ri[2];
-  v0[2] = Pi.vel[2] + Pi.omega[0] * ri[1] - Pi.omega[1] * ri[0];
-  if (Pj) {
-    const double rj[3] = {xcp[0] - Pj->pos[0], xcp[1] - Pj->pos[1], xcp[2] - Pj->pos[2]};
-    v1[0] = Pj->vel[0] + Pj->omega[1] * rj[2] - Pj->omega[2] * rj[1];
-    v1[1] = Pj->vel[1] + Pj->omega[2] * rj[0] - Pj->omega[0] * rj[2];
-    v1[2] = Pj->vel[2] + Pj->omega[0] * rj[1] - Pj->omega[1] * rj[0];
-  }
-  double vr[3], vt[3];
+// Velocity of the material point at offset r from the origin of a particle
+// whose staged (v, omega) are vw[0], vw[1]: v + omega x r.
+__device__ __forceinline__ void point_velocity(const float4* vw, const float r[3], float v[3]) {
+  const float4 a = vw[0], w = vw[1];
+  v[0] = a.x + w.y * r[2] - w.z * r[1];
+  v[1] = a.y + w.z * r[0] - w.x * r[2];
+  v[2] = a.z + w.x * r[1] - w.y * r[0];
+}
+
+// Spring-dashpot force on particle i at the contact point x_c = X_i + ri
+// (the partner j at x_c = X_j + rj, or a wall at rest when vwj == nullptr):
+// normal n (from i towards j), overlap delta.  FP32; the tangential spring
+// of the history entry is FP64 in memory.
+__device__ void spring_dashpot(const DashF& c, const float4* vwi, const float4* vwj, const float ri[3],
+                               const float rj[3], const float n[3], float delta, HistEntry* h, long long substep,
+                               float f[3]) {
+  float v0[3], v1[3] = {0.f, 0.f, 0.f};
+  point_velocity(vwi, ri, v0);
+  if (vwj) point_velocity(vwj, rj, v1);
+  float vr[3], vt[3];
   for (int a = 0; a < 3; ++a) vr[a] = v1[a] - v0[a];
-  const double vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
+  const float vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
   for (int a = 0; a < 3; ++a) vt[a] = vr[a] - vn * n[a];
-  const double Fn = fmax(0.0, cp.kn * delta + cp.eta_n * vn);
-  double xi[3] = {0, 0, 0};
+  const float Fn = fmaxf(0.f, c.kn * delta + c.eta_n * vn);
+  float xi[3] = {0.f, 0.f, 0.f};
   if (h->stamp == substep - 1)
-    for (int a = 0; a < 3; ++a) xi[a] = h->xi[a];
-  const double xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
-  for (int a = 0; a < 3; ++a) xi[a] = xi[a] - xn * n[a] + vt[a] * cp.dt;
-  double Ft[3];
-  for (int a = 0; a < 3; ++a) Ft[a] = cp.kt * xi[a] + cp.eta_t * vt[a];
-  const double nt = sqrt(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
-  if (nt > cp.mu_s * Fn) {
-    if (nt > 0.0)
-      for (int a = 0; a < 3; ++a) Ft[a] *= cp.mu_s * Fn / nt;
-    for (int a = 0; a < 3; ++a) xi[a] = cp.kt > 0.0 ? (Ft[a] - cp.eta_t * vt[a]) / cp.kt : 0.0;
+    for (int a = 0; a < 3; ++a) xi[a] = (float)h->xi[a];
+  const float xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
+  for (int a = 0; a < 3; ++a) xi[a] = xi[a] - xn * n[a] + vt[a] * c.dt;
+  float Ft[3];
+  for (int a = 0; a < 3; ++a) Ft[a] = c.kt * xi[a] + c.eta_t * vt[a];
+  const float nt = sqrtf(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+  if (nt > c.mu_s * Fn) {
+    if (nt > 0.f)
+      for (int a = 0; a < 3; ++a) Ft[a] *= c.mu_s * Fn / nt;
+    for (int a = 0; a < 3; ++a) xi[a] = c.kt > 0.f ? (Ft[a] - c.eta_t * vt[a]) / c.kt : 0.f;
   }
   for (int a = 0; a < 3; ++a) {
     f[a] = Fn * n[a] + Ft[a];
-    h->xi[a] = xi[a];
+    h->xi[a] = (double)xi[a];
   }
   h->stamp = substep;
 }
@@ -81,6 +88,8 @@ __global__ void k_dem_prologue(ContactLaunch L) {
     L.pf[k] = make_float4(hx, hy, hz, P.Rb_f);
     L.plo[k] = make_float4((float)(P.pos[0] - hx), (float)(P.pos[1] - hy), (float)(P.pos[2] - hz), 0.f);
     L.qf[k] = unit_quat_f32(P.quat);
+    L.vw[2 * k] = make_float4((float)P.vel[0], (float)P.vel[1], (float)P.vel[2], 0.f);
+    L.vw[2 * k + 1] = make_float4((float)P.omega[0], (float)P.omega[1], (float)P.omega[2], 0.f);
   }
 }
 
@@ -253,25 +262,14 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
         hp->xm_stamp = substep;
       }
       if (lane == 0 && status == 0 && dl > 0.f) {
-        double xcp[3], nrm[3], f[3];
-        for (int c = 0; c < 3; ++c) {
-          xcp[c] = Pi.pos[c] + (double)rel[c];
-          nrm[c] = (double)nf[c];
-        }
-        spring_dashpot(L.cp, Pi, &Pj, xcp, nrm, (double)dl, hp, substep, f);
-        double vi[6], vj[6];
-        const double ri[3] = {(double)rel[0], (double)rel[1], (double)rel[2]};
-        const double rj[3] = {xcp[0] - Pj.pos[0], xcp[1] - Pj.pos[1], xcp[2] - Pj.pos[2]};
-        for (int a = 0; a < 3; ++a) {
-          vi[a] = f[a];
-          vj[a] = -f[a];
-        }
-        vi[3] = ri[1] * f[2] - ri[2] * f[1];
-        vi[4] = ri[2] * f[0] - ri[0] * f[2];
-        vi[5] = ri[0] * f[1] - ri[1] * f[0];
-        vj[3] = -(rj[1] * f[2] - rj[2] * f[1]);
-        vj[4] = -(rj[2] * f[0] - rj[0] * f[2]);
-        vj[5] = -(rj[0] * f[1] - rj[1] * f[0]);
+        // x_c - X_j = (x_c - X_i) - (X_j - X_i) = rel - 2 h
+        const float rj[3] = {rel[0] - 2.f * h[0], rel[1] - 2.f * h[1], rel[2] - 2.f * h[2]};
+        float f[3];
+        spring_dashpot(L.cf, L.vw + 2 * i, L.vw + 2 * j, rel, rj, nf, dl, hp, substep, f);
+        const float vi[6] = {f[0], f[1], f[2], rel[1] * f[2] - rel[2] * f[1], rel[2] * f[0] - rel[0] * f[2],
+                             rel[0] * f[1] - rel[1] * f[0]};
+        const float vj[6] = {-f[0], -f[1], -f[2], -(rj[1] * f[2] - rj[2] * f[1]), -(rj[2] * f[0] - rj[0] * f[2]),
+                             -(rj[0] * f[1] - rj[1] * f[0])};
         add_fixed6(L.fcacc, i, vi);
         add_fixed6(L.fcacc, j, vj);
         atomicAdd(&L.ctr->n_contacts, 1u);
@@ -332,15 +330,10 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       }
       if (lane == 0 && status == 0 && dl > 0.f) {
         HistEntry* hp = L.hist_wall + ((long long)i * 6 + face);
-        double xcp[3], nrm[3], f[3];
-        for (int c = 0; c < 3; ++c) {
-          xcp[c] = Pi.pos[c] + (double)rel[c];
-          nrm[c] = (double)nw[c];
-        }
-        spring_dashpot(L.cp, Pi, nullptr, xcp, nrm, (double)dl, hp, substep, f);
-        const double ri[3] = {(double)rel[0], (double)rel[1], (double)rel[2]};
-        double vi[6] = {f[0], f[1], f[2], ri[1] * f[2] - ri[2] * f[1], ri[2] * f[0] - ri[0] * f[2],
-                        ri[0] * f[1] - ri[1] * f[0]};
+        float f[3];
+        spring_dashpot(L.cf, L.vw + 2 * i, nullptr, rel, nullptr, nw, dl, hp, substep, f);
+        const float vi[6] = {f[0], f[1], f[2], rel[1] * f[2] - rel[2] * f[1], rel[2] * f[0] - rel[0] * f[2],
+                             rel[0] * f[1] - rel[1] * f[0]};
         add_fixed6(L.fcacc, i, vi);
         atomicAdd(&L.ctr->n_contacts, 1u);
       }

@@ -283,6 +283,9 @@ struct ContactParams {
   int periodic[3];
   int n[3];               // lattice sizes (walls at -1/2 and n - 1/2)
 };
+struct DashF {            // FP32 copy of the spring-dashpot parameters of ContactParams
+  float kn, kt, eta_n, eta_t, mu_s, dt;
+};
 struct ContactLaunch {
   DevParticle* P;
   int np, ncap;           // particles, capacity used to index the pair-history triangle
@@ -302,6 +305,8 @@ struct ContactLaunch {
   float4* pf;             // np FP32 (position rounded to FP32, R_b) of the substep
   float4* plo;            // np FP32 remainders (position - pf.xyz) of the substep
   float4* qf;             // np FP32 unit quaternions (w, x, y, z) of the substep
+  float4* vw;             // 2 np FP32 (velocity, 0), (angular velocity, 0) of the substep
+  DashF cf;               // FP32 spring-dashpot parameters
   int learned;            // 1: pair items start from the learned guess (feat, pred), else the plain guess
   int warm;               // 1: pair items start from the previous substep's closest point when it exists
   float* feat;            // cap_items x 64 features of the pair items (learned)
