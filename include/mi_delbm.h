@@ -480,7 +480,10 @@ enum {
   MI_PAIR_PLAIN = 2,     /* solve from the plain guess                          */
   MI_PAIR_LEARNED = 4,   /* solve from the learned start (pred; X holds the
                             features, computed now when MI_PAIR_FEATURES is set) */
-  MI_PAIR_LABELS = 8     /* write the training targets of converged pairs to T  */
+  MI_PAIR_LABELS = 8,    /* write the training targets of converged pairs to T  */
+  MI_PAIR_GUESS_ONLY = 16 /* with PLAIN: stop at the plain guess (Sec. 2.3.1's
+                            starting point): xm = that point, iters = evals = 0,
+                            status 0; no LABELS                                 */
 };
 
 /* Closest points of n explicitly posed pairs of the handle's particle shapes,

@@ -133,7 +133,7 @@ _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_set_schedule", c_int, _P, c_int)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
-PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS = 1, 2, 4, 8
+PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
 
 
 def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):

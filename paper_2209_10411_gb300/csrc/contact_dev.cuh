@@ -897,14 +897,93 @@ __device__ __forceinline__ void sphere_midpoint_staged(const float4* st, const f
   for (int c = 0; c < 3; ++c) y[c] = 0.5f * ((pa[c] + ra * u[c]) + (pb[c] - rb * u[c]));
 }
 
-// plain_guess from the staged balls.
-__device__ __forceinline__ void plain_staged(const float4* st, const float* rad, int n0, int n1, int lane, float y[3]) {
+// plain_guess from the staged balls, with the search pruned so that its
+// result is unchanged.  With c0, c1 the particle origins and R0, R1 the radii
+// about them that hold every sphere of the particle, the triangle inequality
+// bounds the gap of any pair from below by |p_a - c1| - R1 - r_a (and by
+// |p_b - c0| - R0 - r_b).  The gap of the pair formed by each particle's
+// sphere reaching closest to the other's origin is an upper bound ub on the
+// smallest gap; balls whose bound exceeds ub (plus a margin far above FP32
+// rounding of these sums) cannot take part in a pair that reaches the minimum
+// or ties with it, so the O(n0 n1) search runs over the surviving balls only,
+// in the same ascending order (cand: NT_CAP indices of scratch).
+__device__ __forceinline__ void plain_staged(const float4* st, const float* rad, int n0, int n1, int lane,
+                                             const float c0[3], const float c1[3], unsigned short* cand, float y[3]) {
+  // radii about the origins, and each particle's sphere reaching closest to the other's origin
+  float R0 = 0.f, R1 = 0.f, ra_best = 3.4e38f, rb_best = 3.4e38f;
+  int sa = 0x7fffffff, sb = 0x7fffffff;
+  for (int a = lane; a < n0; a += 32) {
+    const float4 p = st[a];
+    const float r = rad[a];
+    R0 = fmaxf(R0, sqrtf((p.x - c0[0]) * (p.x - c0[0]) + (p.y - c0[1]) * (p.y - c0[1]) + (p.z - c0[2]) * (p.z - c0[2])) + r);
+    const float g = sqrtf((p.x - c1[0]) * (p.x - c1[0]) + (p.y - c1[1]) * (p.y - c1[1]) + (p.z - c1[2]) * (p.z - c1[2])) - r;
+    if (g < ra_best) { ra_best = g; sa = a; }
+  }
+  for (int b = lane; b < n1; b += 32) {
+    const float4 p = st[n0 + b];
+    const float r = rad[n0 + b];
+    R1 = fmaxf(R1, sqrtf((p.x - c1[0]) * (p.x - c1[0]) + (p.y - c1[1]) * (p.y - c1[1]) + (p.z - c1[2]) * (p.z - c1[2])) + r);
+    const float g = sqrtf((p.x - c0[0]) * (p.x - c0[0]) + (p.y - c0[1]) * (p.y - c0[1]) + (p.z - c0[2]) * (p.z - c0[2])) - r;
+    if (g < rb_best) { rb_best = g; sb = b; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    R0 = fmaxf(R0, __shfl_xor_sync(FULL, R0, o));
+    R1 = fmaxf(R1, __shfl_xor_sync(FULL, R1, o));
+    const float g2 = __shfl_xor_sync(FULL, ra_best, o);
+    const int a2 = __shfl_xor_sync(FULL, sa, o);
+    if (g2 < ra_best || (g2 == ra_best && a2 < sa)) { ra_best = g2; sa = a2; }
+    const float h2 = __shfl_xor_sync(FULL, rb_best, o);
+    const int b2 = __shfl_xor_sync(FULL, sb, o);
+    if (h2 < rb_best || (h2 == rb_best && b2 < sb)) { rb_best = h2; sb = b2; }
+  }
+  R0 = __shfl_sync(FULL, R0, 0);
+  R1 = __shfl_sync(FULL, R1, 0);
+  sa = __shfl_sync(FULL, sa, 0);
+  sb = __shfl_sync(FULL, sb, 0);
+  float ub = 3.4e38f;
+  if (sa < n0 && sb < n1) {
+    const float4 pa = st[sa], q = st[n0 + sb];
+    ub = sqrtf((pa.x - q.x) * (pa.x - q.x) + (pa.y - q.y) * (pa.y - q.y) + (pa.z - q.z) * (pa.z - q.z)) - rad[sa] -
+         rad[n0 + sb];
+  }
+  const float dc = sqrtf((c0[0] - c1[0]) * (c0[0] - c1[0]) + (c0[1] - c1[1]) * (c0[1] - c1[1]) +
+                         (c0[2] - c1[2]) * (c0[2] - c1[2]));
+  const float lim = ub + 1e-5f * (R0 + R1 + dc);
+  // survivors, ascending: particle 0's in cand[0, ma), particle 1's in cand[ma, ma + mb)
+  int ma = 0, mb = 0;
+  for (int base = 0; base < n0; base += 32) {
+    const int a = base + lane;
+    bool in = false;
+    if (a < n0) {
+      const float4 p = st[a];
+      in = sqrtf((p.x - c1[0]) * (p.x - c1[0]) + (p.y - c1[1]) * (p.y - c1[1]) + (p.z - c1[2]) * (p.z - c1[2])) - R1 -
+               rad[a] <= lim;
+    }
+    const unsigned m = __ballot_sync(FULL, in);
+    if (in) cand[ma + __popc(m & ((1u << lane) - 1u))] = (unsigned short)a;
+    ma += __popc(m);
+  }
+  for (int base = 0; base < n1; base += 32) {
+    const int b = base + lane;
+    bool in = false;
+    if (b < n1) {
+      const float4 p = st[n0 + b];
+      in = sqrtf((p.x - c0[0]) * (p.x - c0[0]) + (p.y - c0[1]) * (p.y - c0[1]) + (p.z - c0[2]) * (p.z - c0[2])) - R0 -
+               rad[n0 + b] <= lim;
+    }
+    const unsigned m = __ballot_sync(FULL, in);
+    if (in) cand[ma + mb + __popc(m & ((1u << lane) - 1u))] = (unsigned short)b;
+    mb += __popc(m);
+  }
+  __syncwarp();
   float best = 3.4e38f;
   int ba = 0, bb = 0;
-  for (int a = lane; a < n0; a += 32) {
+  for (int u = lane; u < ma; u += 32) {
+    const int a = cand[u];
     const float4 pa = st[a];
     const float ra = rad[a];
-    for (int b = 0; b < n1; ++b) {
+    for (int v = 0; v < mb; ++v) {
+      const int b = cand[ma + v];
       const float4 q = st[n0 + b];
       const float gap = sqrtf((pa.x - q.x) * (pa.x - q.x) + (pa.y - q.y) * (pa.y - q.y) + (pa.z - q.z) * (pa.z - q.z)) -
                         ra - rad[n0 + b];
@@ -952,17 +1031,18 @@ struct PairSolver {
   const float4* __restrict__ balls;
   float4* st;
   float* rad;
+  unsigned short* cand;  // NT_CAP indices of scratch (the plain guess's survivors)
   int lane;
   bool staged;
 
   __device__ __forceinline__ PairSolver(const Frame& f0, const Frame& f1, const float4* __restrict__ b, float4* s,
-                                        float* r, int ln)
-      : F0(f0), F1(f1), balls(b), st(s), rad(r), lane(ln) {
+                                        float* r, unsigned short* cd, int ln)
+      : F0(f0), F1(f1), balls(b), st(s), rad(r), cand(cd), lane(ln) {
     staged = stage_pair(F0, F1, balls, lane, st, rad);
   }
   __device__ __forceinline__ int nballs() const { return F0.n + F1.n; }
   __device__ __forceinline__ void plain(float y[3]) const {
-    if (staged) plain_staged(st, rad, F0.n, F1.n, lane, y);
+    if (staged) plain_staged(st, rad, F0.n, F1.n, lane, F0.t, F1.t, cand, y);
     else plain_guess(F0, F1, balls, lane, y, st);
   }
   __device__ __forceinline__ int newton(float y[3], float tol, int max_it, int& iters) const {
@@ -1016,7 +1096,8 @@ struct PairSolver {
     }
     if (ok) return 0;
     sc.fallback = 1;
-    plain_staged(st, rad, n0, n1, lane, y);
+    __syncwarp();  // the subset lists share cand's memory
+    plain_staged(st, rad, n0, n1, lane, F0.t, F1.t, cand, y);
     int it = 0;
     const int s = newton_staged(st, n0 + n1, lane, y, NEWTON_TOL * Rb, MAX_IT, it);
     sc.iters += it;

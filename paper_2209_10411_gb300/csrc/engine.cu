@@ -894,10 +894,12 @@ mi_status mi_delbm_set_guess(mi_delbm* h, int mode, const float* params) {
 mi_status mi_delbm_pair_solve(mi_delbm* h, int n, const int* ij, const double* poses, int flags, const float* pred,
                               float* X, float* T, double* xm, int* iters, int* evals, int* status) {
   if (!h) return MI_EINVAL;
-  const int known = MI_PAIR_FEATURES | MI_PAIR_PLAIN | MI_PAIR_LEARNED | MI_PAIR_LABELS;
+  const int known = MI_PAIR_FEATURES | MI_PAIR_PLAIN | MI_PAIR_LEARNED | MI_PAIR_LABELS | MI_PAIR_GUESS_ONLY;
   const bool plain = flags & MI_PAIR_PLAIN, lrn = flags & MI_PAIR_LEARNED;
   if (n < 0 || (flags & ~known) || (plain && lrn) || flags == 0)
     return h->fail(MI_EINVAL, "pair_solve: n < 0, unknown flags, or both PLAIN and LEARNED");
+  if ((flags & MI_PAIR_GUESS_ONLY) && (!plain || (flags & MI_PAIR_LABELS)))
+    return h->fail(MI_EINVAL, "pair_solve: GUESS_ONLY needs PLAIN and excludes LABELS");
   if ((flags & MI_PAIR_LABELS) && !plain && !lrn) return h->fail(MI_EINVAL, "pair_solve: LABELS needs a solve");
   if (n == 0) return MI_OK;
   if (!ij || !poses || ((flags & (MI_PAIR_FEATURES | MI_PAIR_LEARNED)) && !X) || (lrn && !pred) ||

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
       Frame F0, F1;
       pair_frames(Pi, Pj, L.qf[i], L.qf[j], h, F0, F1);
       const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
-      const PairSolver S(F0, F1, balls, stage[warp_in_block], rad[warp_in_block], lane);
+      const PairSolver S(F0, F1, balls, stage[warp_in_block], rad[warp_in_block], &sub[warp_in_block][0][0], lane);
       float y[3];
       const int lo = min(i, j), hi = max(i, j);
       HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));

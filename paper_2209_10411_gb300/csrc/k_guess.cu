@@ -74,12 +74,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_solve(PairSolveLaunch S) {
     SolveCount sc = {0, 0, 0};
     if (!(S.flags & (MI_PAIR_LEARNED | MI_PAIR_PLAIN))) continue;  // features only
     __syncwarp();  // the features' use of the buffer is over
-    const PairSolver PS(F0, F1, S.balls, stage[w], rad[w], lane);
+    const PairSolver PS(F0, F1, S.balls, stage[w], rad[w], &sub[w][0][0], lane);
     if (S.flags & MI_PAIR_LEARNED) {
       const float a[3] = {ya[0] / Rb, ya[1] / Rb, ya[2] / Rb};
       const float* pr = S.pred + (size_t)4 * p;
       const float d[4] = {pr[0], pr[1], pr[2], pr[3]};
       status = PS.learned(a, d, Rb, Rb, sub[w][0], sub[w][1], y, sc);
+    } else if (S.flags & MI_PAIR_GUESS_ONLY) {
+      PS.plain(y);
+      if (lane == 0) {
+        for (int c = 0; c < 3; ++c) S.xm[(size_t)3 * p + c] = O[c] + (double)y[c];
+        S.iters[p] = 0;
+        S.evals[p] = 0;
+        S.status[p] = 0;
+      }
+      continue;
     } else {
       status = PS.plain_newton(y, NEWTON_TOL * Rb, sc.iters);
       sc.evals = sc.iters * (F0.n + F1.n);

@@ -228,3 +228,68 @@ def test_step_contacts_learned_equal_plain(trained):
     assert n_ok > 0
     scale = np.abs(fp["F_contact"]).max()
     assert np.abs(fp["F_contact"] - fl["F_contact"]).max() <= 1e-4 * scale + 1e-9
+
+
+def _guess_candidates(Pi, Pj, tol):
+    """All sphere pairs whose surface gap is within tol of the smallest (the
+    oracle's search, vectorised) and the midpoint each one gives."""
+    c0, c1 = contact.world_centers(Pi), contact.world_centers(Pj)
+    r0, r1 = np.sqrt(Pi["k"]), np.sqrt(Pj["k"])
+    gap = np.linalg.norm(c0[:, None, :] - c1[None, :, :], axis=2) - r0[:, None] - r1[None, :]
+    out = []
+    for a, b in zip(*np.nonzero(gap <= gap.min() + tol)):
+        u = c1[b] - c0[a]
+        u = u / np.linalg.norm(u)
+        out.append(0.5 * ((c0[a] + r0[a] * u) + (c1[b] - r1[b] * u)))
+    return out
+
+
+@pytest.mark.parametrize("n_range,npairs", [((4, 128), 64), ((100, 200), 24)])
+def test_plain_guess_matches_oracle(n_range, npairs):
+    """The plain starting point (closest pair of control-point spheres, the
+    midpoint of their surface points) of the GPU's pruned search over staged
+    balls (n_i + n_j <= 256) and of its unstaged search (larger pairs)
+    against the oracle's full search: the same point within FP32 rounding,
+    or, where the oracle's smallest gaps tie within 1e-5 of the size, the
+    point of one of the tied pairs."""
+    B = binding()
+    import torch
+    from paper_2209_10411_gb300 import guess
+    shapes = guess.bed_shapes(31, 10, n_range=n_range)
+    sim = _sim_with(B, shapes)
+    ij, poses = guess.pair_poses(32, shapes, npairs, spacing=(0.7, 1.2))
+    dij, dposes = guess.to_device(ij, poses)
+    out = sim.pair_solve(dij, dposes, B.PAIR_PLAIN | B.PAIR_GUESS_ONLY)
+    torch.cuda.synchronize()
+    xm, st, it = out["xm"].cpu().numpy(), out["status"].cpu().numpy(), out["iters"].cpu().numpy()
+    sim.close()
+    assert (st == 0).all() and (it == 0).all()
+    staged = 0
+    for p, (a, b) in enumerate(ij):
+        Pi, Pj = _oracle_particle(shapes[a], poses[p, :7]), _oracle_particle(shapes[b], poses[p, 7:])
+        size = 2 * max(contact.bounding_radius(Pi["centers"], Pi["k"]), contact.bounding_radius(Pj["centers"], Pj["k"]))
+        ref = contact.pair_guess(Pi, Pj) if p < 8 else None
+        cands = _guess_candidates(Pi, Pj, 1e-5 * size)
+        if ref is not None:  # the vectorised search is the oracle's
+            assert min(np.linalg.norm(c - ref) for c in cands) <= 1e-9 * size
+        err = min(np.linalg.norm(xm[p] - c) for c in cands) / size
+        assert err <= 2e-6, (p, err)
+        staged += len(shapes[a]["k"]) + len(shapes[b]["k"]) <= 256
+    if n_range[1] <= 128:
+        assert staged == len(ij)
+    else:
+        assert 0 < staged < len(ij)
+
+
+def test_guess_only_flag_rejected_without_plain():
+    B = binding()
+    import torch
+    from paper_2209_10411_gb300 import guess
+    shapes = guess.bed_shapes(31, 2)
+    sim = _sim_with(B, shapes)
+    dij, dposes = guess.to_device(*guess.pair_poses(1, shapes, 2))
+    with pytest.raises(RuntimeError):
+        sim.pair_solve(dij, dposes, B.PAIR_GUESS_ONLY)
+    with pytest.raises(RuntimeError):
+        sim.pair_solve(dij, dposes, B.PAIR_PLAIN | B.PAIR_GUESS_ONLY | B.PAIR_LABELS)
+    sim.close()
