@@ -22,6 +22,20 @@ __device__ __forceinline__ float wsum(float v) {
   return __shfl_sync(FULL, v, 0);
 }
 
+// Order-preserving map of a float onto an unsigned key (-0 and +0 equal).
+__device__ __forceinline__ unsigned fkey(float f) {
+  const unsigned u = __float_as_uint(f + 0.0f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Warp argmin: the smallest i among the lanes holding the smallest v (two
+// integer warp reductions); the same in every lane.
+__device__ __forceinline__ unsigned warp_argmin(float v, unsigned i) {
+  const unsigned k = fkey(v);
+  const unsigned m = __reduce_min_sync(FULL, k);
+  return __reduce_min_sync(FULL, k == m ? i : 0xffffffffu);
+}
+
 
 // A particle seen from a local origin O: body point x_b = R^T y + o for local y.
 struct Frame {
@@ -591,6 +605,19 @@ __device__ __forceinline__ void pair_features_staged(const DevParticle& Pi, cons
   }
   float g0, g1;
   field_nearest_staged2(s0, F0.n, F0.s, s1, F1.n, F1.s, ya, iL, lane, sh + 20, sh + 44, g0, g1);
+  // the six logarithms, one per lane 0-5, written by their lanes
+  {
+    float arg = 1.f, scale = 1.f;
+    int slot = 0;
+    if (lane == 0) { arg = g0; slot = 14; }
+    else if (lane == 1) { arg = g1; slot = 15; }
+    else if (lane == 2) { arg = (float)F0.n; slot = 16; scale = 0.2f; }
+    else if (lane == 3) { arg = (float)F1.n; slot = 40; scale = 0.2f; }
+    else if (lane == 4) { arg = Pi.re_f * iL; slot = 17; scale = 2.0f; }
+    else if (lane == 5) { arg = Pj.re_f * iL; slot = 41; scale = 2.0f; }
+    const float lg = logf(arg);
+    if (lane < 6) sh[slot] = lane >= 2 && lane < 4 ? lg / 5.0f : scale * lg;
+  }
   if (lane == 0) {
     for (int c = 0; c < 3; ++c) sh[c] = 2.0f * h[c] * iL;
     for (int side = 0; side < 2; ++side) {
@@ -602,17 +629,10 @@ __device__ __forceinline__ void pair_features_staged(const DevParticle& Pi, cons
       sh[6 + 4 * side] = sg * q.w;
     }
     for (int c = 0; c < 3; ++c) sh[11 + c] = ya[c] * iL;
-    sh[14] = logf(g0);
-    sh[15] = logf(g1);
-    for (int side = 0; side < 2; ++side) {
-      const Frame& F = side ? F1 : F0;
-      const DevParticle& P = side ? Pj : Pi;
-      const int off = side ? 40 : 16;
-      sh[off] = logf((float)F.n) / 5.0f;
-      sh[off + 1] = 2.0f * logf(P.re_f * iL);
-      sh[off + 2] = P.Rb_f * iL;
-      sh[off + 3] = P.skin_f * iL;
-    }
+    sh[18] = Pi.Rb_f * iL;
+    sh[19] = Pi.skin_f * iL;
+    sh[42] = Pj.Rb_f * iL;
+    sh[43] = Pj.skin_f * iL;
   }
   __syncwarp();
   out[lane] = sh[lane];
@@ -630,15 +650,8 @@ namespace cdev {
 // field_nearest_staged calls): the two independent reductions of every step
 // are interleaved, which halves the dependent shuffle latency per pair.
 __device__ __forceinline__ void argmin2(float& b0, int& i0, float& b1, int& i1) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float g0 = __shfl_xor_sync(FULL, b0, o), g1 = __shfl_xor_sync(FULL, b1, o);
-    const int j0 = __shfl_xor_sync(FULL, i0, o), j1 = __shfl_xor_sync(FULL, i1, o);
-    if (g0 < b0 || (g0 == b0 && j0 < i0)) { b0 = g0; i0 = j0; }
-    if (g1 < b1 || (g1 == b1 && j1 < i1)) { b1 = g1; i1 = j1; }
-  }
-  i0 = __shfl_sync(FULL, i0, 0);
-  i1 = __shfl_sync(FULL, i1, 0);
+  i0 = (int)warp_argmin(b0, (unsigned)i0);
+  i1 = (int)warp_argmin(b1, (unsigned)i1);
 }
 
 __device__ __forceinline__ void reaching_staged2(const float4* s0, int n0, const float t0[3], const float4* s1, int n1,
@@ -713,13 +726,13 @@ __device__ __forceinline__ void field_nearest_staged2(const float4* s0, int n0, 
       const float4 q = s0[k];
       const float d2 = (q.x - y[0]) * (q.x - y[0]) + (q.y - y[1]) * (q.y - y[1]) + (q.z - y[2]) * (q.z - y[2]);
       a0 += q.w / d2;
-      topk_insert(kd0, kb0, sqrtf(d2), k);
+      topk_insert(kd0, kb0, d2, k);  // squared distances order the same
     }
     if (k < n1) {
       const float4 q = s1[k];
       const float d2 = (q.x - y[0]) * (q.x - y[0]) + (q.y - y[1]) * (q.y - y[1]) + (q.z - y[2]) * (q.z - y[2]);
       a1 += q.w / d2;
-      topk_insert(kd1, kb1, sqrtf(d2), k);
+      topk_insert(kd1, kb1, d2, k);
     }
   }
 #pragma unroll
@@ -926,20 +939,11 @@ __device__ __forceinline__ void plain_staged(const float4* st, const float* rad,
     const float g = sqrtf((p.x - c0[0]) * (p.x - c0[0]) + (p.y - c0[1]) * (p.y - c0[1]) + (p.z - c0[2]) * (p.z - c0[2])) - r;
     if (g < rb_best) { rb_best = g; sb = b; }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    R0 = fmaxf(R0, __shfl_xor_sync(FULL, R0, o));
-    R1 = fmaxf(R1, __shfl_xor_sync(FULL, R1, o));
-    const float g2 = __shfl_xor_sync(FULL, ra_best, o);
-    const int a2 = __shfl_xor_sync(FULL, sa, o);
-    if (g2 < ra_best || (g2 == ra_best && a2 < sa)) { ra_best = g2; sa = a2; }
-    const float h2 = __shfl_xor_sync(FULL, rb_best, o);
-    const int b2 = __shfl_xor_sync(FULL, sb, o);
-    if (h2 < rb_best || (h2 == rb_best && b2 < sb)) { rb_best = h2; sb = b2; }
-  }
-  R0 = __shfl_sync(FULL, R0, 0);
-  R1 = __shfl_sync(FULL, R1, 0);
-  sa = __shfl_sync(FULL, sa, 0);
-  sb = __shfl_sync(FULL, sb, 0);
+  // non-negative floats order as their bit patterns
+  R0 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(R0)));
+  R1 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(R1)));
+  sa = (int)warp_argmin(ra_best, (unsigned)sa);
+  sb = (int)warp_argmin(rb_best, (unsigned)sb);
   float ub = 3.4e38f;
   if (sa < n0 && sb < n1) {
     const float4 pa = st[sa], q = st[n0 + sb];
@@ -990,14 +994,9 @@ __device__ __forceinline__ void plain_staged(const float4* st, const float* rad,
       if (gap < best) { best = gap; ba = a; bb = b; }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float g2 = __shfl_xor_sync(FULL, best, o);
-    const int a2 = __shfl_xor_sync(FULL, ba, o), b2 = __shfl_xor_sync(FULL, bb, o);
-    if (g2 < best || (g2 == best && (a2 < ba || (a2 == ba && b2 < bb)))) { best = g2; ba = a2; bb = b2; }
-  }
-  ba = __shfl_sync(FULL, ba, 0);
-  bb = __shfl_sync(FULL, bb, 0);
-  sphere_midpoint_staged(st, rad, n0, ba, bb, y);
+  // smallest gap, ties to the lower (a, b): a, b < 256 here
+  const unsigned ab = warp_argmin(best, ((unsigned)ba << 16) | (unsigned)bb);
+  sphere_midpoint_staged(st, rad, n0, (int)(ab >> 16), (int)(ab & 0xffffu), y);
 }
 
 // active_subset over the staged balls st[base, base + n).
