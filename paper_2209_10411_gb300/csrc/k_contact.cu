@@ -179,7 +179,7 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
 }
 
 // Persistent warp-per-candidate Newton solver and forces.
-__global__ void __launch_bounds__(128) k_contacts(ContactLaunch L) {
+__global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
   __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
   __shared__ float4 stage[4][NT_CAP];              // the pair's staged balls, per warp
   __shared__ float rad[4][NT_CAP];

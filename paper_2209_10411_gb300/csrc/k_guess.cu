@@ -13,7 +13,7 @@ constexpr int WARPS = 4;
 
 // Features of every particle-pair candidate of the substep (rows of wall
 // candidates are left alone: walls always start from the plain guess).
-__global__ void __launch_bounds__(WARPS * 32) k_item_features(ContactLaunch L) {
+__global__ void __launch_bounds__(WARPS * 32, 6) k_item_features(ContactLaunch L) {
   __shared__ float sh[WARPS][64];
   __shared__ float4 stage[WARPS][2][PG_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
