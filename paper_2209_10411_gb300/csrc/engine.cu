@@ -1018,7 +1018,7 @@ static bool read_cached(const char* path, const std::string& key, TuneChoice& t)
     int bx = 0, bl = 0, rows = 0, pairs = -1;
     if (grab("bulk_block_x", bx) && grab("list_blocks_per_sm", bl) && grab("bulk_rows", rows) &&
         grab("bulk_pairs", pairs) && bx > 0 && bx <= 256 && bx % 32 == 0 && bl > 0 && bl <= 64 &&
-        (rows == 1 || rows == 2) && (pairs >= 0 && pairs <= 2)) {
+        (rows == 1 || rows == 2) && (pairs >= 0 && pairs <= 3)) {
       t.bulk_block_x = bx;
       t.list_blocks_per_sm = bl;
       t.bulk_rows = rows;

@@ -94,6 +94,36 @@ def test_bulk_16bit_deviation_storage(storage, shape, variant):
     assert np.all(err <= ulp16(ref, storage) + 1e-7), "max err %g" % err.max()
 
 
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("shape,periodic,force", [((64, 6, 5), (True, True, False), (1e-5, -2e-5, 3e-5)),
+                                                  ((40, 5, 7), (True, False, True), None),
+                                                  ((48, 7, 4), (False, True, True), (0.0, 1e-5, 0.0)),
+                                                  ((32, 4, 4), (True, True, True), None)])
+@pytest.mark.parametrize("variant", [5, 6])
+def test_bulk_16bit_periodic_and_forced(storage, shape, periodic, force, variant):
+    """The four-node kernel with periodic x faces (the wrapped word), periodic
+    or wall y / z faces, moving walls and Guo forcing, two steps against the
+    oracle fed the decoded inputs of each step."""
+    B = binding()
+    wv = np.zeros((6, 3))
+    wv[0] = (0.0, 0.01, -0.02)
+    wv[5] = (0.02, -0.01, 0.0)
+    f0 = _initial(shape, seed=33, amp=0.02)
+    bx, rows, pairs = VARIANTS[variant]
+    with B.Simulation(*shape, tau=TAU, periodic=periodic, wall_velocity=wv, storage=storage,
+                      fluid_body_force=force or (0, 0, 0)) as sim:
+        sim.set_tuning(bx, rows, pairs, 8)
+        sim.set_populations(f0)
+        for _ in range(2):
+            h0 = decode(sim.get_raw_populations(), storage)
+            sim.step(1)
+            h1 = decode(sim.get_raw_populations(), storage)
+            fin = h0 + W.reshape(19, 1, 1, 1)
+            ref = lbm.step_bulk(fin, TAU, periodic=periodic, wall_velocity=wv, force=force) - W.reshape(19, 1, 1, 1)
+            err = np.abs(h1 - ref)
+            assert np.all(err <= ulp16(ref, storage) + 1e-7), "max err %g" % err.max()
+
+
 def test_rest_state_and_mass_conservation():
     B = binding()
     shape = (64, 24, 20)
