@@ -227,3 +227,31 @@ def test_mass_properties_quadrature_matches_oracle():
     R = metaball.quat_to_matrix(q)
     assert np.allclose(st["pos"], X + R @ mp["centroid"], atol=1e-9)
     sim.close()
+
+
+@pytest.mark.parametrize("omega", [(0.01, -0.004, 0.002), (0.3, -0.2, 0.1), (0.0, 0.0, 0.0)])
+def test_integrate_rotation_small_and_large_angles(omega):
+    """The rigid-body update alone (no hydrodynamic or contact force): the
+    half rotation angle |omega| dt / 2 below 1/64 takes the series branch,
+    above it the library sin/cos; orientation, angular velocity and position
+    against the oracle's update."""
+    B = binding()
+    rng = np.random.default_rng(21)
+    c, k, _ = scenes.blob_4(rng)
+    spec = scenes.ParticleSpec(c, k, 2.5, 1.0, None, None)
+    P = _prepared(spec, np.array([16.0, 15.5, 17.25]), scenes.random_unit_quaternion(rng), (0.01, -0.02, 0.005),
+                  omega)
+    g = (0.0, 0.0, -1e-4)
+    with B.Simulation(32, 32, 32, tau=TAU, gravity=g) as sim:
+        sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"], P["omega"],
+                         mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
+        state = dict(P)
+        for _ in range(3):
+            sim.step_phases(B.PHASE_INTEGRATE)
+            state = dem.integrate(state, np.zeros(3), np.zeros(3), g)
+        st = sim.get_particle_state(0)
+    assert np.abs(np.abs(st["quat"] @ state["quat"]) - 1.0) < 1e-14
+    assert np.linalg.norm(st["quat"] - state["quat"]) < 1e-13
+    assert np.linalg.norm(st["omega"] - state["omega"]) <= 1e-13 * max(np.linalg.norm(omega), 1.0)
+    assert np.linalg.norm(st["pos"] - state["pos"]) < 1e-12
+    assert np.linalg.norm(st["vel"] - state["vel"]) < 1e-15
