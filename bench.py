@@ -168,11 +168,11 @@ CONFIG = {}
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def build_sim(B, scene, storage, stream):
+def build_sim(B, scene, storage, stream, dem_substeps=1):
     nx, ny, nz = scene.shape
     sim = B.Simulation(nx, ny, nz, tau=scene.tau, gravity=scene.gravity, storage=storage, stream=stream,
                        max_particles=max(16, len(scene.particles)),
-                       max_balls=max(65536, sum(len(p.k) for p in scene.particles)))
+                       max_balls=max(65536, sum(len(p.k) for p in scene.particles)), dem_substeps=dem_substeps)
     for p in scene.particles:
         sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat, p.vel, p.omega)
     return sim
@@ -332,6 +332,31 @@ def storage_variant(B, scene, storage, steps, stream_obj):
             "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bytes_per_node": BYTES_PER_NODE[storage], "tuning": tuning}
 
 
+def dem_ratio(B, scene, storage, steps, stream_obj, nsub=100):
+    """The coupled step at the paper's ratio of DEM substeps per LBM step
+    (contacts re-detected and particles advanced every substep): MLUPS with
+    the fused substep kernel and with one launch sequence per substep."""
+    import torch
+    out = {"dem_substeps": nsub}
+    for name, unfused in (("fused", False), ("per_substep_launches", True)):
+        sim = build_sim(B, scene, storage, stream_obj.cuda_stream, dem_substeps=nsub)
+        sim.set_schedule(unfused_dem=unfused)
+        for _ in range(5):
+            sim.step(1)
+        sim.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream_obj)
+        for _ in range(steps):
+            sim.step(1)
+        ev1.record(stream_obj)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        sim.close()
+        nx, ny, nz = scene.shape
+        out[name] = {"value": nx * ny * nz / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms}
+    return out
+
+
 def run_mine(args):
     import torch
     from paper_2209_10411_gb300 import replicas
@@ -409,6 +434,7 @@ def run_mine(args):
     if storage == 0 and not args.no_variants and rank == 0:
         variants = {name: storage_variant(B, scene, st, max(50, min(args.steps, 200)), stream)
                     for name, st in (("f16-dev", 1), ("bf16-dev", 2))}
+        variants["dem_100_substeps"] = dem_ratio(B, scene, storage, 30, stream)
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node

@@ -363,13 +363,23 @@ mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
  * returned through the non-NULL pointers. */
 mi_status mi_delbm_autotune(mi_delbm *h, const char *cache_path, int *bulk_block_x, int *list_blocks_per_sm);
 
-/* Step schedule.  overlap_boundary != 0: the boundary nodes (interpolated
- * bounce-back, momentum exchange, collision) are computed on the particle
- * side stream while the bulk kernel runs, into a side buffer, and copied into
- * the new populations after the bulk and near kernels (the results are the
- * same bits as the default order, in which they are computed after those
- * kernels).  Applies to steps that run all phases.  Discards captured graphs. */
-mi_status mi_delbm_set_schedule(mi_delbm *h, int overlap_boundary);
+/* Step schedule flags. */
+enum {
+  /* the boundary nodes (interpolated bounce-back, momentum exchange,
+   * collision) are computed on the particle side stream while the bulk kernel
+   * runs, into a side buffer, and copied into the new populations after the
+   * bulk and near kernels (the same bits as the default order, in which they
+   * are computed after those kernels); steps that run all phases */
+  MI_SCHEDULE_OVERLAP_BOUNDARY = 1,
+  /* run the DEM substeps (dem_substeps > 1) as separate launches per
+   * substep.  By default, with at most 64 particles and the plain or warm
+   * start, one kernel runs all substeps of a step in one CTA (the same bits:
+   * the same per-item and per-particle device code, no launch per substep) */
+  MI_SCHEDULE_UNFUSED_DEM = 2
+};
+/* Set the step schedule (an OR of MI_SCHEDULE_* flags; 0 = default).
+ * Discards captured graphs.  Errors: MI_EINVAL (unknown flags). */
+mi_status mi_delbm_set_schedule(mi_delbm *h, int flags);
 
 /* Set the launch shapes directly (what mi_delbm_autotune chooses): bulk
  * kernel threads per block along x (32..256, a multiple of 32; at most 128

@@ -134,6 +134,7 @@ _sig("mi_delbm_set_schedule", c_int, _P, c_int)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
+SCHEDULE_OVERLAP_BOUNDARY, SCHEDULE_UNFUSED_DEM = 1, 2
 
 
 def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):
@@ -384,9 +385,12 @@ class Simulation:
         return {"bulk_block_x": v[0].value, "bulk_rows": v[1].value, "bulk_pairs": v[2].value,
                 "list_blocks_per_sm": v[3].value}
 
-    def set_schedule(self, overlap_boundary):
-        """Compute the boundary nodes beside the bulk kernel (True) or after it."""
-        self._check(lib.mi_delbm_set_schedule(self.h, 1 if overlap_boundary else 0))
+    def set_schedule(self, overlap_boundary=False, unfused_dem=False):
+        """overlap_boundary: compute the boundary nodes beside the bulk kernel
+        (True) or after it; unfused_dem: run DEM substeps as one launch
+        sequence per substep instead of the fused substep kernel."""
+        flags = (SCHEDULE_OVERLAP_BOUNDARY if overlap_boundary else 0) | (SCHEDULE_UNFUSED_DEM if unfused_dem else 0)
+        self._check(lib.mi_delbm_set_schedule(self.h, flags))
 
     def set_graphs(self, on):
         self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))

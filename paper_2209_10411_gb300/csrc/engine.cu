@@ -423,12 +423,32 @@ mi_status mi_delbm::run_phases(unsigned phases) {
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
   if (contact_branch && (s = join_wait(0)) != MI_OK) return s;
   if (phases & (MI_PHASE_CONTACT | MI_PHASE_INTEGRATE)) {
+    // several substeps of a few particles: one fused kernel (plain or warm start)
+    const bool fused = (phases & MI_PHASE_CONTACT) && (phases & MI_PHASE_INTEGRATE) && cfg.dem_substeps > 1 &&
+                       n_particles > 0 && n_particles <= FUSED_DEM_MAX_PARTICLES && !learned && !unfused_dem;
+    if (fused) return phase_dem_fused();
     for (int k = 0; k < cfg.dem_substeps; ++k) {
       if (k > 0 && (phases & MI_PHASE_CONTACT) && (s = phase_contact(stream)) != MI_OK) return s;
       if ((phases & MI_PHASE_INTEGRATE) && (s = phase_integrate((phases & MI_PHASE_CONTACT) != 0)) != MI_OK) return s;
     }
   }
   return MI_OK;
+}
+
+mi_status mi_delbm::phase_dem_fused() {
+  mi_status s = ensure_contact_buffers();
+  if (s != MI_OK) return s;
+  ContactLaunch L = contact_launch(this);
+  IntegrateLaunch I;
+  I.P = dP;
+  I.np = n_particles;
+  I.facc = facc;
+  I.fc = fc;
+  for (int a = 0; a < 3; ++a) I.gravity[a] = cfg.gravity[a];
+  I.rho0 = cfg.rho0;
+  I.dt = 1.0 / cfg.dem_substeps;
+  return launch_phase(this, stream, MI_PHASE_INTEGRATE,
+                      [&] { return launch_dem_substeps(L, I, cfg.dem_substeps, stream); });
 }
 
 void mi_delbm::invalidate_graphs() {
@@ -930,10 +950,14 @@ mi_status mi_delbm_pair_solve(mi_delbm* h, int n, const int* ij, const double* p
   return MI_OK;
 }
 
-mi_status mi_delbm_set_schedule(mi_delbm* h, int overlap_boundary) {
+mi_status mi_delbm_set_schedule(mi_delbm* h, int flags) {
   if (!h) return MI_EINVAL;
-  if (h->overlap_boundary != (overlap_boundary != 0)) h->invalidate_graphs();
-  h->overlap_boundary = overlap_boundary != 0;
+  if (flags & ~(MI_SCHEDULE_OVERLAP_BOUNDARY | MI_SCHEDULE_UNFUSED_DEM))
+    return h->fail(MI_EINVAL, "mi_delbm_set_schedule: unknown flags");
+  const bool ob = (flags & MI_SCHEDULE_OVERLAP_BOUNDARY) != 0, ud = (flags & MI_SCHEDULE_UNFUSED_DEM) != 0;
+  if (h->overlap_boundary != ob || h->unfused_dem != ud) h->invalidate_graphs();
+  h->overlap_boundary = ob;
+  h->unfused_dem = ud;
   return MI_OK;
 }
 

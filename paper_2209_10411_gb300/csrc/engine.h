@@ -92,6 +92,7 @@ struct mi_delbm {
   unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
   void* bc_tmp = nullptr;            // 19 stored values per boundary node (overlapped schedule)
   bool overlap_boundary = false;     // boundary nodes computed beside the bulk kernel, scattered after it
+  bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
   int blocks_per_particle = 1;
 
   TuneChoice tune;
@@ -124,6 +125,7 @@ struct mi_delbm {
   mi_status phase_boundary_beside(cudaStream_t st);
   mi_status phase_scatter_boundary();
   mi_status phase_swap();
+  mi_status phase_dem_fused();
   mi_status phase_integrate(bool with_contacts);
   mi_status phase_contact(cudaStream_t st);
   mi_status graph_step();

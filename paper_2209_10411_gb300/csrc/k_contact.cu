@@ -14,6 +14,7 @@
 // velocities staged per substep, summed per particle in 2^-40 fixed point
 // (order-free); the tangential spring is stored in FP64.
 #include "contact_dev.cuh"
+#include "rigid_dev.cuh"
 
 namespace mi {
 
@@ -71,6 +72,19 @@ __device__ void spring_dashpot(const DashF& c, const float4* vwi, const float4* 
 }
 }  // namespace
 
+// Per-substep FP32 staging of particle k: position split as hi + lo (hi = the
+// position rounded to FP32, lo = the remainder rounded), radius, unit
+// quaternion, velocity and angular velocity.
+__device__ __forceinline__ void stage_particle(const ContactLaunch& L, int k) {
+  const DevParticle& P = L.P[k];
+  const float hx = (float)P.pos[0], hy = (float)P.pos[1], hz = (float)P.pos[2];
+  L.pf[k] = make_float4(hx, hy, hz, P.Rb_f);
+  L.plo[k] = make_float4((float)(P.pos[0] - hx), (float)(P.pos[1] - hy), (float)(P.pos[2] - hz), 0.f);
+  L.qf[k] = unit_quat_f32(P.quat);
+  L.vw[2 * k] = make_float4((float)P.vel[0], (float)P.vel[1], (float)P.vel[2], 0.f);
+  L.vw[2 * k + 1] = make_float4((float)P.omega[0], (float)P.omega[1], (float)P.omega[2], 0.f);
+}
+
 // ---------------------------------------------------------------------------
 __global__ void k_dem_prologue(ContactLaunch L) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -80,17 +94,7 @@ __global__ void k_dem_prologue(ContactLaunch L) {
     *L.work = 0;
   }
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * L.np; k += gridDim.x * blockDim.x) L.fcacc[k] = 0;
-  // per-substep FP32 staging: positions split as hi + lo (hi = the position
-  // rounded to FP32, lo = the remainder rounded), radii, unit quaternions
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.np; k += gridDim.x * blockDim.x) {
-    const DevParticle& P = L.P[k];
-    const float hx = (float)P.pos[0], hy = (float)P.pos[1], hz = (float)P.pos[2];
-    L.pf[k] = make_float4(hx, hy, hz, P.Rb_f);
-    L.plo[k] = make_float4((float)(P.pos[0] - hx), (float)(P.pos[1] - hy), (float)(P.pos[2] - hz), 0.f);
-    L.qf[k] = unit_quat_f32(P.quat);
-    L.vw[2 * k] = make_float4((float)P.vel[0], (float)P.vel[1], (float)P.vel[2], 0.f);
-    L.vw[2 * k + 1] = make_float4((float)P.omega[0], (float)P.omega[1], (float)P.omega[2], 0.f);
-  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.np; k += gridDim.x * blockDim.x) stage_particle(L, k);
 }
 
 cudaError_t launch_dem_prologue(const ContactLaunch& L, cudaStream_t s) {
@@ -109,6 +113,33 @@ __device__ __forceinline__ void append_item(const ContactLaunch& L, int i, int j
 }
 
 constexpr int BP_TILE = 64;
+
+// Pair (i, j) with staged (FP32 position, R_b) pa, pb: FP32 filter with an
+// error band, FP64 decision inside it (the decision is the FP64 one).
+__device__ __forceinline__ bool pair_candidate(const ContactLaunch& L, int i, int j, const float4 pa, const float4 pb) {
+  const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+  const float dd = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float thr = pa.w + pb.w + (float)L.cp.margin;
+  const float band = 2.4e-7f * (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z)) +
+                     1e-5f * thr + 1e-6f;
+  if (dd > thr + band) return false;
+  if (dd >= thr - band) {
+    const DevParticle& P = L.P[i];
+    const DevParticle& Q = L.P[j];
+    const double d0 = P.pos[0] - Q.pos[0], d1 = P.pos[1] - Q.pos[1], d2 = P.pos[2] - Q.pos[2];
+    if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) <= P.Rb + Q.Rb + L.cp.margin)) return false;
+  }
+  return true;
+}
+
+// Particle j against the domain wall on face (0..5), FP64.
+__device__ __forceinline__ bool wall_candidate(const ContactLaunch& L, int j, int face) {
+  const int axis = face / 2;
+  if (L.cp.periodic[axis]) return false;
+  const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
+  const double nw = (face & 1) ? -1.0 : 1.0;
+  return nw * (L.P[j].pos[axis] - pw) <= L.P[j].Rb + L.cp.margin;
+}
 
 // Candidates: pairs i < j with |X_i - X_j| <= R_b,i + R_b,j + margin, and
 // particle-wall items with n_w.(X_i - p_w) <= R_b,i + margin, both decided in
@@ -142,30 +173,12 @@ __global__ void __launch_bounds__(128) k_broad_phase(ContactLaunch L, int n_tile
       const int a = e / BP_TILE, c = e % BP_TILE;
       const int i = i0 + a, j = j0 + c;
       if (i >= j || j >= np) continue;
-      const float4 pa = A[a], pb = Bt[c];
-      const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
-      const float dd = sqrtf(dx * dx + dy * dy + dz * dz);
-      const float thr = pa.w + pb.w + (float)L.cp.margin;
-      const float band = 2.4e-7f * (fabsf(pa.x) + fabsf(pa.y) + fabsf(pa.z) + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z)) +
-                         1e-5f * thr + 1e-6f;
-      if (dd > thr + band) continue;
-      if (dd >= thr - band) {
-        const DevParticle& P = L.P[i];
-        const DevParticle& Q = L.P[j];
-        const double d0 = P.pos[0] - Q.pos[0], d1 = P.pos[1] - Q.pos[1], d2 = P.pos[2] - Q.pos[2];
-        if (!(sqrt(d0 * d0 + d1 * d1 + d2 * d2) <= P.Rb + Q.Rb + L.cp.margin)) continue;
-      }
-      append_item(L, i, j);
+      if (pair_candidate(L, i, j, A[a], Bt[c])) append_item(L, i, j);
     }
   } else {
     const int t = (b - n_tiles) * 128 + threadIdx.x;
     if (t >= 6 * np) return;
-    const int j = t / 6, face = t % 6, axis = face / 2;
-    if (L.cp.periodic[axis]) return;
-    const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
-    const double nw = (face & 1) ? -1.0 : 1.0;
-    if (!(nw * (L.P[j].pos[axis] - pw) <= L.P[j].Rb + L.cp.margin)) return;
-    append_item(L, j, -1 - face);
+    if (wall_candidate(L, t / 6, t % 6)) append_item(L, t / 6, -1 - t % 6);
   }
 }
 
@@ -178,20 +191,14 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Persistent warp-per-candidate Newton solver and forces.
-__global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
-  __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
-  __shared__ float4 stage[4][NT_CAP];              // the pair's staged balls, per warp
-  __shared__ float rad[4][NT_CAP];
-  const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
-  const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
-  const long long substep = *L.substep;
+// One candidate item (a particle pair or a particle-wall pair) by one warp:
+// Newton closest point, contact geometry, spring-dashpot force into the
+// fixed-point sums, and the item's record.  sub, stage and rad are the warp's
+// shared scratch (2 x SUB_CAP indices, NT_CAP balls).
+__device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it, long long substep, int lane,
+                                             unsigned short (*sub)[SUB_CAP], float4* stage, float* rad) {
   const float4* balls = L.balls;
-  for (;;) {
-    unsigned it = 0;
-    if (lane == 0) it = atomicAdd(L.work, 1u);
-    it = __shfl_sync(FULL, it, 0);
-    if (it >= n_items) break;
+  {
     const int i = L.item_i[it], j = L.item_j[it];
     const DevParticle& Pi = L.P[i];
     int status = 1, iters = 0;
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
       Frame F0, F1;
       pair_frames(Pi, Pj, L.qf[i], L.qf[j], h, F0, F1);
       const float Rb = fmaxf(Pi.Rb_f, Pj.Rb_f);
-      const PairSolver S(F0, F1, balls, stage[warp_in_block], rad[warp_in_block], &sub[warp_in_block][0][0], lane);
+      const PairSolver S(F0, F1, balls, stage, rad, &sub[0][0], lane);
       float y[3];
       const int lo = min(i, j), hi = max(i, j);
       HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
         const float* pr = L.pred + (size_t)it * 4;
         const float a[3] = {x[11], x[12], x[13]}, d[4] = {pr[0], pr[1], pr[2], pr[3]};
         SolveCount sc;
-        status = S.learned(a, d, Rb, Rb, sub[warp_in_block][0], sub[warp_in_block][1], y, sc);
+        status = S.learned(a, d, Rb, Rb, sub[0], sub[1], y, sc);
         iters = sc.iters;
       } else {
         // plain start: closest pair of control-point spheres, midpoint of their surface points
@@ -354,8 +361,83 @@ __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
   }
 }
 
+// Persistent warp-per-candidate Newton solver and forces.
+__global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
+  __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
+  __shared__ float4 stage[4][NT_CAP];              // the pair's staged balls, per warp
+  __shared__ float rad[4][NT_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned n_items = min(L.ctr->n_pairs, L.cap_items);
+  const long long substep = *L.substep;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(L.work, 1u);
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= n_items) break;
+    contact_item(L, it, substep, lane, sub[w], stage[w], rad[w]);
+  }
+}
+
 cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s) {
   k_contacts<<<L.grid, 128, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The DEM substeps of one LBM step for a handful of particles in one CTA:
+// the first substep's rigid-body update (its contacts ran beside the bulk
+// kernel), then for every further substep the prologue, every pair and wall
+// candidate test, the warp-per-item solves and the rigid-body update, with
+// block barriers between them instead of launches.  The work per item is the
+// per-kernel path's (same device functions), so the results are the same
+// bits.  Counters and force sums that other threads updated with atomics are
+// read past the L1 (__ldcg); everything else is written and read by this
+// block only.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, IntegrateLaunch I, int n_sub) {
+  __shared__ unsigned short sub[4][2][SUB_CAP];
+  __shared__ float4 stage[4][NT_CAP];
+  __shared__ float rad[4][NT_CAP];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int np = L.np;
+  for (int p = t; p < np; p += blockDim.x) integrate_particle(I, p);
+  __syncthreads();
+  const int npairs = np * (np - 1) / 2;
+  for (int k = 1; k < n_sub; ++k) {
+    if (t == 0) {
+      *L.substep += 1;
+      L.ctr->n_pairs = 0;
+      L.ctr->n_contacts = 0;
+    }
+    for (int q = t; q < 6 * np; q += blockDim.x) L.fcacc[q] = 0;
+    for (int q = t; q < np; q += blockDim.x) stage_particle(L, q);
+    __syncthreads();
+    for (int e = t; e < npairs + 6 * np; e += blockDim.x) {
+      if (e < npairs) {
+        // e = j (j - 1) / 2 + i, 0 <= i < j
+        int j = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+        while (j * (j - 1) / 2 > e) --j;
+        while ((j + 1) * j / 2 <= e) ++j;
+        const int i = e - j * (j - 1) / 2;
+        if (pair_candidate(L, i, j, L.pf[i], L.pf[j])) append_item(L, i, j);
+      } else {
+        const int u = e - npairs;
+        if (wall_candidate(L, u / 6, u % 6)) append_item(L, u / 6, -1 - u % 6);
+      }
+    }
+    __syncthreads();
+    const unsigned n_items = min(__ldcg(&L.ctr->n_pairs), L.cap_items);
+    const long long substep = *L.substep;
+    for (unsigned it = w; it < n_items; it += 4) contact_item(L, it, substep, lane, sub[w], stage[w], rad[w]);
+    __syncthreads();
+    for (int p = t; p < np; p += blockDim.x) integrate_particle(I, p);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_dem_substeps(const ContactLaunch& L, const IntegrateLaunch& I, int n_sub, cudaStream_t s) {
+  if (L.np <= 0 || n_sub <= 0) return cudaSuccess;
+  k_dem_substeps<<<1, 128, 0, s>>>(L, I, n_sub);
   return cudaGetLastError();
 }
 

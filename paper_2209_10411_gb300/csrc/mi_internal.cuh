@@ -365,6 +365,11 @@ struct IntegrateLaunch {
   double dt;
 };
 cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s);
+// Fused DEM loop of one LBM step for at most FUSED_DEM_MAX_PARTICLES particles
+// (one CTA): the first substep's rigid-body update, then n_sub - 1 substeps of
+// prologue, candidates, solves and update.  The plain or warm start only.
+constexpr int FUSED_DEM_MAX_PARTICLES = 64;
+cudaError_t launch_dem_substeps(const ContactLaunch& L, const IntegrateLaunch& I, int n_sub, cudaStream_t s);
 
 // Mass properties by midpoint quadrature of f >= 1 on a grid of spacing h over
 // [-Rb, Rb]^3 (body frame); out: [count, sx, sy, sz, sxx, sxy, sxz, syy, syz, szz]

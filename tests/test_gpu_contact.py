@@ -221,3 +221,71 @@ def test_warm_guess_same_contacts_fewer_iterations():
     it_p = np.mean([c["iters"] for c in pairs_p])
     it_w = np.mean([c["iters"] for c in pairs_w])
     assert it_w < it_p, (it_w, it_p)
+
+
+def _dem_snapshot(sim, n):
+    states = [sim.get_particle_state(i) for i in range(n)]
+    key = lambda c: (c["i"], c["j"])
+    recs = sorted(sim.contacts(), key=key)
+    return states, recs, sim.forces()
+
+
+def _assert_same_bits(a, b):
+    (sa, ra, fa), (sb, rb, fb) = a, b
+    for x, y in zip(sa, sb):
+        for f in ("pos", "quat", "vel", "omega"):
+            assert np.array_equal(x[f], y[f]), f
+    assert [(c["i"], c["j"]) for c in ra] == [(c["i"], c["j"]) for c in rb]
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x["x_cp"], y["x_cp"]) and np.array_equal(x["n"], y["n"])
+        assert x["delta"] == y["delta"] and x["iters"] == y["iters"] and x["status"] == y["status"]
+    for f in fa:
+        assert np.array_equal(fa[f], fb[f]), f
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_fused_dem_substeps_equal_per_substep_launches(warm):
+    """The fused substep kernel (one CTA runs every substep of a step) against
+    one launch sequence per substep: the same bits for the particle states,
+    the contact records and the force sums after six steps of eight
+    substeps, with the plain and with the warm start."""
+    B = binding()
+    shape = (48, 48, 40)
+    parts = _cluster(5)
+    parts[1]["vel"] = np.array([-0.05, 0.0, 0.0])
+    parts[3]["vel"] = np.array([0.0, -0.04, 0.01])
+    snaps = []
+    for unfused in (False, True):
+        sim = _sim(B, shape, parts, dem_substeps=8, gravity=(0, 0, -1e-4),
+                   guess_mode=B.GUESS_WARM if warm else B.GUESS_PLAIN)
+        sim.set_schedule(unfused_dem=unfused)
+        for _ in range(6):
+            sim.step_phases(B.PHASE_CONTACT | B.PHASE_INTEGRATE)
+        snaps.append(_dem_snapshot(sim, len(parts)))
+        sim.close()
+    assert any(c["status"] == 0 and c["delta"] > 0 for c in snaps[0][1])
+    _assert_same_bits(*snaps)
+
+
+def test_fused_dem_substeps_in_coupled_steps():
+    """Whole coupled steps (graph replay) of two particles in contact with
+    five DEM substeps per step: fused and per-substep schedules give the same
+    particle states, contacts, forces and populations."""
+    B = binding()
+    shape = (32, 28, 30)
+    parts = [_particle([[-1, 0, 0], [1, 0, 0]], [3, 3], [13.0, 14.0, 14.0], (0.9, 0.1, 0.2, 0.1),
+                       (0.004, 0.0, 0.001), (0.0, 0.002, 0.0)),
+             _particle([[0, 0, 0], [0.8, 0.3, 0]], [4, 2], [17.8, 14.3, 14.2], (0.8, 0.3, 0.1, 0.4),
+                       (-0.003, 0.001, 0.0), (0.001, 0.0, -0.002))]
+    for P in parts:
+        P["quat"] = P["quat"] / np.linalg.norm(P["quat"])
+    snaps, pops = [], []
+    for unfused in (False, True):
+        sim = _sim(B, shape, parts, dem_substeps=5, gravity=(0.0, 0.0, -1e-4))
+        sim.set_schedule(unfused_dem=unfused)
+        sim.step(4)
+        snaps.append(_dem_snapshot(sim, len(parts)))
+        pops.append(sim.get_populations())
+        sim.close()
+    _assert_same_bits(*snaps)
+    assert np.array_equal(pops[0], pops[1])
