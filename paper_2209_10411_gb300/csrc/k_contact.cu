@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, Integrate
   __shared__ float rad[4][NT_CAP];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int np = L.np;
-  for (int p = t; p < np; p += blockDim.x) integrate_particle(I, p);
+  for (int p = w; p < np; p += 4) integrate_particle_lanes(I, p, lane);
   __syncthreads();
   const int npairs = np * (np - 1) / 2;
   for (int k = 1; k < n_sub; ++k) {
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, Integrate
     const long long substep = *L.substep;
     for (unsigned it = w; it < n_items; it += 4) contact_item(L, it, substep, lane, sub[w], stage[w], rad[w]);
     __syncthreads();
-    for (int p = t; p < np; p += blockDim.x) integrate_particle(I, p);
+    for (int p = w; p < np; p += 4) integrate_particle_lanes(I, p, lane);
     __syncthreads();
   }
 }

@@ -426,16 +426,16 @@ cudaError_t launch_links_q(const ParticleLaunch& L, int grid, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Rigid-body update, one thread per particle (rigid_dev.cuh).
+// Rigid-body update, four lanes of a warp per particle (rigid_dev.cuh).
 // ---------------------------------------------------------------------------
 __global__ void k_integrate(IntegrateLaunch L) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < L.np) integrate_particle(L, p);
+  const int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (p < L.np) integrate_particle_lanes(L, p, threadIdx.x & 31);
 }
 
 cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  k_integrate<<<(L.np + 127) / 128, 128, 0, s>>>(L);
+  k_integrate<<<(L.np + 3) / 4, 128, 0, s>>>(L);
   return cudaGetLastError();
 }
 
