@@ -225,3 +225,37 @@ def config5(seed=0, shape=(384, 384, 768), n_particles=3000):
     parts = [ParticleSpec(c, k, 2.5, 1.0, f32(p), random_unit_quaternion(rng), nominal_radius=r)
              for (c, k, r), p in zip(specs, pos)]
     return Scene("C5 384x384x768 3000-particle bed", shape, 0.8, (0.0, 0.0, -1e-5), parts, 100, seed)
+
+
+# ---------------------------------------------------------------------------
+# Point hulls for the Gradient Search refinement (Sec. 2.2): the scanned hulls
+# of the paper are not available; these stand in for them.
+# ---------------------------------------------------------------------------
+def ellipsoid_hull(rng, m, semi, bumps=0.0):
+    """m points on the surface of an ellipsoid with semi-axes semi (a random
+    direction each, radius scaled along it), optionally with a smooth radial
+    modulation 1 + bumps * sin(3 theta) cos(2 phi); float32 values."""
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(u[:, 2], -1.0, 1.0))
+    phi = np.arctan2(u[:, 1], u[:, 0])
+    r = 1.0 + bumps * np.sin(3.0 * theta) * np.cos(2.0 * phi)
+    return f32(u * r[:, None] * np.asarray(semi, dtype=np.float64)[None, :])
+
+
+def hull_planes(H):
+    """Facet planes (nx, ny, nz, d) of the convex hull of the points H:
+    outward unit normals, n . x <= d inside; float32 values."""
+    from scipy.spatial import ConvexHull
+    eq = ConvexHull(np.asarray(H, dtype=np.float64)).equations  # n . x + off <= 0 inside
+    return f32(np.concatenate([eq[:, :3], -eq[:, 3:4]], axis=1))
+
+
+def gs_start_model(rng, n, semi):
+    """A starting model for the refinement: n control points uniform inside
+    the ellipsoid shrunk to half its size, with equal k that make a single
+    coincident ball of the ellipsoid's volume; float32 values."""
+    c = uniform_in_ball(rng, n, 1.0) * 0.5 * np.asarray(semi, dtype=np.float64)[None, :]
+    r_eq = float(np.prod(semi)) ** (1.0 / 3.0)
+    k = np.full(n, r_eq * r_eq / n)
+    return f32(c), f32(k)
