@@ -357,6 +357,82 @@ def dem_ratio(B, scene, storage, steps, stream_obj, nsub=100):
     return out
 
 
+GS_FLOP_PER_PAIR_EPOCH = 27  # field (9) + gradient (18) per (hull point, control point) and epoch
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
+    """Gradient Search refinement (Algorithm 2) of n_fits models of 8-64
+    control points on synthetic bumpy-ellipsoid hulls of m points (the
+    300-particle tank's shape range), two descents of `epochs` epochs: fits/s
+    and FP32 throughput against the FP32 ALU peak; the FP64 oracle on one fit
+    for a few epochs beside it."""
+    import ctypes
+    import time
+    import torch
+    from oracle import gs as ogs
+    rng = np.random.default_rng(seed)
+    hulls, models, planes = [], [], []
+    for _ in range(n_fits):
+        semi = tuple(rng.uniform(8.0, 16.0, 3))
+        H = scenes.ellipsoid_hull(rng, m, semi, bumps=0.15)
+        c, k = scenes.gs_start_model(rng, int(rng.integers(8, 65)), semi)
+        hulls.append(H)
+        models.append(np.concatenate([c, k[:, None]], 1))
+        planes.append(scenes.hull_planes(H))
+    dev = torch.device("cuda")
+    # the generators return float64 arrays of FP32 values: the kernel takes float32
+    H = torch.as_tensor(np.concatenate(hulls).astype(np.float32), device=dev)
+    M0 = torch.as_tensor(np.concatenate(models).astype(np.float32), device=dev)
+    P = torch.as_tensor(np.concatenate(planes).astype(np.float32), device=dev)
+    off = lambda arrs: torch.as_tensor(np.concatenate([[0], np.cumsum([len(a) for a in arrs])]).astype(np.int32),
+                                       device=dev)
+    ho, bo, po = off(hulls), off(models), off(planes)
+    nb = [len(a) for a in models]
+    active = torch.empty(M0.shape[0], dtype=torch.int32, device=dev)
+    loss = torch.empty((n_fits, 2), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    P_ = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def run(M):
+        st = B.lib.mi_gs_fit(n_fits, P_(ho), P_(H), P_(bo), P_(M), P_(po), P_(P), m, max(nb), epochs, 1e-4,
+                             P_(active), P_(loss), ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0, st
+
+    M = M0.clone()
+    run(M)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        M = M0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(M)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    pairs = m * sum(nb)
+    flop = 2 * epochs * pairs * GS_FLOP_PER_PAIR_EPOCH
+    tflops = flop / (ms * 1e-3) / 1e12
+    # oracle: one fit of the same size, a few epochs, scaled to the whole job
+    o_ep = 3
+    t0 = time.perf_counter()
+    ogs.descend(hulls[0].astype(np.float64), models[0][:, :3].astype(np.float64), models[0][:, 3].astype(np.float64),
+                o_ep, 1e-4)
+    o_s = (time.perf_counter() - t0) * (2 * epochs / o_ep) * (sum(nb) / nb[0])
+    ls = loss.cpu().numpy()
+    return {"value": n_fits / (ms * 1e-3), "unit": "fits/s", "ms": ms, "fits": n_fits, "hull_points": m,
+            "control_points": [int(min(nb)), int(max(nb))], "epochs_per_descent": epochs,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP32_ALU_PEAK_TFLOPS,
+                         "flop_per_point_ball_epoch": GS_FLOP_PER_PAIR_EPOCH},
+            "loss_after_second_over_first_descent_median": float(np.median(ls[:, 1] / np.maximum(ls[:, 0], 1e-30))),
+            "cpu_baseline": {"value": n_fits / o_s, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                             "sample": "FP64 numpy oracle: %d epochs of one fit, scaled by epochs and control "
+                                       "points" % o_ep}}
+
+
 def run_mine(args):
     import torch
     from paper_2209_10411_gb300 import replicas
@@ -435,6 +511,7 @@ def run_mine(args):
         variants = {name: storage_variant(B, scene, st, max(50, min(args.steps, 200)), stream)
                     for name, st in (("f16-dev", 1), ("bf16-dev", 2))}
         variants["dem_100_substeps"] = dem_ratio(B, scene, storage, 30, stream)
+        variants["gs_fit"] = gs_bench(B, scenes)
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node

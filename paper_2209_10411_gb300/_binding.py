@@ -131,6 +131,7 @@ _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_set_schedule", c_int, _P, c_int)
+_sig("mi_gs_fit", c_int, c_int, _P, _P, _P, _P, _P, _P, c_int, c_int, c_int, ctypes.c_float, _P, _P, _P)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
@@ -193,6 +194,40 @@ def mlp_infer(image, X, engine="tcgen05"):
     fn = lib.mi_mlp_infer if engine == "tcgen05" else lib.mi_mlp_infer_mma
     _mlp_check(fn(_tp(image), _tp(X), int(n), _tp(Y), _cur_stream()))
     return Y
+
+
+GS_MAX_POINTS, GS_MAX_BALLS = 12288, 256
+
+
+def gs_fit(hulls, models, planes, epochs, lr):
+    """Gradient Search refinement (mi_gs_fit) of several models at once.
+    hulls: list of (m_f, 3) point arrays, models: list of (c (n_f, 3), k
+    (n_f,)), planes: list of (p_f, 4) facet planes; host arrays, copied to the
+    device in one batch.  Returns a list of (c, k, active) per fit and the
+    (n_fits, 2) losses after the first and the second descent."""
+    import torch
+    nf = len(hulls)
+    dev = torch.device("cuda")
+
+    def cat(arrs, width):
+        a = np.concatenate([np.asarray(x, dtype=np.float32).reshape(-1, width) for x in arrs])
+        off = np.concatenate([[0], np.cumsum([len(np.asarray(x).reshape(-1, width)) for x in arrs])]).astype(np.int32)
+        return torch.as_tensor(a, device=dev).contiguous(), torch.as_tensor(off, device=dev)
+
+    H, hoff = cat(hulls, 3)
+    M, boff = cat([np.concatenate([np.asarray(c, np.float32).reshape(-1, 3), np.asarray(k, np.float32).reshape(-1, 1)],
+                                  1) for c, k in models], 4)
+    P, poff = cat(planes, 4)
+    active = torch.empty(M.shape[0], dtype=torch.int32, device=dev)
+    loss = torch.empty((nf, 2), dtype=torch.float32, device=dev)
+    mp = max(len(np.asarray(h).reshape(-1, 3)) for h in hulls)
+    mb = max(len(np.asarray(k).reshape(-1)) for _, k in models)
+    _mlp_check(lib.mi_gs_fit(nf, _tp(hoff), _tp(H), _tp(boff), _tp(M), _tp(poff), _tp(P), int(mp), int(mb),
+                             int(epochs), float(lr), _tp(active), _tp(loss), _cur_stream()))
+    torch.cuda.synchronize()
+    Mh, ah, bo = M.cpu().numpy(), active.cpu().numpy(), boff.cpu().numpy()
+    out = [(Mh[bo[f]:bo[f + 1], :3], Mh[bo[f]:bo[f + 1], 3], ah[bo[f]:bo[f + 1]].astype(bool)) for f in range(nf)]
+    return out, loss.cpu().numpy()
 
 
 def mlp_mse(Y, T):
