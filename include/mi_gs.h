@@ -26,7 +26,7 @@ extern "C" {
 #endif
 
 /* Largest hull and model one fit may have (shared-memory capacity). */
-#define MI_GS_MAX_POINTS 12288
+#define MI_GS_MAX_POINTS 10240
 #define MI_GS_MAX_BALLS 256
 
 /* Run n_fits refinements asynchronously on `stream` (a cudaStream_t, or

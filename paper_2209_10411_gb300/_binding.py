@@ -196,7 +196,7 @@ def mlp_infer(image, X, engine="tcgen05"):
     return Y
 
 
-GS_MAX_POINTS, GS_MAX_BALLS = 12288, 256
+GS_MAX_POINTS, GS_MAX_BALLS = 10240, 256
 
 
 def gs_fit(hulls, models, planes, epochs, lr):

@@ -2,10 +2,12 @@
 // Algorithm 2, Eq. GSloss), one CTA per fit.  The fit's hull points, model
 // and gradients stay in shared memory for all epochs; an epoch is two passes:
 // threads over hull points evaluate the field and dl/df (kept beside each
-// point), then warps over control points sum their four gradient components
-// over the points with a fixed lane order and butterfly.  Everything is FP32;
-// the reductions have a fixed order, so a fit's result does not depend on
-// the other fits of the call.
+// point; two points per thread at a time for two independent sums), then the
+// (control point, chunk of GS_CHUNKS points) units are spread over the warps,
+// each summing its four gradient components with a fixed lane order and
+// butterfly, and one thread per control point adds its chunks in order.
+// Everything is FP32; the reductions have a fixed order, so a fit's result
+// does not depend on the other fits of the call.
 #include <cmath>
 
 #include "mi_gs.h"
@@ -14,7 +16,8 @@
 namespace mi {
 namespace {
 
-constexpr int GS_THREADS = 256;
+constexpr int GS_THREADS = 1024;
+constexpr int GS_CHUNKS = 8;  // hull-point chunks per control point in the gradient pass
 constexpr unsigned GS_FULL = 0xffffffffu;
 
 // dl/df of Eq. GSloss: 2 (f - 1) on [2, inf), +1 on [1, 2), 2 (f - 1) - 1/f^2 below
@@ -70,8 +73,8 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G) {
   __shared__ float red[GS_THREADS];
   float4* Hs = gsm;                      // hull points (x, y, z, dl/df of the last pass)
   float4* Ms = Hs + G.max_points;        // model (x, y, z, k)
-  float4* Gs = Ms + G.max_balls;         // gradient (d/dx, d/dy, d/dz, d/dk)
-  int* act = reinterpret_cast<int*>(Gs + G.max_balls);
+  float4* Ps = Ms + G.max_balls;         // gradient partial sums per (control point, chunk)
+  int* act = reinterpret_cast<int*>(Ps + (size_t)G.max_balls * GS_CHUNKS);
   const int fit = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int h0 = G.hull_off[fit], m = G.hull_off[fit + 1] - h0;
   const int b0 = G.ball_off[fit], n = G.ball_off[fit + 1] - b0;
@@ -91,17 +94,31 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G) {
   float loss1 = 0.f;
   for (int round = 0; round < 2; ++round) {
     for (int e = 0; e < G.epochs; ++e) {
-      // dl/df at every hull point
-      for (int i = t; i < m; i += GS_THREADS) {
-        const float4 h = Hs[i];
-        Hs[i].w = gs_dl(gs_field(Ms, n, h.x, h.y, h.z));
+      // dl/df at every hull point, two points per thread at a time
+      for (int i = t; i < m; i += 2 * GS_THREADS) {
+        const int i2 = i + GS_THREADS;
+        const float4 ha = Hs[i], hb = Hs[i2 < m ? i2 : i];
+        float fa = 0.f, fb = 0.f;
+        for (int j = 0; j < n; ++j) {
+          const float4 b = Ms[j];
+          const float ax = ha.x - b.x, ay = ha.y - b.y, az = ha.z - b.z;
+          const float bx = hb.x - b.x, by = hb.y - b.y, bz = hb.z - b.z;
+          fa += b.w * __fdividef(1.0f, ax * ax + ay * ay + az * az);
+          fb += b.w * __fdividef(1.0f, bx * bx + by * by + bz * bz);
+        }
+        Hs[i].w = gs_dl(fa);
+        if (i2 < m) Hs[i2].w = gs_dl(fb);
       }
       __syncthreads();
-      // gradient of every control point: dL/dk = sum w / r^2, dL/dc = sum w 2 k (H - c) / r^4
-      for (int j = w; j < n; j += GS_THREADS / 32) {
+      // gradient of every control point: dL/dk = sum w / r^2, dL/dc = sum w 2 k (H - c) / r^4,
+      // as GS_CHUNKS partial sums over contiguous chunks of the points
+      const int csz = (m + GS_CHUNKS - 1) / GS_CHUNKS;
+      for (int u = w; u < n * GS_CHUNKS; u += GS_THREADS / 32) {
+        const int j = u / GS_CHUNKS, ch = u - j * GS_CHUNKS;
+        const int i0 = ch * csz, i1 = min(m, i0 + csz);
         const float4 b = Ms[j];
         float gx = 0.f, gy = 0.f, gz = 0.f, gk = 0.f;
-        for (int i = lane; i < m; i += 32) {
+        for (int i = i0 + lane; i < i1; i += 32) {
           const float4 h = Hs[i];
           const float dx = h.x - b.x, dy = h.y - b.y, dz = h.z - b.z;
           const float inv = __fdividef(1.0f, dx * dx + dy * dy + dz * dz);
@@ -118,12 +135,19 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G) {
           gz += __shfl_xor_sync(GS_FULL, gz, o);
           gk += __shfl_xor_sync(GS_FULL, gk, o);
         }
-        if (lane == 0) Gs[j] = make_float4(gx, gy, gz, gk);
+        if (lane == 0) Ps[u] = make_float4(gx, gy, gz, gk);
       }
       __syncthreads();
       for (int j = t; j < n; j += GS_THREADS)
         if (act[j]) {
-          const float4 g = Gs[j];
+          float4 g = Ps[j * GS_CHUNKS];
+          for (int ch = 1; ch < GS_CHUNKS; ++ch) {
+            const float4 q = Ps[j * GS_CHUNKS + ch];
+            g.x += q.x;
+            g.y += q.y;
+            g.z += q.z;
+            g.w += q.w;
+          }
           float4 b = Ms[j];
           b.x -= G.lr * g.x;
           b.y -= G.lr * g.y;
@@ -198,7 +222,8 @@ extern "C" mi_status mi_gs_fit(int n_fits, const int* hull_off, const float* hul
   G.lr = lr;
   G.active = active;
   G.loss = loss;
-  const size_t smem = sizeof(float4) * ((size_t)max_points + 2 * (size_t)max_balls) + sizeof(int) * max_balls;
+  const size_t smem =
+      sizeof(float4) * ((size_t)max_points + (size_t)(1 + GS_CHUNKS) * max_balls) + sizeof(int) * max_balls;
   cudaError_t e = cudaFuncSetAttribute(k_gs_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return MI_ECUDA;
   k_gs_fit<<<n_fits, GS_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(G);
