@@ -102,7 +102,9 @@ def fitness(H, genes):
 
 
 def crossover_point(c_c, n_genes):
-    return int(np.floor(c_c * n_genes))
+    """p = floor(C_c N_G), with C_c rounded to FP32 first (the kernel's
+    argument type) and the product in FP64."""
+    return int(np.floor(float(np.float32(c_c)) * n_genes))
 
 
 def offspring(pop, seed, gen, c_m, c_c, bbox, krange, planes):

@@ -84,18 +84,13 @@ def descend(H, c, k, epochs, lr, active=None):
 
 def outside_hull_f32(c, planes):
     """Reading G5: True where n . c > d for some plane (nx, ny, nz, d), the
-    dot product and comparison in FP32, left to right."""
-    c32 = np.asarray(c, dtype=np.float32)
+    dot product and comparison in FP32, left to right (every product and sum
+    an FP32 rounding of its own, as numpy float32 arrays compute them)."""
+    c32 = np.asarray(c, dtype=np.float32).reshape(-1, 3)
     P = np.asarray(planes, dtype=np.float32)
-    out = np.zeros(len(c32), dtype=bool)
-    for j in range(len(c32)):
-        for p in P:
-            s = np.float32(np.float32(p[0] * c32[j, 0]) + np.float32(p[1] * c32[j, 1]))
-            s = np.float32(s + np.float32(p[2] * c32[j, 2]))
-            if s > p[3]:
-                out[j] = True
-                break
-    return out
+    s = (P[None, :, 0] * c32[:, None, 0]) + (P[None, :, 1] * c32[:, None, 1])
+    s = s + (P[None, :, 2] * c32[:, None, 2])
+    return np.any(s > P[None, :, 3], axis=1)
 
 
 def anomaly(c, k, planes):

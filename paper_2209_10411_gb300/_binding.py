@@ -131,6 +131,8 @@ _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_set_schedule", c_int, _P, c_int)
+_sig("mi_ga_scratch_bytes", ctypes.c_size_t, c_int, c_int)
+_sig("mi_ga_run", c_int, c_int, c_int, _P, c_int, _P, c_int, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_ulonglong, c_int, c_int, _P, _P, _P, _P, _P, _P)
 _sig("mi_gs_fit", c_int, c_int, _P, _P, _P, _P, _P, _P, c_int, c_int, c_int, ctypes.c_float, _P, _P, _P)
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
@@ -228,6 +230,32 @@ def gs_fit(hulls, models, planes, epochs, lr):
     Mh, ah, bo = M.cpu().numpy(), active.cpu().numpy(), boff.cpu().numpy()
     out = [(Mh[bo[f]:bo[f + 1], :3], Mh[bo[f]:bo[f + 1], 3], ah[bo[f]:bo[f + 1]].astype(bool)) for f in range(nf)]
     return out, loss.cpu().numpy()
+
+
+def ga_run(hull, planes, bbox, krange, n_ind, n_genes, generations, c_m, c_c, seed, pop=None):
+    """Genetic Algorithm capture (mi_ga_run) on one hull: host arrays in,
+    host arrays out: (population (n_ind, n_genes, 4), fitness (n_ind,),
+    children of the last generation, their fitness).  pop=None draws the
+    initial population on the device."""
+    import torch
+    dev = torch.device("cuda")
+    H = torch.as_tensor(np.asarray(hull, dtype=np.float32).reshape(-1, 3), device=dev).contiguous()
+    P = torch.as_tensor(np.asarray(planes, dtype=np.float32).reshape(-1, 4), device=dev).contiguous()
+    if pop is None:
+        Pop = torch.empty((n_ind, n_genes, 4), dtype=torch.float32, device=dev)
+    else:
+        Pop = torch.as_tensor(np.asarray(pop, dtype=np.float32).reshape(n_ind, n_genes, 4), device=dev).contiguous()
+    fit = torch.empty(n_ind, dtype=torch.float32, device=dev)
+    off = torch.empty_like(Pop)
+    fo = torch.empty(n_ind, dtype=torch.float32, device=dev)
+    scratch = torch.empty(int(lib.mi_ga_scratch_bytes(n_ind, n_genes)), dtype=torch.uint8, device=dev)
+    bb = (ctypes.c_float * 6)(*[float(v) for v in np.asarray(bbox, dtype=np.float32)])
+    kr = (ctypes.c_float * 2)(*[float(v) for v in np.asarray(krange, dtype=np.float32)])
+    _mlp_check(lib.mi_ga_run(int(n_ind), int(n_genes), _tp(H), int(H.shape[0]), _tp(P), int(P.shape[0]), ctypes.cast(bb, c_void_p), ctypes.cast(kr, c_void_p),
+                             float(c_m), float(c_c), int(seed), int(generations), 1 if pop is None else 0, _tp(Pop),
+                             _tp(fit), _tp(off), _tp(fo), _tp(scratch), _cur_stream()))
+    torch.cuda.synchronize()
+    return Pop.cpu().numpy(), fit.cpu().numpy(), off.cpu().numpy(), fo.cpu().numpy()
 
 
 def mlp_mse(Y, T):
