@@ -5,7 +5,7 @@
 // hull test of a candidate point spreads the facet planes over the lanes);
 // the crossover (a thread per gene pair); the children's fitness (a CTA per
 // individual, threads over hull points, fixed-order block sum); and the
-// selection (a thread per candidate, its rank by counting over parents and
+// selection (a warp per candidate, its rank by counting over parents and
 // children).  Random numbers come from a counter-based SplitMix64, so every
 // draw is a function of (seed, generation, individual, gene, slot) and the
 // run does not depend on the launch shapes.
@@ -137,17 +137,19 @@ __global__ void k_ga_keys(GaLaunch G, unsigned gen, unsigned long long* keys) {
   if (i < G.n_ind) keys[i] = ga_draw(G.seed, gen, (unsigned long long)i, 0, GA_SLOT_KEY);
 }
 
-// perm[rank of key i] = i, ranks ascending with ties to the lower index
+// perm[rank of key i] = i, ranks ascending with ties to the lower index; a
+// warp per key, its lanes counting over strided keys
 __global__ void k_ga_perm(GaLaunch G, const unsigned long long* keys, int* perm) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= G.n_ind) return;
   const unsigned long long ki = keys[i];
   int r = 0;
-  for (int j = 0; j < G.n_ind; ++j) {
+  for (int j = lane; j < G.n_ind; j += 32) {
     const unsigned long long kj = keys[j];
     r += (kj < ki) || (kj == ki && j < i);
   }
-  perm[r] = i;
+  r = __reduce_add_sync(0xffffffffu, r);
+  if (lane == 0) perm[r] = i;
 }
 
 // the genes whose mutation draw falls below c_m, appended to a list
@@ -191,11 +193,12 @@ __global__ void k_ga_crossover(GaLaunch G, const float4* mut, const int* perm, f
   off[(long long)b * G.n_genes + g] = g < G.p ? mb : ma;
 }
 
-// the n_ind fittest of parents (0..n_ind-1) and children (n_ind..), by counting
+// the n_ind fittest of parents (0..n_ind-1) and children (n_ind..), by
+// counting: a warp per candidate, its lanes over strided candidates
 __global__ void k_ga_select(GaLaunch G, const float4* pop, const float* fit, const float4* off, const float* fit_off,
                             float4* npop, float* nfit) {
   const int n2 = 2 * G.n_ind;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (c >= n2) return;
   auto val = [&](int d) {
     const float v = d < G.n_ind ? fit[d] : fit_off[d - G.n_ind];
@@ -203,14 +206,15 @@ __global__ void k_ga_select(GaLaunch G, const float4* pop, const float* fit, con
   };
   const float fc = val(c);
   int r = 0;
-  for (int d = 0; d < n2; ++d) {
+  for (int d = lane; d < n2; d += 32) {
     const float fd = val(d);
     r += (fd < fc) || (fd == fc && d < c);
   }
+  r = __reduce_add_sync(0xffffffffu, r);
   if (r >= G.n_ind) return;
   const float4* src = c < G.n_ind ? pop + (long long)c * G.n_genes : off + (long long)(c - G.n_ind) * G.n_genes;
-  for (int g = 0; g < G.n_genes; ++g) npop[(long long)r * G.n_genes + g] = src[g];
-  nfit[r] = fc;
+  for (int g = lane; g < G.n_genes; g += 32) npop[(long long)r * G.n_genes + g] = src[g];
+  if (lane == 0) nfit[r] = fc;
 }
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -284,7 +288,7 @@ extern "C" mi_status mi_ga_run(int n_ind, int n_genes, const float* hull, int m,
   const unsigned mut_blocks = (unsigned)(sms > 0 ? 8 * sms : 1024);  // 8 warps per block, grid-strided over the list
   for (int gen = 0; gen < generations; ++gen) {
     k_ga_keys<<<(n_ind + 255) / 256, 256, 0, s>>>(G, (unsigned)gen, keys);
-    k_ga_perm<<<(n_ind + 255) / 256, 256, 0, s>>>(G, keys, perm);
+    k_ga_perm<<<(unsigned)(((long long)n_ind * 32 + 255) / 256), 256, 0, s>>>(G, keys, perm);
     if (cudaMemcpyAsync(mut, cur, sizeof(float4) * ng, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(mcount, 0, sizeof(int), s) != cudaSuccess)
       return MI_ECUDA;
@@ -299,7 +303,7 @@ extern "C" mi_status mi_ga_run(int n_ind, int n_genes, const float* hull, int m,
           cudaMemcpyAsync(fit_offspring, fitO, sizeof(float) * n_ind, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return MI_ECUDA;
     }
-    k_ga_select<<<(2 * n_ind + 255) / 256, 256, 0, s>>>(G, cur, fcur, off, fitO, nxt, fnxt);
+    k_ga_select<<<(unsigned)(((long long)2 * n_ind * 32 + 255) / 256), 256, 0, s>>>(G, cur, fcur, off, fitO, nxt, fnxt);
     float4* t4 = cur;
     cur = nxt;
     nxt = t4;
