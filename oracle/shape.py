@@ -80,6 +80,7 @@ def descriptors(centers, k, h, eps=0.1):
     descriptors of one metaball model (body frame)."""
     centers = np.asarray(centers, dtype=np.float32)
     k = np.asarray(k, dtype=np.float32)
+    h = float(np.float32(h))  # the spacing is the FP32 value the coordinates use
     Rb = np.float32(grid_radius(centers, k, eps))
     n = int(np.ceil(2.0 * float(Rb) / h))
     ax = _axis(n, -Rb, h)
@@ -129,6 +130,6 @@ def descriptors(centers, k, h, eps=0.1):
     Ap = len(cols) * float(h) ** 2
     d_n = (6.0 * V / np.pi) ** (1.0 / 3.0)
     d_s = np.sqrt(4.0 * Ap / np.pi)
-    return {"volume": V, "surface": S, "axes": E, "lengths": L, "projected_area": Ap,
+    return {"volume": V, "surface": S, "axes": E, "eigenvalues": w[::-1], "lengths": L, "projected_area": Ap,
             "sphericity": np.pi * d_n * d_n / S, "d_n": d_n, "d_s": d_s,
             "csf": L[2] / np.sqrt(L[1] * L[0]), "cells": vol_cells}
