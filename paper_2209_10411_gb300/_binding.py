@@ -131,6 +131,8 @@ _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_set_schedule", c_int, _P, c_int)
+_sig("mi_shape_scratch_bytes", ctypes.c_size_t, c_int, c_int)
+_sig("mi_shape_descriptors", c_int, c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P)
 _sig("mi_ga_scratch_bytes", ctypes.c_size_t, c_int, c_int)
 _sig("mi_ga_run", c_int, c_int, c_int, _P, c_int, _P, c_int, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_ulonglong, c_int, c_int, _P, _P, _P, _P, _P, _P)
 _sig("mi_gs_fit", c_int, c_int, _P, _P, _P, _P, _P, _P, c_int, c_int, c_int, ctypes.c_float, _P, _P, _P)
@@ -256,6 +258,48 @@ def ga_run(hull, planes, bbox, krange, n_ind, n_genes, generations, c_m, c_c, se
                              _tp(fit), _tp(off), _tp(fo), _tp(scratch), _cur_stream()))
     torch.cuda.synchronize()
     return Pop.cpu().numpy(), fit.cpu().numpy(), off.cpu().numpy(), fo.cpu().numpy()
+
+
+SHAPE_FIELDS = ("volume", "surface", "l_long", "l_int", "l_short", "projected_area", "sphericity", "d_n", "d_s",
+                "csf", "cells")
+
+
+def shape_descriptors(models, h, eps=0.1):
+    """Shape descriptors (mi_shape_descriptors) of metaball models given as
+    (centres (n, 3), k (n,)) in their body frames: a list of dicts with
+    SHAPE_FIELDS and the principal axes (rows, longest first).  The grid of
+    each model spans +-R_g, R_g = max |c| + sqrt(sum k / (1 - eps)), rounded
+    to FP32, with ceil(2 R_g / h) cells per axis."""
+    import torch
+    dev = torch.device("cuda")
+    rg, ng, rows = [], [], []
+    for c, k in models:
+        c = np.asarray(c, dtype=np.float32).reshape(-1, 3)
+        k = np.asarray(k, dtype=np.float32).reshape(-1)
+        c64, k64 = c.astype(np.float64), k.astype(np.float64)
+        r = np.float32(float(np.sqrt((c64 * c64).sum(1)).max() + np.sqrt(k64.sum() / (1.0 - eps))))
+        rg.append(r)
+        ng.append(int(np.ceil(2.0 * float(r) / h)))
+        rows.append(np.concatenate([c, k[:, None]], 1))
+    off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    balls = torch.as_tensor(np.concatenate(rows), device=dev).contiguous()
+    offs = torch.as_tensor(off, device=dev)
+    R = torch.as_tensor(np.array(rg, dtype=np.float32), device=dev)
+    N = torch.as_tensor(np.array(ng, dtype=np.int32), device=dev)
+    npart, max_n = len(models), max(ng)
+    out = torch.empty((npart, len(SHAPE_FIELDS)), dtype=torch.float64, device=dev)
+    axes = torch.empty((npart, 9), dtype=torch.float32, device=dev)
+    scratch = torch.empty(int(lib.mi_shape_scratch_bytes(npart, max_n)), dtype=torch.uint8, device=dev)
+    _mlp_check(lib.mi_shape_descriptors(npart, _tp(offs), _tp(balls), _tp(R), _tp(N), int(max_n), float(h),
+                                        float(eps), _tp(out), _tp(axes), _tp(scratch), _cur_stream()))
+    torch.cuda.synchronize()
+    o, a = out.cpu().numpy(), axes.cpu().numpy()
+    res = []
+    for p in range(npart):
+        d = {f: float(o[p, i]) for i, f in enumerate(SHAPE_FIELDS)}
+        d["axes"] = a[p].reshape(3, 3)
+        res.append(d)
+    return res
 
 
 def mlp_mse(Y, T):
