@@ -490,6 +490,35 @@ def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21)
                              "sample": "FP64 numpy oracle: one individual's fitness"}}
 
 
+def shape_bench(B, scenes, n=300, h=0.25, seed=0):
+    """Shape descriptors (Sec. 3) of the 300 particle models of the precision
+    tank (8-64 control points, radius 8-16 lu) at spacing h: particles/s and
+    cell evaluations/s; the oracle on one of them beside it."""
+    import time
+    import torch
+    from oracle import shape as oshape
+    sc = scenes.config4(seed=seed, n_particles=n)
+    models = [(p.centers, p.k) for p in sc.particles]
+    B.shape_descriptors(models[:2], h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = B.shape_descriptors(models, h)
+    dt = time.perf_counter() - t0
+    cells = sum(int(np.ceil(2.0 * float(np.float32(float(np.sqrt((np.asarray(c, np.float64) ** 2).sum(1)).max()
+                                                        + np.sqrt(np.asarray(k, np.float64).sum() / 0.9)))) / h)) ** 3
+                for c, k in models)
+    # the oracle on the first model at twice the spacing (one eighth of the cells), scaled back
+    t1 = time.perf_counter()
+    oshape.descriptors(models[0][0], models[0][1], 2 * h)
+    o_s = (time.perf_counter() - t1) * 8.0
+    return {"value": n / dt, "unit": "particles/s", "s": dt, "particles": n, "h": h,
+            "cell_evaluations_per_s": cells / dt, "note": "host wall clock of the binding call (copies included)",
+            "sphericity_median": float(np.median([d["sphericity"] for d in out])),
+            "csf_median": float(np.median([d["csf"] for d in out])),
+            "cpu_baseline": {"value": 1.0 / o_s, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                             "sample": "numpy oracle: the first particle at twice the spacing, time x 8"}}
+
+
 def run_mine(args):
     import torch
     from paper_2209_10411_gb300 import replicas
@@ -570,6 +599,7 @@ def run_mine(args):
         variants["dem_100_substeps"] = dem_ratio(B, scene, storage, 30, stream)
         variants["gs_fit"] = gs_bench(B, scenes)
         variants["ga_capture"] = ga_bench(B, scenes)
+        variants["shape_descriptors"] = shape_bench(B, scenes)
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node
