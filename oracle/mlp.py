@@ -1,8 +1,8 @@
 """Learned Newton guess for contact detection: features, MLP, loss, AdamW
 (oracle side, test infrastructure only; float64).
 
-Not in the paper: the Newton-Raphson closest-point solve of Sec. 2.3.1 is
-kept as the judge, and a small network proposes its starting point and the
+Not in the paper: the Newton-Raphson closest-point solve of Sec. 2.3.1 still
+decides every point, and a small network proposes its starting point and the
 set of control points that matter near the solution.
 
 Features of a candidate pair (i, j), 64 numbers, lengths scaled by

@@ -1,5 +1,5 @@
-// Learned Newton guess for the closest-point solve (Sec. 2.3.1 keeps plain
-// Newton-Raphson as the judge): the feature kernel for the candidate pairs of
+// Learned Newton guess for the closest-point solve (the plain Newton-Raphson
+// of Sec. 2.3.1 still decides every point): the feature kernel for the candidate pairs of
 // a DEM substep, and the batch solver of explicitly posed pairs that makes the
 // training data (features, plain solves, labels) and compares plain and
 // learned starts on the same pairs.  One warp per pair, as in k_contacts.
