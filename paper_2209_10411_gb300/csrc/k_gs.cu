@@ -1,5 +1,6 @@
 // Gradient Search refinement of metaball models on point hulls (Sec. 2.2,
-// Algorithm 2, Eq. GSloss), one CTA per fit.  The fit's hull points, model
+// Algorithm 2, Eq. GSloss), one fit at a time per CTA, the fits taken
+// largest first by persistent CTAs.  The fit's hull points, model
 // and gradients stay in shared memory for all epochs; an epoch is two passes:
 // threads over hull points evaluate the field and dl/df (kept beside each
 // point; two points per thread at a time for two independent sums), then the
@@ -68,14 +69,13 @@ struct GsLaunch {
   float* loss;
 };
 
-__global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G) {
-  extern __shared__ __align__(16) float4 gsm[];
-  __shared__ float red[GS_THREADS];
+// One fit by the whole CTA (every thread calls it with the same fit).
+__device__ __forceinline__ void gs_fit_one(const GsLaunch& G, int fit, float4* gsm, float* red) {
   float4* Hs = gsm;                      // hull points (x, y, z, dl/df of the last pass)
   float4* Ms = Hs + G.max_points;        // model (x, y, z, k)
   float4* Ps = Ms + G.max_balls;         // gradient partial sums per (control point, chunk)
   int* act = reinterpret_cast<int*>(Ps + (size_t)G.max_balls * GS_CHUNKS);
-  const int fit = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int h0 = G.hull_off[fit], m = G.hull_off[fit + 1] - h0;
   const int b0 = G.ball_off[fit], n = G.ball_off[fit + 1] - b0;
   const int p0 = G.plane_off[fit], np_ = G.plane_off[fit + 1] - p0;
@@ -195,6 +195,40 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G) {
     b[3] = v.w;
     G.active[b0 + j] = act[j];
   }
+  __syncthreads();  // the shared buffers are free for the next fit
+}
+
+// Fits in decreasing order of work (hull points x control points, ties to the
+// lower index): order[r] is the fit of rank r.
+__global__ void k_gs_order(GsLaunch G, int n_fits, int* order) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_fits) return;
+  auto work = [&](int f) {
+    return (long long)(G.hull_off[f + 1] - G.hull_off[f]) * (long long)(G.ball_off[f + 1] - G.ball_off[f]);
+  };
+  const long long wj = work(j);
+  int r = 0;
+  for (int i = 0; i < n_fits; ++i) {
+    const long long wi = work(i);
+    r += (wi > wj) || (wi == wj && i < j);
+  }
+  order[r] = j;
+}
+
+// Persistent CTAs take the fits largest first from a counter, so that the
+// SMs' loads even out (longest-processing-time-first scheduling).
+__global__ void __launch_bounds__(GS_THREADS) k_gs_fit(GsLaunch G, int n_fits, const int* order, int* next) {
+  extern __shared__ __align__(16) float4 gsm[];
+  __shared__ float red[GS_THREADS];
+  __shared__ int pick;
+  for (;;) {
+    if (threadIdx.x == 0) pick = atomicAdd(next, 1);
+    __syncthreads();
+    const int q = pick;
+    __syncthreads();
+    if (q >= n_fits) break;
+    gs_fit_one(G, order[q], gsm, red);
+  }
 }
 
 }  // namespace
@@ -224,8 +258,26 @@ extern "C" mi_status mi_gs_fit(int n_fits, const int* hull_off, const float* hul
   G.loss = loss;
   const size_t smem =
       sizeof(float4) * ((size_t)max_points + (size_t)(1 + GS_CHUNKS) * max_balls) + sizeof(int) * max_balls;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaFuncSetAttribute(k_gs_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return MI_ECUDA;
-  k_gs_fit<<<n_fits, GS_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(G);
-  return cudaGetLastError() == cudaSuccess ? MI_OK : MI_ECUDA;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_fit, GS_THREADS, smem) != cudaSuccess)
+    return MI_ECUDA;
+  // the fit order and the pick counter, stream-ordered scratch
+  int* tmp = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(int) * ((size_t)n_fits + 1), s) != cudaSuccess)
+    return MI_ECUDA;
+  int* order = tmp + 1;
+  e = cudaMemsetAsync(tmp, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_gs_order<<<(n_fits + 255) / 256, 256, 0, s>>>(G, n_fits, order);
+    long long grid = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (grid > n_fits) grid = n_fits;
+    k_gs_fit<<<(unsigned)grid, GS_THREADS, smem, s>>>(G, n_fits, order, tmp);
+    e = cudaGetLastError();
+  }
+  const cudaError_t ef = cudaFreeAsync(tmp, s);
+  return e == cudaSuccess && ef == cudaSuccess ? MI_OK : MI_ECUDA;
 }
