@@ -680,8 +680,11 @@ def main():
     ap.add_argument("--small-contact-lattice", action="store_true",
                     help="contact bed on a 16^3 periodic lattice (profiling: same pairs, no walls, little memory)")
     args = ap.parse_args()
-    CONFIG.update({"workload": "settling tank 256x256x512, three cobblestone-like particles",
-                   "lattice": [256, 256, 512], "storage": args.storage})
+    from paper_2209_10411_gb300 import scenes
+    sc = scenes.config2()
+    # the workload both arms name (the GPU arm adds what its run measures)
+    CONFIG.update({"workload": sc.name, "lattice": list(sc.shape), "particles": len(sc.particles),
+                   "metaballs": [int(len(p.k)) for p in sc.particles], "storage": args.storage, "tau": sc.tau})
     if args.impl == "reference":
         run_reference(args)
     else:
