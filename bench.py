@@ -107,51 +107,73 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU side: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(budget_s=15.0, crop=96, seed=0):
-    """Time the oracle's coupled LBM step (flags, links, refill, IBB, momentum
+class OracleSample:
+    """The oracle's coupled LBM step (flags, links, refill, IBB, momentum
     exchange, stream-collide) plus the rigid-body update on a crop^3 window
-    around the first cobble of the settling tank, until about budget_s seconds
-    of CPU work; returns (MLUPS, seconds, steps)."""
-    from oracle import coupling, dem, lbm, metaball
-    from paper_2209_10411_gb300 import scenes
-    spec = scenes.config2(seed=seed).particles[0]
-    shape = (crop, crop, crop)
-    P = {"centers": spec.centers, "k": spec.k, "pos": np.array([crop / 2.0] * 3), "quat": spec.quat,
-         "vel": np.zeros(3), "omega": np.zeros(3), "mass": 1.0, "volume": 0.4,
-         "inertia": np.eye(3) * 100.0}
-    f = lbm.rest_state((crop, crop, crop))
-    owner_prev = metaball.flag_nodes(shape, [P])
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        owner = metaball.flag_nodes(shape, [P])
-        f, F, T = coupling.coupled_lbm_step(f, owner, owner_prev, [P], 0.8)
-        P = dem.integrate(P, F[0], T[0], (0.0, 0.0, -1e-5))
-        owner_prev = owner
-        steps += 1
-        dt = time.perf_counter() - t0
-        if dt >= budget_s:
-            break
-    return crop ** 3 * steps / dt / 1e6, dt, steps
+    around the first cobble of the settling tank; the window is set up once
+    and each call of run() continues the same simulation."""
+
+    def __init__(self, crop=96, seed=0):
+        from oracle import coupling, dem, lbm, metaball
+        from paper_2209_10411_gb300 import scenes
+        self.mods = (coupling, dem, metaball)
+        spec = scenes.config2(seed=seed).particles[0]
+        self.crop = crop
+        self.shape = (crop, crop, crop)
+        self.P = {"centers": spec.centers, "k": spec.k, "pos": np.array([crop / 2.0] * 3), "quat": spec.quat,
+                  "vel": np.zeros(3), "omega": np.zeros(3), "mass": 1.0, "volume": 0.4,
+                  "inertia": np.eye(3) * 100.0}
+        self.f = lbm.rest_state(self.shape)
+        self.owner_prev = metaball.flag_nodes(self.shape, [self.P])
+
+    def step(self):
+        coupling, dem, metaball = self.mods
+        owner = metaball.flag_nodes(self.shape, [self.P])
+        self.f, F, T = coupling.coupled_lbm_step(self.f, owner, self.owner_prev, [self.P], 0.8)
+        self.P = dem.integrate(self.P, F[0], T[0], (0.0, 0.0, -1e-5))
+        self.owner_prev = owner
+
+    def run(self, budget_s=0.0):
+        """One step or more, until about budget_s seconds of CPU work;
+        returns (MLUPS, seconds, steps)."""
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            self.step()
+            steps += 1
+            dt = time.perf_counter() - t0
+            if dt >= budget_s:
+                break
+        return self.crop ** 3 * steps / dt / 1e6, dt, steps
 
 
 def run_reference(args):
+    """The oracle on the host cores, each of the K timed steps one oracle step
+    on a cubic window around a cobble of the tank, the window sized from a
+    calibration so that the whole warm-up + timed run takes about REF_TOTAL_S
+    seconds, between a 64^3 window (the cobble's solid spans 58 nodes along
+    each axis) and a 96^3 one."""
     from paper_2209_10411_gb300 import replicas
     rank, world, _ = replicas.rank_env()
     if rank != 0:
         return
-    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    nsteps = max(1, args.steps + args.warmup)
+    per_step = min(60.0, REF_TOTAL_S / nsteps)
+    cal = OracleSample(crop=REF_MIN_CROP)
+    cal.run()                      # first step pays numpy's one-time costs
+    _, dt, _ = cal.run()
+    t_node = dt / REF_MIN_CROP ** 3
+    crop = int(max(REF_MIN_CROP, min(96, (per_step / t_node) ** (1.0 / 3.0))))
+    sampler = OracleSample(crop=crop)
     for _ in range(args.warmup):
-        oracle_sample(budget_s=0.5)
-    vals = []
+        sampler.run()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, dt, n = oracle_sample(budget_s=per_step_budget)
-        vals.append(v)
+        sampler.run()
     wall = time.perf_counter() - t0
-    value = statistics.median(vals)
-    sample = ("FP64 numpy oracle, coupled step + rigid-body update on a 96^3 window around one "
-              "cobble of the tank, %.1f s of CPU work per step" % per_step_budget)
+    value = crop ** 3 * args.steps / wall / 1e6
+    sample = ("FP64 numpy oracle, one coupled step + rigid-body update per timed step on a %d^3 window around "
+              "one cobble of the tank" % crop)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -159,6 +181,10 @@ def run_reference(args):
            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+REF_TOTAL_S = 120.0  # the reference arm's warm-up + timed steps, about
+REF_MIN_CROP = 64    # smallest window that holds the whole cobble with a margin
 
 
 METRIC = "coupled-step MLUPS (FP32 vs FP16-store) at stated err; contact solves/s"
@@ -633,7 +659,7 @@ def run_mine(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, n = oracle_sample(budget_s=args.cpu_seconds)
+        v, dt, n = OracleSample(crop=96).run(budget_s=args.cpu_seconds)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": "FP64 numpy oracle: coupled step + rigid-body update on a 96^3 window around one "
                          "cobble, %d steps in %.1f s" % (n, dt)}
