@@ -123,7 +123,7 @@ typedef struct mi_delbm_config {
   void (*dev_free)(void *ptr, size_t bytes, void *ctx);
   void *alloc_ctx;
   /* Nonzero: mi_delbm_add_particle rejects (MI_EOVERLAP) a particle whose
-   * core overlaps an existing particle's, judged by the method's own closest-
+   * core overlaps an existing particle's, decided by the method's own closest-
    * point solve (Sec. 2.3.1): for every existing particle whose bounding
    * sphere meets the new one, plain Newton on grad(g_i + g_j) = 0 from the
    * plain guess, overlap when the converged point lies inside a core.

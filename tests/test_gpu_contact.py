@@ -162,7 +162,7 @@ def test_full_coupled_step_with_contacts():
 
 def test_add_particle_overlap_check():
     """With check_overlap, a particle whose core overlaps an existing one is
-    rejected with MI_EOVERLAP (judged by the closest-point solve: the
+    rejected with MI_EOVERLAP (decided by the closest-point solve: the
     converged point lies inside a core) and nothing is added; a particle in
     skin contact only is accepted; without the check both are accepted."""
     B = binding()
