@@ -61,3 +61,34 @@ def test_create_rejects_bad_config_without_touching_gpu(lib):
     B.lib.mi_delbm_config_init(ctypes.byref(cfg))
     cfg.nx = 0
     assert B.lib.mi_delbm_create(ctypes.byref(cfg), ctypes.byref(h)) == B.MI_EINVAL
+
+
+def test_fitting_and_shape_entry_points_validate_on_host(lib):
+    """Argument checks of mi_gs_fit, mi_ga_run and mi_shape_descriptors come
+    before any CUDA call: bad sizes or parameters return MI_EINVAL, empty
+    batches MI_OK, both without a GPU."""
+    from paper_2209_10411_gb300 import _binding as B
+    L = B.lib
+    N = None
+    # Gradient Search: negative batch, point/ball limits, non-finite step
+    assert L.mi_gs_fit(-1, N, N, N, N, N, N, 16, 8, 10, 0.1, N, N, N) == B.MI_EINVAL
+    assert L.mi_gs_fit(1, N, N, N, N, N, N, 10241, 8, 10, 0.1, N, N, N) == B.MI_EINVAL
+    assert L.mi_gs_fit(1, N, N, N, N, N, N, 16, 257, 10, 0.1, N, N, N) == B.MI_EINVAL
+    assert L.mi_gs_fit(1, N, N, N, N, N, N, 16, 8, 10, float("nan"), N, N, N) == B.MI_EINVAL
+    assert L.mi_gs_fit(1, N, N, N, N, N, N, 16, 8, 10, 0.1, N, N, N) == B.MI_EINVAL   # NULL arrays
+    assert L.mi_gs_fit(0, N, N, N, N, N, N, 16, 8, 10, 0.1, N, N, N) == B.MI_OK
+    # Genetic Algorithm: population of one, rates outside [0, 1], NULL arrays
+    args = [N, 64, N, 10, N, N, 0.1, 0.5, 1, 5, 1, N, N, N, N, N, N]
+    assert L.mi_ga_run(1, 4, *args) == B.MI_EINVAL
+    bad_cm = list(args)
+    bad_cm[6] = 1.5
+    assert L.mi_ga_run(8, 4, *bad_cm) == B.MI_EINVAL
+    assert L.mi_ga_run(8, 4, *args) == B.MI_EINVAL
+    assert L.mi_ga_scratch_bytes(0, 4) == 0 and L.mi_ga_scratch_bytes(8, 4) > 0
+    # shape descriptors: spacing, band width
+    assert L.mi_shape_descriptors(1, N, N, N, N, 8, 0.0, 0.1, N, N, N, N) == B.MI_EINVAL
+    assert L.mi_shape_descriptors(1, N, N, N, N, 8, 0.1, 1.0, N, N, N, N) == B.MI_EINVAL
+    assert L.mi_shape_descriptors(1, N, N, N, N, 0, 0.1, 0.1, N, N, N, N) == B.MI_EINVAL
+    assert L.mi_shape_descriptors(1, N, N, N, N, 8, 0.1, 0.1, N, N, N, N) == B.MI_EINVAL  # NULL arrays
+    assert L.mi_shape_descriptors(0, N, N, N, N, 8, 0.1, 0.1, N, N, N, N) == B.MI_OK
+    assert L.mi_shape_scratch_bytes(0, 8) == 0 and L.mi_shape_scratch_bytes(2, 8) > 0
