@@ -8,8 +8,11 @@ Python binding) never imports, calls or links anything in here, and nothing in
 here imports the product package: the two share no code, no tables and no
 constants.
 
-Everything is float64.  Each function names the passage of the paper it
-follows; where the paper is silent or ambiguous the reading taken is stated in
+Arithmetic is float64, except where floating point decides an integer that
+the kernels decide in FP32 (the convex-hull test and the draws of the shape
+fitting, the solid test of the shape descriptors): there the oracle takes the
+same decision in FP32 with the same single roundings, and says so.  Each
+function names the passage of the paper it follows; where the paper is silent or ambiguous the reading taken is stated in
 the function's docstring (the full list of readings, numbered A1..A27, is kept
 with the design notes).
 
@@ -26,10 +29,14 @@ Modules
             spring-dashpot forces
   dem       rigid-body update
   step      the whole coupled step in the order flag -> links -> LBM -> DEM
+  mlp       learned Newton guess: features, the MLP, its loss and AdamW
+  gs        Gradient Search refinement of a metaball model (Algorithm 2)
+  ga        Genetic Algorithm capture of a contour (Algorithm 1)
+  shape     sphericity, nominal and projected-area diameters, Corey shape
+            factor of a metaball model (Sec. 3)
 
 Parity status: every function is pinned by a test under tests/ that checks it
-against something other than itself (closed forms, invariants, brute force),
-except the two stated as "parity unpinned" in their docstrings (the FP16/BF16
-storage error, and the gain of the learned Newton guess), which are measured
-numbers rather than defined results.
+against something other than itself (closed forms, invariants, brute force,
+published generator outputs).  The FP16/BF16 storage error and the gain of the
+learned Newton guess are measured numbers, not functions of this package.
 """
