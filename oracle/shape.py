@@ -25,7 +25,7 @@ Readings (the paper leaves these open):
   D5  the CSF's numerator is the shortest axis length d_sh (the Corey shape
       factor; the paper's symbol is also its projected-area diameter's).  For
       an ellipsoid these readings give d_n / d_s = CSF^(1/3) exactly, and the
-      paper's table follows that relation within 0.6 % for all nine shapes.
+      paper's table follows that relation within 0.9 % for all nine shapes.
 The decision "f >= 1" and the band test are integers taken from FP32 values
 the kernel computes, so they are taken here in FP32 with the same single
 roundings (coordinates, differences, squares, sums, one IEEE division per
