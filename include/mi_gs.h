@@ -49,7 +49,10 @@ extern "C" {
  * whose sizes exceed them, or that has no points or no balls, is left
  * unchanged with loss NaN.  Errors: MI_EINVAL (n_fits < 0, epochs < 0, lr
  * not finite, a bound out of range, a NULL array with n_fits > 0), MI_ECUDA
- * (launch failure).  Results are deterministic (fixed reduction orders). */
+ * (launch failure).  Results are deterministic (fixed reduction orders).
+ * The call takes n_fits + 1 ints of stream-ordered scratch (the fits'
+ * largest-first order and a pick counter) from the device's default memory
+ * pool on `stream` and frees them on the same stream. */
 mi_status mi_gs_fit(int n_fits, const int *hull_off, const float *hull, const int *ball_off, float *balls,
                     const int *plane_off, const float *planes, int max_points, int max_balls, int epochs,
                     float lr, int *active, float *loss, void *stream);
