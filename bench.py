@@ -107,22 +107,70 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU side: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
+_TANK_FRACTION = {}
+
+
+def tank_boundary_fraction(seed=0):
+    """Boundary nodes (fluid nodes with a link into a particle) per lattice
+    node of the settling tank, from the oracle's flags of each cobble alone."""
+    if seed not in _TANK_FRACTION:
+        from oracle import coupling, metaball
+        from paper_2209_10411_gb300 import scenes
+        scene = scenes.config2(seed=seed)
+        nb = 0
+        for spec in scene.particles:
+            side = int(np.ceil(2.0 * metaball.bounding_radius(spec.centers, spec.k))) + 4
+            P = {"centers": spec.centers, "k": spec.k, "pos": np.array([side / 2.0] * 3), "quat": spec.quat}
+            cell, _, _ = coupling.find_links(metaball.flag_nodes((side, side, side), [P]))
+            nb += len(np.unique(cell, axis=0))
+        _TANK_FRACTION[seed] = nb / float(np.prod(scene.shape))
+    return _TANK_FRACTION[seed]
+
+
 class OracleSample:
-    """The oracle's coupled LBM step (flags, links, refill, IBB, momentum
-    exchange, stream-collide) plus the rigid-body update on a crop^3 window
-    around the first cobble of the settling tank; the window is set up once
-    and each call of run() continues the same simulation."""
+    """A bounded sample of the tank's coupled step for the oracle: a crop^3
+    window with the same share of boundary nodes as the whole tank, made by
+    placing the first cobble beside the window so that a cap of its surface
+    reaches in (gravity runs along the window face, so the cap keeps its size
+    while the cobble settles).  Each step is the oracle's coupled LBM step
+    (flags, links, refill, IBB, momentum exchange, stream-collide) plus the
+    rigid-body update; the window is set up once and run() continues it."""
 
     def __init__(self, crop=96, seed=0):
         from oracle import coupling, dem, lbm, metaball
         from paper_2209_10411_gb300 import scenes
         self.mods = (coupling, dem, metaball)
-        spec = scenes.config2(seed=seed).particles[0]
+        scene = scenes.config2(seed=seed)
+        spec = scene.particles[0]
         self.crop = crop
         self.shape = (crop, crop, crop)
-        self.P = {"centers": spec.centers, "k": spec.k, "pos": np.array([crop / 2.0] * 3), "quat": spec.quat,
-                  "vel": np.zeros(3), "omega": np.zeros(3), "mass": 1.0, "volume": 0.4,
-                  "inertia": np.eye(3) * 100.0}
+        self.gravity = tuple(float(g) for g in scene.gravity)
+        # the cobble's own mass properties (unit-spacing quadrature), control
+        # points about its centroid
+        mp = metaball.mass_properties(spec.centers, spec.k, spec.density, h=1.0)
+        P = {"centers": spec.centers - mp["centroid"], "k": spec.k, "quat": spec.quat, "vel": np.zeros(3),
+             "omega": np.zeros(3), "mass": mp["mass"], "volume": mp["volume"], "inertia": mp["inertia"]}
+        self.target = max(1, int(round(tank_boundary_fraction(seed) * crop ** 3)))
+
+        def boundary_nodes(depth):
+            P["pos"] = np.array([-depth, crop / 2.0, crop / 2.0 + 0.37])
+            owner = metaball.flag_nodes(self.shape, [P])
+            xs = np.nonzero((owner >= 0).any(axis=(0, 1)))[0]
+            if len(xs) == 0:
+                return 0
+            # boundary nodes lie within one node of the solid: count on the slab
+            cell, _, _ = coupling.find_links(owner[:, :, :min(crop, int(xs.max()) + 3)])
+            return len(np.unique(cell, axis=0))
+
+        lo, hi = 0.0, metaball.bounding_radius(P["centers"], P["k"])   # cap largest at lo, empty at hi
+        for _ in range(16):
+            mid = 0.5 * (lo + hi)
+            if boundary_nodes(mid) > self.target:
+                lo = mid
+            else:
+                hi = mid
+        self.boundary = boundary_nodes(lo)
+        self.P = P
         self.f = lbm.rest_state(self.shape)
         self.owner_prev = metaball.flag_nodes(self.shape, [self.P])
 
@@ -130,7 +178,7 @@ class OracleSample:
         coupling, dem, metaball = self.mods
         owner = metaball.flag_nodes(self.shape, [self.P])
         self.f, F, T = coupling.coupled_lbm_step(self.f, owner, self.owner_prev, [self.P], 0.8)
-        self.P = dem.integrate(self.P, F[0], T[0], (0.0, 0.0, -1e-5))
+        self.P = dem.integrate(self.P, F[0], T[0], self.gravity)
         self.owner_prev = owner
 
     def run(self, budget_s=0.0):
@@ -146,24 +194,28 @@ class OracleSample:
                 break
         return self.crop ** 3 * steps / dt / 1e6, dt, steps
 
+    def describe(self):
+        return ("FP64 numpy oracle: coupled step + rigid-body update on a %d^3 window holding a cap of one "
+                "cobble with %d boundary nodes, the tank's share (%.2e per node)"
+                % (self.crop, self.boundary, tank_boundary_fraction()))
+
 
 def run_reference(args):
     """The oracle on the host cores, each of the K timed steps one oracle step
-    on a cubic window around a cobble of the tank, the window sized from a
-    calibration so that the whole warm-up + timed run takes about REF_TOTAL_S
-    seconds, between a 64^3 window (the cobble's solid spans 58 nodes along
-    each axis) and a 96^3 one."""
+    on a window of the tank with the tank's share of boundary nodes, the
+    window's edge sized from a calibration so that the whole warm-up + timed
+    run takes about REF_TOTAL_S seconds (between 24 and 96 nodes)."""
     from paper_2209_10411_gb300 import replicas
     rank, world, _ = replicas.rank_env()
     if rank != 0:
         return
     nsteps = max(1, args.steps + args.warmup)
     per_step = min(60.0, REF_TOTAL_S / nsteps)
-    cal = OracleSample(crop=REF_MIN_CROP)
+    cal = OracleSample(crop=32)
     cal.run()                      # first step pays numpy's one-time costs
-    _, dt, _ = cal.run()
-    t_node = dt / REF_MIN_CROP ** 3
-    crop = int(max(REF_MIN_CROP, min(96, (per_step / t_node) ** (1.0 / 3.0))))
+    _, dt, n = cal.run(budget_s=0.5)
+    t_node = dt / n / 32 ** 3
+    crop = int(max(24, min(96, (per_step / t_node) ** (1.0 / 3.0))))
     sampler = OracleSample(crop=crop)
     for _ in range(args.warmup):
         sampler.run()
@@ -172,8 +224,7 @@ def run_reference(args):
         sampler.run()
     wall = time.perf_counter() - t0
     value = crop ** 3 * args.steps / wall / 1e6
-    sample = ("FP64 numpy oracle, one coupled step + rigid-body update per timed step on a %d^3 window around "
-              "one cobble of the tank" % crop)
+    sample = sampler.describe() + ", one oracle step per timed step"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -184,7 +235,6 @@ def run_reference(args):
 
 
 REF_TOTAL_S = 120.0  # the reference arm's warm-up + timed steps, about
-REF_MIN_CROP = 64    # smallest window that holds the whole cobble with a margin
 
 
 METRIC = "coupled-step MLUPS (FP32 vs FP16-store) at stated err; contact solves/s"
@@ -659,10 +709,10 @@ def run_mine(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, n = OracleSample(crop=96).run(budget_s=args.cpu_seconds)
+        sampler = OracleSample(crop=96)
+        v, dt, n = sampler.run(budget_s=args.cpu_seconds)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy oracle: coupled step + rigid-body update on a 96^3 window around one "
-                         "cobble, %d steps in %.1f s" % (n, dt)}
+               "sample": sampler.describe() + ", %d steps in %.1f s" % (n, dt)}
 
     config = {"workload": scene.name, "lattice": list(scene.shape), "particles": npart,
               "metaballs": [int(len(p.k)) for p in scene.particles], "storage": args.storage, "tau": scene.tau,
