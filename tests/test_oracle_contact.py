@@ -1,7 +1,8 @@
 """Pins of the oracle's contact model (no GPU): closed forms for two spheres
 and a sphere at a wall, Newton's stationary point and closest points against
 brute-force dense sampling on tiny metaball sets, and the spring-dashpot law
-against the closed-form restitution and the Coulomb limit."""
+against the closed-form restitution and the Coulomb limit; the broad phase
+at its threshold and against densely sampled solids."""
 import numpy as np
 import pytest
 
@@ -205,3 +206,52 @@ def test_coulomb_limit_sliding_on_a_wall():
     assert abs(Fn - 0.2) < 1e-12
     assert abs(Ft - 0.3 * Fn) < 1e-12
     assert F[0][0] < 0  # friction opposes the sliding of the particle
+
+
+def test_broad_phase_threshold_and_completeness():
+    """Candidates are the pairs with |X_i - X_j| <= R_b,i + R_b,j + margin
+    (two single balls just inside and just outside the threshold), and no pair
+    whose solids (f >= 1, sampled densely) come within the margin is missed."""
+    from oracle import metaball
+    a = _sphere([5.0, 5.0, 5.0], 4.0, 0.5)
+    b = _sphere([5.0 + 6.0 - 1e-9, 5.0, 5.0], 9.0, 0.5)
+    assert contact.broad_phase([a, b], margin=1.0) == [(0, 1)]
+    b["pos"] = np.array([5.0 + 6.0 + 1e-9, 5.0, 5.0])
+    assert contact.broad_phase([a, b], margin=1.0) == []
+
+    rng = np.random.default_rng(5)
+    parts = [_tiny(int(rng.integers(1, 4)), rng.uniform(4.0, 16.0, 3), 100 + s) for s in range(8)]
+    cand = set(contact.broad_phase(parts, margin=1.0))
+    solids = []
+    for P in parts:
+        Rb = metaball.bounding_radius(P["centers"], P["k"])
+        ax = np.arange(-Rb, Rb + 1e-9, 0.2)
+        g = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3) + P["pos"]
+        R = metaball.quat_to_matrix(P["quat"])
+        f = metaball.field(metaball.to_body(g, P["pos"], R), P["centers"], P["k"])
+        solids.append(g[f >= 1.0])
+    close = 0
+    for i in range(len(parts)):
+        for j in range(i + 1, len(parts)):
+            d2 = ((solids[i][::7, None, :] - solids[j][None, ::7, :]) ** 2).sum(-1).min()
+            if np.sqrt(d2) <= 1.0:
+                close += 1
+                assert (i, j) in cand, (i, j)
+    assert close >= 1 and len(cand) > close   # the bounding spheres are conservative
+
+
+def test_wall_candidates_threshold():
+    """A particle is a wall candidate when its centre is within R_b + margin
+    of the halfway wall plane (x = -0.5 or x = n - 0.5); periodic axes have
+    no walls."""
+    shape = (20, 20, 20)
+    for x, expect in ((-0.5 + 4.0 - 1e-9, True), (-0.5 + 4.0 + 1e-9, False),
+                      (19.5 - 4.0 + 1e-9, True), (19.5 - 4.0 - 1e-9, False)):
+        P = _sphere([x, 10.0, 10.0], 9.0, 0.5)          # R_b = 3, margin 1
+        faces = [f for _, f in contact.wall_candidates([P], shape, (False, True, True), margin=1.0)]
+        assert (faces != []) == expect, (x, faces)
+        if expect:
+            assert faces == [0 if x < 10 else 1]
+    P = _sphere([1.0, 1.0, 1.0], 9.0, 0.5)
+    assert contact.wall_candidates([P], shape, (True, True, True), margin=1.0) == []
+    assert sorted(f for _, f in contact.wall_candidates([P], shape, (False, False, False), margin=1.0)) == [0, 2, 4]
