@@ -92,3 +92,27 @@ def test_fitting_and_shape_entry_points_validate_on_host(lib):
     assert L.mi_shape_descriptors(1, N, N, N, N, 8, 0.1, 0.1, N, N, N, N) == B.MI_EINVAL  # NULL arrays
     assert L.mi_shape_descriptors(0, N, N, N, N, 8, 0.1, 0.1, N, N, N, N) == B.MI_OK
     assert L.mi_shape_scratch_bytes(0, 8) == 0 and L.mi_shape_scratch_bytes(2, 8) > 0
+
+
+def test_create_validates_every_config_field_on_host(lib):
+    """Each invalid field of mi_delbm_config is refused with MI_EINVAL and a
+    message naming it, before any CUDA call."""
+    from paper_2209_10411_gb300 import _binding as B
+    cases = [("nx", 0, b"lattice sizes"), ("nz", 70000, b"lattice sizes"), ("rho0", 0.0, b"rho0"),
+             ("storage", 3, b"storage"), ("bb_mode", 7, b"bb_mode"), ("dem_substeps", 0, b"dem_substeps"),
+             ("max_particles", 70000, b"max_particles"), ("max_balls", -1, b"capacities"),
+             ("guess_mode", B.GUESS_LEARNED, b"guess_mode")]
+    for field, value, msg in cases:
+        cfg = B.Config()
+        B.lib.mi_delbm_config_init(ctypes.byref(cfg))
+        setattr(cfg, field, value)
+        h = ctypes.c_void_p()
+        assert B.lib.mi_delbm_create(ctypes.byref(cfg), ctypes.byref(h)) == B.MI_EINVAL, field
+        assert not h.value
+        assert msg in B.lib.mi_delbm_last_error(None), (field, B.lib.mi_delbm_last_error(None))
+    cfg = B.Config()
+    B.lib.mi_delbm_config_init(ctypes.byref(cfg))
+    cfg.nx, cfg.ny, cfg.nz = 2048, 2048, 1024          # 2^32 nodes
+    h = ctypes.c_void_p()
+    assert B.lib.mi_delbm_create(ctypes.byref(cfg), ctypes.byref(h)) == B.MI_EINVAL
+    assert b"2^31-1" in B.lib.mi_delbm_last_error(None)
