@@ -19,7 +19,16 @@ Readings (the paper leaves these open):
   A10  momentum exchange per link: dP = (e_d - u_w) f+_d(x_f, t)
        - (e_{opp d} - u_w) G_{opp d}(x_f, t+1), summed per particle; torque
        arm x_w - X_p.
-  A11  no momentum correction for covered/uncovered nodes.
+  A11  by default no momentum correction for covered/uncovered nodes.  As an
+       option (cover_uncover), the correction of Lorenz et al. (2009), whom
+       the paper cites for its momentum exchange: a node covered this step
+       (fluid at the previous step, solid now) hands the momentum of its
+       stored post-collision populations, J = sum_i e_i f+_i(x, t), to the
+       particle that covers it (F += J, T += (x - X_p) x J); a node
+       uncovered this step takes the momentum of its refilled populations,
+       J' = sum_i e_i f+_i(x_new) after A12, from the particle that uncovered
+       it (F -= J', T -= (x_new - X_p) x J').  With the plain exchange (u_w
+       terms left out) fluid plus particles then conserve momentum exactly.
   A12  refill of a node x_new uncovered this step (fluid now, solid at the
        previous step), applied to its stored post-collision populations before
        streaming: f+_i(x_new) = f+_{opp i}(x_new + e_i) + 6 w_i rho0 (e_i .
@@ -152,7 +161,7 @@ def refill(fpost, owner, owner_prev, particles, periodic=(False, False, False), 
 
 def coupled_lbm_step(fpost, owner, owner_prev, particles, tau, bb_mode="ibb",
                      periodic=(False, False, False), wall_velocity=None, rho0=1.0, force=None,
-                     return_links=False):
+                     return_links=False, cover_uncover=False):
     """One LBM step with particles (A13): refill -> stream (domain walls,
     IBB/Ladd on particle links) -> collide -> momentum exchange.
 
@@ -221,6 +230,21 @@ def coupled_lbm_step(fpost, owner, owner_prev, particles, tau, bb_mode="ibb",
         m = p == pi
         F[pi] = dP[m].sum(0)
         T[pi] = dT[m].sum(0)
+    if cover_uncover:
+        # reading A11, optional: momentum of covered and uncovered nodes
+        covered = (owner >= 0) & (owner_prev < 0)
+        for sel, own, src, sign in ((covered, owner, fpost, 1.0), (new, owner_prev, fr, -1.0)):
+            zz, yy, xx = np.nonzero(sel)
+            if len(xx) == 0:
+                continue
+            J = (_EF.T @ src[:, zz, yy, xx]).T                      # (n, 3)
+            pid = own[zz, yy, xx]
+            xyz = np.stack([xx, yy, zz], axis=1).astype(np.float64)
+            for pi in np.unique(pid):
+                m = pid == pi
+                arm = xyz[m] - np.asarray(particles[pi]["pos"], dtype=np.float64)
+                F[pi] += sign * J[m].sum(0)
+                T[pi] += sign * np.cross(arm, J[m]).sum(0)
     if return_links:
         links = {"cell": cell, "dir": d, "particle": p, "q": q, "G": G, "f_d": f_d, "u_w": u_w, "dP": dP}
         return out, F, T, links

@@ -217,6 +217,54 @@ def test_momentum_and_mass_balance(mode):
     assert np.isfinite(T).all()
 
 
+@pytest.mark.parametrize("mode", ["ibb", "ladd"])
+def test_cover_uncover_momentum_closes_the_balance(mode):
+    # reading A11's option: a particle that moves 0.8 lu covers and uncovers
+    # nodes; fluid momentum is disturbed only within 8 lu of it, so the
+    # periodic box's edges stay at rest and angular momentum about the origin
+    # is also a lattice invariant of streaming and collision.  With the
+    # covered nodes' momentum handed to the particle and the uncovered
+    # nodes' momentum taken from it, fluid + particle conserve both, with
+    # the plain per-link exchange: dP_link = e_d f_d - e_j G, arm x_f.
+    shape = (24, 24, 24)
+    X = np.array([12.3, 11.8, 12.4])
+    dX = np.array([0.7, 0.35, -0.2])
+    P = _blob(X, vel=(0.03, 0.015, -0.01), omega=(0.004, -0.003, 0.006))
+    Pp = dict(P, pos=X - dX)
+    owner = metaball.flag_nodes(shape, [P])
+    owner_prev = metaball.flag_nodes(shape, [Pp])
+    solid, new = coupling.classify(owner, owner_prev)
+    covered = (owner >= 0) & (owner_prev < 0)
+    assert new.sum() > 10 and covered.sum() > 10
+    zz, yy, xx = np.meshgrid(np.arange(24), np.arange(24), np.arange(24), indexing="ij")
+    r2 = (xx - X[0]) ** 2 + (yy - X[1]) ** 2 + (zz - X[2]) ** 2
+    bump = np.where(r2 < 64.0, np.exp(-r2 / 20.0), 0.0)
+    u = np.stack([0.02 * bump, -0.015 * bump, 0.01 * bump])
+    f0 = lbm.equilibrium(np.ones((24, 24, 24)), u)
+    per = (True, True, True)
+    out0, F0, T0, L = coupling.coupled_lbm_step(f0, owner, owner_prev, [P], 0.8, bb_mode=mode, periodic=per,
+                                               return_links=True)
+    out1, F1, T1 = coupling.coupled_lbm_step(f0, owner, owner_prev, [P], 0.8, bb_mode=mode, periodic=per,
+                                             cover_uncover=True)
+    assert np.array_equal(out0[:, owner < 0], out1[:, owner < 0])   # the fluid step is unchanged
+    Ef = E.astype(float)
+    pos = np.stack([xx, yy, zz], axis=-1).astype(float)
+
+    def moments(f, fluid):
+        j = np.einsum("ia,in->na", Ef, f[:, fluid])
+        return j.sum(0), np.cross(pos[fluid], j).sum(0)
+
+    P0, L0 = moments(f0, owner_prev < 0)
+    P1, L1 = moments(out1, owner < 0)
+    ed, ej = Ef[L["dir"]], Ef[OPP[L["dir"]]]
+    plain = ed * L["f_d"][:, None] - ej * L["G"][:, None]
+    xf = L["cell"].astype(float)
+    dF, dT = F1[0] - F0[0], T1[0] - T0[0]
+    assert np.abs(dF).max() > 1e-4                                  # the terms are not empty
+    assert np.abs((P1 - P0) + plain.sum(0) + dF).max() < 1e-12
+    assert np.abs((L1 - L0) + np.cross(xf, plain).sum(0) + dT + np.cross(P["pos"], dF)).max() < 1e-11
+
+
 def test_mass_properties_of_a_sphere():
     k = 16.0
     mp = metaball.mass_properties(np.zeros((1, 3)), np.array([k]), 2.5, h=0.25)
