@@ -381,6 +381,23 @@ enum {
  * Discards captured graphs.  Errors: MI_EINVAL (unknown flags). */
 mi_status mi_delbm_set_schedule(mi_delbm *h, int flags);
 
+/* Momentum rule flags. */
+enum {
+  /* the covered/uncovered correction of Lorenz et al. (2009), whom Sec.
+   * 2.3.2 cites with Chen (2013) for its momentum exchange: a node that a
+   * particle covers this step (fluid before, solid now) hands the momentum
+   * sum_i e_i f+_i(x, t) of its post-collision populations to that particle,
+   * and a node that a particle uncovers takes the momentum of its refilled
+   * populations from it; the forces and torques (arm x - X_p) join the
+   * hydrodynamic sums that mi_delbm_forces returns.  The step that first
+   * flags a particle (after mi_delbm_add_particle) covers nothing.  Off by
+   * default (the paper describes no such term) */
+  MI_MOMENTUM_COVER_UNCOVER = 1
+};
+/* Set the momentum rules (an OR of MI_MOMENTUM_* flags; 0 = default).
+ * Discards captured graphs.  Errors: MI_EINVAL (unknown flags). */
+mi_status mi_delbm_set_momentum_rules(mi_delbm *h, int flags);
+
 /* Set the launch shapes directly (what mi_delbm_autotune chooses): bulk
  * kernel threads per block along x (32..256, a multiple of 32; at most 128
  * with pairs), rows per thread (1 or 2), paired nodes (0: no; 1 or 2: two

@@ -131,6 +131,7 @@ _sig("mi_mlp_infer", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_mlp_infer_mma", c_int, _P, _P, c_int, _P, _P)
 _sig("mi_delbm_set_guess", c_int, _P, c_int, _P)
 _sig("mi_delbm_set_schedule", c_int, _P, c_int)
+_sig("mi_delbm_set_momentum_rules", c_int, _P, c_int)
 _sig("mi_shape_scratch_bytes", ctypes.c_size_t, c_int, c_int)
 _sig("mi_shape_descriptors", c_int, c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P)
 _sig("mi_ga_scratch_bytes", ctypes.c_size_t, c_int, c_int)
@@ -140,6 +141,7 @@ _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P,
 
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
 SCHEDULE_OVERLAP_BOUNDARY, SCHEDULE_UNFUSED_DEM = 1, 2
+MOMENTUM_COVER_UNCOVER = 1
 
 
 def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):
@@ -498,6 +500,11 @@ class Simulation:
         sequence per substep instead of the fused substep kernel."""
         flags = (SCHEDULE_OVERLAP_BOUNDARY if overlap_boundary else 0) | (SCHEDULE_UNFUSED_DEM if unfused_dem else 0)
         self._check(lib.mi_delbm_set_schedule(self.h, flags))
+
+    def set_momentum_rules(self, cover_uncover=False):
+        """cover_uncover: the momentum of nodes a particle covers or uncovers
+        this step joins its hydrodynamic force and torque."""
+        self._check(lib.mi_delbm_set_momentum_rules(self.h, MOMENTUM_COVER_UNCOVER if cover_uncover else 0))
 
     def set_graphs(self, on):
         self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))

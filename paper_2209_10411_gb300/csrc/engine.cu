@@ -159,6 +159,8 @@ ParticleLaunch mi_delbm::particle_launch() const {
   L.link_dir = link_dir;
   L.link_q = link_q;
   L.new_cell = new_cell;
+  L.cov_cell = cov_cell;
+  L.cover_uncover = cover_uncover ? 1 : 0;
   L.cap_bc = cap_bc;
   L.cap_links = cap_links;
   L.cap_new = cap_new;
@@ -556,7 +558,8 @@ mi_status mi_delbm::check_status(bool clear) {
     return fail(MI_ECAPACITY, "a device list overflowed during the step (status bits " + std::to_string(bad) +
                                   "; boundary nodes " + std::to_string(c.n_bc) + "/" + std::to_string(cap_bc) +
                                   ", links " + std::to_string(c.n_links) + "/" + std::to_string(cap_links) +
-                                  ", uncovered " + std::to_string(c.n_new) + "/" + std::to_string(cap_new) + ")");
+                                  ", uncovered " + std::to_string(c.n_new) + "/" + std::to_string(cap_new) +
+                                  ", covered " + std::to_string(c.n_cov) + "/" + std::to_string(cap_new) + ")");
   }
   return MI_OK;
 }
@@ -596,7 +599,7 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   links = links > cap_links ? links : cap_links;
   nnew = nnew > cap_new ? nnew : cap_new;
   dfree(bc_cell); dfree(bc_mask); dfree(bc_loff); dfree(link_bc); dfree(link_p); dfree(link_dir);
-  dfree(link_q); dfree(new_cell); dfree(bc_tmp);
+  dfree(link_q); dfree(new_cell); dfree(cov_cell); dfree(bc_tmp);
   bc_cell = (uint32_t*)dalloc(4ull * bc);
   bc_mask = (uint32_t*)dalloc(4ull * bc);
   bc_loff = (uint32_t*)dalloc(4ull * bc);
@@ -605,8 +608,10 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   link_dir = (uint8_t*)dalloc(1ull * links);
   link_q = (float*)dalloc(4ull * links);
   new_cell = (uint32_t*)dalloc(4ull * nnew);
+  cov_cell = (uint32_t*)dalloc(4ull * nnew);
   bc_tmp = dalloc(19ull * store_bytes(cfg.storage) * bc);
-  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell || !bc_tmp) {
+  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell || !cov_cell ||
+      !bc_tmp) {
     cap_bc = cap_links = cap_new = 0;
     return fail(MI_ENOMEM, "link lists: device allocation failed");
   }
@@ -958,6 +963,15 @@ mi_status mi_delbm_set_schedule(mi_delbm* h, int flags) {
   if (h->overlap_boundary != ob || h->unfused_dem != ud) h->invalidate_graphs();
   h->overlap_boundary = ob;
   h->unfused_dem = ud;
+  return MI_OK;
+}
+
+mi_status mi_delbm_set_momentum_rules(mi_delbm* h, int flags) {
+  if (!h) return MI_EINVAL;
+  if (flags & ~MI_MOMENTUM_COVER_UNCOVER) return h->fail(MI_EINVAL, "mi_delbm_set_momentum_rules: unknown flags");
+  const bool cu = (flags & MI_MOMENTUM_COVER_UNCOVER) != 0;
+  if (h->cover_uncover != cu) h->invalidate_graphs();
+  h->cover_uncover = cu;
   return MI_OK;
 }
 

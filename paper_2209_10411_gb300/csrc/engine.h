@@ -89,10 +89,12 @@ struct mi_delbm {
   uint8_t* link_dir = nullptr;
   float* link_q = nullptr;
   uint32_t* new_cell = nullptr;
+  uint32_t* cov_cell = nullptr;     // nodes covered this step (cover/uncover rule; capacity cap_new)
   unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
   void* bc_tmp = nullptr;            // 19 stored values per boundary node (overlapped schedule)
   bool overlap_boundary = false;     // boundary nodes computed beside the bulk kernel, scattered after it
   bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
+  bool cover_uncover = false;        // covered/uncovered-node momentum joins the hydrodynamic sums
   int blocks_per_particle = 1;
 
   TuneChoice tune;

@@ -422,7 +422,10 @@ cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s) {
 //   f+_i(x_new) = f+_opp(i)(x_new + e_i) + 6 w_i rho0 (e_i . u_new)
 // when x_new + e_i is a fluid node that was also fluid at the previous step,
 // else f_eq,i(rho0, u_new); u_new is the rigid velocity at x_new of the
-// particle that covered it.  One thread per uncovered node.
+// particle that covered it.  One thread per uncovered node.  With the
+// cover/uncover rule the same launch also moves node momenta: an uncovered
+// node's refilled momentum is taken from its particle, a covered node's
+// post-collision momentum is given to the particle that covers it.
 // ---------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ bool nbr_wrap(int x, int y, int z, int dx, int dy, int dz, const LatticeGeom& g,
@@ -479,6 +482,22 @@ __device__ __forceinline__ void moments_at(const typename Store<ST>::T* __restri
 }
 }  // namespace
 
+namespace {
+// Cover/uncover rule: a node's population momentum J (FP32) and its torque
+// about the particle's position, sign * (J, (x - X_p) x J), added to the
+// particle's fixed-point hydrodynamic sums.
+__device__ __forceinline__ void add_node_momentum(long long* facc, const DevParticle* Ps, uint32_t p, int x, int y,
+                                                  int z, const float J[3], float sign) {
+  const DevParticle& P = Ps[p];
+  const float r0 = (float)(x - P.pos[0]), r1 = (float)(y - P.pos[1]), r2 = (float)(z - P.pos[2]);
+  const float v[6] = {J[0], J[1], J[2], r1 * J[2] - r2 * J[1], r2 * J[0] - r0 * J[2], r0 * J[1] - r1 * J[0]};
+  for (int k = 0; k < 6; ++k) {
+    const long long iv = __float2ll_rn(sign * v[k] * 1099511627776.0f);
+    atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * (size_t)p + k), (unsigned long long)iv);
+  }
+}
+}  // namespace
+
 template <int ST>
 __global__ void __launch_bounds__(128) k_refill(BoundaryLaunch L) {
   using T = typename Store<ST>::T;
@@ -490,10 +509,12 @@ __global__ void __launch_bounds__(128) k_refill(BoundaryLaunch L) {
     const long long c = L.pl.new_cell[k];
     int x, y, z;
     coords(c, g, x, y, z);
-    const DevParticle& P = L.pl.P[L.pl.owner_prev[c]];
+    const uint32_t pid = L.pl.owner_prev[c];
+    const DevParticle& P = L.pl.P[pid];
     float u[3];
     rigid_u(P, x, y, z, u);
     const float usq15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    float J[3] = {0.f, 0.f, 0.f};  // momentum of the refilled populations (sum e_i (f_i - w_i))
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
       const float eu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
@@ -506,7 +527,30 @@ __global__ void __launch_bounds__(128) k_refill(BoundaryLaunch L) {
         h = wq(i) * (rho0 - 1.0f) + wq(i) * rho0 * (3.0f * eu + 4.5f * eu * eu - usq15);
       }
       Store<ST>::put(A + i * g.plane + c, i, h);
+      J[0] += cx(i) * h;
+      J[1] += cy(i) * h;
+      J[2] += cz(i) * h;
     }
+    // cover/uncover rule: the particle that uncovered the node gives up this momentum
+    if (L.pl.cover_uncover) add_node_momentum(L.pl.facc, L.pl.P, pid, x, y, z, J, -1.0f);
+  }
+  if (!L.pl.cover_uncover) return;
+  // covered nodes: the momentum of their post-collision populations f+(t)
+  // (still in A: they were fluid) goes to the particle that covered them
+  const unsigned nc = min(L.pl.ctr->n_cov, L.pl.cap_new);
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
+    const long long c = L.pl.cov_cell[k];
+    int x, y, z;
+    coords(c, g, x, y, z);
+    float J[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      const float h = Store<ST>::dev(A + i * g.plane + c, i);
+      J[0] += cx(i) * h;
+      J[1] += cy(i) * h;
+      J[2] += cz(i) * h;
+    }
+    add_node_momentum(L.pl.facc, L.pl.P, L.pl.owner_cur[c], x, y, z, J, 1.0f);
   }
 }
 

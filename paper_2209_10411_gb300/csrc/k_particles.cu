@@ -115,6 +115,7 @@ __global__ void k_prologue(ParticleLaunch L) {
     L.ctr->n_bc = 0;
     L.ctr->n_links = 0;
     L.ctr->n_new = 0;
+    L.ctr->n_cov = 0;
   }
   if (p >= L.np) return;
   DevParticle& P = L.P[p];
@@ -246,10 +247,12 @@ cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Classification over each particle's old and new boxes widened by 2: solid,
 // boundary (fluid with a solid neighbour; 18-bit link mask), uncovered (fluid
-// now, solid at the previous step).  Boxes may overlap: every block writes the
-// same class for a node, and a per-node generation stamp lets exactly one
-// block append it to the boundary / uncovered lists.
+// now, solid at the previous step), and with the cover/uncover rule covered
+// (solid now, fluid at the previous step).  Boxes may overlap: every block
+// writes the same class for a node, and a per-node generation stamp lets
+// exactly one block append it to the boundary / uncovered / covered lists.
 // ---------------------------------------------------------------------------
+template <bool COV>
 __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
   const DevParticle& P = L.P[blockIdx.y];
   int lo[3], ext[3];
@@ -303,8 +306,11 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
       }
     }
     const bool isnew = !solid && was;
+    // covered: listed for the cover/uncover rule only, and not in the step
+    // that first flags the covering particle (it was not there before)
+    const bool iscov = COV && solid && !was && L.P[L.owner_cur[c]].lo_hist[L.prev_buf][0] != BOX_NONE;
     L.cls[c] = (uint8_t)((solid ? CLS_SOLID : 0) | (mask ? CLS_BOUNDARY : 0) | (isnew ? CLS_NEW : 0));
-    if (!(mask || isnew)) continue;
+    if (!(mask || isnew || iscov)) continue;
     if (atomicExch(L.stamp + c, gen) == gen) continue;  // another block listed it
     // list appends aggregated over the lanes that got here: one atomic per
     // counter and warp (all boundary nodes share the counters, and
@@ -330,6 +336,17 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
       const unsigned k = base_new + __popc(newm & below);
       if (k < L.cap_new) L.new_cell[k] = (uint32_t)c;
       else atomicOr(&L.ctr->status, STATUS_NEW_OVERFLOW);
+    }
+    if constexpr (COV) {
+      const unsigned covm = grp.ballot(iscov);
+      unsigned base_cov = 0;
+      if (grp.thread_rank() == 0 && covm) base_cov = atomicAdd(&L.ctr->n_cov, (unsigned)__popc(covm));
+      base_cov = grp.shfl(base_cov, 0);
+      if (iscov) {
+        const unsigned k = base_cov + __popc(covm & below);
+        if (k < L.cap_new) L.cov_cell[k] = (uint32_t)c;
+        else atomicOr(&L.ctr->status, STATUS_NEW_OVERFLOW);
+      }
     }
     if (mask) {
       const unsigned bi = base_bc + __popc(bcm & below);
@@ -362,7 +379,8 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
 cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
   dim3 grid(L.blocks_per_particle, L.np);
-  k_classify<<<grid, 256, 0, s>>>(L);
+  if (L.cover_uncover) k_classify<true><<<grid, 256, 0, s>>>(L);
+  else k_classify<false><<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 

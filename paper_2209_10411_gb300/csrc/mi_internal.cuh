@@ -208,7 +208,7 @@ struct DevCounters {
   unsigned int status;   // STATUS_* bits, sticky until read
   unsigned int n_contacts;
   unsigned int n_pairs;
-  unsigned int pad;
+  unsigned int n_cov;    // covered nodes (cover/uncover rule)
 };
 constexpr unsigned STATUS_BC_OVERFLOW = 1u, STATUS_LINK_OVERFLOW = 2u, STATUS_NEW_OVERFLOW = 4u,
                    STATUS_PAIR_OVERFLOW = 8u, STATUS_CONTACT_OVERFLOW = 16u, STATUS_MOVED_TOO_FAR = 32u,
@@ -233,7 +233,9 @@ struct ParticleLaunch {
   uint8_t* link_dir;
   float* link_q;
   uint32_t* new_cell;
+  uint32_t* cov_cell;         // covered nodes, listed only when cover_uncover (capacity cap_new)
   unsigned cap_bc, cap_links, cap_new;
+  int cover_uncover;
   int blocks_per_particle;
   LatticeGeom g;
 };

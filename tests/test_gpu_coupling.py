@@ -42,7 +42,7 @@ def _initial_flow(shape, seed, umax=0.03):
     return (feq * (1.0 + 0.01 * noise)).astype(np.float32).astype(np.float64)
 
 
-def _run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM):
+def _run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM, cover_uncover=False):
     nx, ny, nz = shape
     sim = B.Simulation(nx, ny, nz, tau=TAU, bb_mode=(B.BB_LADD if mode == "ladd" else B.BB_IBB), storage=storage)
     for Pp in parts_prev:
@@ -50,6 +50,8 @@ def _run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_L
                          Pp["vel"], Pp["omega"],
                          mass_props={"mass": Pp["mass"], "volume": Pp["volume"], "inertia": Pp["inertia"]})
     sim.step_phases(1)  # flags at the previous pose
+    if cover_uncover:
+        sim.set_momentum_rules(cover_uncover=True)
     for i, P in enumerate(parts):
         sim.set_particle_state(i, P["pos"], P["quat"], P["vel"], P["omega"])
     sim.set_populations(f0.astype(np.float32))
@@ -122,6 +124,44 @@ def test_one_step_moving_particle(mode):
     owner = metaball.flag_nodes(shape, [P])
     assert coupling.classify(owner, owner_prev)[1].sum() > 10  # uncovered nodes are exercised
     _compare_step(sim, shape, [Pp], [P], f0, mode)
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", ["ibb", "ladd"])
+def test_cover_uncover_rule(mode):
+    """The optional cover/uncover momentum (Lorenz et al. 2009): one step of a
+    particle that moves 0.8 lu; force and torque against the oracle's with
+    the rule, at the same bar as the plain exchange, the rule's share of the
+    force well above that bar, and the populations unchanged by it."""
+    B = binding()
+    shape = (40, 36, 44)
+    rng = np.random.default_rng(7)
+    c, k, _ = scenes.blob_4(rng)
+    spec = scenes.ParticleSpec(c, k, 2.5, 1.0, None, None)
+    q0 = scenes.random_unit_quaternion(rng)
+    X = np.array([20.3, 17.6, 22.1])
+    dX = np.array([0.7, 0.35, -0.2])
+    P = _prepared(spec, X, q0, (0.02, -0.01, 0.015), (0.004, -0.003, 0.002))
+    Pp = dict(P, pos=X - dX, quat=scenes.f32(q0 + np.array([0.0, 0.05, -0.03, 0.02])))
+    f0 = _initial_flow(shape, seed=3)
+    sim = _run_one_step(B, shape, [Pp], [P], f0, mode, cover_uncover=True)
+    owner_prev = metaball.flag_nodes(shape, [Pp])
+    owner = metaball.flag_nodes(shape, [P])
+    assert ((owner >= 0) & (owner_prev < 0)).sum() > 10 and coupling.classify(owner, owner_prev)[1].sum() > 10
+    ref, F, T, L = coupling.coupled_lbm_step(f0, owner, owner_prev, [P], TAU, bb_mode=mode, return_links=True,
+                                             cover_uncover=True)
+    _, F0, T0 = coupling.coupled_lbm_step(f0, owner, owner_prev, [P], TAU, bb_mode=mode)
+    got = sim.get_populations().astype(np.float64)
+    fl = owner < 0
+    assert (np.abs(got[:, fl] - ref[:, fl]) / np.abs(ref[:, fl])).max() < 1e-5
+    fr = sim.forces()
+    qw = np.full(len(L["q"]), 0.5) if mode == "ladd" else L["q"]
+    arm = L["cell"] + qw[:, None] * E[L["dir"]] - X
+    scaleF = max(np.linalg.norm(F[0]), 1e-3 * np.abs(L["dP"]).sum())
+    scaleT = max(np.linalg.norm(T[0]), 1e-3 * np.abs(np.cross(arm, L["dP"])).sum())
+    assert np.linalg.norm(F[0] - F0[0]) > 10 * 1e-4 * scaleF        # the rule is exercised
+    assert np.linalg.norm(fr["F_hydro"][0] - F[0]) <= 1e-4 * scaleF, (fr["F_hydro"][0], F[0])
+    assert np.linalg.norm(fr["T_hydro"][0] - T[0]) <= 1e-4 * scaleT, (fr["T_hydro"][0], T[0])
     sim.close()
 
 
