@@ -724,7 +724,8 @@ def run_mine(args):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": traffic,
                         "kernel": bulk_name, "peak_kind": peak_kind,
-                        "algorithmic_bytes_per_launch": alg_bytes},
+                        "algorithmic_bytes_per_launch": alg_bytes,
+                        "kernel_mlups": ncell / (bulk_ms / bulk_n * 1e-3) / 1e6 if bulk_n else None},
            "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
            "graphs": not args.no_graphs, "tuning": tuning,
            "storage_variants": variants,
