@@ -12,7 +12,8 @@ class OracleState:
     """Populations, particle states, previous owners and contact springs."""
 
     def __init__(self, shape, f, particles, tau=0.8, periodic=(False, False, False), wall_velocity=None,
-                 gravity=(0.0, 0.0, 0.0), rho0=1.0, bb_mode="ibb", dem_substeps=1, contact_params=None):
+                 gravity=(0.0, 0.0, 0.0), rho0=1.0, bb_mode="ibb", dem_substeps=1, contact_params=None,
+                 cover_uncover=False):
         self.shape = tuple(shape)
         self.f = np.asarray(f, dtype=np.float64)
         self.particles = [dict(P) for P in particles]
@@ -23,6 +24,7 @@ class OracleState:
         self.rho0 = rho0
         self.bb_mode = bb_mode
         self.dem_substeps = dem_substeps
+        self.cover_uncover = cover_uncover   # reading A11's option (coupling.coupled_lbm_step)
         self.contact_params = contact_params or {"kn": 1.0, "kt": 2.0 / 7.0, "eta_n": 0.0, "eta_t": 0.0,
                                                  "mu_s": 0.4}
         self.owner_prev = np.full((shape[2], shape[1], shape[0]), -1, dtype=np.int64)
@@ -39,7 +41,7 @@ def step(S):
     owner = metaball.flag_nodes(S.shape, S.particles)
     S.f, S.F_hydro, S.T_hydro = coupling.coupled_lbm_step(
         S.f, owner, S.owner_prev, S.particles, S.tau, bb_mode=S.bb_mode, periodic=S.periodic,
-        wall_velocity=S.wall_velocity, rho0=S.rho0)
+        wall_velocity=S.wall_velocity, rho0=S.rho0, cover_uncover=S.cover_uncover)
     S.owner_prev = owner
     dt = 1.0 / S.dem_substeps
     for _ in range(S.dem_substeps):
