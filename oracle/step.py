@@ -28,6 +28,10 @@ class OracleState:
         self.contact_params = contact_params or {"kn": 1.0, "kt": 2.0 / 7.0, "eta_n": 0.0, "eta_t": 0.0,
                                                  "mu_s": 0.4}
         self.owner_prev = np.full((shape[2], shape[1], shape[0]), -1, dtype=np.int64)
+        if cover_uncover:
+            # the particles are not inserted into the fluid: the first step
+            # covers nothing (without the option the two starts are the same)
+            self.owner_prev = metaball.flag_nodes(self.shape, self.particles)
         self.history = {}
         self.F_hydro = np.zeros((len(particles), 3))
         self.T_hydro = np.zeros((len(particles), 3))

@@ -50,3 +50,22 @@ def test_resting_particle_substeps_closed_form(n_sub):
     assert np.allclose(Pn["pos"], X + a * (n_sub + 1) / (2.0 * n_sub), rtol=0, atol=1e-14)
     assert np.allclose(Pn["quat"], P["quat"], rtol=0, atol=1e-15)
     assert np.abs(Pn["omega"]).max() < 1e-15
+
+
+def test_cover_uncover_start_covers_nothing():
+    """With the cover/uncover option the particles are not inserted into the
+    fluid: the first step of a resting particle in moving fluid has the same
+    hydrodynamic force as without the option."""
+    shape = (16, 16, 16)
+    P = {"centers": np.zeros((1, 3)), "k": np.array([6.0]), "pos": np.array([8.2, 7.9, 8.1]),
+         "quat": np.array([1.0, 0.0, 0.0, 0.0]), "vel": np.zeros(3), "omega": np.zeros(3), "skin": 0.5,
+         "mass": 100.0, "volume": 40.0, "inertia": np.eye(3) * 200.0}
+    u = np.zeros((3, 16, 16, 16))
+    u[0] = 0.02
+    f0 = lbm.equilibrium(np.ones((16, 16, 16)), u)
+    a = step.OracleState(shape, f0, [P], periodic=(True, True, True))
+    b = step.OracleState(shape, f0, [P], periodic=(True, True, True), cover_uncover=True)
+    step.step(a)
+    step.step(b)
+    assert np.abs(a.F_hydro).max() > 1e-3
+    assert np.array_equal(a.F_hydro, b.F_hydro) and np.array_equal(a.T_hydro, b.T_hydro)
