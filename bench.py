@@ -107,6 +107,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU side: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
+def cores_used(cpu_s, wall_s):
+    """Threads a timed CPU region kept busy: process CPU time (all threads)
+    over wall time, at least 1."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+
+
 _TANK_FRACTION = {}
 
 
@@ -185,6 +191,7 @@ class OracleSample:
         """One step or more, until about budget_s seconds of CPU work;
         returns (MLUPS, seconds, steps)."""
         t0 = time.perf_counter()
+        c0 = time.process_time()
         steps = 0
         while True:
             self.step()
@@ -192,6 +199,7 @@ class OracleSample:
             dt = time.perf_counter() - t0
             if dt >= budget_s:
                 break
+        self.cores = cores_used(time.process_time() - c0, dt)
         return self.crop ** 3 * steps / dt / 1e6, dt, steps
 
     def describe(self):
@@ -220,16 +228,18 @@ def run_reference(args):
     for _ in range(args.warmup):
         sampler.run()
     t0 = time.perf_counter()
+    c0 = time.process_time()
     for _ in range(args.steps):
         sampler.run()
     wall = time.perf_counter() - t0
+    cores = cores_used(time.process_time() - c0, wall)
     value = crop ** 3 * args.steps / wall / 1e6
     sample = sampler.describe() + ", one oracle step per timed step"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": CONFIG,
-           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -494,9 +504,12 @@ def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
     # oracle: one fit of the same size, a few epochs, scaled to the whole job
     o_ep = 3
     t0 = time.perf_counter()
+    c0 = time.process_time()
     ogs.descend(hulls[0].astype(np.float64), models[0][:, :3].astype(np.float64), models[0][:, 3].astype(np.float64),
                 o_ep, 1e-4)
-    o_s = (time.perf_counter() - t0) * (2 * epochs / o_ep) * (sum(nb) / nb[0])
+    o_wall = time.perf_counter() - t0
+    o_cores = cores_used(time.process_time() - c0, o_wall)
+    o_s = o_wall * (2 * epochs / o_ep) * (sum(nb) / nb[0])
     ls = loss.cpu().numpy()
     return {"value": n_fits / (ms * 1e-3), "unit": "fits/s", "ms": ms, "fits": n_fits, "hull_points": m,
             "control_points": [int(min(nb)), int(max(nb))], "epochs_per_descent": epochs,
@@ -504,7 +517,7 @@ def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
                          "frac": tflops / FP32_ALU_PEAK_TFLOPS,
                          "flop_per_point_ball_epoch": GS_FLOP_PER_PAIR_EPOCH},
             "loss_after_second_over_first_descent_median": float(np.median(ls[:, 1] / np.maximum(ls[:, 0], 1e-30))),
-            "cpu_baseline": {"value": n_fits / o_s, "unit": "fits/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": n_fits / o_s, "unit": "fits/s", "cores": o_cores, "kind": "oracle",
                              "sample": "FP64 numpy oracle: %d epochs of one fit, scaled by epochs and control "
                                        "points" % o_ep}}
 
@@ -553,8 +566,10 @@ def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21)
     evals = n_ind * (generations + 1)
     tflops = evals * m * n_genes * 9 / (ms * 1e-3) / 1e12
     t0 = time.perf_counter()
+    c0 = time.process_time()
     oga.fitness(H, pop[0].cpu().numpy())
     o_s = time.perf_counter() - t0
+    o_cores = cores_used(time.process_time() - c0, o_s)
     return {"value": generations / (ms * 1e-3), "unit": "generations/s", "ms": ms, "individuals": n_ind,
             "genes": n_genes, "hull_points": m, "generations": generations,
             "fitness_evals_per_s": evals / (ms * 1e-3),
@@ -562,7 +577,7 @@ def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21)
                          "frac": tflops / FP32_ALU_PEAK_TFLOPS, "flop_per_point_gene": 9,
                          "note": "whole generation timed; the fitness kernel's work only"},
             "best_fitness_initial": f0, "best_fitness_final": float(fit[0].item()),
-            "cpu_baseline": {"value": 1.0 / o_s, "unit": "fitness evals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": 1.0 / o_s, "unit": "fitness evals/s", "cores": o_cores, "kind": "oracle",
                              "sample": "FP64 numpy oracle: one individual's fitness"}}
 
 
@@ -585,13 +600,16 @@ def shape_bench(B, scenes, n=300, h=0.25, seed=0):
                 for c, k in models)
     # the oracle on the first model at twice the spacing (one eighth of the cells), scaled back
     t1 = time.perf_counter()
+    c1 = time.process_time()
     oshape.descriptors(models[0][0], models[0][1], 2 * h)
-    o_s = (time.perf_counter() - t1) * 8.0
+    o_wall = time.perf_counter() - t1
+    o_cores = cores_used(time.process_time() - c1, o_wall)
+    o_s = o_wall * 8.0
     return {"value": n / dt, "unit": "particles/s", "s": dt, "particles": n, "h": h,
             "cell_evaluations_per_s": cells / dt, "note": "host wall clock of the binding call (copies included)",
             "sphericity_median": float(np.median([d["sphericity"] for d in out])),
             "csf_median": float(np.median([d["csf"] for d in out])),
-            "cpu_baseline": {"value": 1.0 / o_s, "unit": "particles/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": 1.0 / o_s, "unit": "particles/s", "cores": o_cores, "kind": "oracle",
                              "sample": "numpy oracle: the first particle at twice the spacing, time x 8"}}
 
 
@@ -711,7 +729,7 @@ def run_mine(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sampler = OracleSample(crop=96)
         v, dt, n = sampler.run(budget_s=args.cpu_seconds)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": "MLUPS", "cores": sampler.cores, "kind": "oracle",
                "sample": sampler.describe() + ", %d steps in %.1f s" % (n, dt)}
 
     config = {"workload": scene.name, "lattice": list(scene.shape), "particles": npart,
