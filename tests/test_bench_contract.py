@@ -26,3 +26,18 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_stated_error_matches_the_precision_test():
+    """The bench line's stated accuracy per storage is the bound the GPU
+    precision test asserts."""
+    import ast
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "tests", "test_gpu_precision.py")).read()
+    node = next(n for n in ast.parse(src).body
+                if isinstance(n, ast.Assign) and getattr(n.targets[0], "id", "") == "BOUNDS")
+    bounds = ast.literal_eval(node.value)
+    for st, (bu, bf) in bounds.items():
+        assert bench.STATED_ERROR[st]["velocity_rel_l2_max"] == bu
+        assert bench.STATED_ERROR[st]["force_rel_max"] == bf
