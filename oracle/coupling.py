@@ -159,6 +159,48 @@ def refill(fpost, owner, owner_prev, particles, periodic=(False, False, False), 
     return out
 
 
+def bounce_back_populations(fr, cell, d, q, u_w, solid, periodic=(False, False, False), bb_mode="ibb",
+                            rho0=1.0):
+    """The population G_{opp d}(x_f, t+1) that the wall returns on each link
+    (x_f, d) (Sec. 2.3.2; readings A8, A9).
+
+    fr: post-collision populations f+(t) after the refill, (19, nz, ny, nx);
+    cell (n, 3) as (x, y, z), d (n,), q (n,): the links and their wall
+    fractions; u_w (n, 3): the wall velocity at x_w; solid: node mask (nz, ny,
+    nx) of the current flags.
+
+    IBB (Eqs. eqneq1, eqneq2, neqd): G = f^eq_d(rho_f, u_d) + [f+_d(x_f) -
+    f^eq_d(rho_f, u_f)] + 6 w_d rho0 (e_{opp d} . u_w), with rho_f, u_f the
+    moments of f+(x_f), u_ff those of x_ff = x_f - e_d when it is a fluid node
+    inside the domain (else u_f), and u_d from `departure_velocity`.
+    Ladd: G = f+_d(x_f) + 6 w_d rho0 (e_{opp d} . u_w).
+    """
+    nz, ny, nx = solid.shape
+    shape = (nx, ny, nz)
+    j = OPP[d]
+    e_j = _EF[j]
+    wd = W[d]
+    f_d = fr[d, cell[:, 2], cell[:, 1], cell[:, 0]]
+    wall = 6.0 * wd * rho0 * (e_j * u_w).sum(1)
+    if bb_mode == "ladd":
+        return f_d + wall
+    rho_f, u_f = _node_moments(fr, cell)
+    ffc, ok = _wrap(cell - E[d], shape, periodic)
+    okf = ok.copy()
+    okf[ok] = ~solid[ffc[ok, 2], ffc[ok, 1], ffc[ok, 0]]
+    u_ff = u_f.copy()
+    if okf.any():
+        _, u_ff[okf] = _node_moments(fr, ffc[okf])
+    u_d = departure_velocity(q, u_f, u_ff, u_w)
+
+    def feq_dir(rho, u, dd):
+        eu = (_EF[dd] * u).sum(1)
+        usq = (u * u).sum(1)
+        return W[dd] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq)
+
+    return feq_dir(rho_f, u_d, d) + (f_d - feq_dir(rho_f, u_f, d)) + wall
+
+
 def coupled_lbm_step(fpost, owner, owner_prev, particles, tau, bb_mode="ibb",
                      periodic=(False, False, False), wall_velocity=None, rho0=1.0, force=None,
                      return_links=False, cover_uncover=False):
@@ -197,25 +239,7 @@ def coupled_lbm_step(fpost, owner, owner_prev, particles, tau, bb_mode="ibb",
         u_w[m] = rigid_velocity(particles[pi], x_w[m])
         X_p[m] = particles[pi]["pos"]
     f_d = fr[d, cell[:, 2], cell[:, 1], cell[:, 0]]
-    wd = W[d]
-    if bb_mode == "ladd":
-        G = f_d + 6.0 * wd * rho0 * (e_j * u_w).sum(1)
-    else:
-        rho_f, u_f = _node_moments(fr, cell)
-        ffc, ok = _wrap(cell - E[d], shape, periodic)
-        okf = ok.copy()
-        okf[ok] = ~solid[ffc[ok, 2], ffc[ok, 1], ffc[ok, 0]]
-        u_ff = u_f.copy()
-        if okf.any():
-            _, u_ff[okf] = _node_moments(fr, ffc[okf])
-        u_d = departure_velocity(q, u_f, u_ff, u_w)
-
-        def feq_dir(rho, u, dd):
-            eu = (_EF[dd] * u).sum(1)
-            usq = (u * u).sum(1)
-            return W[dd] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq)
-
-        G = feq_dir(rho_f, u_d, d) + (f_d - feq_dir(rho_f, u_f, d)) + 6.0 * wd * rho0 * (e_j * u_w).sum(1)
+    G = bounce_back_populations(fr, cell, d, q, u_w, solid, periodic, bb_mode, rho0)
     # missing population j at x_f is replaced by G
     fin[j, cell[:, 2], cell[:, 1], cell[:, 0]] = G
     out = lbm.collide(fin, tau, force)

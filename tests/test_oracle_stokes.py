@@ -19,7 +19,8 @@ Two checks:
     tau = 1/2 + sqrt(3/16), where bounce-back places a flat wall exactly).
 A sphere rotating at Omega about its centre in fluid at rest feels the
 torque -8 pi mu R^3 Omega (the periodic images change it by O((R/L)^3),
-under 1 %): within 5 % once the rotational flow has developed.
+under 1 %): within 2 % once the rotational flow has developed (measured
+0.994; the departure-point velocity u_f in place of u_d gives 1.060).
 The interpolated rule gives 0.957 of the limit here and Ladd's halfway rule
 0.995: the drag checks the coupled physics (momentum exchange, viscosity,
 forcing), not which bounce-back variant runs; the wall fraction q and the
@@ -84,6 +85,6 @@ def test_rotating_sphere_torque():
     for _ in range(400):
         f, F, T = coupling.coupled_lbm_step(f, owner, owner, [P], TAU, periodic=(True, True, True))
     stokes = 8.0 * np.pi * mu * R ** 3 * omega
-    assert abs(-T[0, 2] / stokes - 1.0) < 0.05, -T[0, 2] / stokes
+    assert abs(-T[0, 2] / stokes - 1.0) < 0.02, -T[0, 2] / stokes
     assert np.abs(T[0, :2]).max() < 2e-3 * abs(T[0, 2])
     assert np.abs(F[0]).max() < 1e-2 * abs(T[0, 2]) / R     # zero up to the staircase surface
