@@ -142,6 +142,7 @@ ParticleLaunch mi_delbm::particle_launch() const {
   L.np = n_particles;
   L.balls = dballs;
   L.balls_d = dballs_d;
+  L.balls_s = dballs_s;
   L.max_balls_per_particle = max_balls_pp < 2048 ? max_balls_pp : 2048;
   L.cur_buf = owner_cur;
   L.prev_buf = owner_cur ^ 1;
@@ -183,8 +184,9 @@ mi_status mi_delbm::phase_flag(cudaStream_t st) {
 mi_status mi_delbm::phase_links(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   ParticleLaunch L = particle_launch();
-  return launch_phase(this, st, MI_PHASE_LINKS,
-                      [&] { return launch_links_q(L, sm_count * tune.list_blocks_per_sm, st); });
+  // one link per thread in flight: four 256-thread blocks per SM fill the
+  // register file at the kernel's 64 registers
+  return launch_phase(this, st, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 4, st); });
 }
 
 static BoundaryLaunch boundary_launch(const mi_delbm* h) {
@@ -577,7 +579,8 @@ mi_status mi_delbm::ensure_particle_buffers() {
   dP = (DevParticle*)dalloc(sizeof(DevParticle) * np);
   dballs = (float4*)dalloc(sizeof(float4) * nb);
   dballs_d = (double*)dalloc(sizeof(double) * 4 * nb);
-  if (!owner[0] || !owner[1] || !stamp || !dctr || !facc || !fc || !dP || !dballs || !dballs_d)
+  dballs_s = (float4*)dalloc(sizeof(float4) * 2 * nb);
+  if (!owner[0] || !owner[1] || !stamp || !dctr || !facc || !fc || !dP || !dballs || !dballs_d || !dballs_s)
     return fail(MI_ENOMEM, "particle buffers: device allocation failed");
   cudaError_t e = cudaMemsetAsync(owner[0], 0xFF, ncell * 4, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(owner[1], 0xFF, ncell * 4, stream);
@@ -1292,10 +1295,24 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   std::vector<double> c(centers, centers + 3 * (size_t)n);
   const int off = h->n_balls_total;
   auto upload_balls = [&]() -> cudaError_t {
-    std::vector<float4> bf(n);
+    std::vector<float4> bf(n), bs(2 * (size_t)n);
     std::vector<double> bd(4 * (size_t)n);
     for (int i = 0; i < n; ++i) {
       bf[i] = make_float4((float)c[3 * i], (float)c[3 * i + 1], (float)c[3 * i + 2], (float)k[i]);
+      // hi + lo split for the wall-fraction kernel's float-float residual: a
+      // centre coordinate below 1024 in magnitude as its nearest multiple of
+      // 2^-12 (exact in FP32) plus the FP32 remainder, so that its difference
+      // with a link origin split the same way is exact; k as its FP32 rounding
+      // plus the remainder
+      double hi[4];
+      for (int a = 0; a < 3; ++a) {
+        const double v = c[3 * i + a];
+        hi[a] = std::fabs(v) < 1024.0 ? std::rint(v * 4096.0) / 4096.0 : (double)(float)v;
+      }
+      hi[3] = (double)(float)k[i];
+      bs[2 * i] = make_float4((float)hi[0], (float)hi[1], (float)hi[2], (float)hi[3]);
+      bs[2 * i + 1] = make_float4((float)(c[3 * i] - hi[0]), (float)(c[3 * i + 1] - hi[1]),
+                                  (float)(c[3 * i + 2] - hi[2]), (float)(k[i] - hi[3]));
       bd[4 * i] = c[3 * i];
       bd[4 * i + 1] = c[3 * i + 1];
       bd[4 * i + 2] = c[3 * i + 2];
@@ -1304,6 +1321,8 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
     cudaError_t e = cudaMemcpyAsync(h->dballs + off, bf.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->dballs_d + 4 * (size_t)off, bd.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->dballs_s + 2 * (size_t)off, bs.data(), sizeof(float4) * 2 * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e;
   };

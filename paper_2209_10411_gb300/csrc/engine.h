@@ -57,6 +57,7 @@ struct mi_delbm {
   mi::DevParticle* dP = nullptr;
   float4* dballs = nullptr;
   double* dballs_d = nullptr;
+  float4* dballs_s = nullptr;   // per ball: FP32 (c, k), then the FP32 remainders of the FP64 (c, k)
   int n_balls_total = 0;
   int max_balls_pp = 0;              // largest ball count of one particle
   uint32_t* stamp = nullptr;

@@ -22,7 +22,7 @@ namespace cg = cooperative_groups;
 namespace mi {
 
 namespace {
-constexpr float GUARD = 1e-4f;
+constexpr float GUARD = FIELD_GUARD;
 
 __device__ __forceinline__ void quat_to_R_exact(const double q[4], double R[9]) {
   // body -> world rotation of the normalised quaternion, unfused FP64
@@ -386,10 +386,90 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Wall fraction of each link: root q in (0, 1] of g(q) = f_p(x_f + q e_d) - 1
-// by Newton steps kept inside a shrinking bracket [lo, hi] (bisection when a
-// Newton step leaves it).  FP32 with the body-frame origin of the link formed
-// in FP64.
+// (Sec. 2.3.2; reading A7: along the link that points into the solid, c0 = 1).
+//
+// Stage 1, FP32: Newton steps kept inside a shrinking bracket [lo, hi]
+// (bisection when a step leaves it), the field summed as four independent
+// partial sums, until a Newton step is below 1e-5.  Its accuracy is limited by
+// FP32: the body-frame point carries ~|x_b| 6e-8 of rounding and the field
+// ~1e-7 relative noise, and a link that meets the surface at a grazing angle
+// turns that into an error of q amplified by 1/|cos|.
+// Stage 2, double-float: Newton steps whose residual g(q) is evaluated in
+// float-float arithmetic (an unevaluated sum hi + lo of two floats, ~44
+// significant bits; Knuth's TwoSum and the fused-multiply-add form of
+// Dekker's product are exact), the derivative in FP32, inside a bracket that
+// starts at [0, 1] (the exact flags guarantee g(0) < 0 <= g(1)) and moves with
+// the accurate signs; it stops after a step below 1e-6 (the next step would
+// be below ~1e-10) or after four steps.  Inputs of stage 2: the body-frame
+// link origin p and direction e formed in FP64 and split into float pairs, and
+// the ball table's split copy.  Origins and centres are split on the grid of
+// 2^-12 when the particle's bounding radius is below 1000, so that the hi
+// parts subtract exactly; otherwise the difference goes through TwoSum.
 // ---------------------------------------------------------------------------
+namespace {
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  return {s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// v = hi + lo with hi on the grid of 2^-12 (exact=true) or hi = fl(v)
+__device__ __forceinline__ F2 split(double v, bool grid) {
+  const double h = grid ? rint(v * 4096.0) * (1.0 / 4096.0) : (double)(float)v;
+  return {(float)h, (float)(v - h)};
+}
+
+// g(q) = f(p + q e) - 1 in float-float; g'(q) in FP32.
+__device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int nb, const F2 p[3], const F2 e[3],
+                                             float q, bool grid, float& gp) {
+  float gh = 0.f, gl = 0.f, d1 = 0.f;
+  for (int b = 0; b < nb; ++b) {
+    const float4 ch = __ldg(bs + 2 * b), cl = __ldg(bs + 2 * b + 1);
+    const float c_hi[3] = {ch.x, ch.y, ch.z}, c_lo[3] = {cl.x, cl.y, cl.z};
+    float r2h = 0.f, r2l = 0.f, ae = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      // a = (p - c) + q e as ah + al
+      F2 d;
+      if (grid) d = {__fsub_rn(p[k].hi, c_hi[k]), 0.f};   // exact on the grid
+      else d = two_sum(p[k].hi, -c_hi[k]);
+      const float dl = d.lo + (p[k].lo - c_lo[k]);
+      const F2 m = two_prod(q, e[k].hi);
+      const float ml = __fmaf_rn(q, e[k].lo, m.lo);
+      const F2 a = two_sum(d.hi, m.hi);
+      const float al = a.lo + dl + ml;
+      // a^2 = ah^2 + 2 ah al (al^2 is below the working precision)
+      const F2 sq = two_prod(a.hi, a.hi);
+      const float sql = __fmaf_rn(2.0f * a.hi, al, sq.lo);
+      const F2 t = two_sum(r2h, sq.hi);
+      r2h = t.hi;
+      r2l += t.lo + sql;
+      ae = __fmaf_rn(a.hi, e[k].hi, ae);
+    }
+    const F2 r2 = two_sum(r2h, r2l);
+    // k / r^2: the quotient of the hi parts, corrected by its exact residual
+    const float th = __fdiv_rn(ch.w, r2.hi);
+    float res = __fmaf_rn(-th, r2.hi, ch.w);
+    res = __fmaf_rn(-th, r2.lo, res + cl.w);
+    const float tl = __fdividef(res, r2.hi);
+    const F2 s = two_sum(gh, th);
+    gh = s.hi;
+    gl += s.lo + tl;
+    d1 = __fmaf_rn(-2.0f * th, __fdividef(ae, r2.hi), d1);
+  }
+  gp = d1;
+  const F2 g = two_sum(gh, -1.0f);
+  return g.hi + (g.lo + gl);
+}
+}  // namespace
+
 __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
   const unsigned nl = min(L.ctr->n_links, L.cap_links);
   const unsigned nbc = min(L.ctr->n_bc, L.cap_bc);
@@ -404,34 +484,84 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
     const int x = (int)(cu - row * (unsigned)L.g.nx), z = (int)(row / (unsigned)L.g.ny), y = (int)(row - (unsigned)z * L.g.ny);
     const double* R = P.R;
     const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
-    const float p0 = (float)(R[0] * d0 + R[3] * d1 + R[6] * d2);
-    const float p1 = (float)(R[1] * d0 + R[4] * d1 + R[7] * d2);
-    const float p2 = (float)(R[2] * d0 + R[5] * d1 + R[8] * d2);
-    const float e0 = (float)(R[0] * cx(d) + R[3] * cy(d) + R[6] * cz(d));
-    const float e1 = (float)(R[1] * cx(d) + R[4] * cy(d) + R[7] * cz(d));
-    const float e2 = (float)(R[2] * cx(d) + R[5] * cy(d) + R[8] * cz(d));
+    const double pb[3] = {R[0] * d0 + R[3] * d1 + R[6] * d2, R[1] * d0 + R[4] * d1 + R[7] * d2,
+                          R[2] * d0 + R[5] * d1 + R[8] * d2};
+    const double eb[3] = {R[0] * cx(d) + R[3] * cy(d) + R[6] * cz(d), R[1] * cx(d) + R[4] * cy(d) + R[7] * cz(d),
+                          R[2] * cx(d) + R[5] * cy(d) + R[8] * cz(d)};
+    const float p0 = (float)pb[0], p1 = (float)pb[1], p2 = (float)pb[2];
+    const float e0 = (float)eb[0], e1 = (float)eb[1], e2 = (float)eb[2];
     const float4* bl = L.balls + P.ball_off;
+    const int nb = P.n_balls;
+    // stage 1: FP32 bracketed Newton
     float lo = 0.f, hi = 1.f, q = 0.5f;
     for (int it = 0; it < 30; ++it) {
-      float g = -1.f, gp = 0.f;
-      for (int b = 0; b < P.n_balls; ++b) {
-        const float4 cb = __ldg(bl + b);
-        const float a0 = p0 + q * e0 - cb.x, a1 = p1 + q * e1 - cb.y, a2 = p2 + q * e2 - cb.z;
-        const float r2 = a0 * a0 + a1 * a1 + a2 * a2;
-        const float t = __fdividef(cb.w, r2);
-        g += t;
-        gp -= 2.f * __fdividef(t * (a0 * e0 + a1 * e1 + a2 * e2), r2);
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      const float a0 = p0 + q * e0, a1 = p1 + q * e1, a2 = p2 + q * e2;
+      int b = 0;
+      for (; b + 2 <= nb; b += 2) {
+        const float4 ca = __ldg(bl + b), cb = __ldg(bl + b + 1);
+        const float u0 = a0 - ca.x, u1 = a1 - ca.y, u2 = a2 - ca.z;
+        const float v0 = a0 - cb.x, v1 = a1 - cb.y, v2 = a2 - cb.z;
+        const float ru = u0 * u0 + u1 * u1 + u2 * u2, rv = v0 * v0 + v1 * v1 + v2 * v2;
+        const float iu = __fdividef(1.0f, ru), iv = __fdividef(1.0f, rv);
+        const float tu = ca.w * iu, tv = cb.w * iv;
+        if (b & 2) {
+          g2 += tu;
+          g3 += tv;
+          s2 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
+          s3 -= 2.f * tv * (v0 * e0 + v1 * e1 + v2 * e2) * iv;
+        } else {
+          g0 += tu;
+          g1 += tv;
+          s0 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
+          s1 -= 2.f * tv * (v0 * e0 + v1 * e1 + v2 * e2) * iv;
+        }
       }
+      if (b < nb) {
+        const float4 ca = __ldg(bl + b);
+        const float u0 = a0 - ca.x, u1 = a1 - ca.y, u2 = a2 - ca.z;
+        const float iu = __fdividef(1.0f, u0 * u0 + u1 * u1 + u2 * u2);
+        const float tu = ca.w * iu;
+        g0 += tu;
+        s0 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
+      }
+      const float g = ((g0 + g1) + (g2 + g3)) - 1.f, gp = (s0 + s1) + (s2 + s3);
       if (g >= 0.f) hi = q;
       else lo = q;
-      float qn = q - g / gp;
-      const bool newton = qn > lo && qn < hi;
-      if (!newton) qn = 0.5f * (lo + hi);
-      // a Newton step below 1e-5 leaves an error under the FP32 evaluation
-      // noise (~1e-6); a bisection step only bounds it by the bracket
-      const bool done = (newton && fabsf(qn - q) < 1e-5f) || (hi - lo) < 1e-6f;
+      const float step = g / gp;
+      float qn = q - step;
+      // a step below the tolerance ends the stage even when its end rounds onto
+      // the bracket (which it does once q sits on the root)
+      if (fabsf(step) < 1e-5f) {
+        q = fminf(fmaxf(qn, lo), hi);
+        break;
+      }
+      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
       q = qn;
-      if (done) break;
+      if (hi - lo < 1e-6f) break;
+    }
+    // stage 2: double-float Newton
+    // on the 2^-12 grid (|p|, |c| < 1024, split the same way by the host) the
+    // hi parts subtract exactly; larger particles take TwoSum
+    const bool grid = P.Rb < 1000.0;
+    const F2 ps[3] = {split(pb[0], grid), split(pb[1], grid), split(pb[2], grid)};
+    const F2 es[3] = {split(eb[0], false), split(eb[1], false), split(eb[2], false)};
+    const float4* bs = L.balls_s + 2 * (size_t)P.ball_off;
+    lo = 0.f;
+    hi = 1.f;
+    for (int it = 0; it < 4; ++it) {
+      float gp;
+      const float g = residual_ff(bs, nb, ps, es, q, grid, gp);
+      if (g >= 0.f) hi = q;
+      else lo = q;
+      const float step = g / gp;
+      float qn = q - step;
+      if (fabsf(step) < 1e-6f) {
+        q = fminf(fmaxf(qn, lo), hi);
+        break;
+      }
+      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
+      q = qn;
     }
     L.link_q[l] = fminf(fmaxf(q, 1e-6f), 1.0f);
   }
@@ -472,44 +602,7 @@ __global__ void __launch_bounds__(256) k_mass(const float4* balls, const double*
     const double X = __dadd_rn(-Rb, __dmul_rn(ix + 0.5, h));
     const double Y = __dadd_rn(-Rb, __dmul_rn(iy + 0.5, h));
     const double Z = __dadd_rn(-Rb, __dmul_rn(iz + 0.5, h));
-    const float xf = (float)X, yf = (float)Y, zf = (float)Z;
-    float f = 0.f;
-    bool inside = false, decided = false;
-    for (int b = 0; b < nb; ++b) {
-      const float4 c = balls[b];
-      const float e0 = xf - c.x, e1 = yf - c.y, e2 = zf - c.z;
-      f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
-      if (f > 1.0f + GUARD) {
-        inside = decided = true;
-        break;
-      }
-    }
-    if (!decided) {
-      if (f < 1.0f - GUARD) {
-        inside = false;
-      } else {
-        double fd = 0.0;
-        for (int b = 0; b < nb; ++b) {
-          const double* c = balls_d + 4 * b;
-          const double e0 = __dsub_rn(X, c[0]), e1 = __dsub_rn(Y, c[1]), e2 = __dsub_rn(Z, c[2]);
-          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
-          fd = __dadd_rn(fd, __ddiv_rn(c[3], r2));
-        }
-        inside = fd >= 1.0;
-      }
-    }
-    if (inside) {
-      acc[0] += 1.0;
-      acc[1] += X;
-      acc[2] += Y;
-      acc[3] += Z;
-      acc[4] += X * X;
-      acc[5] += X * Y;
-      acc[6] += X * Z;
-      acc[7] += Y * Y;
-      acc[8] += Y * Z;
-      acc[9] += Z * Z;
-    }
+    if (mass_sample_inside(balls, balls_d, nb, X, Y, Z)) mass_sample_accumulate(acc, X, Y, Z);
   }
   for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
   __syncthreads();

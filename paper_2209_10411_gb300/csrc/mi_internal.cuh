@@ -219,6 +219,7 @@ struct ParticleLaunch {
   int np;
   const float4* balls;        // (c_x, c_y, c_z, k) FP32
   const double* balls_d;      // (c_x, c_y, c_z, k) FP64, 4 per ball
+  const float4* balls_s;      // per ball two float4: FP32 (c, k) and the FP32 remainders of the FP64 values
   int max_balls_per_particle;
   uint32_t* owner_cur;        // buffer being written this step
   const uint32_t* owner_prev; // flags of the previous step
@@ -372,6 +373,51 @@ cudaError_t launch_integrate(const IntegrateLaunch& L, cudaStream_t s);
 // prologue, candidates, solves and update.  The plain or warm start only.
 constexpr int FUSED_DEM_MAX_PARTICLES = 64;
 cudaError_t launch_dem_substeps(const ContactLaunch& L, const IntegrateLaunch& I, int n_sub, cudaStream_t s);
+
+// Half-width of the band around f = 1 inside which an FP32 field value does
+// not decide solid or fluid and the node or sample is re-evaluated in FP64.
+constexpr float FIELD_GUARD = 1e-4f;
+
+// One sample (X, Y, Z) of the midpoint quadrature of the indicator f >= 1
+// (Sec. 2.1 Eq. 1; reading A15), in the body frame: the FP32 field summed ball
+// by ball with an early exit once it passes 1 + FIELD_GUARD (the terms are
+// positive), and inside the band an unfused FP64 re-evaluation in ball order,
+// so that the decision is the FP64 one.  balls: FP32 (c, k); balls_d: the
+// same table as 4 doubles per ball.
+__device__ __forceinline__ bool mass_sample_inside(const float4* balls, const double* balls_d, int nb, double X,
+                                                   double Y, double Z) {
+  const float xf = (float)X, yf = (float)Y, zf = (float)Z;
+  float f = 0.f;
+  for (int b = 0; b < nb; ++b) {
+    const float4 c = balls[b];
+    const float e0 = xf - c.x, e1 = yf - c.y, e2 = zf - c.z;
+    f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
+    if (f > 1.0f + FIELD_GUARD) return true;
+  }
+  if (f < 1.0f - FIELD_GUARD) return false;
+  double fd = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const double* c = balls_d + 4 * b;
+    const double e0 = __dsub_rn(X, c[0]), e1 = __dsub_rn(Y, c[1]), e2 = __dsub_rn(Z, c[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+    fd = __dadd_rn(fd, __ddiv_rn(c[3], r2));
+  }
+  return fd >= 1.0;
+}
+
+// Moment sums of an inside sample: [count, x, y, z, xx, xy, xz, yy, yz, zz].
+__device__ __forceinline__ void mass_sample_accumulate(double acc[10], double X, double Y, double Z) {
+  acc[0] += 1.0;
+  acc[1] += X;
+  acc[2] += Y;
+  acc[3] += Z;
+  acc[4] += X * X;
+  acc[5] += X * Y;
+  acc[6] += X * Z;
+  acc[7] += Y * Y;
+  acc[8] += Y * Z;
+  acc[9] += Z * Z;
+}
 
 // Mass properties by midpoint quadrature of f >= 1 on a grid of spacing h over
 // [-Rb, Rb]^3 (body frame); out: [count, sx, sy, sz, sxx, sxy, sxz, syy, syz, szz]

@@ -1,12 +1,14 @@
 """GPU parity of the particle phases (flagging, links, refill, IBB, momentum
-exchange, rigid-body update) against the FP64 oracle, through the C-ABI.
+exchange, rigid-body update) against the FP64 oracle, through the C-ABI, on
+small particles (1-4 control points); tests/test_gpu_parity_scale.py runs the
+same comparison on the benchmarks' particle sizes.
 
-Bars: node owners, node classes and the link set bit-exact; wall fraction q
-within 1e-5 (FP32 root of an FP32 field whose body-frame point carries ~1e-6
-absolute rounding); populations at fluid nodes within 1e-5 relative; hydro-
-dynamic force and torque within 1e-4 * max(|F_ref|, 1e-3 * sum_links |dP|)
-per particle (the link-sum scale guards the cancellation of O(0.1) link terms
-into a small net force).
+Bars (tests/coupling_parity.py): node owners, node classes and the link set
+bit-exact; wall fraction q within 1e-5 (FP32 root of an FP32 field whose
+body-frame point carries ~1e-6 absolute rounding); populations at fluid nodes
+within 1e-5 relative; hydrodynamic force and torque within
+1e-4 * max(|F_ref|, 1e-3 * sum_links |dP|) per particle (the link-sum scale
+guards the cancellation of O(0.1) link terms into a small net force).
 """
 import numpy as np
 import pytest
@@ -14,96 +16,16 @@ import pytest
 from oracle import coupling, dem, lbm, metaball
 from oracle.d3q19 import E, W
 from paper_2209_10411_gb300 import scenes
+from tests import coupling_parity as cp
 from tests.gpu_helpers import binding
 
 pytestmark = pytest.mark.gpu
 
-TAU = 0.8
-ALL_LBM = 1 | 2 | 4 | 8 | 16 | 32  # flag, links, refill, bulk, boundary, swap
-
-
-def _prepared(spec, pos, quat, vel, omega):
-    """Oracle particle dict with control points shifted to the oracle's
-    quadrature centroid (inputs to both sides)."""
-    mp = metaball.mass_properties(spec.centers, spec.k, spec.density)
-    c = spec.centers - mp["centroid"]
-    mp = metaball.mass_properties(c, spec.k, spec.density)
-    P = {"centers": c, "k": spec.k.copy(), "pos": np.asarray(pos, float), "quat": np.asarray(quat, float),
-         "vel": np.asarray(vel, float), "omega": np.asarray(omega, float), "density": spec.density,
-         "skin": spec.skin, "mass": mp["mass"], "volume": mp["volume"], "inertia": mp["inertia"]}
-    return P
-
-
-def _initial_flow(shape, seed, umax=0.03):
-    nx, ny, nz = shape
-    u = umax * scenes.velocity_field_noise(shape, seed)
-    feq = lbm.equilibrium(np.ones((nz, ny, nx)), u)
-    noise = scenes.lattice_noise(shape, seed).astype(np.float64)
-    return (feq * (1.0 + 0.01 * noise)).astype(np.float32).astype(np.float64)
-
-
-def _run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM, cover_uncover=False):
-    nx, ny, nz = shape
-    sim = B.Simulation(nx, ny, nz, tau=TAU, bb_mode=(B.BB_LADD if mode == "ladd" else B.BB_IBB), storage=storage)
-    for Pp in parts_prev:
-        sim.add_particle(Pp["centers"], Pp["k"], Pp["density"], Pp["skin"], Pp["pos"], Pp["quat"],
-                         Pp["vel"], Pp["omega"],
-                         mass_props={"mass": Pp["mass"], "volume": Pp["volume"], "inertia": Pp["inertia"]})
-    sim.step_phases(1)  # flags at the previous pose
-    if cover_uncover:
-        sim.set_momentum_rules(cover_uncover=True)
-    for i, P in enumerate(parts):
-        sim.set_particle_state(i, P["pos"], P["quat"], P["vel"], P["omega"])
-    sim.set_populations(f0.astype(np.float32))
-    sim.step_phases(phases)
-    return sim
-
-
-def _compare_step(sim, shape, parts_prev, parts, f0, mode):
-    nx, ny, nz = shape
-    owner = metaball.flag_nodes(shape, parts)
-    owner_prev = metaball.flag_nodes(shape, parts_prev)
-    ref, F, T, L = coupling.coupled_lbm_step(f0, owner, owner_prev, parts, TAU, bb_mode=mode, return_links=True)
-    cls, own = sim.node_classes()
-    own = own.astype(np.int64)
-    own[own == 0xFFFFFFFF] = -1
-    # owners and classes bit-exact
-    assert np.array_equal(own, owner), "owner mismatch at %d nodes" % (own != owner).sum()
-    solid, new = coupling.classify(owner, owner_prev)
-    boundary = np.zeros_like(solid)
-    cl = L["cell"]
-    boundary[cl[:, 2], cl[:, 1], cl[:, 0]] = True
-    assert np.array_equal((cls & 1) != 0, solid)
-    assert np.array_equal((cls & 2) != 0, boundary)
-    assert np.array_equal((cls & 4) != 0, new)
-    # link set bit-exact, q within 1e-5
-    g = sim.links()
-    lin_ref = (cl[:, 2] * ny + cl[:, 1]) * nx + cl[:, 0]
-    key_ref = np.stack([L["particle"], lin_ref, L["dir"]], 1)
-    key_gpu = np.stack([g["particle"].astype(np.int64), g["cell"].astype(np.int64), g["dir"].astype(np.int64)], 1)
-    o_ref = np.lexsort(key_ref.T[::-1])
-    o_gpu = np.lexsort(key_gpu.T[::-1])
-    assert np.array_equal(key_ref[o_ref], key_gpu[o_gpu])
-    dq = np.abs(g["q"][o_gpu].astype(np.float64) - L["q"][o_ref])
-    assert dq.max() < 1e-5, "max |dq| %g" % dq.max()
-    # populations at fluid nodes
-    got = sim.get_populations().astype(np.float64)
-    fl = owner < 0
-    rel = np.abs(got[:, fl] - ref[:, fl]) / np.abs(ref[:, fl])
-    assert rel.max() < 1e-5, "max rel population err %g" % rel.max()
-    # force and torque
-    fr = sim.forces()
-    dP = L["dP"]
-    for p in range(len(parts)):
-        m = L["particle"] == p
-        qw = np.full(m.sum(), 0.5) if mode == "ladd" else L["q"][m]
-        xw = L["cell"][m] + qw[:, None] * E[L["dir"][m]]
-        arm = xw - parts[p]["pos"]
-        scaleF = max(np.linalg.norm(F[p]), 1e-3 * np.abs(dP[m]).sum())
-        scaleT = max(np.linalg.norm(T[p]), 1e-3 * np.abs(np.cross(arm, dP[m])).sum())
-        assert np.linalg.norm(fr["F_hydro"][p] - F[p]) <= 1e-4 * scaleF, (fr["F_hydro"][p], F[p])
-        assert np.linalg.norm(fr["T_hydro"][p] - T[p]) <= 1e-4 * scaleT, (fr["T_hydro"][p], T[p])
-    return F, T
+TAU = cp.TAU
+_prepared = cp.prepared
+_initial_flow = cp.initial_flow
+_run_one_step = cp.run_one_step
+_compare_step = cp.compare_step
 
 
 @pytest.mark.parametrize("mode", ["ibb", "ladd"])

@@ -13,7 +13,7 @@ import pytest
 from oracle import lbm, metaball, step as ostep
 from paper_2209_10411_gb300 import scenes
 from tests.gpu_helpers import binding
-from tests.test_gpu_coupling import _prepared
+from tests.coupling_parity import prepared as _prepared
 
 pytestmark = pytest.mark.gpu
 
