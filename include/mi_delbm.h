@@ -330,11 +330,20 @@ mi_status mi_delbm_get_stats(mi_delbm *h, mi_delbm_stats *st);
  *   mi_delbm_add_particle uses).
  * out_dev: device pointer to 14 doubles, written as mass, volume,
  *   centroid[3], inertia[9] (row-major, about the centroid, body axes).
+ *   All 14 are NaN when no sample lies inside the particle (no solid volume
+ *   at this spacing), and when the grid is not run: the ball table is
+ *   ill-formed (a NaN, a non-positive sum of k), or it has more than 2048
+ *   samples per axis (ceil(2 R_b / spacing), R_b = max|c_i| + sqrt(sum k_i)),
+ *   or more than 2^38 (sample, ball) pairs.  R_b is formed on the device, so
+ *   these cases are reported through the outputs, not the return status.
  * stream: cudaStream_t to run on (NULL = the default stream).  The call is
  *   asynchronous; synchronise the stream before reading out_dev.
  * Runs on the current device.  The first call on a device looks up the
- *   scratch's device address (cudaGetSymbolAddress) once for that device;
- *   make that first call before any stream capture.
+ *   scratch's device address (cudaGetSymbolAddress) once for that device and
+ *   keeps it; make that first call before any stream capture.  The kept
+ *   address belongs to the device's primary context of that time: after a
+ *   cudaDeviceReset of the device, do not call this entry point on it again
+ *   in the same process.
  * Every call on a device shares the one scratch array, which keeps the last
  *   call's contents: calls that overlap on the GPU (on different streams, or
  *   from different host threads) race and give wrong results.  Serialise them.

@@ -17,6 +17,12 @@ namespace {
 constexpr int NOALLOC_MAX_BALLS = 4096;  // largest ball table accepted
 constexpr int NOALLOC_BLOCKS = 1024;     // quadrature blocks (one row of 10 sums each)
 constexpr int NOALLOC_MAX_DEVICES = 64;
+// Largest quadrature grid: at most 2048 samples per axis and at most 2^38
+// (sample, ball) field evaluations, about a tenth of a second on this part.
+// Larger grids (a very small spacing, a large or ill-formed ball table) are
+// not run: the outputs are set to NaN instead.
+constexpr long long NOALLOC_MAX_SIDE = 2048;
+constexpr double NOALLOC_MAX_EVALS = 274877906944.0;  // 2^38
 
 struct NoallocScratch {
   float4 balls[NOALLOC_MAX_BALLS];      // FP32 (c_x, c_y, c_z, k)
@@ -32,7 +38,10 @@ NoallocScratch* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
 std::mutex g_scratch_mutex;
 
 // Device address of the scratch on the current device (looked up once per
-// device; the host-side symbol itself is only a stand-in, never a device address).
+// device; the host-side symbol itself is only a stand-in, never a device
+// address).  The cached address belongs to the device's primary context as it
+// was at the first call: a cudaDeviceReset on that device invalidates it, and
+// the entry point must not be called on that device afterwards.
 cudaError_t scratch_address(int dev, NoallocScratch** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
@@ -57,8 +66,15 @@ __global__ void k_noalloc_prep(const double* __restrict__ balls, int n, double h
     maxc = fmax(maxc, r);
     sumk = __dadd_rn(sumk, b[3]);
   }
-  S->Rb = __dadd_rn(maxc, __dsqrt_rn(sumk));
-  S->n_side = (long long)ceil(__ddiv_rn(__dmul_rn(2.0, S->Rb), h));
+  const double Rb = __dadd_rn(maxc, __dsqrt_rn(sumk));
+  S->Rb = Rb;
+  // samples per axis, or 0 (nothing is sampled, the outputs become NaN) when
+  // the table is ill-formed (a NaN, a non-positive sum of k) or the grid is
+  // beyond the limits above; the comparisons are false for NaN
+  const double side = ceil(__ddiv_rn(__dmul_rn(2.0, Rb), h));
+  const bool ok = Rb > 0.0 && side >= 1.0 && side <= (double)NOALLOC_MAX_SIDE &&
+                  side * side * side * (double)n <= NOALLOC_MAX_EVALS;
+  S->n_side = ok ? (long long)side : 0;
 }
 
 // Midpoint quadrature of f >= 1 over [-Rb, Rb]^3: FP32 field with the FP64
@@ -76,44 +92,7 @@ __global__ void __launch_bounds__(256) k_noalloc_quadrature(const double* __rest
     const double X = __dadd_rn(-Rb, __dmul_rn((double)ix + 0.5, h));
     const double Y = __dadd_rn(-Rb, __dmul_rn((double)iy + 0.5, h));
     const double Z = __dadd_rn(-Rb, __dmul_rn((double)iz + 0.5, h));
-    const float xf = (float)X, yf = (float)Y, zf = (float)Z;
-    float f = 0.f;
-    bool inside = false, decided = false;
-    for (int b = 0; b < nb; ++b) {
-      const float4 c = S->balls[b];
-      const float e0 = xf - c.x, e1 = yf - c.y, e2 = zf - c.z;
-      f += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
-      if (f > 1.0f + 1e-4f) {
-        inside = decided = true;
-        break;
-      }
-    }
-    if (!decided) {
-      if (f < 1.0f - 1e-4f) {
-        inside = false;
-      } else {
-        double fd = 0.0;
-        for (int b = 0; b < nb; ++b) {
-          const double* c = balls + 4 * b;
-          const double e0 = __dsub_rn(X, c[0]), e1 = __dsub_rn(Y, c[1]), e2 = __dsub_rn(Z, c[2]);
-          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
-          fd = __dadd_rn(fd, __ddiv_rn(c[3], r2));
-        }
-        inside = fd >= 1.0;
-      }
-    }
-    if (inside) {
-      acc[0] += 1.0;
-      acc[1] += X;
-      acc[2] += Y;
-      acc[3] += Z;
-      acc[4] += X * X;
-      acc[5] += X * Y;
-      acc[6] += X * Z;
-      acc[7] += Y * Y;
-      acc[8] += Y * Z;
-      acc[9] += Z * Z;
-    }
+    if (mi::mass_sample_inside(S->balls, balls, nb, X, Y, Z)) mi::mass_sample_accumulate(acc, X, Y, Z);
   }
   for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
   __syncthreads();
@@ -127,7 +106,8 @@ __global__ void __launch_bounds__(256) k_noalloc_quadrature(const double* __rest
 }
 
 // One thread: sum the block rows in block order and form mass, volume,
-// centroid and inertia about the centroid.  out: 14 doubles.
+// centroid and inertia about the centroid.  out: 14 doubles, all NaN when the
+// grid was not run or no sample lies inside (no solid volume).
 __global__ void k_noalloc_finish(const NoallocScratch* S, double h, double density, double* __restrict__ out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -135,9 +115,12 @@ __global__ void k_noalloc_finish(const NoallocScratch* S, double h, double densi
     for (int k = 0; k < 10; ++k) s[k] += S->partials[10 * b + k];
   const double dv = h * h * h;
   const double vol = s[0] * dv;
+  if (S->n_side == 0 || !(vol > 0.0)) {
+    for (int k = 0; k < 14; ++k) out[k] = __longlong_as_double(0x7FF8000000000000LL);
+    return;
+  }
   double cen[3] = {0, 0, 0};
-  if (vol > 0.0)
-    for (int a = 0; a < 3; ++a) cen[a] = s[1 + a] * dv / vol;
+  for (int a = 0; a < 3; ++a) cen[a] = s[1 + a] * dv / vol;
   double sec[9] = {s[4] * dv, s[5] * dv, s[6] * dv, s[5] * dv, s[7] * dv, s[8] * dv, s[6] * dv, s[8] * dv, s[9] * dv};
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) sec[3 * a + b] -= vol * cen[a] * cen[b];
