@@ -388,23 +388,28 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 // Wall fraction of each link: root q in (0, 1] of g(q) = f_p(x_f + q e_d) - 1
 // (Sec. 2.3.2; reading A7: along the link that points into the solid, c0 = 1).
 //
-// Stage 1, FP32: Newton steps kept inside a shrinking bracket [lo, hi]
-// (bisection when a step leaves it), the field summed as four independent
-// partial sums, until a Newton step is below 1e-5.  Its accuracy is limited by
-// FP32: the body-frame point carries ~|x_b| 6e-8 of rounding and the field
-// ~1e-7 relative noise, and a link that meets the surface at a grazing angle
-// turns that into an error of q amplified by 1/|cos|.
+// Inputs: the body-frame link origin p and direction e formed in FP64 and
+// split into float pairs hi + lo, and the ball table's split copy; origins
+// and centres are split on the grid of 2^-12 when the particle's bounding
+// radius is below 1000, so that p_hi - c_hi is exact in FP32 (otherwise the
+// difference goes through TwoSum).
+//
+// Stage 1, FP32: Newton steps on h(q) = f^(-1/2) - 1, which has the same root
+// and is close to linear along a link for fields of the form k / r^2 (the
+// distance to a lone ball over its radius), kept inside a shrinking bracket
+// [lo, hi] (bisection when a step leaves it), the field summed as four
+// independent partial sums, until a step is below 2e-5.  With the exact
+// differences the body-frame point carries ~1e-7 of rounding, but the FP32
+// field's noise, divided by g'(q) = e . grad f (small on large smooth
+// particles and on links that meet the surface at a grazing angle), still
+// leaves errors up to ~1e-4.
 // Stage 2, double-float: Newton steps whose residual g(q) is evaluated in
 // float-float arithmetic (an unevaluated sum hi + lo of two floats, ~44
 // significant bits; Knuth's TwoSum and the fused-multiply-add form of
 // Dekker's product are exact), the derivative in FP32, inside a bracket that
 // starts at [0, 1] (the exact flags guarantee g(0) < 0 <= g(1)) and moves with
-// the accurate signs; it stops after a step below 1e-6 (the next step would
-// be below ~1e-10) or after four steps.  Inputs of stage 2: the body-frame
-// link origin p and direction e formed in FP64 and split into float pairs, and
-// the ball table's split copy.  Origins and centres are split on the grid of
-// 2^-12 when the particle's bounding radius is below 1000, so that the hi
-// parts subtract exactly; otherwise the difference goes through TwoSum.
+// the accurate signs.  A step below 2e-5 ends it (Newton's quadratic
+// convergence leaves an error ~(g''/2g') step^2 behind); at most four steps.
 // ---------------------------------------------------------------------------
 namespace {
 struct F2 {
@@ -420,10 +425,14 @@ __device__ __forceinline__ F2 two_prod(float a, float b) {
   const float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
-// v = hi + lo with hi on the grid of 2^-12 (exact=true) or hi = fl(v)
+// v = hi + lo with hi on the grid of 2^-12 (grid = true) or hi = fl(v)
 __device__ __forceinline__ F2 split(double v, bool grid) {
   const double h = grid ? rint(v * 4096.0) * (1.0 / 4096.0) : (double)(float)v;
   return {(float)h, (float)(v - h)};
+}
+// p_hi - c_hi as hi + lo (exact on the grid)
+__device__ __forceinline__ F2 diff_hi(float p, float c, bool grid) {
+  return grid ? F2{__fsub_rn(p, c), 0.f} : two_sum(p, -c);
 }
 
 // g(q) = f(p + q e) - 1 in float-float; g'(q) in FP32.
@@ -437,9 +446,7 @@ __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int 
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       // a = (p - c) + q e as ah + al
-      F2 d;
-      if (grid) d = {__fsub_rn(p[k].hi, c_hi[k]), 0.f};   // exact on the grid
-      else d = two_sum(p[k].hi, -c_hi[k]);
+      const F2 d = diff_hi(p[k].hi, c_hi[k], grid);
       const float dl = d.lo + (p[k].lo - c_lo[k]);
       const F2 m = two_prod(q, e[k].hi);
       const float ml = __fmaf_rn(q, e[k].lo, m.lo);
@@ -488,51 +495,65 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
                           R[2] * d0 + R[5] * d1 + R[8] * d2};
     const double eb[3] = {R[0] * cx(d) + R[3] * cy(d) + R[6] * cz(d), R[1] * cx(d) + R[4] * cy(d) + R[7] * cz(d),
                           R[2] * cx(d) + R[5] * cy(d) + R[8] * cz(d)};
-    const float p0 = (float)pb[0], p1 = (float)pb[1], p2 = (float)pb[2];
-    const float e0 = (float)eb[0], e1 = (float)eb[1], e2 = (float)eb[2];
-    const float4* bl = L.balls + P.ball_off;
+    // on the 2^-12 grid (|p|, |c| < 1024, split the same way by the host) the
+    // hi parts subtract exactly; larger particles take TwoSum
+    const bool grid = P.Rb < 1000.0;
+    const F2 ps[3] = {split(pb[0], grid), split(pb[1], grid), split(pb[2], grid)};
+    const F2 es[3] = {split(eb[0], false), split(eb[1], false), split(eb[2], false)};
+    const float4* bs = L.balls_s + 2 * (size_t)P.ball_off;
     const int nb = P.n_balls;
-    // stage 1: FP32 bracketed Newton
+    // stage 1: FP32 Newton on h = f^(-1/2) - 1
     float lo = 0.f, hi = 1.f, q = 0.5f;
-    for (int it = 0; it < 30; ++it) {
-      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      const float a0 = p0 + q * e0, a1 = p1 + q * e1, a2 = p2 + q * e2;
+    for (int it = 0; it < 24; ++it) {
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      float a[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a[k] = __fmaf_rn(q, es[k].hi, ps[k].lo);  // p_lo + q e, then + (p_hi - c_hi) per ball
       int b = 0;
       for (; b + 2 <= nb; b += 2) {
-        const float4 ca = __ldg(bl + b), cb = __ldg(bl + b + 1);
-        const float u0 = a0 - ca.x, u1 = a1 - ca.y, u2 = a2 - ca.z;
-        const float v0 = a0 - cb.x, v1 = a1 - cb.y, v2 = a2 - cb.z;
-        const float ru = u0 * u0 + u1 * u1 + u2 * u2, rv = v0 * v0 + v1 * v1 + v2 * v2;
-        const float iu = __fdividef(1.0f, ru), iv = __fdividef(1.0f, rv);
-        const float tu = ca.w * iu, tv = cb.w * iv;
+        const float4 ha = __ldg(bs + 2 * b), la = __ldg(bs + 2 * b + 1);
+        const float4 hb = __ldg(bs + 2 * b + 2), lb = __ldg(bs + 2 * b + 3);
+        const float u0 = diff_hi(ps[0].hi, ha.x, grid).hi + (a[0] - la.x);
+        const float u1 = diff_hi(ps[1].hi, ha.y, grid).hi + (a[1] - la.y);
+        const float u2 = diff_hi(ps[2].hi, ha.z, grid).hi + (a[2] - la.z);
+        const float v0 = diff_hi(ps[0].hi, hb.x, grid).hi + (a[0] - lb.x);
+        const float v1 = diff_hi(ps[1].hi, hb.y, grid).hi + (a[1] - lb.y);
+        const float v2 = diff_hi(ps[2].hi, hb.z, grid).hi + (a[2] - lb.z);
+        const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2), iv = __fdividef(1.f, v0 * v0 + v1 * v1 + v2 * v2);
+        const float tu = ha.w * iu, tv = hb.w * iv;
+        const float du = -2.f * tu * (u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi) * iu;
+        const float dv = -2.f * tv * (v0 * es[0].hi + v1 * es[1].hi + v2 * es[2].hi) * iv;
         if (b & 2) {
-          g2 += tu;
-          g3 += tv;
-          s2 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
-          s3 -= 2.f * tv * (v0 * e0 + v1 * e1 + v2 * e2) * iv;
+          f2 += tu;
+          f3 += tv;
+          s2 += du;
+          s3 += dv;
         } else {
-          g0 += tu;
-          g1 += tv;
-          s0 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
-          s1 -= 2.f * tv * (v0 * e0 + v1 * e1 + v2 * e2) * iv;
+          f0 += tu;
+          f1 += tv;
+          s0 += du;
+          s1 += dv;
         }
       }
       if (b < nb) {
-        const float4 ca = __ldg(bl + b);
-        const float u0 = a0 - ca.x, u1 = a1 - ca.y, u2 = a2 - ca.z;
-        const float iu = __fdividef(1.0f, u0 * u0 + u1 * u1 + u2 * u2);
-        const float tu = ca.w * iu;
-        g0 += tu;
-        s0 -= 2.f * tu * (u0 * e0 + u1 * e1 + u2 * e2) * iu;
+        const float4 ha = __ldg(bs + 2 * b), la = __ldg(bs + 2 * b + 1);
+        const float u0 = diff_hi(ps[0].hi, ha.x, grid).hi + (a[0] - la.x);
+        const float u1 = diff_hi(ps[1].hi, ha.y, grid).hi + (a[1] - la.y);
+        const float u2 = diff_hi(ps[2].hi, ha.z, grid).hi + (a[2] - la.z);
+        const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2);
+        const float tu = ha.w * iu;
+        f0 += tu;
+        s0 -= 2.f * tu * (u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi) * iu;
       }
-      const float g = ((g0 + g1) + (g2 + g3)) - 1.f, gp = (s0 + s1) + (s2 + s3);
-      if (g >= 0.f) hi = q;
+      const float f = (f0 + f1) + (f2 + f3), fp = (s0 + s1) + (s2 + s3);
+      if (f >= 1.f) hi = q;
       else lo = q;
-      const float step = g / gp;
-      float qn = q - step;
+      // Newton on h: q + 2 f (1 - sqrt f) / f'
+      const float step = 2.f * f * (1.f - f * rsqrtf(f)) / fp;
+      float qn = q + step;
       // a step below the tolerance ends the stage even when its end rounds onto
       // the bracket (which it does once q sits on the root)
-      if (fabsf(step) < 1e-5f) {
+      if (fabsf(step) < 2e-5f) {
         q = fminf(fmaxf(qn, lo), hi);
         break;
       }
@@ -541,12 +562,6 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
       if (hi - lo < 1e-6f) break;
     }
     // stage 2: double-float Newton
-    // on the 2^-12 grid (|p|, |c| < 1024, split the same way by the host) the
-    // hi parts subtract exactly; larger particles take TwoSum
-    const bool grid = P.Rb < 1000.0;
-    const F2 ps[3] = {split(pb[0], grid), split(pb[1], grid), split(pb[2], grid)};
-    const F2 es[3] = {split(eb[0], false), split(eb[1], false), split(eb[2], false)};
-    const float4* bs = L.balls_s + 2 * (size_t)P.ball_off;
     lo = 0.f;
     hi = 1.f;
     for (int it = 0; it < 4; ++it) {
@@ -556,7 +571,7 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
       else lo = q;
       const float step = g / gp;
       float qn = q - step;
-      if (fabsf(step) < 1e-6f) {
+      if (fabsf(step) < 2e-5f) {
         q = fminf(fmaxf(qn, lo), hi);
         break;
       }
