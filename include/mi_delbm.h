@@ -428,6 +428,14 @@ mi_status mi_delbm_get_tuning(const mi_delbm *h, int *bulk_block_x, int *bulk_ro
  * reset (the reset flag clears them after reading). */
 mi_status mi_delbm_set_timing(mi_delbm *h, int enable);
 mi_status mi_delbm_phase_times(mi_delbm *h, double ms[8], long long launches[8], int reset);
+/* The same event timing for one kernel: the summed milliseconds and count of
+ * the timed launches of `kernel` since the last reset of mi_delbm_phase_times
+ * (not reset by this call).  Names: k_prologue, k_clear, k_flag, k_classify,
+ * k_links_q, k_refill, k_bulk (the bulk stream-collide, whichever variant the
+ * tuning selects), k_near, k_boundary, k_scatter_boundary, k_dem_prologue,
+ * k_broad_phase, k_item_features, k_mlp_tc, k_contacts, k_integrate,
+ * k_dem_substeps.  Synchronises.  Errors: MI_EINVAL (NULL argument). */
+mi_status mi_delbm_kernel_time(mi_delbm *h, const char *kernel, double *ms, long long *launches);
 
 /* Number of kernel launches the handle issued since creation (for launch
  * accounting by benchmarks). */

@@ -103,6 +103,7 @@ _sig("mi_delbm_get_tuning", c_int, _P, ctypes.POINTER(c_int), ctypes.POINTER(c_i
      ctypes.POINTER(c_int))
 _sig("mi_delbm_autotune", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int))
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
+_sig("mi_delbm_kernel_time", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong))
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
 _sig("mi_delbm_add_particle", c_int, _P, c_int, _P, _P, c_double, c_double, _P, _P, _P, _P,
      ctypes.POINTER(MassProps), ctypes.POINTER(c_int))
@@ -119,6 +120,7 @@ _sig("mi_delbm_get_links", c_int, _P, c_size_t, _P, _P, _P, _P, ctypes.POINTER(c
 _sig("mi_delbm_get_stats", c_int, _P, ctypes.POINTER(Stats))
 _sig("mi_delbm_contacts", c_int, _P, ctypes.POINTER(Contact), c_int, ctypes.POINTER(c_int))
 _sig("mi_mass_properties_noalloc", c_int, _P, c_int, c_double, c_double, _P, _P)
+_sig("mi_measure_fma_peak", c_int, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_double), _P)
 _sig("mi_mlp_param_count", c_size_t)
 _sig("mi_mlp_forward", c_int, _P, _P, c_int, _P, _P, _P)
 _sig("mi_mlp_mse", c_int, _P, _P, c_int, _P, _P, _P, _P)
@@ -142,6 +144,17 @@ _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P,
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
 SCHEDULE_OVERLAP_BOUNDARY, SCHEDULE_UNFUSED_DEM = 1, 2
 MOMENTUM_COVER_UNCOVER = 1
+
+
+def measure_fma_peak(precision="fp32", stream=None):
+    """Measured dense FMA throughput of the current device (mi_measure_fma_peak):
+    (TFLOP/s, ms of the timed launch)."""
+    tf, ms = c_double(0.0), c_double(0.0)
+    st = lib.mi_measure_fma_peak({"fp32": 0, "fp64": 1}[precision], ctypes.byref(tf), ctypes.byref(ms),
+                                 c_void_p(int(stream) if stream else 0))
+    if st != MI_OK:
+        raise MiDelbmError(st, lib.mi_delbm_last_error(None).decode())
+    return tf.value, ms.value
 
 
 def mass_properties_noalloc(balls_dev_ptr, n_balls, density, spacing, out_dev_ptr, stream=None):
@@ -517,6 +530,13 @@ class Simulation:
         n = (ctypes.c_longlong * 8)()
         self._check(lib.mi_delbm_phase_times(self.h, ms, n, 1 if reset else 0))
         return {PHASE_NAMES[b]: (ms[b], n[b]) for b in range(8)}
+
+    def kernel_time(self, kernel):
+        """(summed ms, launches) of one kernel's event-timed launches since the
+        last phase_times reset."""
+        ms, n = c_double(0.0), ctypes.c_longlong(0)
+        self._check(lib.mi_delbm_kernel_time(self.h, kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def launch_count(self):
         return int(lib.mi_delbm_launch_count(self.h))

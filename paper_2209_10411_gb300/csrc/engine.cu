@@ -28,7 +28,7 @@ namespace {
 // Kernel-launch helper: runs `fn` (which returns a cudaError_t) as one launch
 // of `phase`, bracketed by timing events when timing is enabled.
 template <class F>
-mi_status launch_phase(mi_delbm* h, cudaStream_t st, unsigned phase_bit, F&& fn) {
+mi_status launch_phase(mi_delbm* h, cudaStream_t st, unsigned phase_bit, const char* kernel, F&& fn) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->timing) {
     a = h->event_from_pool();
@@ -43,7 +43,7 @@ mi_status launch_phase(mi_delbm* h, cudaStream_t st, unsigned phase_bit, F&& fn)
     cudaEventRecord(b, st);
     int idx = 0;
     while ((1u << idx) != phase_bit && idx < 7) ++idx;
-    h->timed.push_back({idx, a, b});
+    h->timed.push_back({idx, a, b, kernel});
   }
   return MI_OK;
 }
@@ -175,18 +175,17 @@ mi_status mi_delbm::phase_flag(cudaStream_t st) {
   owner_cur ^= 1;  // the buffer holding the flags of two steps ago becomes current
   ParticleLaunch L = particle_launch();
   mi_status s;
-  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_prologue(L, st); })) != MI_OK) return s;
-  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_clear(L, st); })) != MI_OK) return s;
-  if ((s = launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_flag(L, st); })) != MI_OK) return s;
-  return launch_phase(this, st, MI_PHASE_FLAG, [&] { return launch_classify(L, st); });
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, "k_prologue", [&] { return launch_prologue(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, "k_clear", [&] { return launch_clear(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_FLAG, "k_flag", [&] { return launch_flag(L, st); })) != MI_OK) return s;
+  return launch_phase(this, st, MI_PHASE_FLAG, "k_classify", [&] { return launch_classify(L, st); });
 }
 
 mi_status mi_delbm::phase_links(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   ParticleLaunch L = particle_launch();
-  // one link per thread in flight: four 256-thread blocks per SM fill the
-  // register file at the kernel's 64 registers
-  return launch_phase(this, st, MI_PHASE_LINKS, [&] { return launch_links_q(L, sm_count * 4, st); });
+  return launch_phase(this, st, MI_PHASE_LINKS, "k_links_q",
+                      [&] { return launch_links_q(L, sm_count * tune.list_blocks_per_sm, st); });
 }
 
 static BoundaryLaunch boundary_launch(const mi_delbm* h) {
@@ -206,20 +205,20 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
 mi_status mi_delbm::phase_refill(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
-  return launch_phase(this, st, MI_PHASE_REFILL, [&] { return launch_refill(L, st); });
+  return launch_phase(this, st, MI_PHASE_REFILL, "k_refill", [&] { return launch_refill(L, st); });
 }
 
 mi_status mi_delbm::phase_near() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
   // timed with the boundary phase: the bulk bucket is the lattice-wide kernel alone
-  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_near(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, "k_near", [&] { return launch_near(L, stream); });
 }
 
 mi_status mi_delbm::phase_boundary() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
-  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, "k_boundary", [&] { return launch_boundary(L, stream); });
 }
 
 // Overlapped schedule: the boundary nodes' new values go to bc_tmp on a side
@@ -229,14 +228,14 @@ mi_status mi_delbm::phase_boundary_beside(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
   L.tmp = bc_tmp;
-  return launch_phase(this, st, MI_PHASE_BOUNDARY, [&] { return launch_boundary(L, st); });
+  return launch_phase(this, st, MI_PHASE_BOUNDARY, "k_boundary", [&] { return launch_boundary(L, st); });
 }
 
 mi_status mi_delbm::phase_scatter_boundary() {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
   L.tmp = bc_tmp;
-  return launch_phase(this, stream, MI_PHASE_BOUNDARY, [&] { return launch_scatter_boundary(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BOUNDARY, "k_scatter_boundary", [&] { return launch_scatter_boundary(L, stream); });
 }
 
 mi_status mi_delbm::phase_integrate(bool with_contacts) {
@@ -249,7 +248,7 @@ mi_status mi_delbm::phase_integrate(bool with_contacts) {
   for (int a = 0; a < 3; ++a) L.gravity[a] = cfg.gravity[a];
   L.rho0 = cfg.rho0;
   L.dt = 1.0 / cfg.dem_substeps;
-  return launch_phase(this, stream, MI_PHASE_INTEGRATE, [&] { return launch_integrate(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_INTEGRATE, "k_integrate", [&] { return launch_integrate(L, stream); });
 }
 
 mi_status mi_delbm::ensure_contact_buffers() {
@@ -340,18 +339,18 @@ mi_status mi_delbm::phase_contact(cudaStream_t st) {
   if (s != MI_OK) return s;
   if (learned && (s = ensure_guess_buffers()) != MI_OK) return s;
   ContactLaunch L = contact_launch(this);
-  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_dem_prologue(L, st); })) != MI_OK) return s;
-  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_broad_phase(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_dem_prologue", [&] { return launch_dem_prologue(L, st); })) != MI_OK) return s;
+  if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_broad_phase", [&] { return launch_broad_phase(L, st); })) != MI_OK) return s;
   if (learned) {
     // features of the candidates, then the MLP on as many rows as the broad phase found
-    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_item_features(L, st); })) != MI_OK) return s;
-    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, [&] {
+    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_item_features", [&] { return launch_item_features(L, st); })) != MI_OK) return s;
+    if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_mlp_tc", [&] {
            return mlp_tc_infer(static_cast<unsigned char*>(mlp_image) + mlp_image_bytes(), guess_feat,
                                (int)cap_items, &dctr->n_pairs, guess_pred, &dctr->status, STATUS_GUESS_TIMEOUT, st);
          })) != MI_OK)
       return s;
   }
-  return launch_phase(this, st, MI_PHASE_CONTACT, [&] { return launch_contacts(L, st); });
+  return launch_phase(this, st, MI_PHASE_CONTACT, "k_contacts", [&] { return launch_contacts(L, st); });
 }
 
 mi_status mi_delbm::phase_bulk() {
@@ -366,7 +365,7 @@ mi_status mi_delbm::phase_bulk() {
   L.rows = tune.bulk_rows;
   L.pairs = tune.bulk_pairs != 0;
   L.pair_mode = tune.bulk_pairs;
-  return launch_phase(this, stream, MI_PHASE_BULK, [&] { return launch_bulk(L, stream); });
+  return launch_phase(this, stream, MI_PHASE_BULK, "k_bulk", [&] { return launch_bulk(L, stream); });
 }
 
 mi_status mi_delbm::phase_swap() {
@@ -451,7 +450,7 @@ mi_status mi_delbm::phase_dem_fused() {
   for (int a = 0; a < 3; ++a) I.gravity[a] = cfg.gravity[a];
   I.rho0 = cfg.rho0;
   I.dt = 1.0 / cfg.dem_substeps;
-  return launch_phase(this, stream, MI_PHASE_INTEGRATE,
+  return launch_phase(this, stream, MI_PHASE_INTEGRATE, "k_dem_substeps",
                       [&] { return launch_dem_substeps(L, I, cfg.dem_substeps, stream); });
 }
 
@@ -981,6 +980,23 @@ mi_status mi_delbm_set_momentum_rules(mi_delbm* h, int flags) {
 mi_status mi_delbm_set_timing(mi_delbm* h, int enable) {
   if (!h) return MI_EINVAL;
   h->timing = enable != 0;
+  return MI_OK;
+}
+
+mi_status mi_delbm_kernel_time(mi_delbm* h, const char* kernel, double* ms, long long* launches) {
+  if (!h || !kernel || !ms || !launches) return MI_EINVAL;
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_kernel_time");
+  *ms = 0.0;
+  *launches = 0;
+  for (auto& t : h->timed) {
+    float m = 0.f;
+    if (t.kernel && std::strcmp(t.kernel, kernel) == 0 && cudaEventElapsedTime(&m, t.a, t.b) == cudaSuccess) {
+      *ms += m;
+      *launches += 1;
+    }
+  }
   return MI_OK;
 }
 

@@ -11,6 +11,7 @@
 struct TimedLaunch {
   int phase;
   cudaEvent_t a, b;
+  const char* kernel;  // the kernel's name (a string literal), for mi_delbm_kernel_time
 };
 
 struct TuneChoice {
