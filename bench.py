@@ -38,15 +38,6 @@ BYTES_PER_NODE = {0: 152, 1: 76, 2: 76}   # 19 loads + 19 stores of the stored t
 BULK_TRAFFIC = {(0, False): 4 * 1222.0e6, (1, True): 4 * 591.1e6}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 DTYPE_NAME = {0: "f32", 1: "f16-dev/f32-compute", 2: "bf16-dev/f32-compute"}
-# The stated accuracy of each storage against the FP64 oracle: the bounds that
-# tests/test_gpu_precision.py asserts on a 64^3 box with a particle moving at
-# 0.02 lu/step over 40 coupled steps (relative L2 error of the velocity field,
-# relative error of the hydrodynamic force at the last step).
-STATED_ERROR = {st: {"velocity_rel_l2_max": bu, "force_rel_max": bf,
-                     "asserted_by": "tests/test_gpu_precision.py (64^3, 40 coupled steps vs the FP64 oracle)"}
-                for st, (bu, bf) in {0: (1e-4, 1e-3), 1: (2e-2, 5e-2), 2: (1e-1, 2e-1)}.items()}
-
-
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -215,11 +206,175 @@ class OracleSample:
                 % (self.crop, self.boundary, tank_boundary_fraction()))
 
 
+def _oracle_worker(crop, budget_s, warmup_steps, timed_steps, barrier, queue):
+    """One host core's share of the all-core oracle timing (a spawned process:
+    it never touches the GPU): its own window of the tank, warm-up steps, then
+    after the barrier either timed_steps steps or steps until budget_s."""
+    try:
+        sampler = OracleSample(crop=crop)
+        sampler.run()                          # the first step pays numpy's one-time costs
+        for _ in range(warmup_steps):
+            sampler.run()
+        barrier.wait()
+        t0 = time.time()
+        steps = 0
+        if timed_steps:
+            for _ in range(timed_steps):
+                sampler.run()
+            steps = timed_steps
+        else:
+            _, _, steps = sampler.run(budget_s=budget_s)
+        queue.put((steps, t0, time.time(), None))
+    except Exception as e:  # reported by the parent
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        queue.put((0, 0.0, 0.0, repr(e)))
+
+
+def oracle_all_cores(crop, budget_s=15.0, warmup_steps=0, timed_steps=0, n=None):
+    """The oracle on every host core at once: n = os.cpu_count() spawned
+    processes, each on its own crop^3 window, released together by a barrier.
+    Returns (whole-box MLUPS over the span from the first start to the last
+    end, that span in s, the steps of each process, n)."""
+    import multiprocessing as mp
+    n = n or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    queue = ctx.Queue()
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"                    # one thread per process: n processes on n cores
+    procs = [ctx.Process(target=_oracle_worker, args=(crop, budget_s, warmup_steps, timed_steps, barrier, queue))
+             for _ in range(n)]
+    try:
+        for p_ in procs:
+            p_.start()
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    res = [queue.get(timeout=900) for _ in range(n)]
+    for p_ in procs:
+        p_.join(timeout=60)
+    errs = [r[3] for r in res if r[3]]
+    if errs:
+        raise RuntimeError("oracle worker failed: " + errs[0])
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    steps = [r[0] for r in res]
+    return crop ** 3 * sum(steps) / span / 1e6, span, steps, n
+
+
+def c2_window_parity(B, sim, scene, crop=96):
+    """The settling tank's force and torque against the FP64 oracle on a
+    cropped copy: the crop^3 window around the first cobble, holding the
+    tank's populations and every particle that reaches into it, with the
+    poses of the tank's last two steps (flags at the earlier one), one
+    coupled LBM step on both sides (the window's faces are closed walls on
+    both).  Bar: |F - F_ref| <= 1e-4 max(|F_ref|, 1e-3 sum_links |dP|) per
+    particle, likewise the torque."""
+    import torch
+    from oracle import coupling, metaball
+    from oracle.d3q19 import E
+    nx, ny, nz = scene.shape
+    npart = sim.num_particles()
+    prev = [sim.get_particle_state(i) for i in range(npart)]
+    sim.step(1)
+    sim.synchronize()
+    cur = [sim.get_particle_state(i) for i in range(npart)]
+    shapes = [sim.get_particle_shape(i) for i in range(npart)]
+    lo = [int(min(max(round(cur[0]["pos"][a]) - crop // 2, 0), n - crop)) for a, n in enumerate((nx, ny, nz))]
+    v = sim.device_view()
+    assert v.storage == B.STORE_F32
+    pop = torch.as_tensor(B.CudaArray(v.populations, (19, v.plane_stride), "<f4"), device="cuda")
+    r = [torch.arange(lo[a], lo[a] + crop, device="cuda", dtype=torch.int64) for a in range(3)]
+    zz, yy, xx = torch.meshgrid(r[2], r[1], r[0], indexing="ij")
+    lin = ((zz * ny + yy) * nx + xx).reshape(-1)
+    f0 = pop.index_select(1, lin).cpu().numpy().astype(np.float64).reshape(19, crop, crop, crop)
+    shift = np.array(lo, dtype=float)
+    parts, parts_prev, ids = [], [], []
+    for i in range(npart):
+        X = cur[i]["pos"] - shift
+        if np.any(X + shapes[i]["Rb"] < -1) or np.any(X - shapes[i]["Rb"] > crop):
+            continue
+        base = {"centers": shapes[i]["centers"], "k": shapes[i]["k"], "mass": shapes[i]["mass"],
+                "volume": shapes[i]["volume"], "inertia": shapes[i]["inertia"], "density": scene.particles[i].density,
+                "skin": scene.particles[i].skin}
+        parts.append(dict(base, pos=X, quat=cur[i]["quat"], vel=cur[i]["vel"], omega=cur[i]["omega"]))
+        parts_prev.append(dict(base, pos=prev[i]["pos"] - shift, quat=prev[i]["quat"], vel=prev[i]["vel"],
+                               omega=prev[i]["omega"]))
+        ids.append(i)
+    shape = (crop, crop, crop)
+    win = B.Simulation(crop, crop, crop, tau=scene.tau, storage=B.STORE_F32, max_particles=max(4, len(parts)))
+    for P in parts_prev:
+        win.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"], P["omega"],
+                         mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
+    win.step_phases(B.PHASE_FLAG)
+    for j, P in enumerate(parts):
+        win.set_particle_state(j, P["pos"], P["quat"], P["vel"], P["omega"])
+    win.set_populations(f0.astype(np.float32))
+    win.step_phases(B.PHASE_FLAG | B.PHASE_LINKS | B.PHASE_REFILL | B.PHASE_BULK | B.PHASE_BOUNDARY | B.PHASE_SWAP)
+    fr = win.forces()
+    gl = win.links()
+    win.close()
+    t0 = time.perf_counter()
+    owner = metaball.flag_nodes(shape, parts)
+    owner_prev = metaball.flag_nodes(shape, parts_prev)
+    _, F, T, L = coupling.coupled_lbm_step(f0, owner, owner_prev, parts, scene.tau, return_links=True)
+    oracle_s = time.perf_counter() - t0
+    per = []
+    for j, i in enumerate(ids):
+        m = L["particle"] == j
+        if not m.any():
+            continue   # reaches into the window's box but not its nodes
+        arm = L["cell"][m] + L["q"][m][:, None] * E[L["dir"][m]] - parts[j]["pos"]
+        sF = max(np.linalg.norm(F[j]), 1e-3 * np.abs(L["dP"][m]).sum())
+        sT = max(np.linalg.norm(T[j]), 1e-3 * np.abs(np.cross(arm, L["dP"][m])).sum())
+        per.append({"particle": i, "links": int(m.sum()),
+                    "force_err": float(np.linalg.norm(fr["F_hydro"][j] - F[j]) / sF),
+                    "torque_err": float(np.linalg.norm(fr["T_hydro"][j] - T[j]) / sT),
+                    "F_ref": [float(x) for x in F[j]]})
+    return {"window": [crop] * 3, "corner": lo, "links_oracle": int(len(L["dir"])), "links_gpu": int(len(gl["dir"])),
+            "force_err_max": max(p_["force_err"] for p_ in per), "torque_err_max": max(p_["torque_err"] for p_ in per),
+            "bar": 1e-4, "particles": per, "oracle_s": oracle_s,
+            "scale": "max(|F_ref|, 1e-3 sum_links |dP|) per particle (torque likewise)"}
+
+
+def cpu_leg(B, sim, scene, budget_s):
+    """The oracle beside the GPU (rank 0, one GPU): the tank's cropped-copy
+    force/torque error, then the oracle's throughput on one host core and on
+    all of them (the window with the tank's share of boundary nodes)."""
+    out = {}
+    try:
+        out["c2_force_error"] = c2_window_parity(B, sim, scene)
+    except Exception as e:
+        out["c2_force_error"] = {"error": repr(e)}
+    sampler = OracleSample(crop=96)
+    v1, dt, n = sampler.run(budget_s=budget_s)
+    single = {"value": v1, "unit": "MLUPS", "cores": sampler.cores, "steps": n, "s": dt}
+    try:
+        vall, span, steps, ncores = oracle_all_cores(96, budget_s=budget_s)
+        cpu = {"value": vall, "unit": "MLUPS", "cores": ncores, "kind": "oracle",
+               "sample": sampler.describe() + "; %d processes (one per host core), each its own window, %d steps "
+                         "in %.1f s in total" % (ncores, sum(steps), span),
+               "single_core": single}
+    except Exception as e:
+        cpu = dict(single, kind="oracle", sample=sampler.describe() + ", %d steps in %.1f s (all-core run failed: %r)"
+                   % (n, dt, e))
+    out["cpu_baseline"] = cpu
+    return out
+
+
 def run_reference(args):
-    """The oracle on the host cores, each of the K timed steps one oracle step
-    on a window of the tank with the tank's share of boundary nodes, the
-    window's edge sized from a calibration so that the whole warm-up + timed
-    run takes about REF_TOTAL_S seconds (between 24 and 96 nodes)."""
+    """The oracle on all host cores: one process per core, each of the K timed
+    steps one oracle step per process on its own window of the tank with the
+    tank's share of boundary nodes, the window's edge sized from a one-core
+    calibration so that the whole warm-up + timed run takes about REF_TOTAL_S
+    seconds (between 24 and 96 nodes); value = all processes' node updates
+    over the span from the first start to the last end."""
     from paper_2209_10411_gb300 import replicas
     rank, world, _ = replicas.rank_env()
     if rank != 0:
@@ -231,27 +386,20 @@ def run_reference(args):
     _, dt, n = cal.run(budget_s=0.5)
     t_node = dt / n / 32 ** 3
     crop = int(max(24, min(96, (per_step / t_node) ** (1.0 / 3.0))))
+    value, span, steps, ncores = oracle_all_cores(crop, warmup_steps=args.warmup, timed_steps=args.steps)
     sampler = OracleSample(crop=crop)
-    for _ in range(args.warmup):
-        sampler.run()
-    t0 = time.perf_counter()
-    c0 = time.process_time()
-    for _ in range(args.steps):
-        sampler.run()
-    wall = time.perf_counter() - t0
-    cores = cores_used(time.process_time() - c0, wall)
-    value = crop ** 3 * args.steps / wall / 1e6
-    sample = sampler.describe() + ", one oracle step per timed step"
+    sample = (sampler.describe() + "; %d processes (one per host core), each its own window, %d timed steps each "
+              "after %d warm-up steps" % (ncores, args.steps, args.warmup))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(1, args.steps) * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": span / max(1, args.steps) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": CONFIG,
-           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": ncores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-REF_TOTAL_S = 120.0  # the reference arm's warm-up + timed steps, about
+REF_TOTAL_S = 100.0  # the reference arm's warm-up + timed steps, about (per process, all cores busy)
 
 
 METRIC = "coupled-step MLUPS (FP32 vs FP16-store) at stated err; contact solves/s"
@@ -282,7 +430,8 @@ def train_guess(B):
     shapes = guess.bed_shapes(1, 256)
     sim = B.Simulation(16, 16, 16, max_particles=len(shapes) + 1, max_balls=sum(len(s["k"]) for s in shapes) + 1)
     guess.add_shapes(sim, shapes)
-    ij, poses = guess.pair_poses(1, shapes, 2_000_000)
+    # centre distances of the bed's candidates: 0.5 to 1.6 times R_i + R_j
+    ij, poses = guess.pair_poses(1, shapes, 2_000_000, spacing=(0.5, 1.5))
     X, T, _ = guess.generate(sim, *guess.to_device(ij, poses))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -296,7 +445,26 @@ def train_guess(B):
     return params, info
 
 
-def contact_solves(B, scenes, args):
+CONTACT_FLOP_PER_BALL_ITER = 35   # x - c, r^2, 1/r^2, k/r^2, gradient, six Hessian entries
+CONTACT_FLOP_SOLVE = 60           # the 3x3 (pairs) solve per iteration
+CONTACT_FLOP_SOLVE_WALL = 100     # the 4x4 (walls) solve per iteration
+
+
+def contact_flops(recs, nballs):
+    """Algorithmic FLOPs of the Newton iterations of these contact records:
+    per iteration 35 per ball of both particles plus the 3x3 solve (pairs), or
+    35 per ball plus the 4x4 solve (walls).  The plain start's sphere-gap
+    search and the contact forces are not counted."""
+    total = 0.0
+    for c in recs:
+        if c["j"] >= 0:
+            total += c["iters"] * (CONTACT_FLOP_PER_BALL_ITER * (nballs[c["i"]] + nballs[c["j"]]) + CONTACT_FLOP_SOLVE)
+        else:
+            total += c["iters"] * (CONTACT_FLOP_PER_BALL_ITER * nballs[c["i"]] + CONTACT_FLOP_SOLVE_WALL)
+    return total
+
+
+def contact_solves(B, scenes, args, alu=None):
     """Contact solves per second: the DEM contact phase alone (broad phase +
     persistent Newton/force kernel; with the learned guess also the feature
     kernel and the MLP) on the 3000-particle bed of 4-128 balls in
@@ -330,10 +498,12 @@ def contact_solves(B, scenes, args):
         reps = 20
         for _ in range(reps):
             sim.step_phases(B.PHASE_CONTACT)
+        kc = sim.kernel_time("k_contacts")
         pt = sim.phase_times(reset=True)["contact"]
         recs = sim.contacts()
         sim.close()
         recs_by_mode[mode] = recs
+        kc_ms = kc[0] / max(kc[1], 1)
         n = len(recs)
         pair_iters = np.array([c["iters"] for c in recs if c["j"] >= 0])
         status = np.bincount(np.array([c["status"] for c in recs], dtype=int), minlength=5)
@@ -345,7 +515,17 @@ def contact_solves(B, scenes, args):
                      "status_counts": {"ok": int(status[0]), "not_converged": int(status[1]),
                                        "singular": int(status[2]), "inside_core": int(status[3]),
                                        "out_of_range": int(status[4])},
-                     "ms_per_substep": ms, "launches_per_substep": pt[1] / reps}
+                     "ms_per_substep": ms, "launches_per_substep": pt[1] / reps,
+                     "k_contacts_ms": kc_ms}
+        if alu:
+            fl = contact_flops(recs, [len(p.k) for p in sc.particles])
+            tf = fl / (kc_ms * 1e-3) / 1e12
+            out[mode]["roofline"] = {"bound": "alu", "kernel": "k_contacts (Newton closest points and forces)",
+                                     "achieved": tf, "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+                                     "frac": tf / alu["fp32_tflops"], "peak_kind": "measured (mi_measure_fma_peak)",
+                                     "algorithmic_flop_per_launch": fl,
+                                     "flop_per_iteration": "35 (n_i + n_j) + 60 per pair, 35 n_i + 100 per wall",
+                                     "traffic": None}
     # DEM substeps of a moving bed (contact + rigid-body update, 10 substeps per
     # call: the particles move between substeps), plain vs warm start
     moving = {}
@@ -423,7 +603,7 @@ def storage_variant(B, scene, storage, steps, stream_obj):
     peak, kind = _peaks()
     return {"value": ncell / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
             "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bytes_per_node": BYTES_PER_NODE[storage], "tuning": tuning,
-            "stated_error": STATED_ERROR[storage]}
+            "stated_error": STATED_ERROR_C4[storage]}
 
 
 def dem_ratio(B, scene, storage, steps, stream_obj, nsub=100):
@@ -452,10 +632,12 @@ def dem_ratio(B, scene, storage, steps, stream_obj, nsub=100):
 
 
 GS_FLOP_PER_PAIR_EPOCH = 27  # field (9) + gradient (18) per (hull point, control point) and epoch
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+# nominal FP32 rate (SMs x FP32 lanes x FMA x max SM clock), used only when the
+# measured peak (mi_measure_fma_peak) is not available
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
+def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11, fp32_peak=FP32_ALU_PEAK_TFLOPS, peak_kind="nominal"):
     """Gradient Search refinement (Algorithm 2) of n_fits models of 8-64
     control points on synthetic bumpy-ellipsoid hulls of m points (the
     300-particle tank's shape range), two descents of `epochs` epochs: fits/s
@@ -521,8 +703,8 @@ def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
     ls = loss.cpu().numpy()
     return {"value": n_fits / (ms * 1e-3), "unit": "fits/s", "ms": ms, "fits": n_fits, "hull_points": m,
             "control_points": [int(min(nb)), int(max(nb))], "epochs_per_descent": epochs,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tflops / FP32_ALU_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp32_peak, "peak_kind": peak_kind,
                          "flop_per_point_ball_epoch": GS_FLOP_PER_PAIR_EPOCH},
             "loss_after_second_over_first_descent_median": float(np.median(ls[:, 1] / np.maximum(ls[:, 0], 1e-30))),
             "cpu_baseline": {"value": n_fits / o_s, "unit": "fits/s", "cores": o_cores, "kind": "oracle",
@@ -530,7 +712,8 @@ def gs_bench(B, scenes, n_fits=300, m=2048, epochs=200, seed=11):
                                        "points" % o_ep}}
 
 
-def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21):
+def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21, fp32_peak=FP32_ALU_PEAK_TFLOPS,
+             peak_kind="nominal"):
     """Genetic Algorithm capture (Algorithm 1) with the paper's population of
     1200 individuals: 32-gene models on a 2048-point bumpy-ellipsoid hull,
     `generations` generations: generations/s, fitness evaluations/s and the
@@ -581,8 +764,8 @@ def ga_bench(B, scenes, n_ind=1200, n_genes=32, m=2048, generations=50, seed=21)
     return {"value": generations / (ms * 1e-3), "unit": "generations/s", "ms": ms, "individuals": n_ind,
             "genes": n_genes, "hull_points": m, "generations": generations,
             "fitness_evals_per_s": evals / (ms * 1e-3),
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tflops / FP32_ALU_PEAK_TFLOPS, "flop_per_point_gene": 9,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp32_peak, "peak_kind": peak_kind, "flop_per_point_gene": 9,
                          "note": "whole generation timed; the fitness kernel's work only"},
             "best_fitness_initial": f0, "best_fitness_final": float(fit[0].item()),
             "cpu_baseline": {"value": 1.0 / o_s, "unit": "fitness evals/s", "cores": o_cores, "kind": "oracle",
@@ -621,6 +804,76 @@ def shape_bench(B, scenes, n=300, h=0.25, seed=0):
                              "sample": "numpy oracle: the first particle at twice the spacing, time x 8"}}
 
 
+C4_KERNELS = ("k_prologue", "k_clear", "k_flag", "k_classify", "k_links_q", "k_refill", "k_bulk", "k_near",
+              "k_boundary", "k_dem_prologue", "k_broad_phase", "k_contacts", "k_integrate")
+# stated accuracy of each storage on the precision tank: the bounds that
+# tests/test_gpu_precision.py asserts on the 128^3 sub-run of that tank
+# (eight particles, 30 coupled steps) against the FP64 oracle's reference
+STATED_ERROR_C4 = {st: {"velocity_rel_l2_max": bu, "force_rel_max": bf,
+                        "asserted_by": "tests/test_gpu_precision.py::test_storage_error_c4_subrun (128^3 sub-run of "
+                                       "the 512^3 tank, 8 particles, 30 coupled steps vs the FP64 oracle)"}
+                   for st, (bu, bf) in {0: (3.5e-6, 4e-6), 1: (3.5e-4, 2.5e-4), 2: (2.7e-3, 1.5e-3)}.items()}
+
+
+def c4_leg(B, scenes, stream_obj, steps=100, timed_kernels=20):
+    """The precision tank (512^3, 300 particles of 8-64 control points) in
+    FP32, FP16-deviation and BF16-deviation storage: coupled-step MLUPS (CUDA
+    graph replays, events on the stream), and from a second pass of
+    individually launched steps the bulk kernel's HBM fraction inside the step
+    and each kernel's event-timed milliseconds per step."""
+    import torch
+    sc = scenes.config4()
+    nx, ny, nz = sc.shape
+    ncell = nx * ny * nz
+    peak, kind = _peaks()
+    out = {"workload": sc.name, "lattice": list(sc.shape), "particles": len(sc.particles),
+           "metaballs_min_max": [int(min(len(p.k) for p in sc.particles)), int(max(len(p.k) for p in sc.particles))]}
+    for name, st in (("f32", 0), ("f16-dev", 1), ("bf16-dev", 2)):
+        t_setup = time.perf_counter()
+        sim = build_sim(B, sc, st, stream_obj.cuda_stream)
+        sim.step(1)
+        tuning = sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json"))
+        for _ in range(5):
+            sim.step(1)
+        sim.synchronize()
+        t_setup = time.perf_counter() - t_setup
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream_obj)
+        for _ in range(steps):
+            sim.step(1)
+        ev1.record(stream_obj)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        sim.set_timing(True)
+        sim.phase_times(reset=True)
+        for _ in range(timed_kernels):
+            sim.step(1)
+        kt = {k: sim.kernel_time(k) for k in C4_KERNELS}
+        sim.phase_times(reset=True)
+        sim.set_timing(False)
+        stats = sim.stats()
+        sim.close()
+        bulk_ms = kt["k_bulk"][0] / max(kt["k_bulk"][1], 1)
+        gbs = BYTES_PER_NODE[st] * ncell / (bulk_ms * 1e-3) / 1e9
+        out[name] = {"value": ncell / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                     "bulk_ms": bulk_ms, "bulk_gbs": gbs, "bulk_frac": gbs / peak, "peak_kind": kind,
+                     "step_over_bulk": ms / bulk_ms,
+                     "kernel_ms_per_step": {k: v[0] / timed_kernels for k, v in kt.items() if v[1]},
+                     "boundary_nodes": stats["boundary_nodes"], "links": stats["links"],
+                     "candidate_pairs": stats["candidate_pairs"], "tuning": tuning, "setup_s": t_setup,
+                     "stated_error": STATED_ERROR_C4[st]}
+    return out
+
+
+def measured_alu_peaks(B):
+    """FP32 and FP64 FMA throughput of this GPU from the library's own
+    microbenchmark (mi_measure_fma_peak)."""
+    f32, ms32 = B.measure_fma_peak("fp32")
+    f64, ms64 = B.measure_fma_peak("fp64")
+    return {"fp32_tflops": f32, "fp64_tflops": f64, "fp32_ms": ms32, "fp64_ms": ms64,
+            "how": "mi_measure_fma_peak: 8 independent FMA chains per thread, every SM full, CUDA events"}
+
+
 def run_mine(args):
     import torch
     from paper_2209_10411_gb300 import replicas
@@ -633,7 +886,8 @@ def run_mine(args):
     from paper_2209_10411_gb300 import scenes
 
     storage = STORAGE[args.storage]
-    scene = {"c2": scenes.config2}[args.config](seed=rank)
+    scene = {"c2": scenes.config2, "c4": scenes.config4}[args.config](seed=rank)
+    alu = measured_alu_peaks(B) if rank == 0 else None
     if args.lattice:  # smaller profiling case: same particles, positions scaled into the box
         old = np.array(scene.shape, dtype=float)
         scene.shape = tuple(int(v) for v in args.lattice.split(","))
@@ -692,16 +946,20 @@ def run_mine(args):
     value = replicas.aggregate_throughput(ncell * args.steps, world, ms) / 1e6
     bulk_ms, bulk_n = ptimes["bulk"]
     contacts = None
-    if not args.no_contacts and rank == 0:
-        contacts = contact_solves(B, scenes, args)
+    c2 = args.config == "c2"
+    if c2 and not args.no_contacts and rank == 0:
+        contacts = contact_solves(B, scenes, args, alu)
     variants = None
-    if storage == 0 and not args.no_variants and rank == 0:
+    if c2 and storage == 0 and not args.no_variants and rank == 0:
         variants = {name: storage_variant(B, scene, st, max(50, min(args.steps, 200)), stream)
                     for name, st in (("f16-dev", 1), ("bf16-dev", 2))}
         variants["dem_100_substeps"] = dem_ratio(B, scene, storage, 30, stream)
-        variants["gs_fit"] = gs_bench(B, scenes)
-        variants["ga_capture"] = ga_bench(B, scenes)
+        variants["gs_fit"] = gs_bench(B, scenes, fp32_peak=alu["fp32_tflops"], peak_kind="measured")
+        variants["ga_capture"] = ga_bench(B, scenes, fp32_peak=alu["fp32_tflops"], peak_kind="measured")
         variants["shape_descriptors"] = shape_bench(B, scenes)
+    c4 = None
+    if c2 and not args.no_c4 and rank == 0:
+        c4 = c4_leg(B, scenes, stream)
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node
@@ -733,12 +991,11 @@ def run_mine(args):
            "d2h_bytes_per_step": npart * (13 + 6) * 8, "steps": k_e2e,
            "api": "set_particle_states + step + get_particle_states + forces per step (host wall clock)"}
 
-    cpu = None
+    cpu, c2_err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sampler = OracleSample(crop=96)
-        v, dt, n = sampler.run(budget_s=args.cpu_seconds)
-        cpu = {"value": v, "unit": "MLUPS", "cores": sampler.cores, "kind": "oracle",
-               "sample": sampler.describe() + ", %d steps in %.1f s" % (n, dt)}
+        leg = cpu_leg(B, sim, scene, args.cpu_seconds) if c2 else None
+        if leg:
+            cpu, c2_err = leg["cpu_baseline"], leg["c2_force_error"]
 
     config = {"workload": scene.name, "lattice": list(scene.shape), "particles": npart,
               "metaballs": [int(len(p.k)) for p in scene.particles], "storage": args.storage, "tau": scene.tau,
@@ -747,7 +1004,8 @@ def run_mine(args):
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPE_NAME[storage], "data": "synthetic", "config": config,
-           "stated_error": STATED_ERROR[storage],
+           "stated_error": STATED_ERROR_C4[storage],
+           "c2_force_error": c2_err,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": traffic,
                         "kernel": bulk_name, "peak_kind": peak_kind,
@@ -756,7 +1014,9 @@ def run_mine(args):
            "phase_ms_per_step": {k: v[0] / k_phase for k, v in ptimes.items() if v[1]},
            "graphs": not args.no_graphs, "tuning": tuning,
            "storage_variants": variants,
+           "c4_precision_tank": c4,
            "contacts": contacts,
+           "alu_peaks": alu,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
     if rank == 0:
@@ -772,7 +1032,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c4"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -781,11 +1041,12 @@ def main():
     ap.add_argument("--no-contacts", action="store_true", help="skip the contact-solves measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage measurements")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 512^3 precision-tank measurements")
     ap.add_argument("--small-contact-lattice", action="store_true",
                     help="contact bed on a 16^3 periodic lattice (profiling: same pairs, no walls, little memory)")
     args = ap.parse_args()
     from paper_2209_10411_gb300 import scenes
-    sc = scenes.config2()
+    sc = {"c2": scenes.config2, "c4": scenes.config4}[args.config]()
     # the workload both arms name (the GPU arm adds what its run measures)
     CONFIG.update({"workload": sc.name, "lattice": list(sc.shape), "particles": len(sc.particles),
                    "metaballs": [int(len(p.k)) for p in sc.particles], "storage": args.storage, "tau": sc.tau})

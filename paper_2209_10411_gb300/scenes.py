@@ -209,9 +209,10 @@ def config4(seed=0, shape=(512, 512, 512), n_particles=300):
 
 def config5(seed=0, shape=(384, 384, 768), n_particles=3000):
     """384x384x768 bed: 3000 particles of 4-128 balls (log-uniform), R ~ U[8, 16],
-    packed into the lower 60 % of the box by random sequential addition of
-    spheres of radius 0.9 R, so that neighbouring particles nearly touch
-    (about 14k broad-phase candidate pairs)."""
+    packed into the lower 18 % of the box by random sequential addition of
+    spheres of radius 0.5 R, so dense that neighbouring particles interpenetrate
+    and the broad phase yields about 49k candidate pairs (the ~50k active pairs
+    of the learned-proposal workload)."""
     rng = np.random.default_rng(seed)
     specs = []
     for _ in range(n_particles):
@@ -220,8 +221,8 @@ def config5(seed=0, shape=(384, 384, 768), n_particles=3000):
         c, k, r = clustered(rng, n, R)
         specs.append((c, k, r))
     lo = np.array([2.0, 2.0, 2.0])
-    hi = np.array([shape[0] - 2.0, shape[1] - 2.0, shape[2] * 0.6])
-    pos = _place_non_overlapping(rng, [0.9 * s[2] for s in specs], lo, hi, 0.0)
+    hi = np.array([shape[0] - 2.0, shape[1] - 2.0, shape[2] * 0.18])
+    pos = _place_non_overlapping(rng, [0.5 * s[2] for s in specs], lo, hi, 0.0)
     parts = [ParticleSpec(c, k, 2.5, 1.0, f32(p), random_unit_quaternion(rng), nominal_radius=r)
              for (c, k, r), p in zip(specs, pos)]
     return Scene("C5 384x384x768 3000-particle bed", shape, 0.8, (0.0, 0.0, -1e-5), parts, 100, seed)

@@ -30,14 +30,14 @@ def test_reference_arm_json_line():
 
 def test_stated_error_matches_the_precision_test():
     """The bench line's stated accuracy per storage is the bound the GPU
-    precision test asserts."""
+    precision test asserts on the precision tank's 128^3 sub-run."""
     import ast
     sys.path.insert(0, ROOT)
     import bench
     src = open(os.path.join(ROOT, "tests", "test_gpu_precision.py")).read()
     node = next(n for n in ast.parse(src).body
-                if isinstance(n, ast.Assign) and getattr(n.targets[0], "id", "") == "BOUNDS")
+                if isinstance(n, ast.Assign) and getattr(n.targets[0], "id", "") == "BOUNDS_C4")
     bounds = ast.literal_eval(node.value)
     for st, (bu, bf) in bounds.items():
-        assert bench.STATED_ERROR[st]["velocity_rel_l2_max"] == bu
-        assert bench.STATED_ERROR[st]["force_rel_max"] == bf
+        assert bench.STATED_ERROR_C4[st]["velocity_rel_l2_max"] == bu
+        assert bench.STATED_ERROR_C4[st]["force_rel_max"] == bf
