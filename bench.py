@@ -880,8 +880,7 @@ def run_mine(args):
     rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        replicas.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2209_10411_gb300 import _binding as B
     from paper_2209_10411_gb300 import scenes
 

@@ -307,6 +307,38 @@ typedef struct {
 } mi_delbm_stats;
 mi_status mi_delbm_get_stats(mi_delbm *h, mi_delbm_stats *st);
 
+/* Set the capacities of the per-step lists exactly (boundary nodes, boundary
+ * links, and uncovered nodes, which also bounds the covered-node list of the
+ * cover/uncover rule), smaller or larger than the sizes mi_delbm_add_particle
+ * estimates from the particles' boxes: for callers that budget device memory
+ * (the lists take 12 B per boundary node, 13 B per link and 8 B per uncovered
+ * node, plus 19 stored values per boundary node for the overlapped schedule).
+ * A step whose lists overflow never writes past them: it completes with the
+ * appends that fitted (its populations and forces are then incomplete), and
+ * the next synchronising query (mi_delbm_forces, mi_delbm_contacts) returns
+ * MI_ECAPACITY with the sizes it needed in the message; mi_delbm_get_stats
+ * reports them as the counts.  Before the next step the handle grows the
+ * lists to those sizes plus a quarter and captures its graphs again; restore
+ * the state of the step that overflowed (populations, particle states) to
+ * repeat it.  A later mi_delbm_add_particle may grow the lists again (never
+ * shrinks them).  Synchronises.  Errors: MI_EINVAL (a capacity of 0 or above
+ * 2^32 - 16), MI_ENOMEM. */
+mi_status mi_delbm_reserve_lists(mi_delbm *h, size_t boundary_nodes, size_t links, size_t new_nodes);
+
+/* State check: stored populations that are NaN or infinite at the nodes that
+ * are not solid at the current flags (every node without particles; values
+ * at solid nodes are unspecified), and particles whose position, quaternion,
+ * velocity or angular velocity is not finite.  For 16-bit storages a value is
+ * bad when its exponent bits are all ones.  Synchronises.  Returns MI_OK when
+ * nothing is bad, MI_ESTATE (with the counts in the message and in *out)
+ * otherwise.  first_bad_node is the linear index x + nx (y + ny z), -1 if
+ * none. */
+typedef struct {
+  long long bad_populations, first_bad_node;
+  int bad_particles, first_bad_particle;
+} mi_delbm_health;
+mi_status mi_delbm_check(mi_delbm *h, mi_delbm_health *out);
+
 /* ------------------------------------------------------------------------
  * Allocation-free mass properties (the paper has no counterpart: this is a
  * library convenience for particular callers).
@@ -517,6 +549,18 @@ mi_status mi_mlp_infer_mma(const void *image, const float *X, int n, float *Y, v
  * start from the plain guess.  Discards captured graphs.  Errors: MI_EINVAL,
  * MI_ENOMEM, MI_ECUDA. */
 mi_status mi_delbm_set_guess(mi_delbm *h, int mode, const float *params);
+
+/* Bounded waits of the learned guess's tcgen05 inference kernel: every wait on
+ * its copies and tensor-core work gives up after wait_rounds mbarrier polls
+ * (0: the default, 2^24, well over a second); a wait that gives up marks the
+ * rows it did not finish NaN, the contacts of those rows fall back to plain
+ * Newton from the plain guess, and the next synchronising query returns
+ * MI_ETIMEOUT (mi_delbm_get_stats clears it).  stall != 0 is for
+ * fault-injection tests: before issuing any work the kernel waits on an
+ * mbarrier that nothing arrives at, so that this wait runs out (after
+ * wait_rounds polls) with no copy or MMA in flight.  Discards the captured
+ * graphs. */
+mi_status mi_delbm_set_guess_wait(mi_delbm *h, unsigned wait_rounds, int stall);
 
 /* Flags of mi_delbm_pair_solve. */
 enum {

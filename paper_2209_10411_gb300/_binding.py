@@ -54,6 +54,11 @@ class Config(ctypes.Structure):
     ]
 
 
+class Health(ctypes.Structure):
+    _fields_ = [("bad_populations", ctypes.c_longlong), ("first_bad_node", ctypes.c_longlong),
+                ("bad_particles", c_int), ("first_bad_particle", c_int)]
+
+
 class DeviceView(ctypes.Structure):
     _fields_ = [("populations", c_void_p), ("plane_stride", c_size_t), ("storage", c_int),
                 ("node_class", c_void_p), ("owner", c_void_p), ("stream", c_void_p)]
@@ -103,6 +108,9 @@ _sig("mi_delbm_get_tuning", c_int, _P, ctypes.POINTER(c_int), ctypes.POINTER(c_i
      ctypes.POINTER(c_int))
 _sig("mi_delbm_autotune", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int))
 _sig("mi_delbm_phase_times", c_int, _P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong), c_int)
+_sig("mi_delbm_reserve_lists", c_int, _P, c_size_t, c_size_t, c_size_t)
+_sig("mi_delbm_set_guess_wait", c_int, _P, ctypes.c_uint, c_int)
+_sig("mi_delbm_check", c_int, _P, _P)
 _sig("mi_delbm_kernel_time", c_int, _P, ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong))
 _sig("mi_delbm_launch_count", ctypes.c_longlong, _P)
 _sig("mi_delbm_add_particle", c_int, _P, c_int, _P, _P, c_double, c_double, _P, _P, _P, _P,
@@ -530,6 +538,24 @@ class Simulation:
         n = (ctypes.c_longlong * 8)()
         self._check(lib.mi_delbm_phase_times(self.h, ms, n, 1 if reset else 0))
         return {PHASE_NAMES[b]: (ms[b], n[b]) for b in range(8)}
+
+    def reserve_lists(self, boundary_nodes, links, new_nodes):
+        self._check(lib.mi_delbm_reserve_lists(self.h, int(boundary_nodes), int(links), int(new_nodes)))
+
+    def set_guess_wait(self, wait_rounds=0, stall=False):
+        self._check(lib.mi_delbm_set_guess_wait(self.h, int(wait_rounds), 1 if stall else 0))
+
+    def check(self):
+        """mi_delbm_check: a dict of the counts; raises MiDelbmError (MI_ESTATE)
+        when something is not finite."""
+        hl = Health()
+        st = lib.mi_delbm_check(self.h, ctypes.byref(hl))
+        out = {f: getattr(hl, f) for f, _ in Health._fields_}
+        if st != MI_OK:
+            err = MiDelbmError(st, lib.mi_delbm_last_error(self.h).decode())
+            err.health = out
+            raise err
+        return out
 
     def kernel_time(self, kernel):
         """(summed ms, launches) of one kernel's event-timed launches since the

@@ -1,5 +1,6 @@
 // Engine and C-ABI of libmi_delbm: owns the device state of one lattice and
 // its particles, sequences the kernels of one coupled step on one stream.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -346,7 +347,8 @@ mi_status mi_delbm::phase_contact(cudaStream_t st) {
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_item_features", [&] { return launch_item_features(L, st); })) != MI_OK) return s;
     if ((s = launch_phase(this, st, MI_PHASE_CONTACT, "k_mlp_tc", [&] {
            return mlp_tc_infer(static_cast<unsigned char*>(mlp_image) + mlp_image_bytes(), guess_feat,
-                               (int)cap_items, &dctr->n_pairs, guess_pred, &dctr->status, STATUS_GUESS_TIMEOUT, st);
+                               (int)cap_items, &dctr->n_pairs, guess_pred, &dctr->status, STATUS_GUESS_TIMEOUT, st,
+                               guess_wait_limit, guess_stall);
          })) != MI_OK)
       return s;
   }
@@ -555,6 +557,13 @@ mi_status mi_delbm::check_status(bool clear) {
     cudaMemcpyAsync(&dctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, stream);
     cudaStreamSynchronize(stream);
   }
+  if (bad & (STATUS_BC_OVERFLOW | STATUS_LINK_OVERFLOW | STATUS_NEW_OVERFLOW)) {
+    // the counters hold the full counts (appends are counted before the
+    // capacity test): the lists grow to them before the next step
+    need_bc = std::max(need_bc, c.n_bc);
+    need_links = std::max(need_links, c.n_links);
+    need_new = std::max(need_new, std::max(c.n_new, c.n_cov));
+  }
   if (bad) {
     return fail(MI_ECAPACITY, "a device list overflowed during the step (status bits " + std::to_string(bad) +
                                   "; boundary nodes " + std::to_string(c.n_bc) + "/" + std::to_string(cap_bc) +
@@ -562,6 +571,22 @@ mi_status mi_delbm::check_status(bool clear) {
                                   ", uncovered " + std::to_string(c.n_new) + "/" + std::to_string(cap_new) +
                                   ", covered " + std::to_string(c.n_cov) + "/" + std::to_string(cap_new) + ")");
   }
+  return MI_OK;
+}
+
+// Before a step: lists that a previous step overflowed grow to what it
+// needed plus a quarter (the graphs, which hold the old list pointers, are
+// captured again).
+mi_status mi_delbm::grow_lists_if_needed() {
+  if (need_bc <= cap_bc && need_links <= cap_links && need_new <= cap_new) return MI_OK;
+  auto grown = [](unsigned need, unsigned cap) -> unsigned {
+    if (need <= cap) return cap;
+    const unsigned long long g = (unsigned long long)need + need / 4 + 64;
+    return (unsigned)std::min<unsigned long long>(g, 0xFFFFFFF0ull);
+  };
+  mi_status s = ensure_list_capacity(grown(need_bc, cap_bc), grown(need_links, cap_links), grown(need_new, cap_new));
+  if (s != MI_OK) return s;
+  invalidate_graphs();
   return MI_OK;
 }
 
@@ -800,8 +825,10 @@ mi_status mi_delbm_step(mi_delbm* h, int n_steps) {
   if (!h) return MI_EINVAL;
   if (n_steps < 0) return h->fail(MI_EINVAL, "mi_delbm_step: n_steps < 0");
   if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status s = h->grow_lists_if_needed();
+  if (s != MI_OK) return s;
   for (int n = 0; n < n_steps; ++n) {
-    mi_status s = (h->use_graphs && !h->timing) ? h->graph_step() : h->run_phases(MI_PHASE_ALL);
+    s = (h->use_graphs && !h->timing) ? h->graph_step() : h->run_phases(MI_PHASE_ALL);
     if (s != MI_OK) return s;
   }
   return MI_OK;
@@ -819,7 +846,82 @@ mi_status mi_delbm_step_phases(mi_delbm* h, unsigned phases) {
   if (!h) return MI_EINVAL;
   if (phases & ~0xFFu) return h->fail(MI_EINVAL, "mi_delbm_step_phases: unknown phase bits");
   if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  mi_status s = h->grow_lists_if_needed();
+  if (s != MI_OK) return s;
   return h->run_phases(phases);
+}
+
+mi_status mi_delbm_reserve_lists(mi_delbm* h, size_t boundary_nodes, size_t links, size_t new_nodes) {
+  if (!h) return MI_EINVAL;
+  if (boundary_nodes < 1 || links < 1 || new_nodes < 1 || boundary_nodes > 0xFFFFFFF0ull || links > 0xFFFFFFF0ull ||
+      new_nodes > 0xFFFFFFF0ull)
+    return h->fail(MI_EINVAL, "mi_delbm_reserve_lists: each capacity must be in 1 .. 2^32 - 16");
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  if (!h->particles_ready) {
+    mi_status s = h->ensure_particle_buffers();
+    if (s != MI_OK) return s;
+  }
+  // exactly these sizes: drop the current lists first so that they may shrink
+  mi_status s = h->sync("mi_delbm_reserve_lists");
+  if (s != MI_OK) return s;
+  h->dfree(h->bc_cell); h->dfree(h->bc_mask); h->dfree(h->bc_loff); h->dfree(h->link_bc); h->dfree(h->link_p);
+  h->dfree(h->link_dir); h->dfree(h->link_q); h->dfree(h->new_cell); h->dfree(h->cov_cell); h->dfree(h->bc_tmp);
+  h->bc_cell = h->bc_mask = h->bc_loff = h->link_bc = h->link_p = h->new_cell = h->cov_cell = nullptr;
+  h->link_dir = nullptr;
+  h->link_q = nullptr;
+  h->bc_tmp = nullptr;
+  h->cap_bc = h->cap_links = h->cap_new = 0;
+  h->need_bc = h->need_links = h->need_new = 0;
+  s = h->ensure_list_capacity((unsigned)boundary_nodes, (unsigned)links, (unsigned)new_nodes);
+  h->invalidate_graphs();
+  return s;
+}
+
+mi_status mi_delbm_set_guess_wait(mi_delbm* h, unsigned wait_rounds, int stall) {
+  if (!h) return MI_EINVAL;
+  h->guess_wait_limit = wait_rounds;
+  h->guess_stall = stall ? 1 : 0;
+  h->invalidate_graphs();
+  return MI_OK;
+}
+
+mi_status mi_delbm_check(mi_delbm* h, mi_delbm_health* out) {
+  if (!h || !out) return MI_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->first_bad_node = -1;
+  out->first_bad_particle = -1;
+  if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
+  if (!h->check_buf) {
+    h->check_buf = (long long*)h->dalloc(2 * sizeof(long long));
+    if (!h->check_buf) return h->fail(MI_ENOMEM, "mi_delbm_check: device allocation failed");
+  }
+  const uint32_t* own = h->particles_ready && h->n_particles > 0 ? h->owner[h->owner_cur] : nullptr;
+  cudaError_t e = launch_check(h->pop[h->cur], h->geom(), h->cfg.storage, own, h->check_buf, h->sm_count, h->stream);
+  long long res[2] = {0, -1};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, h->check_buf, sizeof(res), cudaMemcpyDeviceToHost, h->stream);
+  std::vector<DevParticle> parts((size_t)h->n_particles);
+  if (e == cudaSuccess && h->n_particles > 0)
+    e = cudaMemcpyAsync(parts.data(), h->dP, sizeof(DevParticle) * parts.size(), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "mi_delbm_check");
+  out->bad_populations = res[0];
+  out->first_bad_node = res[0] > 0 ? res[1] : -1;
+  for (int p = 0; p < h->n_particles; ++p) {
+    const DevParticle& P = parts[p];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(P.pos[a]) && std::isfinite(P.vel[a]) && std::isfinite(P.omega[a]);
+    for (int a = 0; a < 4; ++a) ok = ok && std::isfinite(P.quat[a]);
+    if (!ok) {
+      if (out->bad_particles == 0) out->first_bad_particle = p;
+      out->bad_particles += 1;
+    }
+  }
+  if (out->bad_populations || out->bad_particles)
+    return h->fail(MI_ESTATE, "non-finite state: " + std::to_string(out->bad_populations) +
+                                  " populations at non-solid nodes (first at node " +
+                                  std::to_string(out->first_bad_node) + "), " + std::to_string(out->bad_particles) +
+                                  " particle states");
+  return MI_OK;
 }
 
 static mi_status pop_copy(mi_delbm* h, const float* src_host, float* dst_host, size_t count) {

@@ -81,6 +81,9 @@ struct mi_delbm {
   float4* bp_vel = nullptr;           // FP32 velocities and angular velocities of the substep (2 per particle)
   // learned contact guess (MI_GUESS_LEARNED): parameters and per-item buffers
   bool learned = false;
+  unsigned guess_wait_limit = 0;     // try_wait rounds of the tcgen05 MLP kernel's waits (0: its default)
+  int guess_stall = 0;               // fault-injection tests: the MLP kernel first waits on a barrier nothing arrives at
+  long long* check_buf = nullptr;    // mi_delbm_check: count of non-finite values and the first node
   bool warm = false;                 // MI_GUESS_WARM
   void* mlp_image = nullptr;         // packed BF16 parameters of the fused inference kernel
   float* guess_feat = nullptr;       // cap_items x 64
@@ -93,6 +96,8 @@ struct mi_delbm {
   uint32_t* new_cell = nullptr;
   uint32_t* cov_cell = nullptr;     // nodes covered this step (cover/uncover rule; capacity cap_new)
   unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
+  // list sizes a step that overflowed needed: the lists grow to them before the next step
+  unsigned need_bc = 0, need_links = 0, need_new = 0;
   void* bc_tmp = nullptr;            // 19 stored values per boundary node (overlapped schedule)
   bool overlap_boundary = false;     // boundary nodes computed beside the bulk kernel, scattered after it
   bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
@@ -119,6 +124,7 @@ struct mi_delbm {
   mi::CollideParams collide_params() const;
   bool forcing() const;
 
+  mi_status grow_lists_if_needed();
   mi_status run_phases(unsigned phases);
   mi_status phase_flag(cudaStream_t st);
   mi_status phase_links(cudaStream_t st);

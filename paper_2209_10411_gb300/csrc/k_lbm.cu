@@ -11,6 +11,7 @@
 // absorb the sector overlap so DRAM sees each element once), FP32 collision,
 // 19 streaming stores.  Algorithmic traffic: 19 * 2 * sizeof(storage) bytes
 // per node update (+1 byte of node class when particles are present).
+#include <climits>
 #include "mi_internal.cuh"
 
 namespace mi {
@@ -917,6 +918,51 @@ __global__ void k_unpack(const typename Store<ST>::T* pop, float* __restrict__ d
 }
 
 static inline long long ncell_of(const LatticeGeom& g) { return (long long)g.nx * g.ny * g.nz; }
+
+// Non-finite stored populations (NaN or infinite) at nodes that are not solid
+// (owner NULL: every node): out[0] += their count, out[1] = the smallest
+// such node index.  For 16-bit storages the test is on the bits (an all-ones
+// exponent).
+__device__ __forceinline__ bool bad_value(float v) { return !isfinite(v); }
+__device__ __forceinline__ bool bad_value(__half v) { return (__half_as_ushort(v) & 0x7C00u) == 0x7C00u; }
+__device__ __forceinline__ bool bad_value(__nv_bfloat16 v) { return (__bfloat16_as_ushort(v) & 0x7F80u) == 0x7F80u; }
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_check(const typename Store<ST>::T* __restrict__ pop, long long ncell,
+                                               long long plane, const uint32_t* __restrict__ owner,
+                                               long long* __restrict__ out) {
+  long long nbad = 0, first = LLONG_MAX;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    if (owner && owner[c] != OWNER_NONE) continue;
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) k += bad_value(pop[i * plane + c]) ? 1 : 0;
+    if (k) {
+      nbad += k;
+      first = c < first ? c : first;
+    }
+  }
+  if (nbad) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)nbad);
+    atomicMin(out + 1, first);
+  }
+}
+
+cudaError_t launch_check(const void* pop, const LatticeGeom& g, int storage, const uint32_t* owner, long long* out,
+                         int sm_count, cudaStream_t s) {
+  const long long init[2] = {0, LLONG_MAX};
+  cudaError_t e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const long long ncell = (long long)g.nx * g.ny * g.nz;
+  const int grid = sm_count * 8;
+  if (storage == MI_STORE_F16_DEV)
+    k_check<MI_STORE_F16_DEV><<<grid, 256, 0, s>>>(static_cast<const __half*>(pop), ncell, g.plane, owner, out);
+  else if (storage == MI_STORE_BF16_DEV)
+    k_check<MI_STORE_BF16_DEV><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), ncell, g.plane, owner, out);
+  else
+    k_check<MI_STORE_F32><<<grid, 256, 0, s>>>(static_cast<const float*>(pop), ncell, g.plane, owner, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fill_rest(void* pop, const LatticeGeom& g, int storage, float rho0, cudaStream_t s) {
   const long long n = ncell_of(g);

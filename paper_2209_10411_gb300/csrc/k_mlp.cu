@@ -636,7 +636,7 @@ __global__ void k_mlp_pack_tc(const float* __restrict__ p, unsigned char* __rest
 namespace mi {
 namespace {
 
-constexpr unsigned TC_WAIT_LIMIT = 1u << 24;  // try_wait rounds before a wait gives up
+constexpr unsigned TC_WAIT_LIMIT = 1u << 24;  // default: try_wait rounds before a wait gives up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -646,9 +646,10 @@ __device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
-// Bounded wait for the completion of the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
-  for (unsigned it = 0; it < TC_WAIT_LIMIT; ++it) {
+// Bounded wait for the completion of the phase with the given parity; false
+// after `limit` try_wait rounds.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity, unsigned limit = TC_WAIT_LIMIT) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -717,9 +718,16 @@ __device__ __forceinline__ unsigned pack_bf2(float a, float b) {
 namespace mi {
 namespace {
 
+// wait_limit: try_wait rounds of every wait on the work's progress (0: the
+// default).  stall != 0 (fault-injection tests only): before any work is
+// issued, thread 0 waits, with that limit, on an mbarrier that nothing
+// arrives at, so that the wait runs out and the abort path runs with no copy
+// or MMA in flight.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* __restrict__ img, const float* __restrict__ X,
                                                    int M, const unsigned* __restrict__ Mdev, float* __restrict__ Y,
-                                                   unsigned* __restrict__ err, unsigned err_bit) {
+                                                   unsigned* __restrict__ err, unsigned err_bit, unsigned wait_limit,
+                                                   int stall) {
+  const unsigned wl = wait_limit ? wait_limit : TC_WAIT_LIMIT;
   extern __shared__ __align__(16) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // warp w reads TMEM lanes 32 (w % 4) ..: this thread's tile row, and column half w / 4
@@ -730,6 +738,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
 
   const unsigned sbase = smem_u32(sm);
   const unsigned full0 = sbase + TS_BAR, empty0 = sbase + TS_BAR + 16, done = sbase + TS_BAR + 32;
+  const unsigned never = sbase + TS_BAR + 48;  // the stall test's barrier: nothing arrives at it
   unsigned* tmem_slot = reinterpret_cast<unsigned*>(sm + TS_BAR + 40);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + TS_BAR + 44);
   float* W3t = reinterpret_cast<float*>(sm + TS_P);
@@ -743,6 +752,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(done, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -770,7 +780,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
 
   auto issue = [&](int c) {  // thread 0: copy weight chunk c into the next ring slot
     const unsigned s = g_issued & 1u, use = g_issued >> 1;
-    if (use > 0 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1u)) { ok = false; return; }
+    if (use > 0 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1u, wl)) { ok = false; return; }
     mbar_expect_tx(full0 + 8 * s, TC_CHUNK);
     bulk_g2s(sbase + TS_W + s * TC_CHUNK, img + TCI_W + (size_t)c * TC_CHUNK, TC_CHUNK, full0 + 8 * s);
     ++g_issued;
@@ -778,7 +788,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
   // thread 0: MMAs of the next copied chunk: A (K extent a_kext, starting K a_k0), accumulate into D
   auto consume = [&](unsigned a_base, unsigned a_kext, unsigned a_k0, bool first) {
     const unsigned s = g_used & 1u, use = g_used >> 1;
-    if (!mbar_wait(full0 + 8 * s, use & 1u)) { ok = false; return; }
+    if (!mbar_wait(full0 + 8 * s, use & 1u, wl)) { ok = false; return; }
     tc_fence_after();
     const unsigned b_base = sbase + TS_W + s * TC_CHUNK;
 #pragma unroll
@@ -791,8 +801,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
     ++g_used;
   };
 
+  if (stall) {
+    if (tid == 0 && !mbar_wait(never, 0u, wl)) *abort_flag = 1;
+    __syncthreads();
+  }
   int t = blockIdx.x;
-  for (; t < tiles; t += gridDim.x) {
+  for (; t < tiles && !*abort_flag; t += gridDim.x) {
     const int r0 = t * TC_M;
     // X tile: this thread's half of its row, BF16, core-matrix layout (K extent 64)
     {
@@ -822,7 +836,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
     __syncthreads();
     if (*abort_flag) break;
     // ---- layer-1 epilogue: H1 = relu(D + b1) as BF16 (A operand of layer 2) ----
-    if (!mbar_wait(done, n_done & 1u)) *abort_flag = 1;
+    if (!mbar_wait(done, n_done & 1u, wl)) *abort_flag = 1;
     ++n_done;
     tc_fence_after();
     __syncthreads();
@@ -857,7 +871,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const unsigned char* _
     __syncthreads();
     if (*abort_flag) break;
     // ---- layer-2 epilogue and the output layer ----
-    if (!mbar_wait(done, n_done & 1u)) *abort_flag = 1;
+    if (!mbar_wait(done, n_done & 1u, wl)) *abort_flag = 1;
     ++n_done;
     tc_fence_after();
     __syncthreads();
@@ -925,7 +939,7 @@ cudaError_t mlp_tc_prepare() {
 }
 
 cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, unsigned* err,
-                         unsigned err_bit, cudaStream_t s) {
+                         unsigned err_bit, cudaStream_t s, unsigned wait_limit, int stall) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -933,7 +947,8 @@ cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigne
   const int tiles = (M + TC_M - 1) / TC_M;
   if (tiles <= 0) return cudaSuccess;
   const int grid = tiles < sms ? tiles : sms;
-  k_mlp_tc<<<grid, TC_THREADS, TS_BYTES, s>>>(reinterpret_cast<const unsigned char*>(image), X, M, Mdev, Y, err, err_bit);
+  k_mlp_tc<<<grid, TC_THREADS, TS_BYTES, s>>>(reinterpret_cast<const unsigned char*>(image), X, M, Mdev, Y, err, err_bit,
+                                              wait_limit, stall);
   return cudaGetLastError();
 }
 

@@ -169,6 +169,9 @@ cudaError_t launch_bulk(const BulkLaunch& L, cudaStream_t s);
 
 // Fill every node with the rest state f_i = w_i rho0.
 cudaError_t launch_fill_rest(void* pop, const LatticeGeom& g, int storage, float rho0, cudaStream_t s);
+// mi_delbm_check: out[0] = non-finite stored populations at non-solid nodes, out[1] = the first such node
+cudaError_t launch_check(const void* pop, const LatticeGeom& g, int storage, const uint32_t* owner, long long* out,
+                         int sm_count, cudaStream_t s);
 // Convert float populations [19][ncell] (dense) to/from the storage layout.
 cudaError_t launch_pack(const float* src, void* pop, const LatticeGeom& g, int storage, cudaStream_t s);
 cudaError_t launch_unpack(const void* pop, float* dst, const LatticeGeom& g, int storage, cudaStream_t s);
@@ -356,7 +359,7 @@ size_t mlp_image_total();  // both images back to back (the C-ABI's packed image
 cudaError_t mlp_tc_pack(const float* params, void* image, cudaStream_t s);
 cudaError_t mlp_tc_prepare();
 cudaError_t mlp_tc_infer(const void* image, const float* X, int M, const unsigned* Mdev, float* Y, unsigned* err,
-                         unsigned err_bit, cudaStream_t s);
+                         unsigned err_bit, cudaStream_t s, unsigned wait_limit = 0, int stall = 0);
 
 struct IntegrateLaunch {
   DevParticle* P;

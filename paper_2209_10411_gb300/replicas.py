@@ -14,10 +14,28 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+class RankFailure(RuntimeError):
+    """A peer rank did not reach a collective in time (it failed or left)."""
+
+
+def init_process_group(backend, timeout_s=600.0, **kw):
+    """torch.distributed's process group with a bounded wait on every
+    collective: a rank that fails or leaves makes the others' next barrier
+    or reduction raise instead of waiting forever."""
+    import datetime
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s), **kw)
+
+
 def barrier(world):
+    """Wait for every rank; RankFailure if a peer does not arrive within the
+    process group's timeout (or has gone)."""
     if world > 1:
         import torch.distributed as dist
-        dist.barrier()
+        try:
+            dist.barrier()
+        except RuntimeError as e:
+            raise RankFailure("a rank did not reach the barrier: %s" % str(e).splitlines()[0]) from e
 
 
 def max_over_ranks(value, world, device=None):
