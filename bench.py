@@ -865,6 +865,44 @@ def c4_leg(B, scenes, stream_obj, steps=100, timed_kernels=20):
     return out
 
 
+def c3_leg(B, scenes, stream_obj, steps=1000):
+    """The drafting-kissing-tumbling channel (192x192x768, a 1-ball sphere and
+    a 32-ball prolate grain 30 lu apart), FP32: MLUPS with all `steps` steps
+    of one call in one CUDA graph launch (a conditional while node over
+    two-step bodies) and with one graph launch per step."""
+    import torch
+    sc = scenes.config3()
+    nx, ny, nz = sc.shape
+    out = {"workload": sc.name, "lattice": list(sc.shape), "particles": len(sc.particles),
+           "metaballs": [int(len(p.k)) for p in sc.particles], "steps": steps}
+    for name, loop in (("one_graph_for_all_steps", True), ("one_graph_per_step", False)):
+        sim = build_sim(B, sc, 0, stream_obj.cuda_stream)
+        sim.set_graphs(True, device_loop=loop)
+        sim.step(1)
+        sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json"))
+        sim.step(4)
+        sim.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = sim.launch_count()
+        t0 = time.perf_counter()
+        ev0.record(stream_obj)
+        if loop:
+            sim.step(steps)
+        else:
+            for _ in range(steps):
+                sim.step(1)
+        ev1.record(stream_obj)
+        host_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = [sim.get_particle_state(i) for i in range(len(sc.particles))]
+        out[name] = {"value": nx * ny * nz * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+                     "kernel_launches": sim.launch_count() - l0, "host_enqueue_s": host_s,
+                     "z_after": [float(x["pos"][2]) for x in st]}
+        sim.close()
+    return out
+
+
 def measured_alu_peaks(B):
     """FP32 and FP64 FMA throughput of this GPU from the library's own
     microbenchmark (mi_measure_fma_peak)."""
@@ -885,7 +923,7 @@ def run_mine(args):
     from paper_2209_10411_gb300 import scenes
 
     storage = STORAGE[args.storage]
-    scene = {"c2": scenes.config2, "c4": scenes.config4}[args.config](seed=rank)
+    scene = {"c2": scenes.config2, "c3": scenes.config3, "c4": scenes.config4}[args.config](seed=rank)
     alu = measured_alu_peaks(B) if rank == 0 else None
     if args.lattice:  # smaller profiling case: same particles, positions scaled into the box
         old = np.array(scene.shape, dtype=float)
@@ -898,7 +936,9 @@ def run_mine(args):
     ncell = nx * ny * nz
     npart = len(scene.particles)
 
-    sim.set_graphs(not args.no_graphs)
+    # the channel's steps all run in one graph launch (a device-side loop)
+    loop = args.config == "c3"
+    sim.set_graphs(not args.no_graphs, device_loop=loop)
     sim.step(1)
     tuning = sim.autotune(os.path.join(tempfile.gettempdir(), "mi_delbm_tune.json")) if not args.no_tune else None
     for _ in range(max(3, args.warmup)):
@@ -915,8 +955,11 @@ def run_mine(args):
     time.sleep(0.25)
     launches0 = sim.launch_count()
     ev0.record(stream)
-    for _ in range(args.steps):
-        sim.step(1)
+    if loop and not args.no_graphs:
+        sim.step(args.steps)
+    else:
+        for _ in range(args.steps):
+            sim.step(1)
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = sim.launch_count() - launches0
@@ -959,6 +1002,9 @@ def run_mine(args):
     c4 = None
     if c2 and not args.no_c4 and rank == 0:
         c4 = c4_leg(B, scenes, stream)
+    c3 = None
+    if c2 and not args.no_c3 and rank == 0:
+        c3 = c3_leg(B, scenes, stream)
     peak, peak_kind = _peaks()
     # the bulk kernel updates every node (boundary nodes are rewritten by the
     # boundary kernel): 19 loads + 19 stores of the stored type per node
@@ -1014,6 +1060,7 @@ def run_mine(args):
            "graphs": not args.no_graphs, "tuning": tuning,
            "storage_variants": variants,
            "c4_precision_tank": c4,
+           "c3_dkt_channel": c3,
            "contacts": contacts,
            "alu_peaks": alu,
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -1031,7 +1078,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2", "c4"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1041,11 +1088,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage measurements")
     ap.add_argument("--no-c4", action="store_true", help="skip the 512^3 precision-tank measurements")
+    ap.add_argument("--no-c3", action="store_true", help="skip the drafting-kissing-tumbling channel measurements")
     ap.add_argument("--small-contact-lattice", action="store_true",
                     help="contact bed on a 16^3 periodic lattice (profiling: same pairs, no walls, little memory)")
     args = ap.parse_args()
     from paper_2209_10411_gb300 import scenes
-    sc = {"c2": scenes.config2, "c4": scenes.config4}[args.config]()
+    sc = {"c2": scenes.config2, "c3": scenes.config3, "c4": scenes.config4}[args.config]()
     # the workload both arms name (the GPU arm adds what its run measures)
     CONFIG.update({"workload": sc.name, "lattice": list(sc.shape), "particles": len(sc.particles),
                    "metaballs": [int(len(p.k)) for p in sc.particles], "storage": args.storage, "tau": sc.tau})

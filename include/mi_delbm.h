@@ -384,11 +384,16 @@ mi_status mi_delbm_check(mi_delbm *h, mi_delbm_health *out);
 mi_status mi_mass_properties_noalloc(const double *balls_dev, int n_balls, double density, double spacing,
                                      double *out_dev, void *stream);
 
-/* Run mi_delbm_step through CUDA graphs (enable != 0, the default) or as
- * individual launches.  A graph of one whole step is captured on first use
- * for each parity of the alternating buffers and replayed afterwards; adding
- * a particle discards the graphs.  While per-phase timing is enabled, steps
- * run as individual launches. */
+/* How mi_delbm_step runs its steps: 0 as individual launches; 1 (the
+ * default) one CUDA graph launch per step: a graph of one whole step is
+ * captured on first use for each parity of the alternating buffers and
+ * replayed afterwards; 2 one graph launch for all the steps of a call: a
+ * graph whose conditional while node repeats a body of two whole steps (both
+ * parities) until a device counter, set before the launch, runs out; an odd
+ * step count adds one single-step graph.  The three give the same bits.
+ * Adding a particle, and every call documented to do so, discards the graphs.
+ * While per-phase timing is enabled, steps run as individual launches.
+ * Errors: MI_EINVAL (enable not 0, 1 or 2). */
 mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
 
 /* Choose the launch shapes of the bulk kernel (threads per block along x,

@@ -527,8 +527,11 @@ class Simulation:
         this step joins its hydrodynamic force and torque."""
         self._check(lib.mi_delbm_set_momentum_rules(self.h, MOMENTUM_COVER_UNCOVER if cover_uncover else 0))
 
-    def set_graphs(self, on):
-        self._check(lib.mi_delbm_set_graphs(self.h, 1 if on else 0))
+    def set_graphs(self, on, device_loop=False):
+        """on=False: individual launches; on=True: one graph per step, or with
+        device_loop=True one graph launch per step() call (a conditional while
+        node over two-step bodies)."""
+        self._check(lib.mi_delbm_set_graphs(self.h, (2 if device_loop else 1) if on else 0))
 
     def set_timing(self, on):
         self._check(lib.mi_delbm_set_timing(self.h, 1 if on else 0))

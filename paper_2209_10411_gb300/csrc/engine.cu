@@ -461,7 +461,97 @@ void mi_delbm::invalidate_graphs() {
     if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
     gexec[k] = nullptr;
     glaunches[k] = 0;
+    if (gloop[k]) cudaGraphExecDestroy(gloop[k]);
+    gloop[k] = nullptr;
+    gloop_launches[k] = 0;
   }
+}
+
+namespace {
+__global__ void k_loop_set(int* count, long long pairs) { *count = (int)pairs; }
+// The last node of the loop body: one step pair done; run the body again
+// while pairs are left.
+__global__ void k_loop_tail(int* count, cudaGraphConditionalHandle h) {
+  const int left = *count - 1;
+  *count = left;
+  cudaGraphSetConditional(h, left > 0 ? 1u : 0u);
+}
+}  // namespace
+
+// `pairs` step pairs as one graph launch: a conditional while node whose body
+// (captured from the same run_phases() as the eager path, twice, so that
+// both buffer parities are in it) ends with a kernel that counts the pairs
+// down on the device.  The host state advances by 2 pairs steps; the
+// buffer parities return to where they were.
+mi_status mi_delbm::loop_steps(long long pairs) {
+  if (pairs <= 0) return MI_OK;
+  if (pairs > 0x7FFFFFFF) return fail(MI_EINVAL, "mi_delbm_step: too many steps for one device loop");
+  const int key = (cur & 1) | ((owner_cur & 1) << 1);
+  if (!loop_count) {
+    loop_count = (int*)dalloc(sizeof(int));
+    if (!loop_count) return fail(MI_ENOMEM, "device loop: counter allocation failed");
+  }
+  if (!gloop[key]) {
+    if (n_particles > 0) {
+      mi_status s = ensure_contact_buffers();
+      if (s != MI_OK) return s;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    cudaGraphConditionalHandle hnd;
+    e = cudaGraphConditionalHandleCreate(&hnd, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "device loop: conditional node");
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const int c0 = cur, o0 = owner_cur;
+    const long long s0 = step_index, l0 = launches;
+    e = cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    }
+    mi_status st = run_phases(MI_PHASE_ALL);
+    if (st == MI_OK) st = run_phases(MI_PHASE_ALL);
+    if (st == MI_OK) {
+      k_loop_tail<<<1, 1, 0, stream>>>(loop_count, hnd);
+      launches += 1;
+      if (cudaGetLastError() != cudaSuccess) st = fail(MI_ECUDA, "device loop: tail launch failed");
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(stream, &captured);
+    gloop_launches[key] = launches - l0;
+    cur = c0;
+    owner_cur = o0;
+    step_index = s0;
+    launches = l0;
+    if (st != MI_OK || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return st != MI_OK ? st : cuda_fail(e2, "cudaStreamEndCapture (device loop)");
+    }
+    e = cudaGraphInstantiate(&gloop[key], g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gloop[key] = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate (device loop)");
+    }
+  }
+  k_loop_set<<<1, 1, 0, stream>>>(loop_count, pairs);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGraphLaunch(gloop[key], stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device loop launch");
+  launches += 1 + pairs * gloop_launches[key];
+  step_index += 2 * pairs;
+  return MI_OK;
 }
 
 // One full step replayed from a CUDA graph.  A step alternates the population
@@ -827,7 +917,12 @@ mi_status mi_delbm_step(mi_delbm* h, int n_steps) {
   if (!h->set_device()) return h->fail(MI_ECUDA, "cudaSetDevice failed");
   mi_status s = h->grow_lists_if_needed();
   if (s != MI_OK) return s;
-  for (int n = 0; n < n_steps; ++n) {
+  int n = 0;
+  if (h->use_graphs && h->loop_graphs && !h->timing && n_steps >= 2) {
+    if ((s = h->loop_steps(n_steps / 2)) != MI_OK) return s;
+    n = 2 * (n_steps / 2);
+  }
+  for (; n < n_steps; ++n) {
     s = (h->use_graphs && !h->timing) ? h->graph_step() : h->run_phases(MI_PHASE_ALL);
     if (s != MI_OK) return s;
   }
@@ -990,7 +1085,9 @@ mi_status mi_delbm_get_device_view(mi_delbm* h, mi_delbm_device_view* v) {
 
 mi_status mi_delbm_set_graphs(mi_delbm* h, int enable) {
   if (!h) return MI_EINVAL;
+  if (enable < 0 || enable > 2) return h->fail(MI_EINVAL, "mi_delbm_set_graphs: mode must be 0, 1 or 2");
   h->use_graphs = enable != 0;
+  h->loop_graphs = enable == 2;
   return MI_OK;
 }
 

@@ -35,6 +35,13 @@ struct mi_delbm {
   bool use_graphs = true;
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
   long long glaunches[4] = {0, 0, 0, 0};
+  // device-loop graphs (mi_delbm_set_graphs(h, 2)): a conditional while node
+  // whose body is two whole steps, keyed like gexec; loop_count is the
+  // device counter of step pairs left
+  bool loop_graphs = false;
+  cudaGraphExec_t gloop[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long gloop_launches[4] = {0, 0, 0, 0};
+  int* loop_count = nullptr;
 
   size_t ncell = 0;   // nx*ny*nz
   size_t plane = 0;   // elements between population planes
@@ -125,6 +132,7 @@ struct mi_delbm {
   bool forcing() const;
 
   mi_status grow_lists_if_needed();
+  mi_status loop_steps(long long pairs);
   mi_status run_phases(unsigned phases);
   mi_status phase_flag(cudaStream_t st);
   mi_status phase_links(cudaStream_t st);

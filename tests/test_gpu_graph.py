@@ -138,3 +138,48 @@ def test_overlapped_boundary_schedule_is_bitwise_identical(storage):
     for x, y in zip(sa, sb):
         for key in x:
             assert np.array_equal(x[key], y[key]), key
+
+
+@pytest.mark.parametrize("nsteps,dem_substeps", [(7, 1), (8, 3)])
+def test_device_loop_graph_is_bitwise_identical(nsteps, dem_substeps):
+    """All steps of one call as one graph launch (a conditional while node
+    over two-step bodies, the pair count on the device; an odd count adds a
+    single-step graph) against one graph launch per step: the same bits, in
+    two calls in a row (the second replays the instantiated loop)."""
+    B = binding()
+    shape = (48, 48, 40)
+    parts = _cluster(6)
+    for P in parts:
+        P["vel"] = P["vel"] * 20.0
+    nx, ny, nz = shape
+    u = 0.02 * scenes.velocity_field_noise(shape, 11)
+    f0 = lbm.equilibrium(np.ones((nz, ny, nx)), u).astype(np.float32)
+    res = []
+    for loop in (False, True):
+        sim = B.Simulation(*shape, tau=0.8, gravity=(0, 0, -1e-4), dem_substeps=dem_substeps, kn=PARAMS["kn"],
+                           kt=PARAMS["kt"], eta_n=PARAMS["eta_n"], eta_t=PARAMS["eta_t"], mu_s=PARAMS["mu_s"],
+                           max_particles=64)
+        sim.set_graphs(True, device_loop=loop)
+        for P in parts:
+            sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"],
+                             P["omega"], mass_props={"mass": P["mass"], "volume": P["volume"],
+                                                     "inertia": P["inertia"]})
+        sim.set_populations(f0)
+        l0 = sim.launch_count()
+        sim.step(nsteps)
+        sim.step(nsteps)
+        launches = sim.launch_count() - l0
+        st = [sim.get_particle_state(i) for i in range(len(parts))]
+        res.append((sim.forces(), st, sim.get_raw_populations(), sim.node_classes(), launches))
+        sim.close()
+    (fa, sa, pa, (ca, oa), la), (fb, sb, pb, (cb, ob), lb) = res
+    for key in fa:
+        assert np.array_equal(fa[key], fb[key]), key
+    for x, y in zip(sa, sb):
+        for key in x:
+            assert np.array_equal(x[key], y[key]), key
+    assert np.array_equal(ca, cb) and np.array_equal(oa, ob)
+    fluid = oa == 0xFFFFFFFF
+    assert np.array_equal(pa[:, fluid].view(np.uint32), pb[:, fluid].view(np.uint32))
+    # the same kernels, plus per call one counter kernel and one loop-tail kernel per step pair
+    assert lb - la == 2 * (nsteps // 2 + 1)
