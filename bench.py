@@ -409,6 +409,9 @@ CONFIG = {}
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+SCHEDULE = {"overlap": False}   # --schedule: boundary nodes beside the bulk kernel
+
+
 def build_sim(B, scene, storage, stream, dem_substeps=1):
     nx, ny, nz = scene.shape
     sim = B.Simulation(nx, ny, nz, tau=scene.tau, gravity=scene.gravity, storage=storage, stream=stream,
@@ -416,6 +419,8 @@ def build_sim(B, scene, storage, stream, dem_substeps=1):
                        max_balls=max(65536, sum(len(p.k) for p in scene.particles)), dem_substeps=dem_substeps)
     for p in scene.particles:
         sim.add_particle(p.centers, p.k, p.density, p.skin, p.pos, p.quat, p.vel, p.omega)
+    if SCHEDULE["overlap"]:
+        sim.set_schedule(overlap_boundary=True)
     return sim
 
 
@@ -1089,9 +1094,12 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 storage measurements")
     ap.add_argument("--no-c4", action="store_true", help="skip the 512^3 precision-tank measurements")
     ap.add_argument("--no-c3", action="store_true", help="skip the drafting-kissing-tumbling channel measurements")
+    ap.add_argument("--schedule", default="default", choices=["default", "overlap"],
+                    help="overlap: boundary nodes computed beside the bulk kernel (same bits)")
     ap.add_argument("--small-contact-lattice", action="store_true",
                     help="contact bed on a 16^3 periodic lattice (profiling: same pairs, no walls, little memory)")
     args = ap.parse_args()
+    SCHEDULE["overlap"] = args.schedule == "overlap"
     from paper_2209_10411_gb300 import scenes
     sc = {"c2": scenes.config2, "c3": scenes.config3, "c4": scenes.config4}[args.config]()
     # the workload both arms name (the GPU arm adds what its run measures)

@@ -10,6 +10,7 @@
 // re-evaluated in FP64 with unfused operations in the order: x - X, R^T,
 // ball by ball k / |x_b - c|^2 accumulated left to right.
 #include <cfloat>
+#include <climits>
 
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
@@ -133,6 +134,8 @@ __global__ void k_prologue(ParticleLaunch L) {
     if (prev != BOX_NONE && abs(P.lo[a] - prev) > 2) atomicOr(&L.ctr->status, STATUS_MOVED_TOO_FAR);
   }
   for (int k = 0; k < 6; ++k) L.facc[6 * p + k] = 0;
+  P.srad2[L.cur_buf] = -1;  // the solid radius of this step, grown by k_flag
+  for (int a = 0; a < 3; ++a) P.sctr[L.cur_buf][a] = (float)P.pos[a];
 }
 
 cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s) {
@@ -177,6 +180,9 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
   const DevParticle& P = L.P[p];
   const int nb = P.n_balls;
   const bool staged = nb <= L.max_balls_per_particle;
+  __shared__ int rr_s;  // the block's largest squared solid distance (float bits)
+  volatile int* rr = &rr_s;
+  if (threadIdx.x == 0) rr_s = -1;
   if (staged)
     for (int i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = L.balls[P.ball_off + i];
   __syncthreads();
@@ -232,8 +238,18 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
       else if (f < 1.0f - GUARD) inside = false;
       else inside = inside_exact(P, L.balls_d, (double)x, (double)y, (double)z);
     }
-    if (inside) atomicMin(L.owner_cur + lin(x, y, z, L.g), (uint32_t)p);
+    if (inside) {
+      atomicMin(L.owner_cur + lin(x, y, z, L.g), (uint32_t)p);
+      // the block's solid radius in shared memory (non-negative floats
+      // order as their bits): an atomic only where it grows; the distance is
+      // formed again here rather than kept live through the ball loop
+      const float e0 = (float)(x - xi0) - xf0, e1 = (float)(y - xi1) - xf1, e2 = (float)(z - xi2) - xf2;
+      const int dd = __float_as_int(e0 * e0 + e1 * e1 + e2 * e2);
+      if (dd > *rr) atomicMax((int*)rr, dd);
+    }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && *rr >= 0) atomicMax(&L.P[p].srad2[L.cur_buf], *rr);
 }
 
 cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s) {
@@ -257,8 +273,9 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
   const DevParticle& P = L.P[blockIdx.y];
   int lo[3], ext[3];
   const int* lp = P.lo_hist[L.prev_buf];
+  const bool had = lp[0] != BOX_NONE;
   for (int a = 0; a < 3; ++a) {
-    if (lp[0] == BOX_NONE) {
+    if (!had) {
       lo[a] = P.lo[a];
       ext[a] = P.ext[a];
     } else {
@@ -266,16 +283,21 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
       ext[a] = max(P.lo[a], lp[a]) + P.ext[a] - lo[a];
     }
   }
+  // nodes whose class can change: the solid nodes of this step and of the
+  // previous one (within their solid radii of the positions they were
+  // flagged at), the fluid nodes next to them (a link is at most sqrt 2
+  // long), and the nodes uncovered at the previous step (solid two steps ago:
+  // within a move of the previous solid, and a particle moves at most two
+  // nodes per step): both spheres widened by 3
+  const int sc = P.srad2[L.cur_buf], sp = had ? P.srad2[L.prev_buf] : -1;
+  if (sc < 0 && sp < 0) return;
+  const float rc = sc >= 0 ? sqrtf(__int_as_float(sc)) + 3.0f : -1.0f;
+  const float rp = sp >= 0 ? sqrtf(__int_as_float(sp)) + 3.0f : -1.0f;
+  const float rc2 = rc * rc, rp2 = rp * rp;
+  const float cc0 = P.sctr[L.cur_buf][0], cc1 = P.sctr[L.cur_buf][1], cc2 = P.sctr[L.cur_buf][2];
+  const float cp0 = P.sctr[L.prev_buf][0], cp1 = P.sctr[L.prev_buf][1], cp2 = P.sctr[L.prev_buf][2];
   const Region r = clip_region(lo, ext, 2, L.g);
   const unsigned gen = L.ctr->gen;
-  // nodes whose class can change lie within Rt + 2 of the particle's old or new
-  // position; each position is within 1.5 of its box centre
-  const float rc = (float)P.Rt + 4.0f, rc2 = rc * rc;
-  float cc[3], cp[3];
-  for (int a = 0; a < 3; ++a) {
-    cc[a] = P.lo[a] + 0.5f * P.ext[a];
-    cp[a] = (lp[0] == BOX_NONE ? P.lo[a] : lp[a]) + 0.5f * P.ext[a];
-  }
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
     const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
@@ -283,9 +305,10 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
     const int y = r.lo[1] + (int)yi;
     const int z = r.lo[2] + (int)zi;
     {
-      const float a0 = x - cc[0], a1 = y - cc[1], a2 = z - cc[2];
-      const float b0 = x - cp[0], b1 = y - cp[1], b2 = z - cp[2];
-      if (a0 * a0 + a1 * a1 + a2 * a2 > rc2 && b0 * b0 + b1 * b1 + b2 * b2 > rc2) continue;
+      const float a0 = x - cc0, a1 = y - cc1, a2 = z - cc2;
+      const float b0 = x - cp0, b1 = y - cp1, b2 = z - cp2;
+      if (!(rc >= 0.f && a0 * a0 + a1 * a1 + a2 * a2 <= rc2) && !(rp >= 0.f && b0 * b0 + b1 * b1 + b2 * b2 <= rp2))
+        continue;
     }
     const long long c = lin(x, y, z, L.g);
     const bool solid = L.owner_cur[c] != OWNER_NONE;
@@ -378,7 +401,9 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
 
 cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  dim3 grid(L.blocks_per_particle, L.np);
+  // most of the node box lies outside the solid spheres: half the blocks of
+  // the flagging kernel
+  dim3 grid((L.blocks_per_particle + 1) / 2, L.np);
   if (L.cover_uncover) k_classify<true><<<grid, 256, 0, s>>>(L);
   else k_classify<false><<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();

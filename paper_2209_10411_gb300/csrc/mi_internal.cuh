@@ -200,6 +200,9 @@ struct DevParticle {
   int ext[3];                                // node box extent per axis (constant)
   int lo[3];                                 // node box origin at the current pose
   int lo_hist[2][3];                         // box origin last flagged into owner buffer b
+  int srad2[2];                              // largest squared distance from the position of that step of a
+                                             //   solid node flagged into owner buffer b, as float bits (-1: none)
+  float sctr[2][3];                          // the position (FP32) the solid nodes of buffer b were flagged at
 };
 
 // Per-step device counters and status (one instance per handle).
