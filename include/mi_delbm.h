@@ -530,6 +530,12 @@ mi_status mi_mlp_backward(const float *params, const float *X, const float *acts
 mi_status mi_mlp_adamw(float *params, const float *grads, float *m, float *v, int step, float lr, float beta1,
                        float beta2, float eps, float weight_decay, void *stream);
 
+/* Column-wise affine map of a row-major n x cols device array, in place:
+ * X[r][c] = (X[r][c] - shift[c]) * scale[c] (shift, scale: cols device
+ * floats).  The training driver standardises the features and weights the
+ * targets with it.  Asynchronous on stream.  Errors: MI_EINVAL, MI_ECUDA. */
+mi_status mi_mlp_scale_columns(float *X, long long n, int cols, const float *shift, const float *scale, void *stream);
+
 /* Fused inference: the parameters packed once into a BF16 image of
  * mi_mlp_image_bytes() bytes (device, 16-byte aligned, owned by the caller),
  * then Y (n x 4) = MLP(X (n x 64)) by one persistent kernel.

@@ -133,6 +133,7 @@ _sig("mi_mlp_param_count", c_size_t)
 _sig("mi_mlp_forward", c_int, _P, _P, c_int, _P, _P, _P)
 _sig("mi_mlp_mse", c_int, _P, _P, c_int, _P, _P, _P, _P)
 _sig("mi_mlp_backward", c_int, _P, _P, _P, _P, c_int, _P, _P, _P)
+_sig("mi_mlp_scale_columns", c_int, _P, ctypes.c_longlong, c_int, _P, _P, _P)
 _sig("mi_mlp_adamw", c_int, _P, _P, _P, _P, c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
      ctypes.c_float, _P)
 _sig("mi_mlp_image_bytes", c_size_t)
@@ -345,6 +346,13 @@ def mlp_backward(params, X, acts, dY):
     _mlp_check(lib.mi_mlp_backward(_tp(params), _tp(X), _tp(acts), _tp(dY), int(n), _tp(grads), _tp(scratch),
                                    _cur_stream()))
     return grads
+
+
+def mlp_scale_columns(X, shift, scale):
+    """In place X[r][c] = (X[r][c] - shift[c]) * scale[c] on a row-major CUDA
+    float32 tensor; shift and scale are float32 CUDA tensors of X.shape[1]."""
+    _mlp_check(lib.mi_mlp_scale_columns(_tp(X), int(X.shape[0]), int(X.shape[1]), _tp(shift), _tp(scale),
+                                        _cur_stream()))
 
 
 def mlp_adamw(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4):

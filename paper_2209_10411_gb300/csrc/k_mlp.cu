@@ -215,6 +215,20 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
 
 using namespace mi;
 
+namespace mi {
+// X[r][c] = (X[r][c] - shift[c]) * scale[c]: the training driver's feature
+// standardisation and target weighting
+__global__ void k_scale_columns(float* __restrict__ X, long long n, int cols, const float* __restrict__ shift,
+                                const float* __restrict__ scale) {
+  const long long total = n * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % cols);
+    X[e] = (X[e] - shift[c]) * scale[c];
+  }
+}
+}  // namespace mi
+
 extern "C" {
 
 // Parameter block layout (floats): W1 64x256, b1 256, W2 256x256, b2 256, W3 256x4, b3 4.
@@ -318,6 +332,20 @@ mi_status mi_mlp_adamw(float* params, const float* grads, float* m, float* v, in
                                                              weight_decay, c1, c2);
   if (cudaGetLastError() != cudaSuccess) {
     set_thread_error("mi_mlp_adamw: launch failed");
+    return MI_ECUDA;
+  }
+  return MI_OK;
+}
+
+mi_status mi_mlp_scale_columns(float* X, long long n, int cols, const float* shift, const float* scale, void* stream) {
+  if (n < 0 || cols < 1 || (n > 0 && (!X || !shift || !scale))) {
+    set_thread_error("mi_mlp_scale_columns: null pointer, n < 0 or cols < 1");
+    return MI_EINVAL;
+  }
+  if (n == 0) return MI_OK;
+  mi::k_scale_columns<<<2048, 256, 0, (cudaStream_t)stream>>>(X, n, cols, shift, scale);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_thread_error("mi_mlp_scale_columns: launch failed");
     return MI_ECUDA;
   }
   return MI_OK;

@@ -22,7 +22,7 @@ import numpy as np
 
 from . import scenes
 from ._binding import (PAIR_FEATURES, PAIR_LABELS, PAIR_LEARNED, PAIR_PLAIN, mlp_adamw, mlp_backward,
-                       mlp_forward, mlp_infer, mlp_mse, mlp_pack, mlp_param_count)
+                       mlp_forward, mlp_infer, mlp_mse, mlp_pack, mlp_param_count, mlp_scale_columns)
 
 
 def bed_shapes(seed, n_shapes, n_range=(4, 128), R_range=(8.0, 16.0), skin=1.0):
@@ -119,30 +119,40 @@ def train(X, T, steps=3000, batch=4096, lr=1e-3, lr_final=5e-5, weight_decay=1e-
     position outputs, which set the Newton start, over log r_act).  Both are
     folded back into the first and last layers afterwards (W1 <- W1 / sd by
     rows, b1 <- b1 - (mu / sd) W1; W3 <- W3 / w by columns, b3 <- b3 / w),
-    so the returned parameters act on raw features and give raw targets."""
+    so the returned parameters act on raw features and give raw targets.
+    The statistics and the fold are FP64 host arithmetic; the device arrays
+    are rescaled by the library's column kernel (mi_mlp_scale_columns)."""
     import torch
     dev = X.device
     mu = sd = None
     if standardize:
-        mu = X.mean(0)
-        sd = X.std(0).clamp_min(1e-3)
-        X = ((X - mu) / sd).contiguous()
+        Xh = X.cpu().numpy()
+        mu = Xh.mean(0, dtype=np.float64)
+        sd = np.maximum(Xh.std(0, dtype=np.float64), 1e-3)
+        X = X.clone()
+        mlp_scale_columns(X, torch.as_tensor(mu.astype(np.float32), device=dev),
+                          torch.as_tensor((1.0 / sd).astype(np.float32), device=dev))
     wt = None
     if target_weights is not None:
-        wt = torch.as_tensor(np.asarray(target_weights, dtype=np.float32), device=dev)
-        T = (T * wt).contiguous()
+        wt = np.asarray(target_weights, dtype=np.float64)
+        T = T.clone()
+        mlp_scale_columns(T, torch.zeros(T.shape[1], dtype=torch.float32, device=dev),
+                          torch.as_tensor(wt.astype(np.float32), device=dev))
     p, history = _fit(X, T, steps, batch, lr, lr_final, weight_decay, seed, params, log_every)
+    if mu is None and wt is None:
+        return p, history
     o1 = 64 * 256
     o3 = o1 + 256 + 256 * 256 + 256
-    W1, b1 = p[:o1].view(64, 256), p[o1:o1 + 256]
-    W3, b3 = p[o3:o3 + 1024].view(256, 4), p[o3 + 1024:o3 + 1028]
+    ph = p.cpu().numpy().astype(np.float64)
+    W1, b1 = ph[:o1].reshape(64, 256), ph[o1:o1 + 256]
+    W3, b3 = ph[o3:o3 + 1024].reshape(256, 4), ph[o3 + 1024:o3 + 1028]
     if mu is not None:
         b1 -= (mu / sd) @ W1
         W1 /= sd[:, None]
     if wt is not None:
         W3 /= wt[None, :]
         b3 /= wt
-    return p, history
+    return torch.as_tensor(ph.astype(np.float32), device=dev), history
 
 
 def _fit(X, T, steps, batch, lr, lr_final, weight_decay, seed, params, log_every):
