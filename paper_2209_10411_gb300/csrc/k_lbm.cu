@@ -633,6 +633,20 @@ __device__ __forceinline__ long long warp_sum_fixed(long long v) {
   return (long long)s0 + ((long long)s1 << 22) + ((long long)s2 << 44);
 }
 
+// v * 2^40 rounded to the nearest integer, ties to even: the same value as
+// __float2ll_rn(v * 2^40) without a 64-bit conversion.  f = v 2^40 is exact;
+// f = h 2^20 + r with h = rint(f 2^-20) (an integer-valued float) and the
+// remainder r, |r| <= 2^19, exact in FP32; h 2^20 is an even integer, so the
+// nearest-even integer to f is h 2^20 plus the nearest-even integer to r,
+// which adding and removing 1.5 2^23 gives (|r| < 2^22).  |v| < 2^10.
+__device__ __forceinline__ long long fixed_2m40(float v) {
+  const float f = v * 1099511627776.0f;
+  const float h = rintf(f * (1.0f / 1048576.0f));
+  const float r = f - h * 1048576.0f;
+  const int ir = __float_as_int(r + 12582912.0f) - 0x4B400000;
+  return ((long long)__float2int_rn(h) << 20) + (long long)ir;
+}
+
 __device__ __forceinline__ void add_fixed_ll(long long* facc, int p, const long long v[6]) {
   for (int k = 0; k < 6; ++k)
     atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)v[k]);
@@ -783,7 +797,7 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
       // v * 2^40 is exact in FP32 and the conversion rounds to nearest even:
       // odd-symmetric, so opposite links of a closed body cancel exactly
 #pragma unroll
-      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? __float2ll_rn(v[k] * 1099511627776.0f) : 0LL;
+      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? fixed_2m40(v[k]) : 0LL;
       if (single) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) iv[k] = warp_sum_fixed(iv[k]);

@@ -121,7 +121,26 @@ __global__ void k_prologue(ParticleLaunch L) {
   if (p >= L.np) return;
   DevParticle& P = L.P[p];
   quat_to_R_exact(P.quat, P.R);
-  for (int k = 0; k < 9; ++k) P.Rf[k] = (float)P.R[k];
+  for (int k = 0; k < 9; ++k) {
+    P.Rf[k] = (float)P.R[k];
+    P.Rs[0][k] = P.Rf[k];
+    P.Rs[1][k] = (float)(P.R[k] - (double)P.Rf[k]);
+  }
+  {
+    double fr[3];
+    for (int a = 0; a < 3; ++a) fr[a] = P.pos[a] - floor(P.pos[a]);
+    for (int k = 0; k < 3; ++k) {
+      const double t = P.R[k] * fr[0] + P.R[3 + k] * fr[1] + P.R[6 + k] * fr[2];
+      P.Ts[0][k] = (float)t;
+      P.Ts[1][k] = (float)(t - (double)P.Ts[0][k]);
+    }
+    for (int d = 0; d < 19; ++d)
+      for (int k = 0; k < 3; ++k) {
+        const double e = P.R[k] * cx(d) + P.R[3 + k] * cy(d) + P.R[6 + k] * cz(d);
+        P.Es[d][k] = (float)e;
+        P.Es[d][3 + k] = (float)(e - (double)P.Es[d][k]);
+      }
+  }
   for (int a = 0; a < 3; ++a) {
     P.lo[a] = (int)floor(P.pos[a] - P.Rt) - 1;
     P.posf[a] = (float)P.pos[a];
@@ -413,8 +432,10 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 // Wall fraction of each link: root q in (0, 1] of g(q) = f_p(x_f + q e_d) - 1
 // (Sec. 2.3.2; reading A7: along the link that points into the solid, c0 = 1).
 //
-// Inputs: the body-frame link origin p and direction e formed in FP64 and
-// split into float pairs hi + lo, and the ball table's split copy; origins
+// Inputs: the body-frame link origin p and direction e as float pairs hi + lo
+// (the prologue forms the particle's frame in FP64 once per step; each link
+// combines it in float-float arithmetic, without FP64, which runs at a small
+// fraction of the FP32 rate on this part), and the ball table's split copy; origins
 // and centres are split on the grid of 2^-12 when the particle's bounding
 // radius is below 1000, so that p_hi - c_hi is exact in FP32 (otherwise the
 // difference goes through TwoSum).
@@ -450,10 +471,14 @@ __device__ __forceinline__ F2 two_prod(float a, float b) {
   const float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
-// v = hi + lo with hi on the grid of 2^-12 (grid = true) or hi = fl(v)
-__device__ __forceinline__ F2 split(double v, bool grid) {
-  const double h = grid ? rint(v * 4096.0) * (1.0 / 4096.0) : (double)(float)v;
-  return {(float)h, (float)(v - h)};
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+  const F2 s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+// a float pair re-split with hi on the grid of 2^-12 (|hi| < 2^11: exact)
+__device__ __forceinline__ F2 to_grid(F2 v) {
+  const float h = rintf(v.hi * 4096.0f) * (1.0f / 4096.0f);
+  return {h, (v.hi - h) + v.lo};
 }
 // p_hi - c_hi as hi + lo (exact on the grid)
 __device__ __forceinline__ F2 diff_hi(float p, float c, bool grid) {
@@ -514,17 +539,28 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
     // node indices of particle lists fit in 32 bits (the lists store them as uint32)
     const unsigned cu = (unsigned)c, row = cu / (unsigned)L.g.nx;
     const int x = (int)(cu - row * (unsigned)L.g.nx), z = (int)(row / (unsigned)L.g.ny), y = (int)(row - (unsigned)z * L.g.ny);
-    const double* R = P.R;
-    const double d0 = x - P.pos[0], d1 = y - P.pos[1], d2 = z - P.pos[2];
-    const double pb[3] = {R[0] * d0 + R[3] * d1 + R[6] * d2, R[1] * d0 + R[4] * d1 + R[7] * d2,
-                          R[2] * d0 + R[5] * d1 + R[8] * d2};
-    const double eb[3] = {R[0] * cx(d) + R[3] * cy(d) + R[6] * cz(d), R[1] * cx(d) + R[4] * cy(d) + R[7] * cz(d),
-                          R[2] * cx(d) + R[5] * cy(d) + R[8] * cz(d)};
+    // body-frame link origin p = R^T (x - X) = R^T n - R^T (X - floor X), n = x - floor X
+    // an exact small integer vector, in float-float arithmetic from the
+    // prologue's float pairs (TwoProduct of R_hi n exact, R_lo n below it)
+    const float n[3] = {(float)(x - P.pos_i[0]), (float)(y - P.pos_i[1]), (float)(z - P.pos_i[2])};
+    F2 ps[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      F2 acc = {-P.Ts[0][k], -P.Ts[1][k]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        F2 t = two_prod(P.Rs[0][3 * a + k], n[a]);
+        t.lo = __fmaf_rn(P.Rs[1][3 * a + k], n[a], t.lo);
+        acc = df_add(acc, t);
+      }
+      ps[k] = acc;
+    }
     // on the 2^-12 grid (|p|, |c| < 1024, split the same way by the host) the
     // hi parts subtract exactly; larger particles take TwoSum
-    const bool grid = P.Rb < 1000.0;
-    const F2 ps[3] = {split(pb[0], grid), split(pb[1], grid), split(pb[2], grid)};
-    const F2 es[3] = {split(eb[0], false), split(eb[1], false), split(eb[2], false)};
+    const bool grid = P.Rb_f < 1000.f;
+    if (grid)
+      for (int k = 0; k < 3; ++k) ps[k] = to_grid(ps[k]);
+    const F2 es[3] = {{P.Es[d][0], P.Es[d][3]}, {P.Es[d][1], P.Es[d][4]}, {P.Es[d][2], P.Es[d][5]}};
     const float4* bs = L.balls_s + 2 * (size_t)P.ball_off;
     const int nb = P.n_balls;
     // stage 1: FP32 Newton on h = f^(-1/2) - 1

@@ -194,6 +194,11 @@ struct DevParticle {
   int pos_i[3];                              // floor(pos), and pos - floor(pos) in FP32: node offsets
   float pos_fr[3];                           //   x - X = (x - pos_i) - pos_fr without FP64 arithmetic
   float Rf[9];                               // R rounded to FP32 (set with pos_i, pos_fr each step)
+  // float pairs (hi, lo) of the body frame at the current pose, for the wall
+  // fraction's float-float arithmetic (set by the prologue each step):
+  float Rs[2][9];                            //   R
+  float Ts[2][3];                            //   R^T (X - floor X)
+  float Es[19][6];                           //   R^T e_d: hi xyz, lo xyz per direction d
   float core_s;                              // core scale s = ((r_e - R_s) / r_e)^2 (constant)
   float Rb_f, re_f, skin_f;                  // FP32 copies of R_b, r_e, R_s (constant)
   int ball_off, n_balls;
