@@ -167,6 +167,7 @@ ParticleLaunch mi_delbm::particle_launch() const {
   L.cap_links = cap_links;
   L.cap_new = cap_new;
   L.blocks_per_particle = blocks_per_particle;
+  L.classify_blocks = classify_blocks;
   L.g = geom();
   return L;
 }
@@ -1673,6 +1674,10 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   if (st != MI_OK) return st;
   long long bpp = (maxvol + 1023) / 1024;
   h->blocks_per_particle = (int)(bpp < 1 ? 1 : (bpp > 8192 ? 8192 : bpp));
+  long long maxrows = 1;
+  for (const auto& q : h->hp) maxrows = std::max<long long>(maxrows, (long long)(q.ext[1] + 8) * (q.ext[2] + 8));
+  const long long cb = (maxrows + 63) / 64;  // 8 warps per block, about 8 rows per warp
+  h->classify_blocks = (int)(cb < 1 ? 1 : (cb > 4096 ? 4096 : cb));
   h->invalidate_graphs();
   if (id_out) *id_out = id;
   return MI_OK;

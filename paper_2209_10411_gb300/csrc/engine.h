@@ -110,6 +110,7 @@ struct mi_delbm {
   bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
   bool cover_uncover = false;        // covered/uncovered-node momentum joins the hydrodynamic sums
   int blocks_per_particle = 1;
+  int classify_blocks = 1;
 
   TuneChoice tune;
 

@@ -87,18 +87,19 @@ __device__ __forceinline__ long long lin(int x, int y, int z, const LatticeGeom&
 // Neighbour along direction d with periodic wrap; false if outside the domain.
 __device__ __forceinline__ bool neighbour(int x, int y, int z, int dx, int dy, int dz, const LatticeGeom& g,
                                           long long& out) {
+  // |dx|, |dy|, |dz| <= 1: one wrap at most
   int a = x + dx, b = y + dy, c = z + dz;
   if (a < 0 || a >= g.nx) {
     if (!g.periodic[0]) return false;
-    a = (a + g.nx) % g.nx;
+    a += a < 0 ? g.nx : -g.nx;
   }
   if (b < 0 || b >= g.ny) {
     if (!g.periodic[1]) return false;
-    b = (b + g.ny) % g.ny;
+    b += b < 0 ? g.ny : -g.ny;
   }
   if (c < 0 || c >= g.nz) {
     if (!g.periodic[2]) return false;
-    c = (c + g.nz) % g.nz;
+    c += c < 0 ? g.nz : -g.nz;
   }
   out = lin(a, b, c, g);
   return true;
@@ -317,18 +318,37 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
   const float cp0 = P.sctr[L.prev_buf][0], cp1 = P.sctr[L.prev_buf][1], cp2 = P.sctr[L.prev_buf][2];
   const Region r = clip_region(lo, ext, 2, L.g);
   const unsigned gen = L.ctr->gen;
-  const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
-    const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
-    const int x = r.lo[0] + (int)(rem - yi * n0);
-    const int y = r.lo[1] + (int)yi;
+  // one warp per (y, z) row of the region: the row's x-interval inside
+  // either sphere, computed once per row (rows that miss both are skipped by
+  // the whole warp), its nodes taken 32 at a time
+  const int lane = threadIdx.x & 31;
+  const unsigned rows = (unsigned)r.n[1] * (unsigned)r.n[2];
+  const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned row = wid; row < rows; row += nw) {
+    const unsigned zi = row / (unsigned)r.n[1];
+    const int y = r.lo[1] + (int)(row - zi * (unsigned)r.n[1]);
     const int z = r.lo[2] + (int)zi;
+    int xa = INT_MAX, xb = INT_MIN;
     {
-      const float a0 = x - cc0, a1 = y - cc1, a2 = z - cc2;
-      const float b0 = x - cp0, b1 = y - cp1, b2 = z - cp2;
-      if (!(rc >= 0.f && a0 * a0 + a1 * a1 + a2 * a2 <= rc2) && !(rp >= 0.f && b0 * b0 + b1 * b1 + b2 * b2 <= rp2))
-        continue;
+      const float hc = rc2 - ((y - cc1) * (y - cc1) + (z - cc2) * (z - cc2));
+      if (rc >= 0.f && hc >= 0.f) {
+        const float w = sqrtf(hc);
+        xa = (int)ceilf(cc0 - w);
+        xb = (int)floorf(cc0 + w);
+      }
+      const float hp = rp2 - ((y - cp1) * (y - cp1) + (z - cp2) * (z - cp2));
+      if (rp >= 0.f && hp >= 0.f) {
+        const float w = sqrtf(hp);
+        xa = min(xa, (int)ceilf(cp0 - w));
+        xb = max(xb, (int)floorf(cp0 + w));
+      }
+      xa = max(xa, r.lo[0]);
+      xb = min(xb, r.lo[0] + r.n[0] - 1);
     }
+    // a row outside both spheres (xa > xb) is skipped before any index is
+    // formed: xa = INT_MAX + lane would overflow
+    if (xa > xb) continue;
+    for (int x = xa + lane; x <= xb; x += 32) {
     const long long c = lin(x, y, z, L.g);
     const bool solid = L.owner_cur[c] != OWNER_NONE;
     const bool was = L.owner_prev[c] != OWNER_NONE;
@@ -341,6 +361,7 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
         for (int d = 1; d < 19; ++d)
           if (__ldg(L.owner_cur + c + cx(d) + sy * cy(d) + sz * cz(d)) != OWNER_NONE) mask |= 1u << d;
       } else {
+#pragma unroll 1
         for (int d = 1; d < 19; ++d) {
           long long nbr;
           if (neighbour(x, y, z, cx(d), cy(d), cz(d), L.g, nbr) && L.owner_cur[nbr] != OWNER_NONE) mask |= 1u << d;
@@ -416,13 +437,13 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
       }
     }
   }
+  }
 }
 
 cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  // most of the node box lies outside the solid spheres: half the blocks of
-  // the flagging kernel
-  dim3 grid((L.blocks_per_particle + 1) / 2, L.np);
+  // a warp per (y, z) row, about eight rows per warp
+  dim3 grid(L.classify_blocks, L.np);
   if (L.cover_uncover) k_classify<true><<<grid, 256, 0, s>>>(L);
   else k_classify<false><<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();

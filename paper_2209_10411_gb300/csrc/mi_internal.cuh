@@ -249,6 +249,7 @@ struct ParticleLaunch {
   unsigned cap_bc, cap_links, cap_new;
   int cover_uncover;
   int blocks_per_particle;
+  int classify_blocks;        // per particle: 256-thread blocks of the row-per-warp classification
   LatticeGeom g;
 };
 cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s);
