@@ -810,7 +810,7 @@ def shape_bench(B, scenes, n=300, h=0.25, seed=0):
 
 
 C4_KERNELS = ("k_prologue", "k_clear", "k_flag", "k_classify", "k_links_q", "k_refill", "k_bulk", "k_near",
-              "k_boundary", "k_dem_prologue", "k_broad_phase", "k_contacts", "k_integrate")
+              "k_links_ibb", "k_boundary", "k_dem_prologue", "k_broad_phase", "k_contacts", "k_integrate")
 # stated accuracy of each storage on the precision tank: the bounds that
 # tests/test_gpu_precision.py asserts on the 128^3 sub-run of that tank
 # (eight particles, 30 coupled steps) against the FP64 oracle's reference

@@ -421,7 +421,13 @@ enum {
    * substep.  By default, with at most 64 particles and the plain or warm
    * start, one kernel runs all substeps of a step in one CTA (the same bits:
    * the same per-item and per-particle device code, no launch per substep) */
-  MI_SCHEDULE_UNFUSED_DEM = 2
+  MI_SCHEDULE_UNFUSED_DEM = 2,
+  /* the links' interpolated bounce-back and momentum exchange run on the
+   * particle side stream while the bulk kernel runs, instead of after it
+   * (the same bits; the boundary nodes' collision still follows the bulk
+   * kernel); steps that run the wall fractions, the refill and the boundary
+   * phase.  Implied by MI_SCHEDULE_OVERLAP_BOUNDARY */
+  MI_SCHEDULE_LINKS_BESIDE = 4
 };
 /* Set the step schedule (an OR of MI_SCHEDULE_* flags; 0 = default).
  * Discards captured graphs.  Errors: MI_EINVAL (unknown flags). */

@@ -151,7 +151,7 @@ _sig("mi_gs_fit", c_int, c_int, _P, _P, _P, _P, _P, _P, c_int, c_int, c_int, cty
 _sig("mi_delbm_pair_solve", c_int, _P, c_int, _P, _P, c_int, _P, _P, _P, _P, _P, _P, _P)
 
 PAIR_FEATURES, PAIR_PLAIN, PAIR_LEARNED, PAIR_LABELS, PAIR_GUESS_ONLY = 1, 2, 4, 8, 16
-SCHEDULE_OVERLAP_BOUNDARY, SCHEDULE_UNFUSED_DEM = 1, 2
+SCHEDULE_OVERLAP_BOUNDARY, SCHEDULE_UNFUSED_DEM, SCHEDULE_LINKS_BESIDE = 1, 2, 4
 MOMENTUM_COVER_UNCOVER = 1
 
 
@@ -523,11 +523,14 @@ class Simulation:
         return {"bulk_block_x": v[0].value, "bulk_rows": v[1].value, "bulk_pairs": v[2].value,
                 "list_blocks_per_sm": v[3].value}
 
-    def set_schedule(self, overlap_boundary=False, unfused_dem=False):
+    def set_schedule(self, overlap_boundary=False, unfused_dem=False, links_beside=False):
         """overlap_boundary: compute the boundary nodes beside the bulk kernel
         (True) or after it; unfused_dem: run DEM substeps as one launch
-        sequence per substep instead of the fused substep kernel."""
-        flags = (SCHEDULE_OVERLAP_BOUNDARY if overlap_boundary else 0) | (SCHEDULE_UNFUSED_DEM if unfused_dem else 0)
+        sequence per substep instead of the fused substep kernel;
+        links_beside: the links' bounce-back and momentum exchange beside the
+        bulk kernel instead of after it."""
+        flags = (SCHEDULE_OVERLAP_BOUNDARY if overlap_boundary else 0) | (SCHEDULE_UNFUSED_DEM if unfused_dem else 0) | \
+            (SCHEDULE_LINKS_BESIDE if links_beside else 0)
         self._check(lib.mi_delbm_set_schedule(self.h, flags))
 
     def set_momentum_rules(self, cover_uncover=False):

@@ -143,9 +143,11 @@ __device__ __forceinline__ GEval eval(const Frame& F, const float4* __restrict__
 // The pivot search swaps row i with each later row whose entry in column i
 // is larger in magnitude than the current pivot: the pivot chosen is the
 // first largest, and every index is a compile-time constant, so the system
-// stays in registers.
+// stays in registers.  Each pivot is inverted once (correctly rounded) and
+// its row's multipliers and unknown are products with that reciprocal.
 template <int N>
 __device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
+  float ip[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -157,9 +159,10 @@ __device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
       }
     }
     if (!(fabsf(A[i][i]) > 0.f)) return false;
+    ip[i] = __frcp_rn(A[i][i]);
 #pragma unroll
     for (int r = i + 1; r < N; ++r) {
-      const float m = A[r][i] / A[i][i];
+      const float m = A[r][i] * ip[i];
 #pragma unroll
       for (int c = i; c < N; ++c) A[r][c] -= m * A[i][c];
       b[r] -= m * b[i];
@@ -170,7 +173,7 @@ __device__ __forceinline__ bool solve(float A[N][N], float b[N], float x[N]) {
     float acc = b[i];
 #pragma unroll
     for (int c = i + 1; c < N; ++c) acc -= A[i][c] * x[c];
-    x[i] = acc / A[i][i];
+    x[i] = acc * ip[i];
   }
   return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && (N < 4 || isfinite(x[N - 1]));
 }
@@ -982,16 +985,28 @@ __device__ __forceinline__ void plain_staged(const float4* st, const float* rad,
   __syncwarp();
   float best = 3.4e38f;
   int ba = 0, bb = 0;
-  for (int u = lane; u < ma; u += 32) {
-    const int a = cand[u];
-    const float4 pa = st[a];
-    const float ra = rad[a];
-    for (int v = 0; v < mb; ++v) {
-      const int b = cand[ma + v];
-      const float4 q = st[n0 + b];
+  if (ma > 0 && mb > 0) {
+    // the ma x mb surviving pairs over the lanes, 32 at a time: lane l takes
+    // pairs l, l + 32, ... of the row-major (survivor a, survivor b) order,
+    // its indices advanced by 32 without a division per step
+    const int q32 = 32 / mb, r32 = 32 - q32 * mb;
+    int ia = lane / mb, ib = lane - (lane / mb) * mb;
+    for (int u = lane; u < ma * mb; u += 32) {
+      const int a = cand[ia], b = cand[ma + ib];
+      const float4 pa = st[a], q = st[n0 + b];
       const float gap = sqrtf((pa.x - q.x) * (pa.x - q.x) + (pa.y - q.y) * (pa.y - q.y) + (pa.z - q.z) * (pa.z - q.z)) -
-                        ra - rad[n0 + b];
-      if (gap < best) { best = gap; ba = a; bb = b; }
+                        rad[a] - rad[n0 + b];
+      if (gap < best || (gap == best && (((unsigned)a << 16) | (unsigned)b) < (((unsigned)ba << 16) | (unsigned)bb))) {
+        best = gap;
+        ba = a;
+        bb = b;
+      }
+      ia += q32;
+      ib += r32;
+      if (ib >= mb) {
+        ib -= mb;
+        ++ia;
+      }
     }
   }
   // smallest gap, ties to the lower (a, b): a, b < 256 here

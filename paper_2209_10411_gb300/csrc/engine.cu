@@ -160,6 +160,7 @@ ParticleLaunch mi_delbm::particle_launch() const {
   L.link_p = link_p;
   L.link_dir = link_dir;
   L.link_q = link_q;
+  L.link_g = link_g;
   L.new_cell = new_cell;
   L.cov_cell = cov_cell;
   L.cover_uncover = cover_uncover ? 1 : 0;
@@ -201,6 +202,8 @@ static BoundaryLaunch boundary_launch(const mi_delbm* h) {
   L.bb_mode = h->cfg.bb_mode;
   L.grid = h->sm_count * h->tune.list_blocks_per_sm;
   L.tmp = nullptr;
+  L.part = h->ibb_part;
+  L.part_blocks = h->sm_count * IBB_BLOCKS_PER_SM;
   return L;
 }
 
@@ -215,6 +218,12 @@ mi_status mi_delbm::phase_near() {
   BoundaryLaunch L = boundary_launch(this);
   // timed with the boundary phase: the bulk bucket is the lattice-wide kernel alone
   return launch_phase(this, stream, MI_PHASE_BOUNDARY, "k_near", [&] { return launch_near(L, stream); });
+}
+
+mi_status mi_delbm::phase_links_ibb(cudaStream_t st) {
+  if (n_particles == 0) return MI_OK;
+  BoundaryLaunch L = boundary_launch(this);
+  return launch_phase(this, st, MI_PHASE_BOUNDARY, "k_links_ibb", [&] { return launch_links_ibb(L, st); });
 }
 
 mi_status mi_delbm::phase_boundary() {
@@ -379,11 +388,12 @@ mi_status mi_delbm::phase_swap() {
 
 // The phases of one step.  The bulk stream-collide of every node runs on the
 // handle's stream; concurrently, on high-priority side streams, run the
-// particle chain (flag, classify, refill; the wall fractions fork off it) and
-// the first DEM substep's contacts (they read only the particle state, which
-// changes at the rigid-body update).  After the bulk kernel and the particle
-// chain meet, the neighbours of uncovered nodes are recomputed (k_near), then
-// the boundary nodes (after the wall fractions), then the DEM substeps.
+// particle chain (flag, classify, refill; the wall fractions fork off it and
+// the links' bounce-back and momentum exchange follow both) and the first
+// DEM substep's contacts (they read only the particle state, which changes at
+// the rigid-body update).  After the bulk kernel and the particle chain meet,
+// the neighbours of uncovered nodes are recomputed (k_near), then the
+// boundary nodes, then the DEM substeps.
 mi_status mi_delbm::run_phases(unsigned phases) {
   mi_status s = MI_OK;
   const bool particles = n_particles > 0;
@@ -393,6 +403,9 @@ mi_status mi_delbm::run_phases(unsigned phases) {
   // overlapped boundary schedule: needs the whole chain, the wall fractions and the bulk kernel in this call
   const bool beside = overlap_boundary && links_branch && (phases & MI_PHASE_BOUNDARY) && (phases & MI_PHASE_BULK) &&
                       (phases & MI_PHASE_FLAG) && (phases & MI_PHASE_REFILL);
+  // the links' bounce-back on the chain: needs the wall fractions and the refill in this call
+  const bool ibb_beside = (links_beside || beside) && chain && links_branch && (phases & MI_PHASE_BOUNDARY) &&
+                          (phases & MI_PHASE_REFILL);
   if (contact_branch) {
     if ((s = ensure_contact_buffers()) != MI_OK) return s;
     if ((s = fork(stream, aux[1], 0)) != MI_OK) return s;
@@ -408,12 +421,14 @@ mi_status mi_delbm::run_phases(unsigned phases) {
       if ((s = join_record(aux[0], 1)) != MI_OK) return s;
     }
     if ((phases & MI_PHASE_REFILL) && (s = phase_refill(aux[2])) != MI_OK) return s;
-    if (beside) {
-      // the boundary nodes beside the bulk kernel: after the refill and the wall fractions
+    if (ibb_beside) {
+      // after the refill and the wall fractions: the links' bounce-back, and in
+      // the overlapped schedule the boundary nodes too
       cudaError_t e = cudaEventRecord(ev_join[1], aux[0]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(aux[2], ev_join[1], 0);
       if (e != cudaSuccess) return cuda_fail(e, "join");
-      if ((s = phase_boundary_beside(aux[2])) != MI_OK) return s;
+      if ((s = phase_links_ibb(aux[2])) != MI_OK) return s;
+      if (beside && (s = phase_boundary_beside(aux[2])) != MI_OK) return s;
     }
     if ((s = join_record(aux[2], 2)) != MI_OK) return s;
   }
@@ -424,6 +439,7 @@ mi_status mi_delbm::run_phases(unsigned phases) {
     if ((s = phase_scatter_boundary()) != MI_OK) return s;
   } else {
     if (links_branch && (s = join_wait(1)) != MI_OK) return s;
+    if ((phases & MI_PHASE_BOUNDARY) && !ibb_beside && (s = phase_links_ibb(stream)) != MI_OK) return s;
     if ((phases & MI_PHASE_BOUNDARY) && (s = phase_boundary()) != MI_OK) return s;
   }
   if ((phases & MI_PHASE_SWAP) && (s = phase_swap()) != MI_OK) return s;
@@ -695,6 +711,10 @@ mi_status mi_delbm::ensure_particle_buffers() {
   dballs = (float4*)dalloc(sizeof(float4) * nb);
   dballs_d = (double*)dalloc(sizeof(double) * 4 * nb);
   dballs_s = (float4*)dalloc(sizeof(float4) * 2 * nb);
+  if (np <= IBB_SHARED_PARTICLES) {
+    ibb_part = (long long*)dalloc(sizeof(long long) * 6 * (size_t)np * sm_count * IBB_BLOCKS_PER_SM);
+    if (!ibb_part) return fail(MI_ENOMEM, "particle buffers: device allocation failed");
+  }
   if (!owner[0] || !owner[1] || !stamp || !dctr || !facc || !fc || !dP || !dballs || !dballs_d || !dballs_s)
     return fail(MI_ENOMEM, "particle buffers: device allocation failed");
   cudaError_t e = cudaMemsetAsync(owner[0], 0xFF, ncell * 4, stream);
@@ -717,7 +737,7 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   links = links > cap_links ? links : cap_links;
   nnew = nnew > cap_new ? nnew : cap_new;
   dfree(bc_cell); dfree(bc_mask); dfree(bc_loff); dfree(link_bc); dfree(link_p); dfree(link_dir);
-  dfree(link_q); dfree(new_cell); dfree(cov_cell); dfree(bc_tmp);
+  dfree(link_q); dfree(link_g); dfree(new_cell); dfree(cov_cell); dfree(bc_tmp);
   bc_cell = (uint32_t*)dalloc(4ull * bc);
   bc_mask = (uint32_t*)dalloc(4ull * bc);
   bc_loff = (uint32_t*)dalloc(4ull * bc);
@@ -725,10 +745,12 @@ mi_status mi_delbm::ensure_list_capacity(unsigned bc, unsigned links, unsigned n
   link_p = (uint32_t*)dalloc(4ull * links);
   link_dir = (uint8_t*)dalloc(1ull * links);
   link_q = (float*)dalloc(4ull * links);
+  link_g = (float*)dalloc(4ull * links);
   new_cell = (uint32_t*)dalloc(4ull * nnew);
   cov_cell = (uint32_t*)dalloc(4ull * nnew);
   bc_tmp = dalloc(19ull * store_bytes(cfg.storage) * bc);
-  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !new_cell || !cov_cell ||
+  if (!bc_cell || !bc_mask || !bc_loff || !link_bc || !link_p || !link_dir || !link_q || !link_g || !new_cell ||
+      !cov_cell ||
       !bc_tmp) {
     cap_bc = cap_links = cap_new = 0;
     return fail(MI_ENOMEM, "link lists: device allocation failed");
@@ -961,10 +983,12 @@ mi_status mi_delbm_reserve_lists(mi_delbm* h, size_t boundary_nodes, size_t link
   mi_status s = h->sync("mi_delbm_reserve_lists");
   if (s != MI_OK) return s;
   h->dfree(h->bc_cell); h->dfree(h->bc_mask); h->dfree(h->bc_loff); h->dfree(h->link_bc); h->dfree(h->link_p);
-  h->dfree(h->link_dir); h->dfree(h->link_q); h->dfree(h->new_cell); h->dfree(h->cov_cell); h->dfree(h->bc_tmp);
+  h->dfree(h->link_dir); h->dfree(h->link_q); h->dfree(h->link_g); h->dfree(h->new_cell); h->dfree(h->cov_cell);
+  h->dfree(h->bc_tmp);
   h->bc_cell = h->bc_mask = h->bc_loff = h->link_bc = h->link_p = h->new_cell = h->cov_cell = nullptr;
   h->link_dir = nullptr;
   h->link_q = nullptr;
+  h->link_g = nullptr;
   h->bc_tmp = nullptr;
   h->cap_bc = h->cap_links = h->cap_new = 0;
   h->need_bc = h->need_links = h->need_new = 0;
@@ -1159,12 +1183,14 @@ mi_status mi_delbm_pair_solve(mi_delbm* h, int n, const int* ij, const double* p
 
 mi_status mi_delbm_set_schedule(mi_delbm* h, int flags) {
   if (!h) return MI_EINVAL;
-  if (flags & ~(MI_SCHEDULE_OVERLAP_BOUNDARY | MI_SCHEDULE_UNFUSED_DEM))
+  if (flags & ~(MI_SCHEDULE_OVERLAP_BOUNDARY | MI_SCHEDULE_UNFUSED_DEM | MI_SCHEDULE_LINKS_BESIDE))
     return h->fail(MI_EINVAL, "mi_delbm_set_schedule: unknown flags");
   const bool ob = (flags & MI_SCHEDULE_OVERLAP_BOUNDARY) != 0, ud = (flags & MI_SCHEDULE_UNFUSED_DEM) != 0;
-  if (h->overlap_boundary != ob || h->unfused_dem != ud) h->invalidate_graphs();
+  const bool lb = (flags & MI_SCHEDULE_LINKS_BESIDE) != 0;
+  if (h->overlap_boundary != ob || h->unfused_dem != ud || h->links_beside != lb) h->invalidate_graphs();
   h->overlap_boundary = ob;
   h->unfused_dem = ud;
+  h->links_beside = lb;
   return MI_OK;
 }
 
@@ -1363,7 +1389,10 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
         for (int bl : {2, 4, 8, 16, 32}) {
           h->tune.list_blocks_per_sm = bl;
           BoundaryLaunch B = boundary_launch(h);
-          const float ms = h->time_launches(5, [&] { return launch_boundary(B, h->stream); });
+          const float ms = h->time_launches(5, [&] {
+            const cudaError_t e = launch_links_ibb(B, h->stream);
+            return e != cudaSuccess ? e : launch_boundary(B, h->stream);
+          });
           if (ms > 0.f && ms < best) {
             best = ms;
             t.list_blocks_per_sm = bl;

@@ -100,6 +100,8 @@ struct mi_delbm {
   uint32_t *link_bc = nullptr, *link_p = nullptr;
   uint8_t* link_dir = nullptr;
   float* link_q = nullptr;
+  float* link_g = nullptr;
+  long long* ibb_part = nullptr;     // per-block momentum-exchange sums of the link kernel
   uint32_t* new_cell = nullptr;
   uint32_t* cov_cell = nullptr;     // nodes covered this step (cover/uncover rule; capacity cap_new)
   unsigned cap_bc = 0, cap_links = 0, cap_new = 0;
@@ -107,6 +109,7 @@ struct mi_delbm {
   unsigned need_bc = 0, need_links = 0, need_new = 0;
   void* bc_tmp = nullptr;            // 19 stored values per boundary node (overlapped schedule)
   bool overlap_boundary = false;     // boundary nodes computed beside the bulk kernel, scattered after it
+  bool links_beside = false;         // the links' bounce-back beside the bulk kernel
   bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
   bool cover_uncover = false;        // covered/uncovered-node momentum joins the hydrodynamic sums
   int blocks_per_particle = 1;
@@ -140,6 +143,7 @@ struct mi_delbm {
   mi_status phase_refill(cudaStream_t st);
   mi_status phase_near();
   mi_status phase_bulk();
+  mi_status phase_links_ibb(cudaStream_t st);
   mi_status phase_boundary();
   mi_status phase_boundary_beside(cudaStream_t st);
   mi_status phase_scatter_boundary();

@@ -583,19 +583,33 @@ __global__ void __launch_bounds__(128) k_near(BoundaryLaunch L) {
 }
 
 // ---------------------------------------------------------------------------
-// Boundary nodes, one warp per node, lane j < 19 handling direction j: pull
-// streaming where the source is fluid, halfway bounce-back where it is outside
-// the domain, and for a link (x_f, d = opp j) to a solid neighbour the paper's
-// interpolated bounce-back (Eqs. eqneq1, eqneq2, neqd):
+// Boundary nodes (Sec. 2.3.2) in two kernels.
+//
+// k_links_ibb, one thread per link (x_f, d): x_f a fluid boundary node,
+// x_f + e_d a solid node of particle p at wall fraction q.  The population
+// that would have streamed from the solid neighbour into x_f along
+// j = opp(d) is the paper's interpolated bounce-back (Eqs. eqneq1, eqneq2,
+// neqd):
 //   G_j = f_eq,d(rho_f, u_d) + [f+_d(x_f) - f_eq,d(rho_f, u_f)] + 6 w_d rho0 (e_j . u_w)
 //   u_d = u*/3 + 2 u**/3 (piecewise in q), u_w = v_p + omega_p x (x_w - X_p)
-// (or the halfway rule f+_d + 6 w_d rho0 e_j.u_w in Ladd mode); then BGK
-// collision with the node's moments from warp sums.  The Galilean-invariant
-// momentum exchange of each link,
+// (or the halfway rule f+_d + 6 w_d rho0 e_j.u_w in Ladd mode), kept per
+// link.  The Galilean-invariant momentum exchange of the link,
 //   dP = (e_d - u_w) f+_d - (e_j - u_w) G_j = e_d (2 w_d + h_d + h_G) - u_w (h_d - h_G),
-// and its torque about X_p are warp-summed per node, converted to 2^-40 fixed
-// point per node and added with 64-bit integer atomics: the result does not
-// depend on the order in which nodes are visited.
+// and its torque about X_p are rounded to 2^-40 fixed point per link, summed
+// over the warp in integers and added with 64-bit integer atomics: the sums
+// do not depend on the order in which links are visited.  It reads f+(t)
+// only (A, after the refill), so it runs beside the bulk kernel.
+//
+// k_boundary, one thread per boundary node, for each direction j: pull
+// streaming where the source is fluid, halfway bounce-back where it is
+// outside the domain, the link's G_j where it is solid; then BGK collision,
+// written into f+(t+1).  Up to IBB_SHARED_PARTICLES particles the link kernel
+// leaves its momentum exchange as per-block sums, which this kernel adds into
+// the particles' sums first (no launch of its own).
+//
+// A link is used only when every link of its node fitted into the link list
+// (an overflow, reported by the classification, leaves the node on halfway
+// bounce-back without momentum exchange until the lists grow).
 // ---------------------------------------------------------------------------
 namespace {
 constexpr unsigned FULLW = 0xffffffffu;
@@ -613,12 +627,6 @@ __device__ __forceinline__ int ley(int j) { return (int)((EYB >> (2 * j)) & 3ull
 __device__ __forceinline__ int lez(int j) { return (int)((EZB >> (2 * j)) & 3ull) - 1; }
 __device__ __forceinline__ float lw(int j) { return j == 0 ? (1.0f / 3.0f) : (j <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
 __device__ __forceinline__ int lopp(int j) { return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1); }
-
-__device__ __forceinline__ float wsumf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLW, v, o);
-  return __shfl_sync(FULLW, v, 0);
-}
 
 // Exact warp sum of 64-bit fixed-point values (|v| < 2^62): three 22-bit
 // pieces, each summed by one integer warp reduction (at most 32 x 2^22 < 2^27,
@@ -647,49 +655,211 @@ __device__ __forceinline__ long long fixed_2m40(float v) {
   return ((long long)__float2int_rn(h) << 20) + (long long)ir;
 }
 
-__device__ __forceinline__ void add_fixed_ll(long long* facc, int p, const long long v[6]) {
-  for (int k = 0; k < 6; ++k)
-    atomicAdd(reinterpret_cast<unsigned long long*>(facc + 6 * p + k), (unsigned long long)v[k]);
-}
 }  // namespace
 
-template <int ST, bool FORCE, bool LADD>
-__global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
+// The link entries of node bi fit into the list (its links were written by
+// the classification of this step).
+__device__ __forceinline__ bool links_fit(uint32_t loff, uint32_t mask, unsigned cap_links) {
+  return (unsigned long long)loff + (unsigned)__popc(mask) <= (unsigned long long)cap_links;
+}
+
+template <int ST, bool LADD, bool SHARED>
+__global__ void __launch_bounds__(256) k_links_ibb(BoundaryLaunch L) {
+  // the block's sums per particle (SHARED) as 64-bit integers in two 32-bit
+  // words (native 32-bit shared atomics, the carry of the low word added to
+  // the high word), else the global sums directly
+  __shared__ unsigned s_lo[SHARED ? 6 * IBB_SHARED_PARTICLES : 1], s_hi[SHARED ? 6 * IBB_SHARED_PARTICLES : 1];
+  using T = typename Store<ST>::T;
+  const T* __restrict__ A = static_cast<const T*>(L.A);
+  const ParticleLaunch& pl = L.pl;
+  const LatticeGeom& g = pl.g;
+  const unsigned nl = min(pl.ctr->n_links, pl.cap_links);
+  const unsigned nbc = min(pl.ctr->n_bc, pl.cap_bc);
+  const float rho0 = L.p.rho0;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned stride = gridDim.x * blockDim.x;
+  const int n6 = 6 * pl.np;
+  if constexpr (SHARED) {
+    for (int k = threadIdx.x; k < n6; k += blockDim.x) s_lo[k] = s_hi[k] = 0u;
+    __syncthreads();
+  }
+  const auto flush = [&](int q, const long long* w) {
+    for (int k = 0; k < 6; ++k) {
+      if constexpr (SHARED) {
+        // (hi, lo) += w modulo 2^64: every wrap of the low word is seen by
+        // exactly the addition that made it, which carries it into the high word
+        const unsigned long long u = (unsigned long long)w[k];
+        const unsigned lo = (unsigned)u, old = atomicAdd(&s_lo[6 * q + k], lo);
+        const unsigned hi = (unsigned)(u >> 32) + (old + lo < old ? 1u : 0u);
+        if (hi) atomicAdd(&s_hi[6 * q + k], hi);
+      } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(pl.facc + 6 * q + k), (unsigned long long)w[k]);
+      }
+    }
+  };
+  int pacc = -1;  // lane 0: particle of the running fixed-point sums
+  long long iacc[6] = {0, 0, 0, 0, 0, 0};
+  // whole warps step together (the sums below are warp collectives)
+  for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nl; base += stride) {
+    const unsigned l = base + lane;
+    int p = -1;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const unsigned bi = l < nl ? pl.link_bc[l] : 0xffffffffu;
+    uint32_t loff = 0, mask = 0;
+    if (bi < nbc) {
+      loff = pl.bc_loff[bi];
+      mask = pl.bc_mask[bi];
+    }
+    // an entry of this step: inside the range of the node it names, which fitted
+    if (bi < nbc && l >= loff && l - loff < (unsigned)__popc(mask) && links_fit(loff, mask, pl.cap_links)) {
+      const long long c = pl.bc_cell[bi];
+      int x, y, z;
+      coords(c, g, x, y, z);
+      const int d = pl.link_dir[l];
+      const int j = lopp(d);
+      const int ed[3] = {lex(d), ley(d), lez(d)};
+      const bool inside = (g.periodic[0] || (unsigned)(x + ed[0]) < (unsigned)g.nx) &&
+                          (g.periodic[1] || (unsigned)(y + ed[1]) < (unsigned)g.ny) &&
+                          (g.periodic[2] || (unsigned)(z + ed[2]) < (unsigned)g.nz);
+      if (inside) {
+        // own post-collision populations and moments (rho_f, u_f)
+        float h[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) h[i] = Store<ST>::dev(A + i * g.plane + c, i);
+        float dr = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+          dr += h[i];
+          j0 += cx(i) * h[i];
+          j1 += cy(i) * h[i];
+          j2 += cz(i) * h[i];
+        }
+        float hopp = h[0];  // f+_d(x_f) - w_d
+#pragma unroll
+        for (int i = 1; i < 19; ++i) hopp = i == d ? h[i] : hopp;
+        const float rho_f = 1.0f + dr;
+        const float irho_f = 1.0f / rho_f;
+        const float uf[3] = {j0 * irho_f, j1 * irho_f, j2 * irho_f};
+        p = (int)pl.link_p[l];
+        const DevParticle& P = pl.P[p];
+        const float q = LADD ? 0.5f : pl.link_q[l];
+        const float wj = lw(j);
+        // wall point relative to the particle position: x - X = (x - floor X) - frac X,
+        // the integer part exact and the fraction rounded once to FP32
+        const float r0 = ((float)(x - P.pos_i[0]) - P.pos_fr[0]) + q * ed[0];
+        const float r1 = ((float)(y - P.pos_i[1]) - P.pos_fr[1]) + q * ed[1];
+        const float r2 = ((float)(z - P.pos_i[2]) - P.pos_fr[2]) + q * ed[2];
+        float uw[3];
+        uw[0] = P.velf[0] + (P.omegaf[1] * r2 - P.omegaf[2] * r1);
+        uw[1] = P.velf[1] + (P.omegaf[2] * r0 - P.omegaf[0] * r2);
+        uw[2] = P.velf[2] + (P.omegaf[0] * r1 - P.omegaf[1] * r0);
+        const float wall = 6.0f * wj * rho0 * (-ed[0] * uw[0] - ed[1] * uw[1] - ed[2] * uw[2]);
+        float G;
+        if (LADD) {
+          G = hopp + wall;
+        } else {
+          // u at the second fluid node x_f - e_d when it is fluid, else u_f
+          float uff[3] = {uf[0], uf[1], uf[2]};
+          long long ff;
+          if (nbr_wrap(x, y, z, -ed[0], -ed[1], -ed[2], g, ff) && pl.owner_cur[ff] == OWNER_NONE) {
+            float rr;
+            moments_at<ST>(A, g.plane, ff, rr, uff);
+          }
+          float ud[3];
+          const float i1q = 1.0f / (1.0f + q), iq = 1.0f / q;
+          const float a1 = (1.0f - q) * i1q, a2 = 2.0f * q * i1q;
+          const float b1 = (1.0f - q) * iq, b2 = (2.0f * q - 1.0f) * iq;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float us = q <= 0.5f ? 2.0f * q * uf[a] + (1.0f - 2.0f * q) * uff[a] : b1 * uf[a] + b2 * uw[a];
+            ud[a] = us / 3.0f + 2.0f * (a1 * uff[a] + a2 * uw[a]) / 3.0f;
+          }
+          const float eud = ed[0] * ud[0] + ed[1] * ud[1] + ed[2] * ud[2];
+          const float euf = ed[0] * uf[0] + ed[1] * uf[1] + ed[2] * uf[2];
+          const float ud2 = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+          const float uf2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+          G = hopp + wj * rho_f * (3.0f * (eud - euf) + 4.5f * (eud * eud - euf * euf) - 1.5f * (ud2 - uf2)) + wall;
+        }
+        pl.link_g[l] = G;
+        const float s2 = 2.0f * wj + hopp + G, dl = hopp - G;
+        v[0] = ed[0] * s2 - uw[0] * dl;
+        v[1] = ed[1] * s2 - uw[1] * dl;
+        v[2] = ed[2] * s2 - uw[2] * dl;
+        v[3] = r1 * v[2] - r2 * v[1];
+        v[4] = r2 * v[0] - r0 * v[2];
+        v[5] = r0 * v[1] - r1 * v[0];
+      }
+    }
+    // momentum exchange: each link's contribution rounded to 2^-40 fixed point
+    // in its own lane (v * 2^40 is exact in FP32 and the rounding is to nearest
+    // even: odd-symmetric, so opposite links of a closed body cancel exactly),
+    // summed over the warp in integers and kept by lane 0 while the particle
+    // does not change
+    if (__any_sync(FULLW, p >= 0)) {
+      const int pmin = __reduce_min_sync(FULLW, p >= 0 ? p : 0x7fffffff);
+      const bool single = __all_sync(FULLW, p < 0 || p == pmin);
+      long long iv[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? fixed_2m40(v[k]) : 0LL;
+      if (single) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) iv[k] = warp_sum_fixed(iv[k]);
+        if (lane == 0) {
+          if (pacc != pmin) {
+            if (pacc >= 0) flush(pacc, iacc);
+            pacc = pmin;
+            for (int k = 0; k < 6; ++k) iacc[k] = 0;
+          }
+          for (int k = 0; k < 6; ++k) iacc[k] += iv[k];
+        }
+      } else if (p >= 0) {  // links to several particles: per-link atomics
+        flush(p, iv);
+      }
+    }
+  }
+  if (lane == 0 && pacc >= 0) flush(pacc, iacc);
+  if constexpr (SHARED) {
+    __syncthreads();
+    long long* out = L.part + (size_t)blockIdx.x * n6;
+    for (int k = threadIdx.x; k < n6; k += blockDim.x)
+      out[k] = (long long)(((unsigned long long)s_hi[k] << 32) | (unsigned long long)s_lo[k]);
+  }
+}
+
+template <int ST, bool FORCE>
+__global__ void __launch_bounds__(256) k_boundary(BoundaryLaunch L) {
   using T = typename Store<ST>::T;
   const T* __restrict__ A = static_cast<const T*>(L.A);
   T* __restrict__ B = static_cast<T*>(L.B);
   const LatticeGeom& g = L.pl.g;
   const ParticleLaunch& pl = L.pl;
   const unsigned nbc = min(pl.ctr->n_bc, pl.cap_bc);
-  const float rho0 = L.p.rho0, om = L.p.omega;
-  const int j = threadIdx.x & 31;
-  const bool dirlane = j < 19;
-  const int ej[3] = {lex(j), ley(j), lez(j)};
-  const int d = lopp(j);  // link direction of lane j (towards the solid)
-  const int ed[3] = {-ej[0], -ej[1], -ej[2]};
-  const float wj = dirlane ? lw(j) : 0.f;
-  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-  int pacc = -1;              // lane 0: particle of the running fixed-point sums
-  long long iacc[6] = {0, 0, 0, 0, 0, 0};
-  for (unsigned bi = warp; bi < nbc; bi += nwarps) {
+  const float om = L.p.omega;
+  if (L.part && pl.np <= IBB_SHARED_PARTICLES) {
+    // the link kernel's per-block momentum-exchange sums into the particles'
+    // fixed-point sums (it ran before this kernel), a warp per component
+    const int n6 = 6 * pl.np;
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < (unsigned)n6;
+         k += (gridDim.x * blockDim.x) >> 5) {
+      long long v = 0;
+      for (int b = (int)lane; b < L.part_blocks; b += 32) v += L.part[(size_t)b * n6 + k];
+      v = warp_sum_fixed(v);
+      if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(pl.facc + k), (unsigned long long)v);
+    }
+  }
+  for (unsigned bi = blockIdx.x * blockDim.x + threadIdx.x; bi < nbc; bi += gridDim.x * blockDim.x) {
     const long long c = pl.bc_cell[bi];
     const uint32_t mask = pl.bc_mask[bi];
     const uint32_t loff = pl.bc_loff[bi];
+    const bool fit = links_fit(loff, mask, pl.cap_links);
     int x, y, z;
     coords(c, g, x, y, z);
-    // own post-collision populations and moments (rho_f, u_f)
-    const float hown = dirlane ? Store<ST>::dev(A + j * g.plane + c, j) : 0.f;
-    const float hopp = __shfl_sync(FULLW, hown, d < 19 ? d : 0);  // f+_d(x_f) - w_d
-    const float rho_f = 1.0f + wsumf(hown);
-    const float irho_f = 1.0f / rho_f;
-    const float uf0 = wsumf(ej[0] * hown) * irho_f, uf1 = wsumf(ej[1] * hown) * irho_f,
-                uf2 = wsumf(ej[2] * hown) * irho_f;
-    float hin = 0.f;
-    float dP[3] = {0.f, 0.f, 0.f}, dT[3] = {0.f, 0.f, 0.f};
-    int p = -1;
-    if (dirlane) {
-      int sx = x - ej[0], sy = y - ej[1], sz = z - ej[2];
+    float h[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+      const int d = opp(j);  // link direction of j (towards the source node)
+      int sx = x - cx(j), sy = y - cy(j), sz = z - cz(j);
       int face = -1;  // a corner crossing is attributed to x, then y, then z
       if (sz < 0) { if (g.periodic[2]) sz += g.nz; else face = 4; }
       else if (sz >= g.nz) { if (g.periodic[2]) sz -= g.nz; else face = 5; }
@@ -698,71 +868,27 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
       if (sx < 0) { if (g.periodic[0]) sx += g.nx; else face = 0; }
       else if (sx >= g.nx) { if (g.periodic[0]) sx -= g.nx; else face = 1; }
       if (face >= 0) {
-        hin = hopp + L.p.bb_wall[face][j];
+        h[j] = Store<ST>::dev(A + d * g.plane + c, d) + L.p.bb_wall[face][j];
       } else if (j == 0 || !((mask >> d) & 1u)) {
-        hin = Store<ST>::dev(A + j * g.plane + (sx + (long long)g.nx * (sy + (long long)g.ny * sz)), j);
+        h[j] = Store<ST>::dev(A + j * g.plane + (sx + (long long)g.nx * (sy + (long long)g.ny * sz)), j);
+      } else if (fit) {
+        h[j] = pl.link_g[loff + __popc(mask & ((1u << d) - 1u))];
       } else {
-        const unsigned l = loff + __popc(mask & ((1u << d) - 1u));
-        if (l >= pl.cap_links) {
-          hin = hopp;
-        } else {
-          p = (int)pl.link_p[l];
-          const DevParticle& P = pl.P[p];
-          const float q = LADD ? 0.5f : pl.link_q[l];
-          // wall point relative to the particle position: x - X = (x - floor X) - frac X,
-          // the integer part exact and the fraction rounded once to FP32 (no FP64 here:
-          // it runs at a small fraction of the FP32 rate on this part)
-          const float r0 = ((float)(x - P.pos_i[0]) - P.pos_fr[0]) + q * ed[0];
-          const float r1 = ((float)(y - P.pos_i[1]) - P.pos_fr[1]) + q * ed[1];
-          const float r2 = ((float)(z - P.pos_i[2]) - P.pos_fr[2]) + q * ed[2];
-          float uw[3];
-          uw[0] = P.velf[0] + (P.omegaf[1] * r2 - P.omegaf[2] * r1);
-          uw[1] = P.velf[1] + (P.omegaf[2] * r0 - P.omegaf[0] * r2);
-          uw[2] = P.velf[2] + (P.omegaf[0] * r1 - P.omegaf[1] * r0);
-          const float wall = 6.0f * wj * rho0 * (ej[0] * uw[0] + ej[1] * uw[1] + ej[2] * uw[2]);
-          float G;
-          if (LADD) {
-            G = hopp + wall;
-          } else {
-            float uff[3] = {uf0, uf1, uf2};
-            long long ff;
-            if (nbr_wrap(x, y, z, ej[0], ej[1], ej[2], g, ff) && pl.owner_cur[ff] == OWNER_NONE) {
-              float rr;
-              moments_at<ST>(A, g.plane, ff, rr, uff);
-            }
-            const float uf[3] = {uf0, uf1, uf2};
-            float ud[3];
-            const float i1q = 1.0f / (1.0f + q), iq = 1.0f / q;
-            const float a1 = (1.0f - q) * i1q, a2 = 2.0f * q * i1q;
-            const float b1 = (1.0f - q) * iq, b2 = (2.0f * q - 1.0f) * iq;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float us = q <= 0.5f ? 2.0f * q * uf[a] + (1.0f - 2.0f * q) * uff[a] : b1 * uf[a] + b2 * uw[a];
-              ud[a] = us / 3.0f + 2.0f * (a1 * uff[a] + a2 * uw[a]) / 3.0f;
-            }
-            const float eud = ed[0] * ud[0] + ed[1] * ud[1] + ed[2] * ud[2];
-            const float euf = ed[0] * uf[0] + ed[1] * uf[1] + ed[2] * uf[2];
-            const float ud2 = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
-            const float uf2 = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-            G = hopp + wj * rho_f * (3.0f * (eud - euf) + 4.5f * (eud * eud - euf * euf) - 1.5f * (ud2 - uf2)) + wall;
-          }
-          hin = G;
-          const float s2 = 2.0f * wj + hopp + G, dl = hopp - G;
-          dP[0] = ed[0] * s2 - uw[0] * dl;
-          dP[1] = ed[1] * s2 - uw[1] * dl;
-          dP[2] = ed[2] * s2 - uw[2] * dl;
-          dT[0] = r1 * dP[2] - r2 * dP[1];
-          dT[1] = r2 * dP[0] - r0 * dP[2];
-          dT[2] = r0 * dP[1] - r1 * dP[0];
-        }
+        h[j] = Store<ST>::dev(A + d * g.plane + c, d);
       }
     }
-    // collision of the node (moments of the incoming populations by warp sums)
-    const float drho = wsumf(hin);
+    // BGK collision of the node
+    float drho = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      drho += h[i];
+      j0 += cx(i) * h[i];
+      j1 += cy(i) * h[i];
+      j2 += cz(i) * h[i];
+    }
     const float rho = 1.0f + drho;
-    const float j0 = wsumf(ej[0] * hin), j1 = wsumf(ej[1] * hin), j2 = wsumf(ej[2] * hin);
-    float u0, u1, u2;
     const float irho = 1.0f / rho;
+    float u0, u1, u2;
     if (FORCE) {
       u0 = (j0 + 0.5f * L.p.force[0]) * irho;
       u1 = (j1 + 0.5f * L.p.force[1]) * irho;
@@ -772,49 +898,21 @@ __global__ void __launch_bounds__(256, 4) k_boundary(BoundaryLaunch L) {
       u1 = j1 * irho;
       u2 = j2 * irho;
     }
-    if (dirlane) {
-      const float eu = ej[0] * u0 + ej[1] * u1 + ej[2] * u2;
-      const float usq15 = 1.5f * (u0 * u0 + u1 * u1 + u2 * u2);
-      const float feq_dev = wj * (drho + rho * (3.0f * eu + 4.5f * eu * eu - usq15));
-      float hp = hin + om * (feq_dev - hin);
+    const float usq15 = 1.5f * (u0 * u0 + u1 * u1 + u2 * u2);
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+      const float eu = cx(j) * u0 + cy(j) * u1 + cz(j) * u2;
+      const float feq_dev = wq(j) * (drho + rho * (3.0f * eu + 4.5f * eu * eu - usq15));
+      float hp = h[j] + om * (feq_dev - h[j]);
       if (FORCE) {
-        const float eF = ej[0] * L.p.force[0] + ej[1] * L.p.force[1] + ej[2] * L.p.force[2];
+        const float eF = cx(j) * L.p.force[0] + cy(j) * L.p.force[1] + cz(j) * L.p.force[2];
         const float uF = u0 * L.p.force[0] + u1 * L.p.force[1] + u2 * L.p.force[2];
-        hp += (1.0f - 0.5f * om) * wj * (3.0f * (eF - uF) + 9.0f * eu * eF);
+        hp += (1.0f - 0.5f * om) * wq(j) * (3.0f * (eF - uF) + 9.0f * eu * eF);
       }
       if (L.tmp) Store<ST>::put(static_cast<T*>(L.tmp) + 19 * (size_t)bi + j, j, hp);
       else Store<ST>::put(B + j * g.plane + c, j, hp);
     }
-    // momentum exchange: every link's contribution is rounded to 2^-40 fixed
-    // point in its own lane (the rounding is odd-symmetric, so opposite links
-    // of a closed body cancel exactly), summed over the warp in integers, and
-    // kept by lane 0 while the particle does not change
-    if (__any_sync(FULLW, p >= 0)) {
-      const int pmin = __reduce_min_sync(FULLW, p >= 0 ? p : 0x7fffffff);
-      const bool single = __all_sync(FULLW, p < 0 || p == pmin);
-      const float v[6] = {dP[0], dP[1], dP[2], dT[0], dT[1], dT[2]};
-      long long iv[6];
-      // v * 2^40 is exact in FP32 and the conversion rounds to nearest even:
-      // odd-symmetric, so opposite links of a closed body cancel exactly
-#pragma unroll
-      for (int k = 0; k < 6; ++k) iv[k] = p >= 0 ? fixed_2m40(v[k]) : 0LL;
-      if (single) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) iv[k] = warp_sum_fixed(iv[k]);
-        if (j == 0) {
-          if (pacc != pmin) {
-            if (pacc >= 0) add_fixed_ll(pl.facc, pacc, iacc);
-            pacc = pmin;
-            for (int k = 0; k < 6; ++k) iacc[k] = 0;
-          }
-          for (int k = 0; k < 6; ++k) iacc[k] += iv[k];
-        }
-      } else if (p >= 0) {  // links to several particles: per-link atomics
-        add_fixed_ll(pl.facc, p, iv);
-      }
-    }
   }
-  if (j == 0 && pacc >= 0) add_fixed_ll(pl.facc, pacc, iacc);
 }
 
 template <int ST>
@@ -833,11 +931,27 @@ cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-template <int ST, bool FORCE>
-static cudaError_t launch_boundary_f(const BoundaryLaunch& L, cudaStream_t s) {
-  if (L.bb_mode == MI_BB_LADD) k_boundary<ST, FORCE, true><<<L.grid, 256, 0, s>>>(L);
-  else k_boundary<ST, FORCE, false><<<L.grid, 256, 0, s>>>(L);
+template <int ST>
+static cudaError_t launch_links_ibb_st(const BoundaryLaunch& L, cudaStream_t s) {
+  const bool ladd = L.bb_mode == MI_BB_LADD;
+  if (L.part && L.pl.np <= IBB_SHARED_PARTICLES) {
+    if (ladd) k_links_ibb<ST, true, true><<<L.part_blocks, 256, 0, s>>>(L);
+    else k_links_ibb<ST, false, true><<<L.part_blocks, 256, 0, s>>>(L);
+  } else {
+    if (ladd) k_links_ibb<ST, true, false><<<L.grid, 256, 0, s>>>(L);
+    else k_links_ibb<ST, false, false><<<L.grid, 256, 0, s>>>(L);
+  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_links_ibb(const BoundaryLaunch& L, cudaStream_t s) {
+  if (L.pl.np == 0) return cudaSuccess;
+  switch (L.storage) {
+    case MI_STORE_F32: return launch_links_ibb_st<MI_STORE_F32>(L, s);
+    case MI_STORE_F16_DEV: return launch_links_ibb_st<MI_STORE_F16_DEV>(L, s);
+    case MI_STORE_BF16_DEV: return launch_links_ibb_st<MI_STORE_BF16_DEV>(L, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int ST>
@@ -859,7 +973,9 @@ cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s) {
 
 template <int ST>
 static cudaError_t launch_boundary_st(const BoundaryLaunch& L, cudaStream_t s) {
-  return L.forcing ? launch_boundary_f<ST, true>(L, s) : launch_boundary_f<ST, false>(L, s);
+  if (L.forcing) k_boundary<ST, true><<<L.grid, 256, 0, s>>>(L);
+  else k_boundary<ST, false><<<L.grid, 256, 0, s>>>(L);
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -554,6 +554,10 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
   for (unsigned l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
     const unsigned bi = L.link_bc[l];
     if (bi >= nbc) continue;
+    // an entry of this step: inside the range of the node it names, whose
+    // links all fitted (entries of a node that overflowed were not written)
+    const unsigned loff = L.bc_loff[bi], m = __popc(L.bc_mask[bi]);
+    if (l < loff || l - loff >= m || (unsigned long long)loff + m > (unsigned long long)L.cap_links) continue;
     const long long c = L.bc_cell[bi];
     const int d = L.link_dir[l];
     const DevParticle& P = L.P[L.link_p[l]];

@@ -244,6 +244,7 @@ struct ParticleLaunch {
   uint32_t *link_bc, *link_p;
   uint8_t* link_dir;
   float* link_q;
+  float* link_g;               // interpolated bounce-back population of each link (k_links_ibb)
   uint32_t* new_cell;
   uint32_t* cov_cell;         // covered nodes, listed only when cover_uncover (capacity cap_new)
   unsigned cap_bc, cap_links, cap_new;
@@ -268,8 +269,21 @@ struct BoundaryLaunch {
   int bb_mode;
   int grid;
   void* tmp;  // when set, k_boundary writes node k's 19 values to tmp[19 k ..] instead of B
+  // per-block momentum-exchange sums of k_links_ibb (part_blocks x 6 np
+  // int64), or null: the link kernel then adds into pl.facc directly
+  long long* part;
+  int part_blocks;
 };
+// Up to this many particles the link kernel sums the momentum exchange per
+// block in shared memory and the boundary-node kernel adds the blocks' sums,
+// so that warps do not contend for the same global addresses (thousands of
+// 64-bit atomics on the same few addresses serialise).
+constexpr int IBB_SHARED_PARTICLES = 1000;
+constexpr int IBB_BLOCKS_PER_SM = 4;
 cudaError_t launch_refill(const BoundaryLaunch& L, cudaStream_t s);
+// Every link's bounce-back population into L.pl.link_g and its momentum exchange
+// into the fixed-point sums (reads A only).
+cudaError_t launch_links_ibb(const BoundaryLaunch& L, cudaStream_t s);
 cudaError_t launch_boundary(const BoundaryLaunch& L, cudaStream_t s);
 cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s);
 // Copy the boundary nodes' values from L.tmp into B (stored format, no arithmetic).

@@ -106,8 +106,9 @@ def test_autotune_cache_and_bitwise_results(tmp_path):
 @pytest.mark.parametrize("storage", [0, 1])
 def test_overlapped_boundary_schedule_is_bitwise_identical(storage):
     """Computing the boundary nodes beside the bulk kernel into a side buffer
-    and scattering them afterwards changes no bit of the populations, the
-    forces or the particle states (graph replay, moving particles, contacts)."""
+    and scattering them afterwards, or only the links' bounce-back beside it,
+    changes no bit of the populations, the forces or the particle states
+    (graph replay, moving particles, contacts)."""
     B = binding()
     shape = (48, 48, 40)
     parts = _cluster(8)
@@ -117,10 +118,10 @@ def test_overlapped_boundary_schedule_is_bitwise_identical(storage):
     u = 0.02 * scenes.velocity_field_noise(shape, 5)
     f0 = lbm.equilibrium(np.ones((nz, ny, nx)), u).astype(np.float32)
     out = []
-    for overlap in (False, True):
+    for schedule in ({}, {"overlap_boundary": True}, {"links_beside": True}):
         sim = B.Simulation(*shape, tau=0.8, gravity=(0, 0, -1e-4), storage=storage, kn=PARAMS["kn"], kt=PARAMS["kt"],
                            eta_n=PARAMS["eta_n"], eta_t=PARAMS["eta_t"], mu_s=PARAMS["mu_s"], max_particles=64)
-        sim.set_schedule(overlap)
+        sim.set_schedule(**schedule)
         for P in parts:
             sim.add_particle(P["centers"], P["k"], P["density"], P["skin"], P["pos"], P["quat"], P["vel"], P["omega"],
                              mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
@@ -129,15 +130,16 @@ def test_overlapped_boundary_schedule_is_bitwise_identical(storage):
         st = [sim.get_particle_state(i) for i in range(len(parts))]
         out.append((sim.get_raw_populations(), sim.forces(), st, sim.node_classes()))
         sim.close()
-    (pa, fa, sa, (ca, oa)), (pb, fb, sb, (cb, ob)) = out
-    assert np.array_equal(ca, cb) and np.array_equal(oa, ob)
+    pa, fa, sa, (ca, oa) = out[0]
     fluid = oa == 0xFFFFFFFF
-    assert np.ascontiguousarray(pa[:, fluid]).tobytes() == np.ascontiguousarray(pb[:, fluid]).tobytes()
-    for key in fa:
-        assert np.array_equal(fa[key], fb[key]), key
-    for x, y in zip(sa, sb):
-        for key in x:
-            assert np.array_equal(x[key], y[key]), key
+    for pb, fb, sb, (cb, ob) in out[1:]:
+        assert np.array_equal(ca, cb) and np.array_equal(oa, ob)
+        assert np.ascontiguousarray(pa[:, fluid]).tobytes() == np.ascontiguousarray(pb[:, fluid]).tobytes()
+        for key in fa:
+            assert np.array_equal(fa[key], fb[key]), key
+        for x, y in zip(sa, sb):
+            for key in x:
+                assert np.array_equal(x[key], y[key]), key
 
 
 @pytest.mark.parametrize("nsteps,dem_substeps", [(7, 1), (8, 3)])
