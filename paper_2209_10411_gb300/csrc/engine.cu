@@ -167,7 +167,9 @@ ParticleLaunch mi_delbm::particle_launch() const {
   L.cap_bc = cap_bc;
   L.cap_links = cap_links;
   L.cap_new = cap_new;
-  L.blocks_per_particle = blocks_per_particle;
+  L.flag_off = dblk_off;
+  L.cls_off = dblk_off ? dblk_off + cfg.max_particles + 1 : nullptr;
+  L.flag_blocks = flag_blocks;
   L.classify_blocks = classify_blocks;
   L.g = geom();
   return L;
@@ -711,6 +713,8 @@ mi_status mi_delbm::ensure_particle_buffers() {
   dballs = (float4*)dalloc(sizeof(float4) * nb);
   dballs_d = (double*)dalloc(sizeof(double) * 4 * nb);
   dballs_s = (float4*)dalloc(sizeof(float4) * 2 * nb);
+  dblk_off = (int*)dalloc(sizeof(int) * 2 * ((size_t)np + 1));
+  if (!dblk_off) return fail(MI_ENOMEM, "particle buffers: device allocation failed");
   if (np <= IBB_SHARED_PARTICLES) {
     ibb_part = (long long*)dalloc(sizeof(long long) * 6 * (size_t)np * sm_count * IBB_BLOCKS_PER_SM);
     if (!ibb_part) return fail(MI_ENOMEM, "particle buffers: device allocation failed");
@@ -1691,22 +1695,30 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   h->n_particles += 1;
   // list capacities and box-kernel grid from the particles' box extents
   unsigned long long sbc = 0;
-  long long maxvol = 1;
   for (const auto& q : h->hp) {
     const unsigned long long e2 = (unsigned long long)(q.ext[0] + 4) * (q.ext[0] + 4);
     sbc += 6ull * e2;
-    const long long v = (long long)(q.ext[0] + 8) * (q.ext[1] + 8) * (q.ext[2] + 8);
-    if (v > maxvol) maxvol = v;
   }
   if (sbc > 0x3FFFFFFFull) sbc = 0x3FFFFFFFull;
   st = h->ensure_list_capacity((unsigned)sbc, (unsigned)std::min<unsigned long long>(6ull * sbc, 0xFFFFFFF0ull), (unsigned)sbc);
   if (st != MI_OK) return st;
-  long long bpp = (maxvol + 1023) / 1024;
-  h->blocks_per_particle = (int)(bpp < 1 ? 1 : (bpp > 8192 ? 8192 : bpp));
-  long long maxrows = 1;
-  for (const auto& q : h->hp) maxrows = std::max<long long>(maxrows, (long long)(q.ext[1] + 8) * (q.ext[2] + 8));
-  const long long cb = (maxrows + 63) / 64;  // 8 warps per block, about 8 rows per warp
-  h->classify_blocks = (int)(cb < 1 ? 1 : (cb > 4096 ? 4096 : cb));
+  // box-kernel blocks per particle: about 1024 box nodes per flag block, and
+  // 8 warps of about 8 rows each per classification block (the classified
+  // region, old and new box widened by 2, has fewer than (ext + 8)^2 rows)
+  const int npart = h->n_particles, stride = h->cfg.max_particles + 1;
+  std::vector<int> boff(2 * (size_t)stride, 0);
+  for (int q = 0; q < npart; ++q) {
+    const int* e = h->hp[q].ext;
+    const long long fb = ((long long)e[0] * e[1] * e[2] + 1023) / 1024;
+    const long long cb = ((long long)(e[1] + 8) * (e[2] + 8) + 63) / 64;
+    boff[q + 1] = boff[q] + (int)std::min<long long>(std::max<long long>(fb, 1), 8192);
+    boff[stride + q + 1] = boff[stride + q] + (int)std::min<long long>(std::max<long long>(cb, 1), 4096);
+  }
+  h->flag_blocks = std::max(boff[npart], 1);
+  h->classify_blocks = std::max(boff[stride + npart], 1);
+  cudaError_t ce = cudaMemcpyAsync(h->dblk_off, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return h->cuda_fail(ce, "mi_delbm_add_particle: block offsets");
   h->invalidate_graphs();
   if (id_out) *id_out = id;
   return MI_OK;

@@ -112,8 +112,11 @@ struct mi_delbm {
   bool links_beside = false;         // the links' bounce-back beside the bulk kernel
   bool unfused_dem = false;          // DEM substeps as separate launches even where the fused kernel applies
   bool cover_uncover = false;        // covered/uncovered-node momentum joins the hydrodynamic sums
-  int blocks_per_particle = 1;
-  int classify_blocks = 1;
+  // blocks of the box kernels, sized per particle: device offsets (particle
+  // p owns blocks [off[p], off[p + 1])) of the flag and clear kernels, then of
+  // the classification, max_particles + 1 each; the totals are the grids
+  int* dblk_off = nullptr;
+  int flag_blocks = 1, classify_blocks = 1;
 
   TuneChoice tune;
 

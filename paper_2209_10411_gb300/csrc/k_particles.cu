@@ -164,17 +164,34 @@ cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The particle owning block b of a box kernel's 1D grid (off[p] <= b <
+// off[p + 1], off[0] = 0) by binary search, its first block and block count.
+struct BoxBlock {
+  int p, b, nb;
+};
+__device__ __forceinline__ BoxBlock box_block(const int* __restrict__ off, int np, int b) {
+  int lo = 0, hi = np;  // off[lo] <= b < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const int o = off[lo];
+  return {lo, b - o, off[lo + 1] - o};
+}
+
 // ---------------------------------------------------------------------------
 // Clear the owner buffer about to be rewritten, over the boxes it was last
 // written with.
 // ---------------------------------------------------------------------------
 __global__ void k_clear(ParticleLaunch L) {
-  const DevParticle& P = L.P[blockIdx.y];
+  const BoxBlock bb = box_block(L.flag_off, L.np, blockIdx.x);
+  const DevParticle& P = L.P[bb.p];
   const int* lo = P.lo_hist[L.cur_buf];
   if (lo[0] == BOX_NONE) return;
   const Region r = clip_region(lo, P.ext, 0, L.g);
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bb.b * blockDim.x + threadIdx.x; i < r.total; i += bb.nb * blockDim.x) {
     const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
     const int x = r.lo[0] + (int)(rem - yi * n0);
     const int y = r.lo[1] + (int)yi;
@@ -185,8 +202,7 @@ __global__ void k_clear(ParticleLaunch L) {
 
 cudaError_t launch_clear(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  dim3 grid(L.blocks_per_particle, L.np);
-  k_clear<<<grid, 256, 0, s>>>(L);
+  k_clear<<<L.flag_blocks, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -196,7 +212,8 @@ cudaError_t launch_clear(const ParticleLaunch& L, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
   extern __shared__ float4 sb[];
-  const int p = blockIdx.y;
+  const BoxBlock bb = box_block(L.flag_off, L.np, blockIdx.x);
+  const int p = bb.p;
   const DevParticle& P = L.P[p];
   const int nb = P.n_balls;
   const bool staged = nb <= L.max_balls_per_particle;
@@ -207,7 +224,7 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
     for (int i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = L.balls[P.ball_off + i];
   __syncthreads();
   const float4* bl = staged ? sb : L.balls + P.ball_off;
-  if (blockIdx.x == 0 && threadIdx.x == 0)
+  if (bb.b == 0 && threadIdx.x == 0)
     for (int a = 0; a < 3; ++a) L.P[p].lo_hist[L.cur_buf][a] = P.lo[a];
   const Region r = clip_region(P.lo, P.ext, 0, L.g);
   // x - X = (x - Xi) - Xf with Xi = floor(X): the integer part is exact in
@@ -220,7 +237,7 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
   for (int k = 0; k < 9; ++k) Rf[k] = P.Rf[k];
   const float rt = (float)P.Rt * (1.0f + 1e-6f) + 1e-4f, rt2 = rt * rt;
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bb.b * blockDim.x + threadIdx.x; i < r.total; i += bb.nb * blockDim.x) {
     const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
     const int x = r.lo[0] + (int)(rem - yi * n0);
     const int y = r.lo[1] + (int)yi;
@@ -274,9 +291,8 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
 
 cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  dim3 grid(L.blocks_per_particle, L.np);
   const size_t smem = sizeof(float4) * (size_t)L.max_balls_per_particle;
-  k_flag<<<grid, 256, smem, s>>>(L);
+  k_flag<<<L.flag_blocks, 256, smem, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -290,7 +306,8 @@ cudaError_t launch_flag(const ParticleLaunch& L, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <bool COV>
 __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
-  const DevParticle& P = L.P[blockIdx.y];
+  const BoxBlock bb = box_block(L.cls_off, L.np, blockIdx.x);
+  const DevParticle& P = L.P[bb.p];
   int lo[3], ext[3];
   const int* lp = P.lo_hist[L.prev_buf];
   const bool had = lp[0] != BOX_NONE;
@@ -323,7 +340,7 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
   // the whole warp), its nodes taken 32 at a time
   const int lane = threadIdx.x & 31;
   const unsigned rows = (unsigned)r.n[1] * (unsigned)r.n[2];
-  const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned wid = (bb.b * blockDim.x + threadIdx.x) >> 5, nw = (bb.nb * blockDim.x) >> 5;
   for (unsigned row = wid; row < rows; row += nw) {
     const unsigned zi = row / (unsigned)r.n[1];
     const int y = r.lo[1] + (int)(row - zi * (unsigned)r.n[1]);
@@ -443,9 +460,8 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
 cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
   // a warp per (y, z) row, about eight rows per warp
-  dim3 grid(L.classify_blocks, L.np);
-  if (L.cover_uncover) k_classify<true><<<grid, 256, 0, s>>>(L);
-  else k_classify<false><<<grid, 256, 0, s>>>(L);
+  if (L.cover_uncover) k_classify<true><<<L.classify_blocks, 256, 0, s>>>(L);
+  else k_classify<false><<<L.classify_blocks, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -465,7 +481,7 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 // and is close to linear along a link for fields of the form k / r^2 (the
 // distance to a lone ball over its radius), kept inside a shrinking bracket
 // [lo, hi] (bisection when a step leaves it), the field summed as four
-// independent partial sums, until a step is below 2e-5.  With the exact
+// independent partial sums, until a step is below 1e-3.  With the exact
 // differences the body-frame point carries ~1e-7 of rounding, but the FP32
 // field's noise, divided by g'(q) = e . grad f (small on large smooth
 // particles and on links that meet the surface at a grazing angle), still
@@ -475,8 +491,10 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 // significant bits; Knuth's TwoSum and the fused-multiply-add form of
 // Dekker's product are exact), the derivative in FP32, inside a bracket that
 // starts at [0, 1] (the exact flags guarantee g(0) < 0 <= g(1)) and moves with
-// the accurate signs.  A step below 2e-5 ends it (Newton's quadratic
-// convergence leaves an error ~(g''/2g') step^2 behind); at most four steps.
+// the accurate signs.  A step ends it when it is below 2e-5 or when the error
+// Newton's quadratic convergence leaves behind, |g''/2g'| step^2 with g'' in
+// FP32 from the same sums, is below 1e-7 (usually the first step); at most
+// four steps.
 // ---------------------------------------------------------------------------
 namespace {
 struct F2 {
@@ -506,10 +524,10 @@ __device__ __forceinline__ F2 diff_hi(float p, float c, bool grid) {
   return grid ? F2{__fsub_rn(p, c), 0.f} : two_sum(p, -c);
 }
 
-// g(q) = f(p + q e) - 1 in float-float; g'(q) in FP32.
+// g(q) = f(p + q e) - 1 in float-float; g'(q) and g''(q) in FP32 (ee = e . e).
 __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int nb, const F2 p[3], const F2 e[3],
-                                             float q, bool grid, float& gp) {
-  float gh = 0.f, gl = 0.f, d1 = 0.f;
+                                             float q, bool grid, float ee, float& gp, float& gpp) {
+  float gh = 0.f, gl = 0.f, d1 = 0.f, d2 = 0.f;
   for (int b = 0; b < nb; ++b) {
     const float4 ch = __ldg(bs + 2 * b), cl = __ldg(bs + 2 * b + 1);
     const float c_hi[3] = {ch.x, ch.y, ch.z}, c_lo[3] = {cl.x, cl.y, cl.z};
@@ -540,9 +558,14 @@ __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int 
     const F2 s = two_sum(gh, th);
     gh = s.hi;
     gl += s.lo + tl;
-    d1 = __fmaf_rn(-2.0f * th, __fdividef(ae, r2.hi), d1);
+    // k / r^2 along the link: r^2' = 2 a.e, r^2'' = 2 e.e, so
+    // g' = -2 t (a.e) / r^2 and g'' = t / r^2 (8 (a.e)^2 / r^2 - 2 e.e), t = k / r^2
+    const float ir2 = __fdividef(1.0f, r2.hi), u = ae * ir2;
+    d1 = __fmaf_rn(-2.0f * th, u, d1);
+    d2 = __fmaf_rn(th * ir2, __fmaf_rn(8.0f * ae, u, -2.0f * ee), d2);
   }
   gp = d1;
+  gpp = d2;
   const F2 g = two_sum(gh, -1.0f);
   return g.hi + (g.lo + gl);
 }
@@ -637,9 +660,10 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
       // Newton on h: q + 2 f (1 - sqrt f) / f'
       const float step = 2.f * f * (1.f - f * rsqrtf(f)) / fp;
       float qn = q + step;
-      // a step below the tolerance ends the stage even when its end rounds onto
-      // the bracket (which it does once q sits on the root)
-      if (fabsf(step) < 2e-5f) {
+      // a step below 1e-3 ends the stage (taken, clamped to the bracket): h is
+      // close to linear, so the step leaves far less than the FP32 field's
+      // noise behind, which the accurate stage removes
+      if (fabsf(step) < 1e-3f) {
         q = fminf(fmaxf(qn, lo), hi);
         break;
       }
@@ -650,14 +674,17 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
     // stage 2: double-float Newton
     lo = 0.f;
     hi = 1.f;
+    const float ee = es[0].hi * es[0].hi + es[1].hi * es[1].hi + es[2].hi * es[2].hi;
     for (int it = 0; it < 4; ++it) {
-      float gp;
-      const float g = residual_ff(bs, nb, ps, es, q, grid, gp);
+      float gp, gpp;
+      const float g = residual_ff(bs, nb, ps, es, q, grid, ee, gp, gpp);
       if (g >= 0.f) hi = q;
       else lo = q;
       const float step = g / gp;
       float qn = q - step;
-      if (fabsf(step) < 2e-5f) {
+      // the step ends the stage when it is below 2e-5, or when Newton's error
+      // after it, |g'' / 2 g'| step^2, is below 1e-7 (and it stays in the bracket)
+      if (fabsf(step) < 2e-5f || (qn >= lo && qn <= hi && fabsf(gpp) * step * step <= 2e-7f * fabsf(gp))) {
         q = fminf(fmaxf(qn, lo), hi);
         break;
       }

@@ -249,8 +249,12 @@ struct ParticleLaunch {
   uint32_t* cov_cell;         // covered nodes, listed only when cover_uncover (capacity cap_new)
   unsigned cap_bc, cap_links, cap_new;
   int cover_uncover;
-  int blocks_per_particle;
-  int classify_blocks;        // per particle: 256-thread blocks of the row-per-warp classification
+  // box kernels: particle p owns blocks [off[p], off[p + 1]) of a 1D grid,
+  // flag_off for the flag and clear kernels (flag_blocks in all), cls_off for
+  // the row-per-warp classification (classify_blocks in all)
+  const int* flag_off;
+  const int* cls_off;
+  int flag_blocks, classify_blocks;
   LatticeGeom g;
 };
 cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s);
