@@ -480,8 +480,9 @@ cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
 // Stage 1, FP32: Newton steps on h(q) = f^(-1/2) - 1, which has the same root
 // and is close to linear along a link for fields of the form k / r^2 (the
 // distance to a lone ball over its radius), kept inside a shrinking bracket
-// [lo, hi] (bisection when a step leaves it), the field summed as four
-// independent partial sums, until a step is below 1e-3.  With the exact
+// [lo, hi] (bisection when a step leaves it), the field summed as two
+// independent partial sums from the hi parts of the centres, until a step is
+// below 1e-3.  With the exact
 // differences the body-frame point carries ~1e-7 of rounding, but the FP32
 // field's noise, divided by g'(q) = e . grad f (small on large smooth
 // particles and on links that meet the surface at a grazing angle), still
@@ -525,8 +526,9 @@ __device__ __forceinline__ F2 diff_hi(float p, float c, bool grid) {
 }
 
 // g(q) = f(p + q e) - 1 in float-float; g'(q) and g''(q) in FP32 (ee = e . e).
+template <bool GRID>
 __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int nb, const F2 p[3], const F2 e[3],
-                                             float q, bool grid, float ee, float& gp, float& gpp) {
+                                             float q, float ee, float& gp, float& gpp) {
   float gh = 0.f, gl = 0.f, d1 = 0.f, d2 = 0.f;
   for (int b = 0; b < nb; ++b) {
     const float4 ch = __ldg(bs + 2 * b), cl = __ldg(bs + 2 * b + 1);
@@ -535,8 +537,8 @@ __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int 
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       // a = (p - c) + q e as ah + al
-      const F2 d = diff_hi(p[k].hi, c_hi[k], grid);
-      const float dl = d.lo + (p[k].lo - c_lo[k]);
+      const F2 d = diff_hi(p[k].hi, c_hi[k], GRID);
+      const float dl = GRID ? p[k].lo - c_lo[k] : d.lo + (p[k].lo - c_lo[k]);
       const F2 m = two_prod(q, e[k].hi);
       const float ml = __fmaf_rn(q, e[k].lo, m.lo);
       const F2 a = two_sum(d.hi, m.hi);
@@ -544,14 +546,20 @@ __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int 
       // a^2 = ah^2 + 2 ah al (al^2 is below the working precision)
       const F2 sq = two_prod(a.hi, a.hi);
       const float sql = __fmaf_rn(2.0f * a.hi, al, sq.lo);
-      const F2 t = two_sum(r2h, sq.hi);
-      r2h = t.hi;
-      r2l += t.lo + sql;
+      if (k == 0) {
+        r2h = sq.hi;
+        r2l = sql;
+      } else {
+        const F2 t = two_sum(r2h, sq.hi);
+        r2h = t.hi;
+        r2l += t.lo + sql;
+      }
       ae = __fmaf_rn(a.hi, e[k].hi, ae);
     }
     const F2 r2 = two_sum(r2h, r2l);
-    // k / r^2: the quotient of the hi parts, corrected by its exact residual
-    const float th = __fdiv_rn(ch.w, r2.hi);
+    // k / r^2: a quotient of the hi parts (within 2 ulps), corrected by its
+    // residual (formed by FMA, rounded at ~2^-46 of k)
+    const float th = __fdividef(ch.w, r2.hi);
     float res = __fmaf_rn(-th, r2.hi, ch.w);
     res = __fmaf_rn(-th, r2.lo, res + cl.w);
     const float tl = __fdividef(res, r2.hi);
@@ -570,6 +578,87 @@ __device__ __forceinline__ float residual_ff(const float4* __restrict__ bs, int 
   return g.hi + (g.lo + gl);
 }
 }  // namespace
+
+// The root q of one link from its body-frame origin ps and direction es
+// (float pairs) over the particle's nb split balls bs; GRID: ps and the
+// centres share the 2^-12 grid (hi parts subtract exactly).
+template <bool GRID>
+__device__ __forceinline__ float link_root(const float4* __restrict__ bs, int nb, const F2 ps[3], const F2 es[3]) {
+  // stage 1: FP32 Newton on h = f^(-1/2) - 1
+  float lo = 0.f, hi = 1.f, q = 0.5f;
+  for (int it = 0; it < 24; ++it) {
+    float f0 = 0.f, f1 = 0.f, s0 = 0.f, s1 = 0.f;
+    // p_lo + q e, then + (p_hi - c_hi) per ball: the centres' lo parts (2^-24
+    // of a centre) are left to the accurate stage
+    float a[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] = __fmaf_rn(q, es[k].hi, ps[k].lo);
+    int b = 0;
+    for (; b + 2 <= nb; b += 2) {
+      const float4 ha = __ldg(bs + 2 * b), hb = __ldg(bs + 2 * b + 2);
+      const float u0 = diff_hi(ps[0].hi, ha.x, GRID).hi + a[0];
+      const float u1 = diff_hi(ps[1].hi, ha.y, GRID).hi + a[1];
+      const float u2 = diff_hi(ps[2].hi, ha.z, GRID).hi + a[2];
+      const float v0 = diff_hi(ps[0].hi, hb.x, GRID).hi + a[0];
+      const float v1 = diff_hi(ps[1].hi, hb.y, GRID).hi + a[1];
+      const float v2 = diff_hi(ps[2].hi, hb.z, GRID).hi + a[2];
+      const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2), iv = __fdividef(1.f, v0 * v0 + v1 * v1 + v2 * v2);
+      const float tu = ha.w * iu, tv = hb.w * iv;
+      f0 += tu;
+      f1 += tv;
+      // f' = -2 sum k (a . e) / r^4: the factor -2 is applied to the sums
+      s0 = __fmaf_rn(tu * iu, u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi, s0);
+      s1 = __fmaf_rn(tv * iv, v0 * es[0].hi + v1 * es[1].hi + v2 * es[2].hi, s1);
+    }
+    if (b < nb) {
+      const float4 ha = __ldg(bs + 2 * b);
+      const float u0 = diff_hi(ps[0].hi, ha.x, GRID).hi + a[0];
+      const float u1 = diff_hi(ps[1].hi, ha.y, GRID).hi + a[1];
+      const float u2 = diff_hi(ps[2].hi, ha.z, GRID).hi + a[2];
+      const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2);
+      const float tu = ha.w * iu;
+      f0 += tu;
+      s0 = __fmaf_rn(tu * iu, u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi, s0);
+    }
+    const float f = f0 + f1, fp = -2.f * (s0 + s1);
+    if (f >= 1.f) hi = q;
+    else lo = q;
+    // Newton on h: q + 2 f (1 - sqrt f) / f'
+    const float step = 2.f * f * (1.f - f * rsqrtf(f)) / fp;
+    float qn = q + step;
+    // a step below 1e-3 ends the stage (taken, clamped to the bracket): h is
+    // close to linear, so the step leaves far less than the FP32 field's
+    // noise behind, which the accurate stage removes
+    if (fabsf(step) < 1e-3f) {
+      q = fminf(fmaxf(qn, lo), hi);
+      break;
+    }
+    if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
+    q = qn;
+    if (hi - lo < 1e-6f) break;
+  }
+  // stage 2: double-float Newton
+  lo = 0.f;
+  hi = 1.f;
+  const float ee = es[0].hi * es[0].hi + es[1].hi * es[1].hi + es[2].hi * es[2].hi;
+  for (int it = 0; it < 4; ++it) {
+    float gp, gpp;
+    const float g = residual_ff<GRID>(bs, nb, ps, es, q, ee, gp, gpp);
+    if (g >= 0.f) hi = q;
+    else lo = q;
+    const float step = g / gp;
+    float qn = q - step;
+    // the step ends the stage when it is below 2e-5, or when Newton's error
+    // after it, |g'' / 2 g'| step^2, is below 1e-7 (and it stays in the bracket)
+    if (fabsf(step) < 2e-5f || (qn >= lo && qn <= hi && fabsf(gpp) * step * step <= 2e-7f * fabsf(gp))) {
+      q = fminf(fmaxf(qn, lo), hi);
+      break;
+    }
+    if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
+    q = qn;
+  }
+  return q;
+}
 
 __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
   const unsigned nl = min(L.ctr->n_links, L.cap_links);
@@ -611,86 +700,7 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
     const F2 es[3] = {{P.Es[d][0], P.Es[d][3]}, {P.Es[d][1], P.Es[d][4]}, {P.Es[d][2], P.Es[d][5]}};
     const float4* bs = L.balls_s + 2 * (size_t)P.ball_off;
     const int nb = P.n_balls;
-    // stage 1: FP32 Newton on h = f^(-1/2) - 1
-    float lo = 0.f, hi = 1.f, q = 0.5f;
-    for (int it = 0; it < 24; ++it) {
-      float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      float a[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) a[k] = __fmaf_rn(q, es[k].hi, ps[k].lo);  // p_lo + q e, then + (p_hi - c_hi) per ball
-      int b = 0;
-      for (; b + 2 <= nb; b += 2) {
-        const float4 ha = __ldg(bs + 2 * b), la = __ldg(bs + 2 * b + 1);
-        const float4 hb = __ldg(bs + 2 * b + 2), lb = __ldg(bs + 2 * b + 3);
-        const float u0 = diff_hi(ps[0].hi, ha.x, grid).hi + (a[0] - la.x);
-        const float u1 = diff_hi(ps[1].hi, ha.y, grid).hi + (a[1] - la.y);
-        const float u2 = diff_hi(ps[2].hi, ha.z, grid).hi + (a[2] - la.z);
-        const float v0 = diff_hi(ps[0].hi, hb.x, grid).hi + (a[0] - lb.x);
-        const float v1 = diff_hi(ps[1].hi, hb.y, grid).hi + (a[1] - lb.y);
-        const float v2 = diff_hi(ps[2].hi, hb.z, grid).hi + (a[2] - lb.z);
-        const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2), iv = __fdividef(1.f, v0 * v0 + v1 * v1 + v2 * v2);
-        const float tu = ha.w * iu, tv = hb.w * iv;
-        const float du = -2.f * tu * (u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi) * iu;
-        const float dv = -2.f * tv * (v0 * es[0].hi + v1 * es[1].hi + v2 * es[2].hi) * iv;
-        if (b & 2) {
-          f2 += tu;
-          f3 += tv;
-          s2 += du;
-          s3 += dv;
-        } else {
-          f0 += tu;
-          f1 += tv;
-          s0 += du;
-          s1 += dv;
-        }
-      }
-      if (b < nb) {
-        const float4 ha = __ldg(bs + 2 * b), la = __ldg(bs + 2 * b + 1);
-        const float u0 = diff_hi(ps[0].hi, ha.x, grid).hi + (a[0] - la.x);
-        const float u1 = diff_hi(ps[1].hi, ha.y, grid).hi + (a[1] - la.y);
-        const float u2 = diff_hi(ps[2].hi, ha.z, grid).hi + (a[2] - la.z);
-        const float iu = __fdividef(1.f, u0 * u0 + u1 * u1 + u2 * u2);
-        const float tu = ha.w * iu;
-        f0 += tu;
-        s0 -= 2.f * tu * (u0 * es[0].hi + u1 * es[1].hi + u2 * es[2].hi) * iu;
-      }
-      const float f = (f0 + f1) + (f2 + f3), fp = (s0 + s1) + (s2 + s3);
-      if (f >= 1.f) hi = q;
-      else lo = q;
-      // Newton on h: q + 2 f (1 - sqrt f) / f'
-      const float step = 2.f * f * (1.f - f * rsqrtf(f)) / fp;
-      float qn = q + step;
-      // a step below 1e-3 ends the stage (taken, clamped to the bracket): h is
-      // close to linear, so the step leaves far less than the FP32 field's
-      // noise behind, which the accurate stage removes
-      if (fabsf(step) < 1e-3f) {
-        q = fminf(fmaxf(qn, lo), hi);
-        break;
-      }
-      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
-      q = qn;
-      if (hi - lo < 1e-6f) break;
-    }
-    // stage 2: double-float Newton
-    lo = 0.f;
-    hi = 1.f;
-    const float ee = es[0].hi * es[0].hi + es[1].hi * es[1].hi + es[2].hi * es[2].hi;
-    for (int it = 0; it < 4; ++it) {
-      float gp, gpp;
-      const float g = residual_ff(bs, nb, ps, es, q, grid, ee, gp, gpp);
-      if (g >= 0.f) hi = q;
-      else lo = q;
-      const float step = g / gp;
-      float qn = q - step;
-      // the step ends the stage when it is below 2e-5, or when Newton's error
-      // after it, |g'' / 2 g'| step^2, is below 1e-7 (and it stays in the bracket)
-      if (fabsf(step) < 2e-5f || (qn >= lo && qn <= hi && fabsf(gpp) * step * step <= 2e-7f * fabsf(gp))) {
-        q = fminf(fmaxf(qn, lo), hi);
-        break;
-      }
-      if (!(qn > lo && qn < hi)) qn = 0.5f * (lo + hi);
-      q = qn;
-    }
+    const float q = grid ? link_root<true>(bs, nb, ps, es) : link_root<false>(bs, nb, ps, es);
     L.link_q[l] = fminf(fmaxf(q, 1e-6f), 1.0f);
   }
 }
