@@ -342,7 +342,12 @@ static ContactLaunch contact_launch(const mi_delbm* h) {
   L.cp.n[0] = h->cfg.nx;
   L.cp.n[1] = h->cfg.ny;
   L.cp.n[2] = h->cfg.nz;
-  L.grid = h->sm_count * 6;  // 128-thread blocks of <= 85 registers: six fit on an SM
+  // 128-thread blocks of <= 85 registers: six fit on an SM; never more warps
+  // than there can be candidates (pairs and walls), so that a few particles
+  // do not take every SM's registers from the kernels running beside
+  const long long npl = h->n_particles;
+  const long long most = std::min<long long>(npl * (npl - 1) / 2 + 6 * npl, (long long)h->cap_items);
+  L.grid = (int)std::max<long long>(1, std::min<long long>((long long)h->sm_count * 6, (most + 3) / 4));
   return L;
 }
 
