@@ -208,7 +208,7 @@ constexpr int PG_CAP = 128;  // balls of particle 1 the plain guess stages in sh
 // (local centre, radius) are formed once and read back by broadcast instead
 // of being transformed again for every ball of particle 0; the arithmetic
 // and the order are the same either way.
-__device__ __forceinline__ void plain_guess(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+static __device__ __noinline__ void plain_guess(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
                                             int lane, float y[3], float4* stage = nullptr) {
   float best = 3.4e38f;
   int ba = 0, bb = 0;
@@ -295,7 +295,7 @@ __device__ __forceinline__ void anchor_guess(const Frame& F0, const Frame& F1, c
 // cores) from y, over all balls or over the listed subsets.  Stops when
 // |dx| <= tol; returns 0 converged, 1 not converged in max_it, 2 singular;
 // iters counts the iterations taken (a failed solve included).
-__device__ __forceinline__ int newton_pair(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+static __device__ __noinline__ int newton_pair(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
                                            int lane, float y[3], float tol, int max_it, int& iters,
                                            const unsigned short* l0 = nullptr, int m0 = 0,
                                            const unsigned short* l1 = nullptr, int m1 = 0) {
@@ -357,7 +357,7 @@ struct SolveCount {
 // balls), for at most SUB_IT iterations to the coarse SUB_TOL, and its point
 // is kept only if it converged; then on the full set to the plain tolerance.
 // If the full-set solve fails, plain Newton from the plain guess decides.
-__device__ __forceinline__ int learned_newton(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+static __device__ __noinline__ int learned_newton(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
                                               int lane, const float a[3], const float d[4], float L, float Rb,
                                               unsigned short* l0, unsigned short* l1, float y[3], SolveCount& sc,
                                               float4* stage = nullptr) {
@@ -1036,6 +1036,21 @@ __device__ __forceinline__ int active_staged(const float4* st, int base, int n, 
   return cnt;
 }
 
+// Core values and gradients of both particles at y from the ball table (the
+// final evaluation of a pair too large to stage).  Out of line: the staged
+// path is the common one, and the kernel's hot code stays small.
+static __device__ __noinline__ void final_unstaged(const Frame& F0, const Frame& F1, const float4* __restrict__ balls,
+                                            int lane, const float y[3], float& g0, float gr0[3], float& g1,
+                                            float gr1[3]) {
+  const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
+  g0 = e0.g;
+  g1 = e1.g;
+  for (int c = 0; c < 3; ++c) {
+    gr0[c] = e0.gr[c];
+    gr1[c] = e1.gr[c];
+  }
+}
+
 // A pair's solver state: the frames, and (when the pair fits) its staged
 // balls; every piece of the solve goes through the staged path when it can
 // and through the unstaged warp evaluation otherwise.
@@ -1069,17 +1084,8 @@ struct PairSolver {
     return newton(y, tol, MAX_IT, iters);
   }
   __device__ __forceinline__ void final_eval(const float y[3], float& g0, float gr0[3], float& g1, float gr1[3]) const {
-    if (staged) {
-      final_staged(st, F0.n, F0.n + F1.n, lane, y, g0, gr0, g1, gr1);
-    } else {
-      const GEval e0 = eval(F0, balls, y, lane), e1 = eval(F1, balls, y, lane);
-      g0 = e0.g;
-      g1 = e1.g;
-      for (int c = 0; c < 3; ++c) {
-        gr0[c] = e0.gr[c];
-        gr1[c] = e1.gr[c];
-      }
-    }
+    if (staged) final_staged(st, F0.n, F0.n + F1.n, lane, y, g0, gr0, g1, gr1);
+    else final_unstaged(F0, F1, balls, lane, y, g0, gr0, g1, gr1);
   }
   // learned_newton through the staged path (same stages, gates and fallback)
   __device__ __forceinline__ int learned(const float a[3], const float d[4], float L, float Rb, unsigned short* l0,

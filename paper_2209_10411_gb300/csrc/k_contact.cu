@@ -194,7 +194,10 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
 // One candidate item (a particle pair or a particle-wall pair) by one warp:
 // Newton closest point, contact geometry, spring-dashpot force into the
 // fixed-point sums, and the item's record.  sub, stage and rad are the warp's
-// shared scratch (2 x SUB_CAP indices, NT_CAP balls).
+// shared scratch (2 x SUB_CAP indices, NT_CAP balls).  WARM and LEARNED are
+// the handle's warm-start and learned-start switches, fixed per kernel
+// variant so that each variant holds only the code of its starts.
+template <bool WARM, bool LEARNED>
 __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it, long long substep, int lane,
                                              unsigned short (*sub)[SUB_CAP], float4* stage, float* rad) {
   const float4* balls = L.balls;
@@ -220,7 +223,7 @@ __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it
       const int lo = min(i, j), hi = max(i, j);
       HistEntry* hp = L.hist_pair + ((long long)lo * L.ncap - (long long)lo * (lo + 1) / 2 + (hi - lo - 1));
       // substeps count from 1 and the history starts zeroed: a stamp is valid from 1 on
-      const bool have_warm = L.warm && substep >= 2 && hp->xm_stamp == substep - 1;
+      const bool have_warm = WARM && substep >= 2 && hp->xm_stamp == substep - 1;
       if (have_warm) {
         // warm start: the pair's closest point of the previous substep (x - O = (x - X_i) - h)
         for (int c = 0; c < 3; ++c) y[c] = hp->xm_rel[c] - h[c];
@@ -230,7 +233,7 @@ __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it
           status = S.plain_newton(y, NEWTON_TOL * Rb, more);
           iters += more;
         }
-      } else if (L.learned) {
+      } else if (LEARNED) {
         // learned start: anchor and prediction of this item (features and MLP ran before)
         const float* x = L.feat + (size_t)it * 64;
         const float* pr = L.pred + (size_t)it * 4;
@@ -264,7 +267,7 @@ __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it
         nf[c] = dist > 0.f ? d[c] / dist : 0.f;
         rel[c] = h[c] + xc0[c] - (Pi.skin_f - 0.5f * dl) * nf[c];
       }
-      if (lane == 0 && L.warm && status == 0) {
+      if (lane == 0 && WARM && status == 0) {
         for (int c = 0; c < 3; ++c) hp->xm_rel[c] = y[c] + h[c];
         hp->xm_stamp = substep;
       }
@@ -362,6 +365,7 @@ __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it
 }
 
 // Persistent warp-per-candidate Newton solver and forces.
+template <bool WARM, bool LEARNED>
 __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
   __shared__ unsigned short sub[4][2][SUB_CAP];  // active subsets of the learned start, per warp
   __shared__ float4 stage[4][NT_CAP];              // the pair's staged balls, per warp
@@ -374,12 +378,18 @@ __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
     if (lane == 0) it = atomicAdd(L.work, 1u);
     it = __shfl_sync(FULL, it, 0);
     if (it >= n_items) break;
-    contact_item(L, it, substep, lane, sub[w], stage[w], rad[w]);
+    contact_item<WARM, LEARNED>(L, it, substep, lane, sub[w], stage[w], rad[w]);
   }
 }
 
 cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s) {
-  k_contacts<<<L.grid, 128, 0, s>>>(L);
+  if (L.warm) {
+    if (L.learned) k_contacts<true, true><<<L.grid, 128, 0, s>>>(L);
+    else k_contacts<true, false><<<L.grid, 128, 0, s>>>(L);
+  } else {
+    if (L.learned) k_contacts<false, true><<<L.grid, 128, 0, s>>>(L);
+    else k_contacts<false, false><<<L.grid, 128, 0, s>>>(L);
+  }
   return cudaGetLastError();
 }
 
@@ -394,6 +404,7 @@ cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s) {
 // read past the L1 (__ldcg); everything else is written and read by this
 // block only.
 // ---------------------------------------------------------------------------
+template <bool WARM>
 __global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, IntegrateLaunch I, int n_sub) {
   __shared__ unsigned short sub[4][2][SUB_CAP];
   __shared__ float4 stage[4][NT_CAP];
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, Integrate
     __syncthreads();
     const unsigned n_items = min(__ldcg(&L.ctr->n_pairs), L.cap_items);
     const long long substep = *L.substep;
-    for (unsigned it = w; it < n_items; it += 4) contact_item(L, it, substep, lane, sub[w], stage[w], rad[w]);
+    for (unsigned it = w; it < n_items; it += 4) contact_item<WARM, false>(L, it, substep, lane, sub[w], stage[w], rad[w]);
     __syncthreads();
     for (int p = w; p < np; p += 4) integrate_particle_lanes(I, p, lane);
     __syncthreads();
@@ -437,7 +448,8 @@ __global__ void __launch_bounds__(128) k_dem_substeps(ContactLaunch L, Integrate
 
 cudaError_t launch_dem_substeps(const ContactLaunch& L, const IntegrateLaunch& I, int n_sub, cudaStream_t s) {
   if (L.np <= 0 || n_sub <= 0) return cudaSuccess;
-  k_dem_substeps<<<1, 128, 0, s>>>(L, I, n_sub);
+  if (L.warm) k_dem_substeps<true><<<1, 128, 0, s>>>(L, I, n_sub);
+  else k_dem_substeps<false><<<1, 128, 0, s>>>(L, I, n_sub);
   return cudaGetLastError();
 }
 
