@@ -397,8 +397,9 @@ mi_status mi_mass_properties_noalloc(const double *balls_dev, int n_balls, doubl
 mi_status mi_delbm_set_graphs(mi_delbm *h, int enable);
 
 /* Choose the launch shapes of the bulk kernel (threads per block along x,
- * from 32/64/128/256) and of the list kernels (blocks per SM for the link,
- * refill and boundary kernels, from 2/4/8/16/32) by timing each candidate
+ * from 32/64/128/256) and of the list kernels (blocks per SM for the wall
+ * fraction, refill and boundary-node kernels, from 2/4/8/16/32; the links'
+ * bounce-back and the boundary nodes are timed together) by timing each candidate
  * with CUDA events on the handle's stream, and use the fastest from then on.
  * With cache_path != NULL, a line {"key": ..., "bulk_block_x": .., "list_blocks_per_sm": ..}
  * for this device, lattice, storage and particle count is read from that file
@@ -475,7 +476,7 @@ mi_status mi_delbm_phase_times(mi_delbm *h, double ms[8], long long launches[8],
  * the timed launches of `kernel` since the last reset of mi_delbm_phase_times
  * (not reset by this call).  Names: k_prologue, k_clear, k_flag, k_classify,
  * k_links_q, k_refill, k_bulk (the bulk stream-collide, whichever variant the
- * tuning selects), k_near, k_boundary, k_scatter_boundary, k_dem_prologue,
+ * tuning selects), k_near, k_links_ibb, k_boundary, k_scatter_boundary, k_dem_prologue,
  * k_broad_phase, k_item_features, k_mlp_tc, k_contacts, k_integrate,
  * k_dem_substeps.  Synchronises.  Errors: MI_EINVAL (NULL argument). */
 mi_status mi_delbm_kernel_time(mi_delbm *h, const char *kernel, double *ms, long long *launches);

@@ -236,7 +236,8 @@ mi_status mi_delbm::phase_boundary() {
 
 // Overlapped schedule: the boundary nodes' new values go to bc_tmp on a side
 // stream while the bulk kernel writes B (k_boundary reads only A, which the
-// refill completes before it), and are scattered into B after k_near.
+// refill completes before it, and the links' G, which k_links_ibb writes
+// before it on the same stream), and are scattered into B after k_near.
 mi_status mi_delbm::phase_boundary_beside(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   BoundaryLaunch L = boundary_launch(this);
@@ -1389,7 +1390,8 @@ extern "C" mi_status mi_delbm_autotune(mi_delbm* h, const char* cache_path, int*
         }
       }
     }
-    // list kernels: blocks per SM of the boundary kernel (lists of the last step)
+    // list kernels: blocks per SM of the links' bounce-back and boundary-node
+    // kernels, timed together (lists of the last step)
     if (h->n_particles > 0 && h->particles_ready) {
       DevCounters c;
       if (cudaMemcpy(&c, h->dctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess && c.n_bc > 0) {
