@@ -915,9 +915,17 @@ __global__ void __launch_bounds__(256) k_boundary(BoundaryLaunch L) {
   }
 }
 
+// A list kernel's grid: the tuned block count, but no more blocks than the
+// list's capacity (`items` work units at `threads` per block) can use, so
+// that small lists do not dispatch thousands of empty blocks.
+static inline int list_grid(int tuned, unsigned long long items, int threads) {
+  const unsigned long long need = (items + (unsigned long long)threads - 1) / (unsigned long long)threads;
+  return (int)(need < 1 ? 1 : (need < (unsigned long long)tuned ? need : (unsigned long long)tuned));
+}
+
 template <int ST>
 static cudaError_t launch_refill_st(const BoundaryLaunch& L, cudaStream_t s) {
-  k_refill<ST><<<L.grid, 128, 0, s>>>(L);
+  k_refill<ST><<<list_grid(L.grid, L.pl.cap_new, 128), 128, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -938,8 +946,9 @@ static cudaError_t launch_links_ibb_st(const BoundaryLaunch& L, cudaStream_t s) 
     if (ladd) k_links_ibb<ST, true, true><<<L.part_blocks, 256, 0, s>>>(L);
     else k_links_ibb<ST, false, true><<<L.part_blocks, 256, 0, s>>>(L);
   } else {
-    if (ladd) k_links_ibb<ST, true, false><<<L.grid, 256, 0, s>>>(L);
-    else k_links_ibb<ST, false, false><<<L.grid, 256, 0, s>>>(L);
+    const int grid = list_grid(L.grid, L.pl.cap_links, 256);
+    if (ladd) k_links_ibb<ST, true, false><<<grid, 256, 0, s>>>(L);
+    else k_links_ibb<ST, false, false><<<grid, 256, 0, s>>>(L);
   }
   return cudaGetLastError();
 }
@@ -956,8 +965,9 @@ cudaError_t launch_links_ibb(const BoundaryLaunch& L, cudaStream_t s) {
 
 template <int ST>
 static cudaError_t launch_near_st(const BoundaryLaunch& L, cudaStream_t s) {
-  if (L.forcing) k_near<ST, true><<<L.grid, 128, 0, s>>>(L);
-  else k_near<ST, false><<<L.grid, 128, 0, s>>>(L);
+  const int grid = list_grid(L.grid, 18ull * L.pl.cap_new, 128);
+  if (L.forcing) k_near<ST, true><<<grid, 128, 0, s>>>(L);
+  else k_near<ST, false><<<grid, 128, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -973,8 +983,9 @@ cudaError_t launch_near(const BoundaryLaunch& L, cudaStream_t s) {
 
 template <int ST>
 static cudaError_t launch_boundary_st(const BoundaryLaunch& L, cudaStream_t s) {
-  if (L.forcing) k_boundary<ST, true><<<L.grid, 256, 0, s>>>(L);
-  else k_boundary<ST, false><<<L.grid, 256, 0, s>>>(L);
+  const int grid = list_grid(L.grid, L.pl.cap_bc, 256);
+  if (L.forcing) k_boundary<ST, true><<<grid, 256, 0, s>>>(L);
+  else k_boundary<ST, false><<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 
@@ -991,8 +1002,9 @@ __global__ void __launch_bounds__(256) k_scatter_boundary(BoundaryLaunch L) {
 
 cudaError_t launch_scatter_boundary(const BoundaryLaunch& L, cudaStream_t s) {
   if (L.pl.np == 0 || !L.tmp) return cudaSuccess;
-  if (L.storage == MI_STORE_F32) k_scatter_boundary<float><<<L.grid, 256, 0, s>>>(L);
-  else k_scatter_boundary<unsigned short><<<L.grid, 256, 0, s>>>(L);
+  const int grid = list_grid(L.grid, 19ull * L.pl.cap_bc, 256);
+  if (L.storage == MI_STORE_F32) k_scatter_boundary<float><<<grid, 256, 0, s>>>(L);
+  else k_scatter_boundary<unsigned short><<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
 

@@ -707,6 +707,9 @@ __global__ void __launch_bounds__(256) k_links_q(ParticleLaunch L) {
 
 cudaError_t launch_links_q(const ParticleLaunch& L, int grid, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
+  // no more blocks than the link list's capacity can use
+  const unsigned long long need = ((unsigned long long)L.cap_links + 255ull) / 256ull;
+  if (need < (unsigned long long)grid) grid = need < 1 ? 1 : (int)need;
   k_links_q<<<grid, 256, 0, s>>>(L);
   return cudaGetLastError();
 }
