@@ -42,20 +42,31 @@ __device__ __forceinline__ void quat_to_R_exact(const double q[4], double R[9]) 
   R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
 }
 
-// f(x) >= 1 in FP64, unfused, same operation order as the definition above.
-__device__ __noinline__ bool inside_exact(const DevParticle& P, const double* balls_d, double xw, double yw,
-                                          double zw) {
-  const double d0 = __dsub_rn(xw, P.pos[0]), d1 = __dsub_rn(yw, P.pos[1]), d2 = __dsub_rn(zw, P.pos[2]);
+// f(x) >= 1 in FP64, unfused, same operation order as the definition above,
+// for the node (x, y, z) that every lane of the warp passes: the lanes form
+// the terms of 32 balls at a time and the sum is taken in ball order, so the
+// value is that of one thread summing ball after ball.
+__device__ __noinline__ bool inside_exact_warp(const DevParticle& P, const double* balls_d, int x, int y, int z,
+                                               unsigned lane) {
+  const double d0 = __dsub_rn((double)x, P.pos[0]), d1 = __dsub_rn((double)y, P.pos[1]),
+               d2 = __dsub_rn((double)z, P.pos[2]);
   const double* R = P.R;
   const double b0 = __dadd_rn(__dadd_rn(__dmul_rn(R[0], d0), __dmul_rn(R[3], d1)), __dmul_rn(R[6], d2));
   const double b1 = __dadd_rn(__dadd_rn(__dmul_rn(R[1], d0), __dmul_rn(R[4], d1)), __dmul_rn(R[7], d2));
   const double b2 = __dadd_rn(__dadd_rn(__dmul_rn(R[2], d0), __dmul_rn(R[5], d1)), __dmul_rn(R[8], d2));
+  const int nb = P.n_balls;
   double f = 0.0;
-  for (int i = 0; i < P.n_balls; ++i) {
-    const double* c = balls_d + 4 * (size_t)(P.ball_off + i);
-    const double e0 = __dsub_rn(b0, c[0]), e1 = __dsub_rn(b1, c[1]), e2 = __dsub_rn(b2, c[2]);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
-    f = __dadd_rn(f, __ddiv_rn(c[3], r2));
+  for (int base = 0; base < nb; base += 32) {
+    double t = 0.0;
+    const int i = base + (int)lane;
+    if (i < nb) {
+      const double* c = balls_d + 4 * (size_t)(P.ball_off + i);
+      const double e0 = __dsub_rn(b0, c[0]), e1 = __dsub_rn(b1, c[1]), e2 = __dsub_rn(b2, c[2]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+      t = __ddiv_rn(c[3], r2);
+    }
+    const int m = nb - base < 32 ? nb - base : 32;
+    for (int j = 0; j < m; ++j) f = __dadd_rn(f, __shfl_sync(0xffffffffu, t, j));
   }
   return f >= 1.0;
 }
@@ -237,43 +248,59 @@ __global__ void __launch_bounds__(256, 3) k_flag(ParticleLaunch L) {
   for (int k = 0; k < 9; ++k) Rf[k] = P.Rf[k];
   const float rt = (float)P.Rt * (1.0f + 1e-6f) + 1e-4f, rt2 = rt * rt;
   const unsigned n0 = (unsigned)r.n[0], n01 = n0 * (unsigned)r.n[1];
-  for (unsigned i = bb.b * blockDim.x + threadIdx.x; i < r.total; i += bb.nb * blockDim.x) {
-    const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
-    const int x = r.lo[0] + (int)(rem - yi * n0);
-    const int y = r.lo[1] + (int)yi;
-    const int z = r.lo[2] + (int)zi;
-    const float d0 = (float)(x - xi0) - xf0, d1 = (float)(y - xi1) - xf1, d2 = (float)(z - xi2) - xf2;
-    if (d0 * d0 + d1 * d1 + d2 * d2 > rt2) continue;  // beyond the tight radius: fluid
-    const float b0 = Rf[0] * d0 + Rf[3] * d1 + Rf[6] * d2;
-    const float b1 = Rf[1] * d0 + Rf[4] * d1 + Rf[7] * d2;
-    const float b2 = Rf[2] * d0 + Rf[5] * d1 + Rf[8] * d2;
-    // four independent partial sums (the terms are positive, so any partial
-    // sum above 1 + GUARD decides "inside"; FP32 reordering moves the sum by
-    // far less than GUARD, and sums within GUARD of 1 are redone in FP64)
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-    bool inside = false, decided = false;
-    int b = 0;
-    for (; b + 4 <= nb; b += 4) {
-      const float4 c0 = bl[b], c1 = bl[b + 1], c2 = bl[b + 2], c3 = bl[b + 3];
-      f0 += __fdividef(c0.w, (b0 - c0.x) * (b0 - c0.x) + (b1 - c0.y) * (b1 - c0.y) + (b2 - c0.z) * (b2 - c0.z));
-      f1 += __fdividef(c1.w, (b0 - c1.x) * (b0 - c1.x) + (b1 - c1.y) * (b1 - c1.y) + (b2 - c1.z) * (b2 - c1.z));
-      f2 += __fdividef(c2.w, (b0 - c2.x) * (b0 - c2.x) + (b1 - c2.y) * (b1 - c2.y) + (b2 - c2.z) * (b2 - c2.z));
-      f3 += __fdividef(c3.w, (b0 - c3.x) * (b0 - c3.x) + (b1 - c3.y) * (b1 - c3.y) + (b2 - c3.z) * (b2 - c3.z));
-      if ((f0 + f1) + (f2 + f3) > 1.0f + GUARD) {  // partial sums only grow: inside for sure
-        inside = decided = true;
-        break;
+  // whole warps step together (the guard band's FP64 field is a warp collective)
+  const unsigned lane = threadIdx.x & 31u;
+  for (unsigned base = bb.b * blockDim.x + (threadIdx.x & ~31u); base < r.total; base += bb.nb * blockDim.x) {
+    const unsigned i = base + lane;
+    int x = 0, y = 0, z = 0;
+    bool inside = false, band = false;
+    if (i < r.total) {
+      const unsigned zi = i / n01, rem = i - zi * n01, yi = rem / n0;
+      x = r.lo[0] + (int)(rem - yi * n0);
+      y = r.lo[1] + (int)yi;
+      z = r.lo[2] + (int)zi;
+      const float d0 = (float)(x - xi0) - xf0, d1 = (float)(y - xi1) - xf1, d2 = (float)(z - xi2) - xf2;
+      // beyond the tight radius: fluid
+      if (d0 * d0 + d1 * d1 + d2 * d2 <= rt2) {
+        const float b0 = Rf[0] * d0 + Rf[3] * d1 + Rf[6] * d2;
+        const float b1 = Rf[1] * d0 + Rf[4] * d1 + Rf[7] * d2;
+        const float b2 = Rf[2] * d0 + Rf[5] * d1 + Rf[8] * d2;
+        // four independent partial sums (the terms are positive, so any partial
+        // sum above 1 + GUARD decides "inside"; FP32 reordering moves the sum by
+        // far less than GUARD, and sums within GUARD of 1 are redone in FP64)
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        bool decided = false;
+        int b = 0;
+        for (; b + 4 <= nb; b += 4) {
+          const float4 c0 = bl[b], c1 = bl[b + 1], c2 = bl[b + 2], c3 = bl[b + 3];
+          f0 += __fdividef(c0.w, (b0 - c0.x) * (b0 - c0.x) + (b1 - c0.y) * (b1 - c0.y) + (b2 - c0.z) * (b2 - c0.z));
+          f1 += __fdividef(c1.w, (b0 - c1.x) * (b0 - c1.x) + (b1 - c1.y) * (b1 - c1.y) + (b2 - c1.z) * (b2 - c1.z));
+          f2 += __fdividef(c2.w, (b0 - c2.x) * (b0 - c2.x) + (b1 - c2.y) * (b1 - c2.y) + (b2 - c2.z) * (b2 - c2.z));
+          f3 += __fdividef(c3.w, (b0 - c3.x) * (b0 - c3.x) + (b1 - c3.y) * (b1 - c3.y) + (b2 - c3.z) * (b2 - c3.z));
+          if ((f0 + f1) + (f2 + f3) > 1.0f + GUARD) {  // partial sums only grow: inside for sure
+            inside = decided = true;
+            break;
+          }
+        }
+        if (!decided) {
+          for (; b < nb; ++b) {
+            const float4 c = bl[b];
+            const float e0 = b0 - c.x, e1 = b1 - c.y, e2 = b2 - c.z;
+            f0 += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
+          }
+          const float f = (f0 + f1) + (f2 + f3);
+          if (f > 1.0f + GUARD) inside = true;
+          else if (f < 1.0f - GUARD) inside = false;
+          else band = true;  // within GUARD of 1 (or not a number): decided in FP64 below
+        }
       }
     }
-    if (!decided) {
-      for (; b < nb; ++b) {
-        const float4 c = bl[b];
-        const float e0 = b0 - c.x, e1 = b1 - c.y, e2 = b2 - c.z;
-        f0 += __fdividef(c.w, e0 * e0 + e1 * e1 + e2 * e2);
-      }
-      const float f = (f0 + f1) + (f2 + f3);
-      if (f > 1.0f + GUARD) inside = true;
-      else if (f < 1.0f - GUARD) inside = false;
-      else inside = inside_exact(P, L.balls_d, (double)x, (double)y, (double)z);
+    // the nodes in the guard band, one at a time by the whole warp
+    for (unsigned m = __ballot_sync(0xffffffffu, band); m; m &= m - 1u) {
+      const int src = __ffs(m) - 1;
+      const bool in = inside_exact_warp(P, L.balls_d, __shfl_sync(0xffffffffu, x, src),
+                                        __shfl_sync(0xffffffffu, y, src), __shfl_sync(0xffffffffu, z, src), lane);
+      if ((int)lane == src) inside = in;
     }
     if (inside) {
       atomicMin(L.owner_cur + lin(x, y, z, L.g), (uint32_t)p);
