@@ -189,8 +189,11 @@ mi_status mi_delbm::phase_flag(cudaStream_t st) {
 mi_status mi_delbm::phase_links(cudaStream_t st) {
   if (n_particles == 0) return MI_OK;
   ParticleLaunch L = particle_launch();
+  // at most four blocks per SM: the kernel runs beside the bulk kernel,
+  // which it slows less with fewer blocks resident at a time
+  const int per_sm = tune.list_blocks_per_sm < 4 ? tune.list_blocks_per_sm : 4;
   return launch_phase(this, st, MI_PHASE_LINKS, "k_links_q",
-                      [&] { return launch_links_q(L, sm_count * tune.list_blocks_per_sm, st); });
+                      [&] { return launch_links_q(L, sm_count * per_sm, st); });
 }
 
 static BoundaryLaunch boundary_launch(const mi_delbm* h) {
@@ -1709,15 +1712,19 @@ mi_status mi_delbm_add_particle(mi_delbm* h, int n, const double* centers, const
   if (sbc > 0x3FFFFFFFull) sbc = 0x3FFFFFFFull;
   st = h->ensure_list_capacity((unsigned)sbc, (unsigned)std::min<unsigned long long>(6ull * sbc, 0xFFFFFFF0ull), (unsigned)sbc);
   if (st != MI_OK) return st;
-  // box-kernel blocks per particle: about 1024 box nodes per flag block, and
-  // 8 warps of about 8 rows each per classification block (the classified
-  // region, old and new box widened by 2, has fewer than (ext + 8)^2 rows)
+  // box-kernel blocks per particle: about 8192 box nodes per flag block, and
+  // 8 warps of about 64 rows each per classification block (the classified
+  // region, old and new box widened by 2, has fewer than (ext + 8)^2 rows).
+  // Few long-lived blocks: these kernels run beside the bulk kernel, and the
+  // fewer SM slots they hold at a time, the less they slow it (eight times
+  // more blocks made the settling-tank step 2.4 % slower; sixteen times
+  // fewer made the particle chain outlast the 16-bit bulk kernel)
   const int npart = h->n_particles, stride = h->cfg.max_particles + 1;
   std::vector<int> boff(2 * (size_t)stride, 0);
   for (int q = 0; q < npart; ++q) {
     const int* e = h->hp[q].ext;
-    const long long fb = ((long long)e[0] * e[1] * e[2] + 1023) / 1024;
-    const long long cb = ((long long)(e[1] + 8) * (e[2] + 8) + 63) / 64;
+    const long long fb = ((long long)e[0] * e[1] * e[2] + 8191) / 8192;
+    const long long cb = ((long long)(e[1] + 8) * (e[2] + 8) + 511) / 512;
     boff[q + 1] = boff[q] + (int)std::min<long long>(std::max<long long>(fb, 1), 8192);
     boff[stride + q + 1] = boff[stride + q] + (int)std::min<long long>(std::max<long long>(cb, 1), 4096);
   }

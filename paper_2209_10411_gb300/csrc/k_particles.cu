@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(256) k_classify(ParticleLaunch L) {
 
 cudaError_t launch_classify(const ParticleLaunch& L, cudaStream_t s) {
   if (L.np == 0) return cudaSuccess;
-  // a warp per (y, z) row, about eight rows per warp
+  // a warp per (y, z) row, about 64 rows per warp
   if (L.cover_uncover) k_classify<true><<<L.classify_blocks, 256, 0, s>>>(L);
   else k_classify<false><<<L.classify_blocks, 256, 0, s>>>(L);
   return cudaGetLastError();
