@@ -595,10 +595,11 @@ __global__ void __launch_bounds__(128) k_near(BoundaryLaunch L) {
 // (or the halfway rule f+_d + 6 w_d rho0 e_j.u_w in Ladd mode), kept per
 // link.  The Galilean-invariant momentum exchange of the link,
 //   dP = (e_d - u_w) f+_d - (e_j - u_w) G_j = e_d (2 w_d + h_d + h_G) - u_w (h_d - h_G),
-// and its torque about X_p are rounded to 2^-40 fixed point per link, summed
-// over the warp in integers and added with 64-bit integer atomics: the sums
-// do not depend on the order in which links are visited.  It reads f+(t)
-// only (A, after the refill), so it runs beside the bulk kernel.
+// and its torque about X_p are rounded to 2^-40 fixed point per link and
+// summed in integers (over the warp, then per block, then over the blocks):
+// the sums do not depend on the order in which links are visited.  It reads
+// f+(t) only (A, after the refill), so it may run beside the bulk kernel
+// (a schedule option); by default it runs after it.
 //
 // k_boundary, one thread per boundary node, for each direction j: pull
 // streaming where the source is fluid, halfway bounce-back where it is
