@@ -191,77 +191,6 @@ cudaError_t launch_broad_phase(const ContactLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// One particle-wall item by one warp (the rarer kind: kept out of line so
-// that the pair path's code stays small): Newton on the 4x4 system of the
-// closest core point to the wall (Eq. metawallcp), the overlap and contact
-// point (Eq. contactprop2), the spring-dashpot force into the sums.
-__device__ __noinline__ void wall_item(const ContactLaunch& L, int i, int j, long long substep, int lane,
-                                       int& status, int& iters, float rel[3], float nf[3], float& dl) {
-  const float4* balls = L.balls;
-  const DevParticle& Pi = L.P[i];
-  const int face = -1 - j, axis = face / 2;
-  const float zero[3] = {0.f, 0.f, 0.f};
-  const Frame F0 = frame_f32(Pi, L.qf[i], zero);  // local origin X_i
-  float nw[3] = {0.f, 0.f, 0.f};
-  nw[axis] = (face & 1) ? -1.f : 1.f;
-  const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
-  const float distO = (float)((double)nw[axis] * (Pi.pos[axis] - pw));
-  const float Rb = Pi.Rb_f;
-  // guess: the core sphere reaching deepest towards the wall
-  float best = 3.4e38f;
-  int ba = 0;
-  for (int a = lane; a < F0.n; a += 32) {
-    const float4 ca = __ldg(balls + F0.off + a);
-    const float pn = (F0.R[3 * axis] * ca.x + F0.R[3 * axis + 1] * ca.y + F0.R[3 * axis + 2] * ca.z + F0.t[axis]) * nw[axis];
-    const float v = pn - sqrtf(F0.s * ca.w);
-    if (v < best) { best = v; ba = a; }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float g2 = __shfl_xor_sync(FULL, best, o);
-    const int a2 = __shfl_xor_sync(FULL, ba, o);
-    if (g2 < best || (g2 == best && a2 < ba)) { best = g2; ba = a2; }
-  }
-  ba = __shfl_sync(FULL, ba, 0);
-  float y[3];
-  {
-    const float4 ca = __ldg(balls + F0.off + ba);
-    const float rs = sqrtf(F0.s * ca.w);
-    for (int c = 0; c < 3; ++c)
-      y[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c] - rs * nw[c];
-  }
-  GEval e = eval(F0, balls, y, lane);
-  float lam = sqrtf(e.gr[0] * e.gr[0] + e.gr[1] * e.gr[1] + e.gr[2] * e.gr[2]);
-  for (iters = 1; iters <= MAX_IT; ++iters) {
-    e = eval(F0, balls, y, lane);
-    float A[4][4] = {{e.H[0], e.H[1], e.H[2], -nw[0]},
-                     {e.H[1], e.H[3], e.H[4], -nw[1]},
-                     {e.H[2], e.H[4], e.H[5], -nw[2]},
-                     {e.gr[0], e.gr[1], e.gr[2], 0.f}};
-    float b[4] = {e.gr[0] - lam * nw[0], e.gr[1] - lam * nw[1], e.gr[2] - lam * nw[2], e.g - 1.f};
-    float dz[4];
-    if (!solve<4>(A, b, dz)) { status = 2; break; }
-    for (int c = 0; c < 3; ++c) y[c] -= dz[c];
-    lam -= dz[3];
-    if (sqrtf(dz[0] * dz[0] + dz[1] * dz[1] + dz[2] * dz[2]) <= NEWTON_TOL * Rb) { status = 0; break; }
-  }
-  if (iters > MAX_IT) iters = MAX_IT;
-  const float dist = nw[0] * y[0] + nw[1] * y[1] + nw[2] * y[2] + distO;
-  dl = Pi.skin_f - dist;
-  for (int c = 0; c < 3; ++c) {
-    nf[c] = nw[c];
-    rel[c] = (y[c] - dist * nw[c]) + 0.5f * dl * nw[c];
-  }
-  if (lane == 0 && status == 0 && dl > 0.f) {
-    HistEntry* hp = L.hist_wall + ((long long)i * 6 + face);
-    float f[3];
-    spring_dashpot(L.cf, L.vw + 2 * i, nullptr, rel, nullptr, nw, dl, hp, substep, f);
-    const float vi[6] = {f[0], f[1], f[2], rel[1] * f[2] - rel[2] * f[1], rel[2] * f[0] - rel[0] * f[2],
-                         rel[0] * f[1] - rel[1] * f[0]};
-    add_fixed6(L.fcacc, i, vi);
-    atomicAdd(&L.ctr->n_contacts, 1u);
-  }
-}
-
 // One candidate item (a particle pair or a particle-wall pair) by one warp:
 // Newton closest point, contact geometry, spring-dashpot force into the
 // fixed-point sums, and the item's record.  sub, stage and rad are the warp's
@@ -356,7 +285,68 @@ __device__ __forceinline__ void contact_item(const ContactLaunch& L, unsigned it
         atomicAdd(&L.ctr->n_contacts, 1u);
       }
     } else {
-      wall_item(L, i, j, substep, lane, status, iters, rel, nf, dl);
+      // ---------------- particle - wall ----------------
+      const int face = -1 - j, axis = face / 2;
+      const float zero[3] = {0.f, 0.f, 0.f};
+      const Frame F0 = frame_f32(Pi, L.qf[i], zero);  // local origin X_i
+      float nw[3] = {0.f, 0.f, 0.f};
+      nw[axis] = (face & 1) ? -1.f : 1.f;
+      const double pw = (face & 1) ? L.cp.n[axis] - 0.5 : -0.5;
+      const float distO = (float)((double)nw[axis] * (Pi.pos[axis] - pw));
+      const float Rb = Pi.Rb_f;
+      // guess: the core sphere reaching deepest towards the wall
+      float best = 3.4e38f;
+      int ba = 0;
+      for (int a = lane; a < F0.n; a += 32) {
+        const float4 ca = __ldg(balls + F0.off + a);
+        const float pn = (F0.R[3 * axis] * ca.x + F0.R[3 * axis + 1] * ca.y + F0.R[3 * axis + 2] * ca.z + F0.t[axis]) * nw[axis];
+        const float v = pn - sqrtf(F0.s * ca.w);
+        if (v < best) { best = v; ba = a; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float g2 = __shfl_xor_sync(FULL, best, o);
+        const int a2 = __shfl_xor_sync(FULL, ba, o);
+        if (g2 < best || (g2 == best && a2 < ba)) { best = g2; ba = a2; }
+      }
+      ba = __shfl_sync(FULL, ba, 0);
+      float y[3];
+      {
+        const float4 ca = __ldg(balls + F0.off + ba);
+        const float rs = sqrtf(F0.s * ca.w);
+        for (int c = 0; c < 3; ++c)
+          y[c] = F0.R[3 * c] * ca.x + F0.R[3 * c + 1] * ca.y + F0.R[3 * c + 2] * ca.z + F0.t[c] - rs * nw[c];
+      }
+      GEval e = eval(F0, balls, y, lane);
+      float lam = sqrtf(e.gr[0] * e.gr[0] + e.gr[1] * e.gr[1] + e.gr[2] * e.gr[2]);
+      for (iters = 1; iters <= MAX_IT; ++iters) {
+        e = eval(F0, balls, y, lane);
+        float A[4][4] = {{e.H[0], e.H[1], e.H[2], -nw[0]},
+                         {e.H[1], e.H[3], e.H[4], -nw[1]},
+                         {e.H[2], e.H[4], e.H[5], -nw[2]},
+                         {e.gr[0], e.gr[1], e.gr[2], 0.f}};
+        float b[4] = {e.gr[0] - lam * nw[0], e.gr[1] - lam * nw[1], e.gr[2] - lam * nw[2], e.g - 1.f};
+        float dz[4];
+        if (!solve<4>(A, b, dz)) { status = 2; break; }
+        for (int c = 0; c < 3; ++c) y[c] -= dz[c];
+        lam -= dz[3];
+        if (sqrtf(dz[0] * dz[0] + dz[1] * dz[1] + dz[2] * dz[2]) <= NEWTON_TOL * Rb) { status = 0; break; }
+      }
+      if (iters > MAX_IT) iters = MAX_IT;
+      const float dist = nw[0] * y[0] + nw[1] * y[1] + nw[2] * y[2] + distO;
+      dl = Pi.skin_f - dist;
+      for (int c = 0; c < 3; ++c) {
+        nf[c] = nw[c];
+        rel[c] = (y[c] - dist * nw[c]) + 0.5f * dl * nw[c];
+      }
+      if (lane == 0 && status == 0 && dl > 0.f) {
+        HistEntry* hp = L.hist_wall + ((long long)i * 6 + face);
+        float f[3];
+        spring_dashpot(L.cf, L.vw + 2 * i, nullptr, rel, nullptr, nw, dl, hp, substep, f);
+        const float vi[6] = {f[0], f[1], f[2], rel[1] * f[2] - rel[2] * f[1], rel[2] * f[0] - rel[0] * f[2],
+                             rel[0] * f[1] - rel[1] * f[0]};
+        add_fixed6(L.fcacc, i, vi);
+        atomicAdd(&L.ctr->n_contacts, 1u);
+      }
     }
     if (lane == 0) {
       ContactRec& r = L.recs[it];
