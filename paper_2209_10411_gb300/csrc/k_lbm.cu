@@ -614,18 +614,8 @@ __global__ void __launch_bounds__(128) k_near(BoundaryLaunch L) {
 // ---------------------------------------------------------------------------
 namespace {
 constexpr unsigned FULLW = 0xffffffffu;
-// direction tables as 2-bit fields (value + 1), so that a lane can look up its
-// own direction without local or constant memory
-__host__ __device__ constexpr unsigned long long pack2(int axis) {
-  unsigned long long v = 0;
-  for (int i = 0; i < 19; ++i)
-    v |= (unsigned long long)((axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
-  return v;
-}
-constexpr unsigned long long EXB = pack2(0), EYB = pack2(1), EZB = pack2(2);
-__device__ __forceinline__ int lex(int j) { return (int)((EXB >> (2 * j)) & 3ull) - 1; }
-__device__ __forceinline__ int ley(int j) { return (int)((EYB >> (2 * j)) & 3ull) - 1; }
-__device__ __forceinline__ int lez(int j) { return (int)((EZB >> (2 * j)) & 3ull) - 1; }
+// weight and opposite of a direction given at run time (lex, ley, lez: the
+// shared header's packed direction tables)
 __device__ __forceinline__ float lw(int j) { return j == 0 ? (1.0f / 3.0f) : (j <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
 __device__ __forceinline__ int lopp(int j) { return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1); }
 

@@ -122,8 +122,11 @@ __device__ __forceinline__ bool neighbour(int x, int y, int z, int dx, int dy, i
 // sums, rotation matrices and node boxes at the current pose.
 // ---------------------------------------------------------------------------
 __global__ void k_prologue(ParticleLaunch L) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) {
+  // one warp per particle: every lane forms the rotation (the same FP64
+  // operations, so the same bits), then the lanes share out the float pairs
+  // of its entries and of the directions
+  const int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (p == 0 && lane == 0) {
     L.ctr->gen += 1u;
     L.ctr->n_bc = 0;
     L.ctr->n_links = 0;
@@ -132,45 +135,59 @@ __global__ void k_prologue(ParticleLaunch L) {
   }
   if (p >= L.np) return;
   DevParticle& P = L.P[p];
-  quat_to_R_exact(P.quat, P.R);
-  for (int k = 0; k < 9; ++k) {
-    P.Rf[k] = (float)P.R[k];
-    P.Rs[0][k] = P.Rf[k];
-    P.Rs[1][k] = (float)(P.R[k] - (double)P.Rf[k]);
-  }
-  {
-    double fr[3];
+  double R[9];
+  quat_to_R_exact(P.quat, R);
+  if (lane < 9) {
+    double r = R[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r = lane == k ? R[k] : r;
+    const float rf = (float)r;
+    P.R[lane] = r;
+    P.Rf[lane] = rf;
+    P.Rs[0][lane] = rf;
+    P.Rs[1][lane] = (float)(r - (double)rf);
+  } else if (lane < 12) {
+    // R^T (X - floor X), entry k
+    const int k = lane - 9;
+    double fr[3], c[3];
     for (int a = 0; a < 3; ++a) fr[a] = P.pos[a] - floor(P.pos[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = k == 0 ? R[3 * a] : (k == 1 ? R[3 * a + 1] : R[3 * a + 2]);
+    const double t = c[0] * fr[0] + c[1] * fr[1] + c[2] * fr[2];
+    P.Ts[0][k] = (float)t;
+    P.Ts[1][k] = (float)(t - (double)P.Ts[0][k]);
+  }
+  if (lane < 19) {
+    // R^T e_d for direction d = lane
+    const int d = lane;
+    const double ex = lex(d), ey = ley(d), ez = lez(d);
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double t = P.R[k] * fr[0] + P.R[3 + k] * fr[1] + P.R[6 + k] * fr[2];
-      P.Ts[0][k] = (float)t;
-      P.Ts[1][k] = (float)(t - (double)P.Ts[0][k]);
+      const double e = R[k] * ex + R[3 + k] * ey + R[6 + k] * ez;
+      P.Es[d][k] = (float)e;
+      P.Es[d][3 + k] = (float)(e - (double)P.Es[d][k]);
     }
-    for (int d = 0; d < 19; ++d)
-      for (int k = 0; k < 3; ++k) {
-        const double e = P.R[k] * cx(d) + P.R[3 + k] * cy(d) + P.R[6 + k] * cz(d);
-        P.Es[d][k] = (float)e;
-        P.Es[d][3 + k] = (float)(e - (double)P.Es[d][k]);
-      }
   }
-  for (int a = 0; a < 3; ++a) {
-    P.lo[a] = (int)floor(P.pos[a] - P.Rt) - 1;
-    P.posf[a] = (float)P.pos[a];
-    const double fl = floor(P.pos[a]);
-    P.pos_i[a] = (int)fl;
-    P.pos_fr[a] = (float)(P.pos[a] - fl);
-    P.velf[a] = (float)P.vel[a];
-    P.omegaf[a] = (float)P.omega[a];
-    const int prev = P.lo_hist[L.prev_buf][a];
-    if (prev != BOX_NONE && abs(P.lo[a] - prev) > 2) atomicOr(&L.ctr->status, STATUS_MOVED_TOO_FAR);
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      P.lo[a] = (int)floor(P.pos[a] - P.Rt) - 1;
+      P.posf[a] = (float)P.pos[a];
+      const double fl = floor(P.pos[a]);
+      P.pos_i[a] = (int)fl;
+      P.pos_fr[a] = (float)(P.pos[a] - fl);
+      P.velf[a] = (float)P.vel[a];
+      P.omegaf[a] = (float)P.omega[a];
+      const int prev = P.lo_hist[L.prev_buf][a];
+      if (prev != BOX_NONE && abs(P.lo[a] - prev) > 2) atomicOr(&L.ctr->status, STATUS_MOVED_TOO_FAR);
+    }
+    P.srad2[L.cur_buf] = -1;  // the solid radius of this step, grown by k_flag
+    for (int a = 0; a < 3; ++a) P.sctr[L.cur_buf][a] = (float)P.pos[a];
   }
-  for (int k = 0; k < 6; ++k) L.facc[6 * p + k] = 0;
-  P.srad2[L.cur_buf] = -1;  // the solid radius of this step, grown by k_flag
-  for (int a = 0; a < 3; ++a) P.sctr[L.cur_buf][a] = (float)P.pos[a];
+  if (lane < 6) L.facc[6 * p + lane] = 0;
 }
 
 cudaError_t launch_prologue(const ParticleLaunch& L, cudaStream_t s) {
-  const int blocks = L.np > 0 ? (L.np + 127) / 128 : 1;
+  const int blocks = L.np > 0 ? (L.np + 3) / 4 : 1;  // four warps per block, a warp per particle
   k_prologue<<<blocks, 128, 0, s>>>(L);
   return cudaGetLastError();
 }

@@ -35,6 +35,19 @@ __host__ __device__ constexpr double wq_d(int i) {
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// Direction components as 2-bit fields (value + 1), so that a thread can look
+// up a direction given at run time without local or constant memory.
+__host__ __device__ constexpr unsigned long long dir_pack(int axis) {
+  unsigned long long v = 0;
+  for (int i = 0; i < 19; ++i)
+    v |= (unsigned long long)((axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
+  return v;
+}
+constexpr unsigned long long EXB = dir_pack(0), EYB = dir_pack(1), EZB = dir_pack(2);
+__device__ __forceinline__ int lex(int j) { return (int)((EXB >> (2 * j)) & 3ull) - 1; }
+__device__ __forceinline__ int ley(int j) { return (int)((EYB >> (2 * j)) & 3ull) - 1; }
+__device__ __forceinline__ int lez(int j) { return (int)((EZB >> (2 * j)) & 3ull) - 1; }
+
 constexpr uint32_t OWNER_NONE = 0xFFFFFFFFu;
 
 // node class bits
