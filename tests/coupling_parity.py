@@ -49,12 +49,14 @@ def add_particles(sim, parts):
                          mass_props={"mass": P["mass"], "volume": P["volume"], "inertia": P["inertia"]})
 
 
-def run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM, cover_uncover=False):
+def run_one_step(B, shape, parts_prev, parts, f0, mode, storage=0, phases=ALL_LBM, cover_uncover=False,
+                 max_particles=None):
     """GPU: flag at the previous poses, then one step of the given phases at
-    the current poses from the populations f0."""
+    the current poses from the populations f0 (handle capacity max_particles,
+    by default the particle count, at least 4)."""
     nx, ny, nz = shape
     sim = B.Simulation(nx, ny, nz, tau=TAU, bb_mode=(B.BB_LADD if mode == "ladd" else B.BB_IBB), storage=storage,
-                       max_particles=max(4, len(parts)))
+                       max_particles=max_particles or max(4, len(parts)))
     add_particles(sim, parts_prev)
     sim.step_phases(1)  # flags at the previous pose
     if cover_uncover:
