@@ -383,13 +383,10 @@ __global__ void __launch_bounds__(128, 6) k_contacts(ContactLaunch L) {
 }
 
 cudaError_t launch_contacts(const ContactLaunch& L, cudaStream_t s) {
-  if (L.warm) {
-    if (L.learned) k_contacts<true, true><<<L.grid, 128, 0, s>>>(L);
-    else k_contacts<true, false><<<L.grid, 128, 0, s>>>(L);
-  } else {
-    if (L.learned) k_contacts<false, true><<<L.grid, 128, 0, s>>>(L);
-    else k_contacts<false, false><<<L.grid, 128, 0, s>>>(L);
-  }
+  // the starts are exclusive (the handle's guess mode)
+  if (L.learned) k_contacts<false, true><<<L.grid, 128, 0, s>>>(L);
+  else if (L.warm) k_contacts<true, false><<<L.grid, 128, 0, s>>>(L);
+  else k_contacts<false, false><<<L.grid, 128, 0, s>>>(L);
   return cudaGetLastError();
 }
 
